@@ -1,0 +1,222 @@
+"""Python face of the CPU oracle (plain C, FP64) -- TEST INFRASTRUCTURE ONLY.
+
+The oracle restates the batched varying-parameter RNG method of Mahani &
+Sharabiani (arXiv 1412.4825, Sec. 2) in plain, slow FP64 C.  Only tests/,
+``__graft_entry__.smoke()`` and bench.py's CPU-baseline / reference legs may
+import it; the product path (the CUDA library and its binding) never does.
+Every function takes numpy arrays and returns new numpy arrays; stream
+positions are passed in and returned, so calls can be chained exactly like
+the stateful object of Sec. 2.2.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DOM_U, DOM_N, DOM_E, DOM_DATA, DOM_U64 = 0, 1, 2, 3, 4
+OK, EINVAL, EDOMAIN, EREJECT = 0, 1, 4, 5
+GAMMA_MAX_ATTEMPTS = 64
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        u32, u64, i32, dbl = C.c_uint32, C.c_uint64, C.c_int, C.c_double
+        vp = C.c_void_p
+        L.or_philox4x32_10.argtypes = [vp, vp, vp]
+        L.or_philox_words.argtypes = [u64, u32, u32, u64, u64, vp]
+        L.or_log.argtypes = [dbl]
+        L.or_log.restype = dbl
+        L.or_log_many.argtypes = [u64, vp, vp]
+        L.or_sincospi_many.argtypes = [u64, vp, vp, vp]
+        L.or_elem_values.argtypes = [u64, u32, u32, u64, u64, vp, vp]
+        for name in ("or_uniform", "or_normal", "or_laplace", "or_weibull"):
+            getattr(L, name).argtypes = [u64, u32, vp, u64, vp, vp, vp, vp, u32]
+            getattr(L, name).restype = i32
+        for name in ("or_exponential", "or_gamma"):
+            getattr(L, name).argtypes = [u64, u32, vp, u64, vp, vp, vp, u32]
+            getattr(L, name).restype = i32
+        L.or_dirichlet.argtypes = [u64, u32, vp, u64, u32, vp, vp, u32]
+        L.or_dirichlet.restype = i32
+        L.or_mixed_streams.argtypes = [u64, u32, u32, u32, vp, u64, vp, vp, vp, vp, vp, u32]
+        L.or_mixed_streams.restype = i32
+        L.or_mixed_mt.argtypes = [u64, u32, vp, u64, vp, vp, vp, vp, vp, u32, i32]
+        L.or_mixed_mt.restype = i32
+        L.or_gibbs_triangle_mt.argtypes = [u64, u64, u32, u32, vp, vp, vp, u32, i32]
+        L.or_gibbs_triangle_mt.restype = i32
+        L.or_gibbs_normal_gamma_mt.argtypes = [u64, u64, u32, u32, vp, vp, vp, vp, vp, vp, vp, u32, i32]
+        L.or_gibbs_normal_gamma_mt.restype = i32
+        L.or_gibbs_lda_mt.argtypes = [u64, u64, u32, u32, u32, vp, vp, vp, vp, u32, i32]
+        L.or_gibbs_lda_mt.restype = i32
+        L.or_mt_accept.argtypes = [dbl, dbl, dbl]
+        L.or_mt_accept.restype = i32
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _threads(nthreads):
+    return os.cpu_count() or 1 if nthreads is None else int(nthreads)
+
+
+# ---- core engine and elementary functions --------------------------------
+
+def philox4x32_10(ctr, key):
+    """One Philox4x32-10 block: 4 counter words, 2 key words -> 4 words."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def philox_words(seed, domain, stream, first_block, n_blocks):
+    out = np.zeros(4 * n_blocks, dtype=np.uint32)
+    lib().or_philox_words(seed, domain, stream, first_block, n_blocks, _p(out))
+    return out
+
+
+def log(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    lib().or_log_many(x.size, _p(x), _p(out))
+    return out
+
+
+def sincospi(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    s = np.empty_like(a)
+    c = np.empty_like(a)
+    lib().or_sincospi_many(a.size, _p(a), _p(s), _p(c))
+    return s, c
+
+
+def elements(seed, domain, stream, j0, n):
+    """Elements j0..j0+n-1 of one domain of one stream: (values, words)."""
+    out = np.empty(n, dtype=np.float64)
+    words = np.empty(n, dtype=np.uint32)
+    lib().or_elem_values(seed, domain, stream, j0, n, _p(out), _p(words))
+    return out, words
+
+
+def mt_accept(alpha, z, u_open):
+    return lib().or_mt_accept(float(alpha), float(z), float(u_open))
+
+
+# ---- bulk varying-parameter streams ---------------------------------------
+
+def new_positions(n_streams):
+    return np.zeros(3 * n_streams, dtype=np.uint64)
+
+
+def _bulk(name, seed, S, pos, n, params, buf_len, with_words=True):
+    pos = np.array(pos if pos is not None else new_positions(S), dtype=np.uint64, copy=True)
+    out = np.empty(n, dtype=np.float64)
+    words = np.zeros(n, dtype=np.uint32) if with_words else None
+    ps = [_f32(p) for p in params]
+    st = getattr(lib(), name)(seed, S, _p(pos), n, *[_p(p) for p in ps], _p(out), _p(words), buf_len)
+    return out, words, pos, st
+
+
+def uniform(seed, S, a, b, pos=None, buf_len=64):
+    return _bulk("or_uniform", seed, S, pos, len(a), [a, b], buf_len)
+
+
+def normal(seed, S, mu, sigma, pos=None, buf_len=64):
+    return _bulk("or_normal", seed, S, pos, len(mu), [mu, sigma], buf_len)
+
+
+def exponential(seed, S, lam, pos=None, buf_len=64):
+    return _bulk("or_exponential", seed, S, pos, len(lam), [lam], buf_len)
+
+
+def gamma(seed, S, alpha, pos=None, buf_len=64):
+    return _bulk("or_gamma", seed, S, pos, len(alpha), [alpha], buf_len)
+
+
+def laplace(seed, S, mu, scale, pos=None, buf_len=64):
+    return _bulk("or_laplace", seed, S, pos, len(mu), [mu, scale], buf_len)
+
+
+def weibull(seed, S, shape, scale, pos=None, buf_len=64):
+    return _bulk("or_weibull", seed, S, pos, len(shape), [shape, scale], buf_len)
+
+
+def dirichlet(seed, S, alpha, pos=None, buf_len=64):
+    alpha = _f32(alpha)
+    n_rows, K = alpha.shape
+    pos = np.array(pos if pos is not None else new_positions(S), dtype=np.uint64, copy=True)
+    out = np.empty((n_rows, K), dtype=np.float64)
+    st = lib().or_dirichlet(seed, S, _p(pos), n_rows, K, _p(alpha), _p(out), buf_len)
+    return out, pos, st
+
+
+def mixed(seed, S, tag, p0, p1, pos=None, buf_len=64, streams=None, nthreads=1):
+    """Mixed-tag stream; `streams=(s0, s1)` restricts to those streams only
+    (the other outputs stay NaN / 0)."""
+    tag = np.ascontiguousarray(tag, dtype=np.uint8)
+    p0, p1 = _f32(p0), _f32(p1)
+    n = tag.size
+    pos = np.array(pos if pos is not None else new_positions(S), dtype=np.uint64, copy=True)
+    out = np.full(n, np.nan, dtype=np.float64)
+    words = np.zeros(n, dtype=np.uint32)
+    if streams is None:
+        st = lib().or_mixed_mt(seed, S, _p(pos), n, _p(tag), _p(p0), _p(p1), _p(out), _p(words),
+                               buf_len, _threads(nthreads))
+    else:
+        st = lib().or_mixed_streams(seed, S, streams[0], streams[1], _p(pos), n, _p(tag), _p(p0),
+                                    _p(p1), _p(out), _p(words), buf_len)
+    return out, words, pos, st
+
+
+# ---- Gibbs models ---------------------------------------------------------
+
+def gibbs_triangle(seed, n_chains, n_sweeps, chain_offset=0, xy=None, pos=None, mom=None,
+                   buf_len=256, nthreads=1):
+    xy = np.full(2 * n_chains, 0.5) if xy is None else np.array(xy, dtype=np.float64, copy=True)
+    pos = np.zeros(n_chains, np.uint64) if pos is None else np.array(pos, np.uint64, copy=True)
+    mom = np.zeros(5 * n_chains) if mom is None else np.array(mom, dtype=np.float64, copy=True)
+    st = lib().or_gibbs_triangle_mt(seed, chain_offset, n_chains, n_sweeps, _p(xy), _p(pos),
+                                    _p(mom), buf_len, _threads(nthreads))
+    return dict(xy=xy.reshape(n_chains, 2), pos=pos, mom=mom.reshape(n_chains, 5), status=st)
+
+
+def gibbs_normal_gamma(seed, n_sweeps, nobs, xbar, sc, prior=(2.0, 1.0, 0.0, 0.01),
+                       chain_offset=0, state=None, pos=None, mom=None, buf_len=64, nthreads=1):
+    nobs, xbar, sc = _f32(nobs), _f32(xbar), _f32(sc)
+    n_chains = nobs.size
+    prior = np.ascontiguousarray(prior, dtype=np.float32)
+    state = np.zeros(2 * n_chains) if state is None else np.array(state, np.float64, copy=True)
+    pos = np.zeros(2 * n_chains, np.uint64) if pos is None else np.array(pos, np.uint64, copy=True)
+    mom = np.zeros(4 * n_chains) if mom is None else np.array(mom, np.float64, copy=True)
+    st = lib().or_gibbs_normal_gamma_mt(seed, chain_offset, n_chains, n_sweeps, _p(prior),
+                                        _p(nobs), _p(xbar), _p(sc), _p(state), _p(pos), _p(mom),
+                                        buf_len, _threads(nthreads))
+    return dict(state=state.reshape(n_chains, 2), pos=pos.reshape(n_chains, 2),
+                mom=mom.reshape(n_chains, 4), status=st)
+
+
+def gibbs_lda(seed, n_sweeps, alpha, doc_offset=0, pos=None, mom=None, buf_len=64, nthreads=1):
+    alpha = _f32(alpha)
+    n_docs, K = alpha.shape
+    theta = np.zeros((n_docs, K))
+    pos = np.zeros(2 * n_docs * K, np.uint64) if pos is None else np.array(pos, np.uint64, copy=True)
+    mom = np.zeros((n_docs, K)) if mom is None else np.array(mom, np.float64, copy=True)
+    st = lib().or_gibbs_lda_mt(seed, doc_offset, n_docs, K, n_sweeps, _p(alpha), _p(theta),
+                               _p(pos), _p(mom), buf_len, _threads(nthreads))
+    return dict(theta=theta, pos=pos.reshape(n_docs, K, 2), mom=mom, status=st)

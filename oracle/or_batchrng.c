@@ -1,0 +1,318 @@
+/*
+ * or_batchrng.c -- the paper's buffered RNG object and the varying-parameter
+ * distributions built on it, in FP64.  TEST INFRASTRUCTURE ONLY (oracle.h).
+ *
+ * The object follows Sec. 2.2 member for member: per reducible distribution
+ * a buffer_length, a buffer and a buffer_counter; the constructor fills every
+ * buffer; a Get* call refills its buffer from the core engine when the
+ * counter has reached the end, resets the counter, and returns
+ * buffer[counter++].  Irreducible distributions (Gamma, Laplace, Weibull) are
+ * composed from the reducible Get* calls (Sec. 2.2, Sec. 2.1 key concept 1).
+ *
+ * Readings where the paper is silent (Gamma source withheld, Sec. 3 note;
+ * Laplace/Weibull formulas not given, Sec. 2.2):
+ *   Gamma(alpha, 1): Marsaglia & Tsang (2000).  a = alpha (alpha >= 1) or
+ *     alpha + 1 (alpha < 1); d = a - 1/3; c = 1/sqrt(9d).  Each attempt takes
+ *     one Gaussian z; t = 1 + c z; if t <= 0 the attempt ends; otherwise
+ *     v = t^3, one U' is taken and the attempt accepts iff
+ *     ln U' < z^2/2 + d (1 - v + ln v), giving d v.  For alpha < 1 one more
+ *     U' is taken after the accept and the result is d v U'^(1/alpha).
+ *     After 64 attempts the draw is NaN (never reached in practice).
+ *   Laplace(mu, b): one exponential e, then one uniform u; mu - b e if
+ *     u < 1/2, else mu + b e.
+ *   Weibull(k, lambda): lambda e^(1/k) for one exponential e.
+ * An invalid parameter gives NaN and consumes nothing.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "oracle.h"
+#include "or_internal.h"
+
+/* ---- the buffered object --------------------------------------------- */
+
+static void or_fill(or_batchrng *g, uint32_t dom) {
+  or_buffer *b = &g->buf[dom];
+  or_elem_values(g->seed, dom, g->stream, b->first, b->length, b->buffer, b->words);
+}
+
+void or_batchrng_init(or_batchrng *g, uint64_t seed, uint32_t stream, const uint64_t *start,
+                      const uint32_t *length) {
+  g->seed = seed;
+  g->stream = stream;
+  for (uint32_t d = 0; d < OR_NDOM; ++d) {
+    or_buffer *b = &g->buf[d];
+    b->length = length[d];
+    b->counter = 0;
+    b->first = start[d];
+    b->buffer = b->length ? (double *)malloc(sizeof(double) * b->length) : NULL;
+    b->words = b->length ? (uint32_t *)malloc(sizeof(uint32_t) * b->length) : NULL;
+    if (b->length) or_fill(g, d);
+  }
+}
+
+void or_batchrng_free(or_batchrng *g, uint64_t *end) {
+  for (uint32_t d = 0; d < OR_NDOM; ++d) {
+    or_buffer *b = &g->buf[d];
+    if (end) end[d] = b->first + b->counter;
+    free(b->buffer);
+    free(b->words);
+    b->buffer = NULL;
+    b->words = NULL;
+  }
+}
+
+double or_get(or_batchrng *g, uint32_t dom, uint32_t *word) {
+  or_buffer *b = &g->buf[dom];
+  if (b->length == 0) abort(); /* the caller disabled a domain it uses */
+  if (b->counter == b->length) {
+    b->first += b->length;
+    b->counter = 0;
+    or_fill(g, dom);
+  }
+  if (word) *word = b->words[b->counter];
+  return b->buffer[b->counter++];
+}
+
+/* GetUniform returns U in [0,1); the open-left U' = U + 2^-24 is exact */
+double or_get_uniform(or_batchrng *g, uint32_t *word) { return or_get(g, OR_DOM_U, word); }
+double or_get_uniform_open(or_batchrng *g) { return or_get(g, OR_DOM_U, NULL) + 0x1p-24; }
+double or_get_log_uniform(or_batchrng *g) { return or_log(or_get_uniform_open(g)); }
+double or_get_gaussian(or_batchrng *g, uint32_t *word) { return or_get(g, OR_DOM_N, word); }
+double or_get_exponential(or_batchrng *g, uint32_t *word) { return or_get(g, OR_DOM_E, word); }
+double or_get_u64(or_batchrng *g) { return or_get(g, OR_DOM_U64, NULL); }
+
+int or_mt_accept(double alpha, double z, double u_open) {
+  double a = alpha < 1.0 ? alpha + 1.0 : alpha;
+  double d = a - 1.0 / 3.0;
+  double c = 1.0 / sqrt(9.0 * d);
+  double t = 1.0 + c * z;
+  if (t <= 0.0) return -1;
+  double v = t * t * t;
+  return or_log(u_open) < 0.5 * z * z + d * ((1.0 - v) + or_log(v));
+}
+
+double or_get_gamma(or_batchrng *g, float alpha_f, uint32_t *first_word, double *log_y,
+                    int *rejected) {
+  double alpha = (double)alpha_f;
+  double a = alpha < 1.0 ? alpha + 1.0 : alpha;
+  double d = a - 1.0 / 3.0;
+  double c = 1.0 / sqrt(9.0 * d);
+  for (int attempt = 0; attempt < OR_GAMMA_MAX_ATTEMPTS; ++attempt) {
+    uint32_t w;
+    double z = or_get_gaussian(g, &w);
+    if (attempt == 0 && first_word) *first_word = w;
+    double t = 1.0 + c * z;
+    if (t <= 0.0) continue;
+    double v = t * t * t;
+    double u = or_get_uniform_open(g);
+    if (or_log(u) < 0.5 * z * z + d * ((1.0 - v) + or_log(v))) {
+      double y = d * v;
+      double ly = log(y);
+      if (alpha < 1.0) {
+        double ub = or_get_uniform_open(g);
+        y = y * pow(ub, 1.0 / alpha);
+        ly = ly + log(ub) / alpha;
+      }
+      if (log_y) *log_y = ly;
+      return y;
+    }
+  }
+  if (rejected) *rejected = 1;
+  if (log_y) *log_y = NAN;
+  return NAN;
+}
+
+/* ---- bulk varying-parameter streams ----------------------------------- */
+
+static int finite_f(float x) { return isfinite(x); }
+
+/* open stream s positioned at pos[3s..3s+2] (U, N, E) with buffers of L */
+static void open_stream(or_batchrng *g, uint64_t seed, uint32_t s, const uint64_t *pos3,
+                        uint32_t L) {
+  uint64_t start[OR_NDOM] = {pos3[0], pos3[1], pos3[2], 0, 0};
+  uint32_t len[OR_NDOM] = {L, L, L, 0, 0};
+  or_batchrng_init(g, seed, s, start, len);
+}
+
+static void close_stream(or_batchrng *g, uint64_t *pos3) {
+  uint64_t end[OR_NDOM];
+  or_batchrng_free(g, end);
+  pos3[0] = end[0];
+  pos3[1] = end[1];
+  pos3[2] = end[2];
+}
+
+/* one draw of distribution `tag` with parameters (p0, p1); returns the value,
+ * sets *word to the first raw word it consumed (0 if none), and counts
+ * errors. */
+static double draw_tagged(or_batchrng *g, unsigned tag, float p0, float p1, uint32_t *word,
+                          int *n_domain, int *n_reject) {
+  uint32_t w = 0;
+  double out = NAN;
+  switch (tag) {
+  case 0: /* Uniform[a, b) = a + (b - a) U */
+    if (finite_f(p0) && finite_f(p1) && p0 <= p1) {
+      double u = or_get_uniform(g, &w);
+      out = (double)p0 + ((double)p1 - (double)p0) * u;
+    } else ++*n_domain;
+    break;
+  case 1: /* Normal(mu, sigma) = mu + sigma z */
+    if (finite_f(p0) && finite_f(p1) && p1 > 0.0f) {
+      double z = or_get_gaussian(g, &w);
+      out = (double)p0 + (double)p1 * z;
+    } else ++*n_domain;
+    break;
+  case 2: /* Exponential(rate lambda) = E / lambda */
+    if (finite_f(p0) && p0 > 0.0f) {
+      double e = or_get_exponential(g, &w);
+      out = e / (double)p0;
+    } else ++*n_domain;
+    break;
+  case 3: /* Gamma(alpha, 1) */
+    if (finite_f(p0) && p0 > 0.0f) {
+      int rej = 0;
+      out = or_get_gamma(g, p0, &w, NULL, &rej);
+      if (rej) ++*n_reject;
+    } else ++*n_domain;
+    break;
+  case 4: /* Laplace(mu, b) */
+    if (finite_f(p0) && finite_f(p1) && p1 > 0.0f) {
+      double e = or_get_exponential(g, &w);
+      double u = or_get_uniform(g, NULL);
+      out = u < 0.5 ? (double)p0 - (double)p1 * e : (double)p0 + (double)p1 * e;
+    } else ++*n_domain;
+    break;
+  case 5: /* Weibull(shape k, scale lambda) = lambda E^(1/k) */
+    if (finite_f(p0) && finite_f(p1) && p0 > 0.0f && p1 > 0.0f) {
+      double e = or_get_exponential(g, &w);
+      out = (double)p1 * pow(e, 1.0 / (double)p0);
+    } else ++*n_domain;
+    break;
+  default:
+    ++*n_domain;
+  }
+  if (word) *word = w;
+  return out;
+}
+
+static int status_of(int n_domain, int n_reject) {
+  if (n_domain) return OR_EDOMAIN;
+  if (n_reject) return OR_EREJECT;
+  return OR_OK;
+}
+
+int or_mixed_streams(uint64_t seed, uint32_t S, uint32_t s_begin, uint32_t s_end, uint64_t *pos,
+                     uint64_t n, const uint8_t *tag, const float *p0, const float *p1,
+                     double *out, uint32_t *words, uint32_t buf_len) {
+  int n_domain = 0, n_reject = 0;
+  if (S == 0 || buf_len == 0) return OR_EINVAL;
+  for (uint32_t s = s_begin; s < s_end && s < S; ++s) {
+    if ((uint64_t)s >= n) break;
+    or_batchrng g;
+    open_stream(&g, seed, s, pos + 3 * (uint64_t)s, buf_len);
+    for (uint64_t i = s; i < n; i += S) {
+      uint32_t w;
+      out[i] = draw_tagged(&g, tag[i], p0[i], p1 ? p1[i] : 0.0f, &w, &n_domain, &n_reject);
+      if (words) words[i] = w;
+    }
+    close_stream(&g, pos + 3 * (uint64_t)s);
+  }
+  return status_of(n_domain, n_reject);
+}
+
+int or_mixed(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const uint8_t *tag,
+             const float *p0, const float *p1, double *out, uint32_t *words, uint32_t buf_len) {
+  return or_mixed_streams(seed, S, 0, S, pos, n, tag, p0, p1, out, words, buf_len);
+}
+
+/* single-distribution streams: the mixed stream with a constant tag */
+static int single(unsigned tagv, uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n,
+                  const float *p0, const float *p1, double *out, uint32_t *words,
+                  uint32_t buf_len) {
+  int n_domain = 0, n_reject = 0;
+  if (S == 0 || buf_len == 0) return OR_EINVAL;
+  for (uint32_t s = 0; s < S && (uint64_t)s < n; ++s) {
+    or_batchrng g;
+    open_stream(&g, seed, s, pos + 3 * (uint64_t)s, buf_len);
+    for (uint64_t i = s; i < n; i += S) {
+      uint32_t w;
+      out[i] = draw_tagged(&g, tagv, p0[i], p1 ? p1[i] : 0.0f, &w, &n_domain, &n_reject);
+      if (words) words[i] = w;
+    }
+    close_stream(&g, pos + 3 * (uint64_t)s);
+  }
+  return status_of(n_domain, n_reject);
+}
+
+int or_uniform(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *a,
+               const float *b, double *out, uint32_t *words, uint32_t buf_len) {
+  return single(0, seed, S, pos, n, a, b, out, words, buf_len);
+}
+int or_normal(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *mu,
+              const float *sigma, double *out, uint32_t *words, uint32_t buf_len) {
+  return single(1, seed, S, pos, n, mu, sigma, out, words, buf_len);
+}
+int or_exponential(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *lambda,
+                   double *out, uint32_t *words, uint32_t buf_len) {
+  return single(2, seed, S, pos, n, lambda, NULL, out, words, buf_len);
+}
+int or_gamma(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *alpha,
+             double *out, uint32_t *words, uint32_t buf_len) {
+  return single(3, seed, S, pos, n, alpha, NULL, out, words, buf_len);
+}
+int or_laplace(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *mu,
+               const float *scale, double *out, uint32_t *words, uint32_t buf_len) {
+  return single(4, seed, S, pos, n, mu, scale, out, words, buf_len);
+}
+int or_weibull(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *shape,
+               const float *scale, double *out, uint32_t *words, uint32_t buf_len) {
+  return single(5, seed, S, pos, n, shape, scale, out, words, buf_len);
+}
+
+/* Dirichlet (Sec. 1 footnote): y_k ~ Gamma(alpha_k, 1), x_k = y_k / sum y.
+ * The normalisation is taken on log y_k (x_k = exp(l_k - M) / sum exp(l_j - M),
+ * M = max l), the same quotient without underflow of tiny y_k. */
+void or_dirichlet_row(or_batchrng *comp, uint32_t K, const float *alpha, double *out,
+                      double *scratch_l, int *n_domain, int *n_reject) {
+  for (uint32_t k = 0; k < K; ++k) {
+    if (!(finite_f(alpha[k]) && alpha[k] > 0.0f)) {
+      ++*n_domain;
+      for (uint32_t j = 0; j < K; ++j) out[j] = NAN;
+      return;
+    }
+  }
+  int rej = 0;
+  for (uint32_t k = 0; k < K; ++k) or_get_gamma(&comp[k], alpha[k], NULL, &scratch_l[k], &rej);
+  if (rej) {
+    ++*n_reject;
+    for (uint32_t j = 0; j < K; ++j) out[j] = NAN;
+    return;
+  }
+  double M = scratch_l[0];
+  for (uint32_t k = 1; k < K; ++k) M = scratch_l[k] > M ? scratch_l[k] : M;
+  double sum = 0.0;
+  for (uint32_t k = 0; k < K; ++k) sum += exp(scratch_l[k] - M);
+  for (uint32_t k = 0; k < K; ++k) out[k] = exp(scratch_l[k] - M) / sum;
+}
+
+int or_dirichlet(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n_rows, uint32_t K,
+                 const float *alpha, double *out, uint32_t buf_len) {
+  if (S == 0 || K == 0 || S % K != 0 || buf_len == 0) return OR_EINVAL;
+  uint32_t R = S / K;
+  int n_domain = 0, n_reject = 0;
+  or_batchrng *comp = (or_batchrng *)malloc(sizeof(or_batchrng) * K);
+  double *l = (double *)malloc(sizeof(double) * K);
+  for (uint32_t r = 0; r < R && (uint64_t)r < n_rows; ++r) {
+    for (uint32_t k = 0; k < K; ++k)
+      open_stream(&comp[k], seed, r * K + k, pos + 3 * ((uint64_t)r * K + k), buf_len);
+    for (uint64_t i = r; i < n_rows; i += R)
+      or_dirichlet_row(comp, K, alpha + i * K, out + i * K, l, &n_domain, &n_reject);
+    for (uint32_t k = 0; k < K; ++k) close_stream(&comp[k], pos + 3 * ((uint64_t)r * K + k));
+  }
+  free(comp);
+  free(l);
+  return status_of(n_domain, n_reject);
+}

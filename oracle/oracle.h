@@ -1,0 +1,137 @@
+/*
+ * oracle.h -- the CPU oracle of the batched varying-parameter RNG method.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, FP64 restatement of the
+ * method (Mahani & Sharabiani, "Efficient SIMD RNG for Varying-Parameter
+ * Streams: C++ Class BatchRNG", arXiv 1412.4825), written to check the CUDA
+ * path.  Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+ * reference legs may load it.  It shares no code, header, table or constant
+ * with the CUDA library; the two agree only through the definitions below.
+ *
+ * Conventions (the paper leaves the engine open, Sec. 2.2; these are the
+ * readings this project fixes):
+ *   - core engine: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
+ *     key = (seed & 0xffffffff, seed >> 32),
+ *     counter = (block & 0xffffffff, domain, stream, block >> 32);
+ *   - a stream is one BatchRNG object (Sec. 2.2); each reducible
+ *     distribution ("domain") has its own element sequence, element j of a
+ *     4-word domain living in block j/4, word j%4 (U64: block j/2, words
+ *     2(j%2), 2(j%2)+1);
+ *   - buffers (Sec. 2.2 "buffer_length", "buffer", "buffer_counter") hold a
+ *     window of that sequence and are refilled when the counter reaches the
+ *     end, so every value is independent of the buffer length.
+ */
+#ifndef BRNG_ORACLE_H
+#define BRNG_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* domain tags (counter word 1) */
+#define OR_DOM_U 0u    /* 24-bit uniforms, one word per element           */
+#define OR_DOM_N 1u    /* Box-Muller Gaussians, a word pair per two elems  */
+#define OR_DOM_E 2u    /* exponentials -ln U', one word per element        */
+#define OR_DOM_DATA 3u /* reserved for synthetic data / set-up draws       */
+#define OR_DOM_U64 4u  /* 53-bit uniforms, two words per element           */
+#define OR_NDOM 5
+
+/* status bits returned by the bulk and Gibbs functions */
+#define OR_OK 0
+#define OR_EDOMAIN 4
+#define OR_EREJECT 5
+#define OR_EINVAL 1
+
+/* Marsaglia-Tsang attempts before a Gamma draw gives up (NaN + EREJECT) */
+#define OR_GAMMA_MAX_ATTEMPTS 64
+
+/* ---- core engine ------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void or_philox_words(uint64_t seed, uint32_t domain, uint32_t stream,
+                     uint64_t first_block, uint64_t n_blocks, uint32_t *out);
+
+/* ---- FP64 elementary functions written for the oracle ----------------- */
+double or_log(double x);
+void or_sincospi(double a, double *s, double *c);
+void or_log_many(uint64_t n, const double *x, double *out);
+void or_sincospi_many(uint64_t n, const double *a, double *s, double *c);
+
+/* ---- element accessors: element j of a domain, straight from the engine */
+uint32_t or_elem_word(uint64_t seed, uint32_t domain, uint32_t stream, uint64_t j);
+double or_elem_value(uint64_t seed, uint32_t domain, uint32_t stream, uint64_t j);
+void or_elem_values(uint64_t seed, uint32_t domain, uint32_t stream, uint64_t j0,
+                    uint64_t n, double *out, uint32_t *words);
+
+/* ---- bulk varying-parameter streams (Sec. 2.3: per-draw parameters read
+ *      from memory, every output written).  Draw i goes to stream i mod S.
+ *      pos[3*s + {0,1,2}] = next U, N, E element of stream s (in/out).   */
+int or_uniform(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *a,
+               const float *b, double *out, uint32_t *words, uint32_t buf_len);
+int or_normal(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *mu,
+              const float *sigma, double *out, uint32_t *words, uint32_t buf_len);
+int or_exponential(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *lambda,
+                   double *out, uint32_t *words, uint32_t buf_len);
+int or_gamma(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *alpha,
+             double *out, uint32_t *words, uint32_t buf_len);
+int or_laplace(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *mu,
+               const float *scale, double *out, uint32_t *words, uint32_t buf_len);
+int or_weibull(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *shape,
+               const float *scale, double *out, uint32_t *words, uint32_t buf_len);
+/* rows of K components; S % K == 0; component k of row i draws from stream
+ * (i mod (S/K))*K + k */
+int or_dirichlet(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n_rows, uint32_t K,
+                 const float *alpha, double *out, uint32_t buf_len);
+/* tag 0 U(p0,p1), 1 N(p0,p1), 2 Exp(rate p0), 3 Gamma(p0), 4 Laplace(p0,p1),
+ * 5 Weibull(shape p0, scale p1) */
+int or_mixed(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const uint8_t *tag,
+             const float *p0, const float *p1, double *out, uint32_t *words, uint32_t buf_len);
+/* the same, for the streams in [s_begin, s_end) only (sampled parity) */
+int or_mixed_streams(uint64_t seed, uint32_t S, uint32_t s_begin, uint32_t s_end, uint64_t *pos,
+                     uint64_t n, const uint8_t *tag, const float *p0, const float *p1,
+                     double *out, uint32_t *words, uint32_t buf_len);
+
+/* ---- Gibbs models (Markov-dependent consumers) ------------------------ */
+/* Eq. 1 / Fig. 1: xy[2c] = x, xy[2c+1] = y; pos[c] = next U64 element;
+ * mom[5c..5c+4] += (x, y, x^2, y^2, xy) per sweep. */
+int or_gibbs_triangle(uint64_t seed, uint64_t chain_offset, uint32_t n_chains, uint32_t n_sweeps,
+                      double *xy, uint64_t *pos, double *mom, uint32_t buf_len);
+/* Normal model with unknown mean and precision, semi-conjugate priors
+ * mu ~ N(mu0, 1/prec0), tau ~ Gamma(a0, rate b0).  prior = {a0, b0, mu0, prec0}.
+ * state[2c] = mu, state[2c+1] = tau; pos[2c] = N, pos[2c+1] = U;
+ * mom[4c..4c+3] += (mu, tau, mu^2, tau^2). */
+int or_gibbs_normal_gamma(uint64_t seed, uint64_t chain_offset, uint32_t n_chains,
+                          uint32_t n_sweeps, const float *prior, const float *nobs,
+                          const float *xbar, const float *sc, double *state, uint64_t *pos,
+                          double *mom, uint32_t buf_len);
+/* LDA-style document-topic draws theta_d ~ Dir(alpha_d) every sweep; component
+ * (d, k) is stream (doc_offset + d)*K + k; pos[2(dK+k)] = N, [..+1] = U;
+ * theta = last draw; mom[dK+k] += theta_dk per sweep. */
+int or_gibbs_lda(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K,
+                 uint32_t n_sweeps, const float *alpha, double *theta, uint64_t *pos,
+                 double *mom, uint32_t buf_len);
+
+/* the same on `nthreads` host threads over contiguous chain ranges */
+int or_gibbs_triangle_mt(uint64_t seed, uint64_t chain_offset, uint32_t n_chains,
+                         uint32_t n_sweeps, double *xy, uint64_t *pos, double *mom,
+                         uint32_t buf_len, int nthreads);
+int or_gibbs_normal_gamma_mt(uint64_t seed, uint64_t chain_offset, uint32_t n_chains,
+                             uint32_t n_sweeps, const float *prior, const float *nobs,
+                             const float *xbar, const float *sc, double *state, uint64_t *pos,
+                             double *mom, uint32_t buf_len, int nthreads);
+int or_gibbs_lda_mt(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K,
+                    uint32_t n_sweeps, const float *alpha, double *theta, uint64_t *pos,
+                    double *mom, uint32_t buf_len, int nthreads);
+int or_mixed_mt(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const uint8_t *tag,
+                const float *p0, const float *p1, double *out, uint32_t *words,
+                uint32_t buf_len, int nthreads);
+
+/* Marsaglia-Tsang acceptance test of one attempt, exactly as the Gamma
+ * sampler takes it (for tests): returns 1 accept, 0 reject, -1 if t <= 0. */
+int or_mt_accept(double alpha, double z, double u_open);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,106 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds no arithmetic of the method itself (no generator, no
+transform, no Gibbs update): it only draws the *inputs* -- per-draw parameter
+arrays, observation summaries, topic counts -- with numpy's own seeded
+generator.  The CUDA path and the oracle are both fed from here.
+
+Workloads (arXiv 1412.4825):
+  * triangle Gibbs of Eq. 1 / Fig. 1 needs no input beyond the start (0.5, 0.5);
+  * normal-gamma Gibbs: per chain n observations ~ N(mean, sd^2), reduced to
+    (n, xbar, S = sum (x - xbar)^2) in FP64 and handed over as FP32;
+  * LDA document-topic step (Sec. 1, LDA paragraph): per document a topic mix
+    phi ~ Dir(prior * 1_K), a length L ~ U{len_lo..len_hi}, counts ~ Mult(L, phi),
+    and the Dirichlet parameter alpha = prior + counts formed in FP32;
+  * varying-parameter streams (Sec. 2.3, parameters read from memory per
+    draw): log-uniform parameters, and for the mixed stream a tag per draw.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+TAG_UNIFORM, TAG_NORMAL, TAG_EXPONENTIAL, TAG_GAMMA, TAG_LAPLACE, TAG_WEIBULL = 0, 1, 2, 3, 4, 5
+
+
+def log_uniform(rng: np.random.Generator, lo: float, hi: float, n: int) -> np.ndarray:
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), n)).astype(np.float32)
+
+
+def normal_gamma_data(n_chains: int, n_obs: int = 100, mean: float = 1.5, sd: float = 2.0,
+                      seed: int = 42, chunk: int = 8192):
+    """Per-chain sufficient statistics (nobs, xbar, S) as float32 arrays."""
+    rng = np.random.default_rng(seed)
+    nobs = np.full(n_chains, n_obs, dtype=np.float32)
+    xbar = np.empty(n_chains, dtype=np.float32)
+    sc = np.empty(n_chains, dtype=np.float32)
+    for c0 in range(0, n_chains, chunk):
+        c1 = min(n_chains, c0 + chunk)
+        x = rng.normal(mean, sd, size=(c1 - c0, n_obs))
+        xb = x.mean(axis=1)
+        xbar[c0:c1] = xb
+        sc[c0:c1] = ((x - xb[:, None]) ** 2).sum(axis=1)
+    return nobs, xbar, sc
+
+
+def lda_alpha(n_docs: int, K: int = 64, len_lo: int = 50, len_hi: int = 500, prior: float = 0.1,
+              seed: int = 42):
+    """(alpha float32 [n_docs, K], counts uint32 [n_docs, K], lengths)."""
+    rng = np.random.default_rng(seed)
+    phi = rng.dirichlet(np.full(K, prior), size=n_docs)
+    lengths = rng.integers(len_lo, len_hi + 1, size=n_docs)
+    counts = np.stack([rng.multinomial(int(L), p) for L, p in zip(lengths, phi)]).astype(np.uint32)
+    alpha = (np.float32(prior) + counts.astype(np.float32)).astype(np.float32)
+    return alpha, counts, lengths
+
+
+def uniform_params(n: int, seed: int = 42, lo: float = 1e-3, hi: float = 1e3):
+    rng = np.random.default_rng(seed)
+    a = log_uniform(rng, lo, hi, n)
+    b = log_uniform(rng, lo, hi, n)
+    return np.minimum(a, b), np.maximum(a, b)
+
+
+def normal_params(n: int, seed: int = 42):
+    rng = np.random.default_rng(seed)
+    mu = log_uniform(rng, 1e-3, 1e3, n) * np.where(rng.random(n) < 0.5, -1, 1).astype(np.float32)
+    sigma = log_uniform(rng, 1e-2, 1e2, n)
+    return mu.astype(np.float32), sigma
+
+
+def rate_params(n: int, seed: int = 42):
+    return log_uniform(np.random.default_rng(seed), 1e-2, 1e2, n)
+
+
+def shape_params(n: int, seed: int = 42, lo: float = 0.05, hi: float = 50.0):
+    return log_uniform(np.random.default_rng(seed), lo, hi, n)
+
+
+def mixed_stream(n: int, seed: int = 42, n_tags: int = 4):
+    """Tag per draw (uniform over the first n_tags distributions) and its
+    parameters (p0, p1): U(a,b) a,b log-U[1e-3,1e3] sorted; N(mu, sigma)
+    mu = +-log-U[1e-3,1e3], sigma log-U[1e-2,1e2]; Exp(rate) log-U[1e-2,1e2];
+    Gamma(alpha) log-U[0.05, 50]; Laplace(mu, b) like Normal; Weibull(k, lambda)
+    k log-U[0.5, 5], lambda log-U[1e-2, 1e2]."""
+    rng = np.random.default_rng(seed)
+    tag = rng.integers(0, n_tags, size=n, dtype=np.uint8)
+    p0 = np.empty(n, dtype=np.float32)
+    p1 = np.zeros(n, dtype=np.float32)
+    for t in range(n_tags):
+        idx = np.nonzero(tag == t)[0]
+        m = idx.size
+        if t == TAG_UNIFORM:
+            a = log_uniform(rng, 1e-3, 1e3, m)
+            b = log_uniform(rng, 1e-3, 1e3, m)
+            p0[idx], p1[idx] = np.minimum(a, b), np.maximum(a, b)
+        elif t in (TAG_NORMAL, TAG_LAPLACE):
+            sign = np.where(rng.random(m) < 0.5, -1.0, 1.0).astype(np.float32)
+            p0[idx] = log_uniform(rng, 1e-3, 1e3, m) * sign
+            p1[idx] = log_uniform(rng, 1e-2, 1e2, m)
+        elif t == TAG_EXPONENTIAL:
+            p0[idx] = log_uniform(rng, 1e-2, 1e2, m)
+        elif t == TAG_GAMMA:
+            p0[idx] = log_uniform(rng, 0.05, 50.0, m)
+        elif t == TAG_WEIBULL:
+            p0[idx] = log_uniform(rng, 0.5, 5.0, m)
+            p1[idx] = log_uniform(rng, 1e-2, 1e2, m)
+    return tag, p0, p1
