@@ -1,0 +1,314 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched varying-parameter RNG hot path on GB300.
+
+Workload (one step): the normal-gamma Gibbs sampler -- 65,536 chains, each
+with n = 100 synthetic observations ~ N(1.5, 2^2), 2,000 sweeps of
+tau | mu ~ Gamma(52, rate) (Marsaglia-Tsang from the Gaussian and uniform
+rings) and mu | tau ~ Normal -- one library call, one kernel launch.  The
+metric is Gibbs updates per second (2 updates per chain-sweep), whole job over
+all ranks; every rank runs its own 65,536 chains (global chain ids offset by
+rank: weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the FP64 CPU oracle on this host's cores on a bounded
+sample of the same workload (the oracle is the reference of this project; the
+paper's own code is not available).  Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CHAINS = 65536
+N_SWEEPS = 2000
+N_OBS = 100
+SEED = 42
+PRIOR = (2.0, 1.0, 0.0, 0.01)
+UPDATES_PER_STEP = 2 * N_CHAINS * N_SWEEPS
+WORKLOAD = ("normal-gamma Gibbs: 65,536 chains x 2,000 sweeps, n=100 obs/chain ~N(1.5,2^2), "
+            "tau|mu ~ Gamma(52, 1+SS/2) (Marsaglia-Tsang) then mu|tau ~ Normal, Philox4x32-10 seed 42")
+METRIC = "Gibbs updates/s (normal-gamma, varying-parameter Gamma+Normal draws)"
+UNIT = "updates/s"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+PHILOX_MULS_PER_BLOCK = 20
+
+
+def _clock_sampler(uuid):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    cmd = ["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits", "-lms", "50"]
+    if uuid:
+        cmd += ["-i", uuid]
+    try:
+        return subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return None
+
+
+def _clock_summary(proc):
+    if proc is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        out, _ = proc.communicate()
+    sm, smax, reasons, power = [], [], set(), []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax.append(float(f[2]))
+            power.append(float(f[3]))
+        except ValueError:
+            continue
+        for name, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "power_w_max": max(power) if power else None,
+            "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _oracle_sample(n_chains, n_sweeps, nthreads, seed=SEED):
+    """The oracle on `n_chains` chains (a bounded sample of the workload)."""
+    import oracle as O
+    from paper_1412_4825_gb300 import inputs
+    nobs, xbar, sc = inputs.normal_gamma_data(n_chains, n_obs=N_OBS, seed=seed)
+    O.lib()
+    t0 = time.perf_counter()
+    O.gibbs_normal_gamma(seed, n_sweeps, nobs, xbar, sc, prior=PRIOR, nthreads=nthreads)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(n_chains=8192, n_sweeps=N_SWEEPS):
+    cores = os.cpu_count() or 1
+    dt = _oracle_sample(n_chains, n_sweeps, cores)
+    return {"value": 2.0 * n_chains * n_sweeps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of the 65,536 chains x %d sweeps (FP64 C oracle, %d threads, %.1f s)"
+                      % (n_chains, n_sweeps, cores, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    n_chains = 2048
+    for _ in range(args.warmup):
+        _oracle_sample(256, 200, cores)
+    times = [_oracle_sample(n_chains, N_SWEEPS, cores) for _ in range(args.steps)]
+    upd = 2.0 * n_chains * N_SWEEPS
+    value = upd * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_chains_per_step": n_chains},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d chains x %d sweeps per step, %d threads" % (n_chains, N_SWEEPS, cores)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    from paper_1412_4825_gb300 import build_lib
+    build_lib.build()
+    from paper_1412_4825_gb300 import brng as B
+    from paper_1412_4825_gb300 import inputs
+
+    chain_offset = rank * N_CHAINS
+    nobs, xbar, sc = inputs.normal_gamma_data(N_CHAINS, n_obs=N_OBS, seed=SEED + rank)
+    stream = torch.cuda.Stream(device=dev)
+    h = B.Handle(SEED, 1)
+    if args.buf_len or args.warps_per_block:
+        h.tune(buf_len=args.buf_len, warps_per_block=args.warps_per_block)
+    d_nobs, d_xbar, d_sc = (torch.from_numpy(a).to(dev) for a in (nobs, xbar, sc))
+    params = B.brng_normal_gamma_params_t(*PRIOR, d_nobs.data_ptr(), d_xbar.data_ptr(), d_sc.data_ptr())
+    state = B.normal_gamma_state(N_CHAINS, mu0=PRIOR[2], device=dev)
+    mom = torch.zeros((N_CHAINS, 4), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        B.brng_gibbs_run(h.h, B.MODEL_NORMAL_GAMMA, chain_offset, N_CHAINS, N_SWEEPS, params, state, mom,
+                         stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    barrier()
+    # consumption of one step (exact count of Philox blocks the method used)
+    before = state.clone()
+    with torch.cuda.stream(stream):
+        step()
+    torch.cuda.synchronize(dev)
+    _, _, pn0, pu0 = B.normal_gamma_unpack(before)
+    _, _, pn1, pu1 = B.normal_gamma_unpack(state)
+    blocks_per_step = float((pn1 - pn0).astype(np.float64).sum() + (pu1 - pu0).astype(np.float64).sum()) / 4.0
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    sampler = _clock_sampler(uuid) if rank == 0 else None
+    time.sleep(0.2 if sampler else 0)
+    barrier()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)  # between timed steps: write > L2
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = _clock_summary(sampler) if rank == 0 else None
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = torch.tensor([sum(ms)], dtype=torch.float64, device=dev)
+    if pg is not None:
+        pg.all_reduce(total_ms, op=pg.ReduceOp.MAX)
+    total_s = float(total_ms.item()) / 1e3
+    value = world * UPDATES_PER_STEP * args.steps / total_s
+
+    # end to end through the public API: host inputs -> device -> run -> host results
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    h_nobs, h_xbar, h_sc = pin(nobs), pin(xbar), pin(sc)
+    h_state_in = B.normal_gamma_state(N_CHAINS, mu0=PRIOR[2], device="cpu").pin_memory()
+    h_state_out = torch.empty_like(h_state_in).pin_memory()
+    h_mom = torch.empty((N_CHAINS, 4), dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in (h_nobs, h_xbar, h_sc, h_state_in))
+    d2h = sum(t.numel() * t.element_size() for t in (h_state_out, h_mom))
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            e_ev[k][0].record(stream)
+            d_nobs.copy_(h_nobs, non_blocking=True)
+            d_xbar.copy_(h_xbar, non_blocking=True)
+            d_sc.copy_(h_sc, non_blocking=True)
+            state.copy_(h_state_in, non_blocking=True)
+            mom.zero_()
+            step()
+            h_state_out.copy_(state, non_blocking=True)
+            h_mom.copy_(mom, non_blocking=True)
+            e_ev[k][1].record(stream)
+    barrier()
+    e_ms = torch.tensor([sum(a.elapsed_time(b) for a, b in e_ev)], dtype=torch.float64, device=dev)
+    if pg is not None:
+        pg.all_reduce(e_ms, op=pg.ReduceOp.MAX)
+    e2e_value = world * UPDATES_PER_STEP * args.steps / (float(e_ms.item()) / 1e3)
+
+    # integer-pipe roofline: Philox blocks the step consumed / kernel time,
+    # against 152 SMs x (64 32-bit multiply results per clock per SM / 2 per
+    # 64-bit product / 20 products per block) x SM clock
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_blocks = sm_count * (64.0 / 2.0 / PHILOX_MULS_PER_BLOCK) * sm_max * 1e6
+    kernel_s = total_s / args.steps  # one launch per step, events bracket it alone
+    achieved = blocks_per_step / kernel_s
+    # measured Philox probe for context
+    sink = torch.empty(sm_count * 8 * 256, dtype=torch.int32, device=dev)
+    B.brng_philox_peak(64, sm_count * 8, 256, sink, stream)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    B.brng_philox_peak(2048, sm_count * 8, 256, sink, stream)
+    pe1.record(stream)
+    torch.cuda.synchronize(dev)
+    probe_blocks_s = 4.0 * 2048 * sm_count * 8 * 256 / (pe0.elapsed_time(pe1) / 1e3)
+
+    if rank != 0:
+        if pg is not None:
+            pg.barrier()
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "chains_per_gpu": N_CHAINS, "sweeps": N_SWEEPS,
+                   "updates_per_step_per_gpu": UPDATES_PER_STEP, "parallelism": "chains sharded by rank",
+                   "l2": "flushed between timed steps (512 MB write)", "tuning": h.tuning},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_blocks / 1e9,
+                     "unit": "GPhilox-block/s", "frac": achieved / peak_blocks, "traffic": None,
+                     "kernel": "normal_gamma_kernel",
+                     "probe_measured": probe_blocks_s / 1e9,
+                     "note": "integer pipe: 20 32x32->64 multiplies per Philox4x32-10 block; blocks = "
+                             "exact consumption of the step (N+U elements / 4)"},
+        "wall_s_timed": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--buf-len", type=int, default=0)
+    ap.add_argument("--warps-per-block", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,251 @@
+/*
+ * brng.h -- C ABI of libbrng.so, the GB300 (sm_103a) implementation of the
+ * batched varying-parameter RNG method of Mahani & Sharabiani, "Efficient
+ * SIMD RNG for Varying-Parameter Streams: C++ Class BatchRNG" (arXiv
+ * 1412.4825).
+ *
+ * The paper's object (Sec. 2.2) keeps, per reducible distribution (uniform,
+ * Gaussian, exponential), a buffer of base deviates that the vectorised core
+ * engine fills in bulk; Get* calls consume it one draw at a time with
+ * per-draw parameters and refill it when the counter reaches the end.  Here
+ * every stream is a GPU lane, the core engine is Philox4x32-10 (Salmon et al.,
+ * SC'11), buffers are shared-memory rings that a whole warp refills at once,
+ * and all state stays on the device.
+ *
+ * Stream conventions (fixed; every value depends only on these):
+ *   key     = (seed & 0xffffffff, seed >> 32)
+ *   counter = (block & 0xffffffff, domain, stream, block >> 32)
+ *   element j of domain U, N or E lives in block j/4, word j%4;
+ *   element j of domain U64 lives in block j/2, words 2(j%2), 2(j%2)+1.
+ *   U = (w>>8) 2^-24 in [0,1);  U' = ((w>>8)+1) 2^-24 in (0,1];
+ *   N: (w0, w1) -> sqrt(-2 ln U'(w0)) * (cos, sin)(2 pi U(w1)), cos first;
+ *   E = -ln U'(w);  U64 = ((w0>>5) 2^26 + (w1>>6)) 2^-53.
+ * Values never depend on buffer length, block size, lanes per chain, call
+ * splitting or how chains are sharded over calls or devices.
+ *
+ * Memory: every array argument marked "device" is caller-owned device memory
+ * (e.g. a torch CUDA tensor), read or written asynchronously on `stream`; the
+ * call returns once the work is enqueued.  "host" arrays are read or written
+ * before the call returns.  Parameter arrays are float32 and contiguous.
+ *
+ * Errors: every call returns a brng_status_t.  Argument errors are detected
+ * on the host before any launch (BRNG_EINVAL); CUDA launch/alloc failures give
+ * BRNG_ECUDA / BRNG_ENOMEM.  Invalid per-draw parameters are *not* an error
+ * of the call: the draw's output is NaN, it consumes nothing, and the
+ * handle's device counters record it; brng_read_counters() synchronises the
+ * stream and reports BRNG_EDOMAIN / BRNG_EREJECT from those counters.
+ */
+#ifndef BRNG_H
+#define BRNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct brng_handle brng_t;
+typedef struct CUstream_st *brng_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  BRNG_OK = 0,
+  BRNG_EINVAL = 1,   /* bad argument (NULL pointer, size, unsupported option)     */
+  BRNG_ENOMEM = 2,   /* device allocation failed / memory budget exceeded         */
+  BRNG_ECUDA = 3,    /* a CUDA runtime call failed                                */
+  BRNG_EDOMAIN = 4,  /* some per-draw parameter was invalid (outputs NaN)         */
+  BRNG_EREJECT = 5,  /* some Gamma draw hit the 64-attempt cap (output NaN)       */
+  BRNG_ETIMEOUT = 6, /* a bounded device wait expired                             */
+  BRNG_EAGAIN = 7,   /* not done yet / not admitted yet                           */
+  BRNG_ENOTFOUND = 8 /* unknown job id                                            */
+} brng_status_t;
+
+/* domain tags (counter word 1) */
+enum { BRNG_DOMAIN_U = 0, BRNG_DOMAIN_N = 1, BRNG_DOMAIN_E = 2, BRNG_DOMAIN_DATA = 3,
+       BRNG_DOMAIN_U64 = 4 };
+
+/* distribution tags of the mixed stream */
+enum { BRNG_TAG_UNIFORM = 0, BRNG_TAG_NORMAL = 1, BRNG_TAG_EXPONENTIAL = 2, BRNG_TAG_GAMMA = 3,
+       BRNG_TAG_LAPLACE = 4, BRNG_TAG_WEIBULL = 5 };
+
+/* Gibbs models */
+typedef enum {
+  BRNG_MODEL_TRIANGLE = 0,     /* Sec. 1, Eq. 1 and Fig. 1                              */
+  BRNG_MODEL_NORMAL_GAMMA = 1, /* mean/precision of a normal sample, Gamma + Normal steps */
+  BRNG_MODEL_LDA = 2           /* LDA document-topic Dirichlet step (Sec. 1, footnote)   */
+} brng_model_t;
+
+/* Device-side counters of a handle (brng_read_counters). */
+typedef struct {
+  uint64_t n_domain;   /* draws with an invalid parameter (NaN output)               */
+  uint64_t n_reject;   /* Gamma draws that hit the attempt cap (NaN output)           */
+  uint64_t n_recheck;  /* Gamma tests re-decided in FP64 (FP32 margin within tolerance) */
+  uint64_t n_flip;     /* ... of which the FP64 decision differed from the FP32 sign  */
+  float max_flip_ratio;/* max |FP32 margin| / tolerance over the flips (must stay < 1) */
+  uint32_t pad;
+} brng_counters_t;
+
+/* Tuning knobs; zero fields mean "library default". */
+typedef struct {
+  uint32_t buf_len;         /* ring length per lane and domain, elements, power of 2 in [4, 512] */
+  uint32_t warps_per_block; /* 1..16                                                         */
+  uint32_t lanes_per_chain; /* triangle model only: 1, 2, 4, 8, 16 or 32                       */
+  uint32_t lookahead;       /* Dirichlet/LDA: sweeps a component may run ahead, 1..16         */
+} brng_tuning_t;
+
+/* ---- handle (Sec. 2.2 constructor / destructor) ---------------------------
+ * brng_create: a handle with `n_streams` streams (>= 1, < 2^32) keyed by
+ * `seed`, buffer length `buf_len` (0 = default 32; power of two, 4..512),
+ * on the current CUDA device.  It owns per-stream positions (3 x uint64 per
+ * stream, all zero = every stream at its start) and the counters.  The
+ * paper's constructor fills the buffers at once; here rings are filled lazily
+ * inside each kernel, which gives the same values.  *out is set only on
+ * BRNG_OK.  brng_destroy frees it (NULL is a no-op); no call on the handle
+ * may be in flight. */
+int brng_create(uint64_t seed, uint32_t n_streams, uint32_t buf_len, brng_t **out);
+int brng_destroy(brng_t *h);
+int brng_set_tuning(brng_t *h, const brng_tuning_t *t); /* host struct */
+int brng_get_tuning(const brng_t *h, brng_tuning_t *t);
+uint32_t brng_n_streams(const brng_t *h);
+uint64_t brng_seed(const brng_t *h);
+
+/* Checkpoint / resume of the stream positions: host array of 3*n_streams
+ * uint64, laid out [stream][U, N, E].  Synchronous (device-wide sync). */
+int brng_get_positions(brng_t *h, uint64_t *host_pos);
+int brng_set_positions(brng_t *h, const uint64_t *host_pos);
+
+/* Reads (and if `reset`, zeroes) the device counters after synchronising
+ * `stream`.  Returns BRNG_EDOMAIN if n_domain > 0, else BRNG_EREJECT if
+ * n_reject > 0, else BRNG_OK (or a CUDA error).  `out` (host) may be NULL. */
+int brng_read_counters(brng_t *h, brng_stream_t stream, brng_counters_t *out, int reset);
+
+/* ---- core engine (Sec. 2.2 "vectorized RNG for uniform distribution") ----
+ * Raw Philox4x32-10 words of blocks [first_block, first_block + n_blocks) of
+ * (domain, stream_id) under the handle's key: out (device, 4*n_blocks uint32)
+ * gets the 4 words of each block in order.  Stateless. */
+int brng_philox_words(brng_t *h, uint32_t domain, uint32_t stream_id, uint64_t first_block,
+                      size_t n_blocks, uint32_t *out, brng_stream_t stream);
+
+/* ---- integer-pipe probe ------------------------------------------------------
+ * Runs `blocks` x `threads` (<= 256) threads, each generating 4 x `iters`
+ * Philox4x32-10 blocks in registers (4 independent counter chains) and
+ * writing one checksum word to sink[thread] (device, blocks*threads uint32).
+ * Timing it gives the Philox generation rate of the device: the integer-pipe
+ * roofline of the method (no memory traffic on the measured path). */
+int brng_philox_peak(uint64_t iters, uint32_t blocks, uint32_t threads, uint32_t *sink,
+                     brng_stream_t stream);
+
+/* ---- FP64 elementary functions of the Gamma accept recheck ----------------
+ * out[i] = f(in[i]) on the device for fn = 0: log, 1: sin(pi x), 2: cos(pi x),
+ * the fixed-operation-order FP64 functions the Gamma sampler uses when it
+ * re-decides an accept test in FP64 (log by the atanh series, sin/cos(pi x) by
+ * exact reduction and Taylor series).  Exposed so that their bits can be
+ * checked against a reference.  in, out: device double[n]. */
+int brng_fp64_eval(uint32_t fn, size_t n, const double *in, double *out, brng_stream_t stream);
+
+/* ---- varying-parameter streams (Sec. 2.2 Get* functions; Sec. 2.3 method:
+ * parameters read from memory per draw, every output written) -------------
+ * Draw i (0 <= i < n) goes to stream i mod n_streams and takes that stream's
+ * next elements; draws of one stream are taken in increasing i, and the
+ * positions persist in the handle, so a later call continues every stream.
+ * out (device, n float32) gets the deviate; words (device, n uint32, or
+ * NULL) gets the raw Philox word of the first element the draw consumed
+ * (0 if none).  An invalid parameter gives NaN, consumes nothing and counts
+ * in n_domain. */
+/* U[a, b):  a + (b - a) U.  Needs finite a <= b. */
+int brng_uniform(brng_t *h, size_t n, const float *a, const float *b, float *out,
+                 uint32_t *words, brng_stream_t stream);
+/* N(mu, sigma): mu + sigma z.  Needs finite mu, finite sigma > 0. */
+int brng_normal(brng_t *h, size_t n, const float *mu, const float *sigma, float *out,
+                uint32_t *words, brng_stream_t stream);
+/* Exp(rate lambda): E / lambda.  Needs finite lambda > 0. */
+int brng_exponential(brng_t *h, size_t n, const float *lambda, float *out, uint32_t *words,
+                     brng_stream_t stream);
+/* Gamma(alpha, 1) by Marsaglia-Tsang (the paper withholds its GetGamma,
+ * Sec. 3 note): per attempt one N element z, t = 1 + z/sqrt(9d), d = a - 1/3,
+ * a = alpha (alpha >= 1) or alpha + 1; if t > 0 one U element u' and accept
+ * iff ln u' < z^2/2 + d (1 - t^3 + ln t^3), result d t^3; alpha < 1 takes one
+ * more U element u_b after the accept and multiplies by u_b^(1/alpha).  The
+ * accept test runs in FP32 and is re-decided in FP64 (from the same Philox
+ * bits) when the FP32 margin lies within its error bound.  Needs finite
+ * alpha > 0; 64 rejected attempts give NaN (n_reject). */
+int brng_gamma(brng_t *h, size_t n, const float *alpha, float *out, uint32_t *words,
+               brng_stream_t stream);
+/* Laplace(mu, b): one E element e, then one U element u; mu - b e if
+ * u < 1/2 else mu + b e.  Needs finite mu, finite b > 0. */
+int brng_laplace(brng_t *h, size_t n, const float *mu, const float *b, float *out,
+                 uint32_t *words, brng_stream_t stream);
+/* Weibull(shape k, scale lambda): lambda E^(1/k).  Needs finite k, lambda > 0. */
+int brng_weibull(brng_t *h, size_t n, const float *k, const float *lambda, float *out,
+                 uint32_t *words, brng_stream_t stream);
+/* Mixed stream: draw i is distribution tag[i] (BRNG_TAG_*) with parameters
+ * (p0[i], p1[i]) as in the calls above (Gamma, Exponential ignore p1).
+ * Unknown tags give NaN (n_domain).  tag: device uint8[n]. */
+int brng_mixed(brng_t *h, size_t n, const uint8_t *tag, const float *p0, const float *p1,
+               float *out, uint32_t *words, brng_stream_t stream);
+/* Dirichlet rows (Sec. 1 footnote: K Gammas, normalised).  alpha and out are
+ * device float32 [n_rows][K].  Needs K >= 1, K <= 128 and n_streams % K == 0:
+ * component k of row i draws its Gamma from stream (i mod (n_streams/K))*K + k.
+ * A row with any invalid alpha is all NaN and consumes nothing. */
+int brng_dirichlet(brng_t *h, size_t n_rows, uint32_t K, const float *alpha, float *out,
+                   brng_stream_t stream);
+
+/* ---- Gibbs models (Markov-dependent consumers; Sec. 1) ----------------------
+ * Runs `n_sweeps` sweeps of chains chain_offset .. chain_offset+n_chains-1
+ * (global chain id = Philox stream id; chains never share draws, so any split
+ * of a chain range over calls or devices gives identical results).  Uses the
+ * handle's seed and tuning, not its stream positions: each chain's positions
+ * are part of its device state, so a run continues from where the previous
+ * one stopped (checkpoint = copy the state arrays).  All arrays are device
+ * memory, per chain, contiguous:
+ *
+ * TRIANGLE (Eq. 1, Fig. 1): per sweep x <- (1 - y) U64, then y <- (1 - x) U64,
+ *   FP64 without contraction.  params: NULL.  state: brng_triangle_state_t[n].
+ *   moments: double[n][5] += (x, y, x^2, y^2, x y) per sweep.
+ * NORMAL_GAMMA: tau | mu ~ Gamma(a0 + n/2, rate b0 + SS/2), SS = S + n (xbar -
+ *   mu)^2, then mu | tau ~ N((prec0 mu0 + tau n xbar)/P, 1/P), P = prec0 + n tau.
+ *   params: brng_normal_gamma_params_t (host struct, copied at the call).
+ *   state: brng_normal_gamma_state_t[n].  moments: double[n][4] += (mu, tau,
+ *   mu^2, tau^2) per sweep.  FP32 arithmetic, FP64 accumulators.
+ * LDA: per sweep theta_d ~ Dirichlet(alpha_d); here a "chain" is a document
+ *   and component (d, k) is stream (chain_offset + d)*K + k.  params:
+ *   brng_lda_params_t (host struct).  state: brng_lda_state_t view (below).
+ *   moments: double[n][K] += theta per sweep.
+ */
+typedef struct {
+  double x, y;  /* current point, start (0.5, 0.5) */
+  uint64_t pos; /* next U64 element of the chain */
+  uint64_t pad;
+} brng_triangle_state_t;
+
+typedef struct {
+  float a0, b0, mu0, prec0; /* priors: tau ~ Gamma(a0, rate b0), mu ~ N(mu0, 1/prec0) */
+  const float *nobs;        /* device [n]: number of observations of each chain       */
+  const float *xbar;        /* device [n]: their mean                                  */
+  const float *sc;          /* device [n]: sum of squared deviations from the mean     */
+} brng_normal_gamma_params_t;
+
+typedef struct {
+  float mu, tau;     /* current values; start mu = mu0 (tau is drawn first) */
+  uint64_t pos_n;    /* next N element                                      */
+  uint64_t pos_u;    /* next U element                                      */
+} brng_normal_gamma_state_t;
+
+typedef struct {
+  uint32_t K;          /* topics, 1..128                                        */
+  const float *alpha;  /* device [n][K]: Dirichlet parameter of each document   */
+} brng_lda_params_t;
+
+typedef struct {
+  float *theta;   /* device [n][K]: last draw (output)                          */
+  uint64_t *pos;  /* device [n][K][2]: next (N, U) element of each component      */
+} brng_lda_state_t;
+
+int brng_gibbs_run(brng_t *h, brng_model_t model, uint64_t chain_offset, uint32_t n_chains,
+                   uint32_t n_sweeps, const void *params, void *state, double *moments,
+                   brng_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BRNG_H */

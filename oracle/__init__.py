@@ -38,23 +38,26 @@ def lib():
         L.or_log_many.argtypes = [u64, vp, vp]
         L.or_sincospi_many.argtypes = [u64, vp, vp, vp]
         L.or_elem_values.argtypes = [u64, u32, u32, u64, u64, vp, vp]
-        for name in ("or_uniform", "or_normal", "or_laplace", "or_weibull"):
+        for name in ("or_uniform", "or_normal", "or_laplace"):
             getattr(L, name).argtypes = [u64, u32, vp, u64, vp, vp, vp, vp, u32]
             getattr(L, name).restype = i32
-        for name in ("or_exponential", "or_gamma"):
-            getattr(L, name).argtypes = [u64, u32, vp, u64, vp, vp, vp, u32]
-            getattr(L, name).restype = i32
-        L.or_dirichlet.argtypes = [u64, u32, vp, u64, u32, vp, vp, u32]
+        L.or_weibull.argtypes = [u64, u32, vp, u64, vp, vp, vp, vp, vp, u32]
+        L.or_weibull.restype = i32
+        L.or_exponential.argtypes = [u64, u32, vp, u64, vp, vp, vp, u32]
+        L.or_exponential.restype = i32
+        L.or_gamma.argtypes = [u64, u32, vp, u64, vp, vp, vp, vp, u32]
+        L.or_gamma.restype = i32
+        L.or_dirichlet.argtypes = [u64, u32, vp, u64, u32, vp, vp, vp, vp, u32]
         L.or_dirichlet.restype = i32
-        L.or_mixed_streams.argtypes = [u64, u32, u32, u32, vp, u64, vp, vp, vp, vp, vp, u32]
+        L.or_mixed_streams.argtypes = [u64, u32, u32, u32, vp, u64, vp, vp, vp, vp, vp, vp, u32]
         L.or_mixed_streams.restype = i32
-        L.or_mixed_mt.argtypes = [u64, u32, vp, u64, vp, vp, vp, vp, vp, u32, i32]
+        L.or_mixed_mt.argtypes = [u64, u32, vp, u64, vp, vp, vp, vp, vp, vp, u32, i32]
         L.or_mixed_mt.restype = i32
         L.or_gibbs_triangle_mt.argtypes = [u64, u64, u32, u32, vp, vp, vp, u32, i32]
         L.or_gibbs_triangle_mt.restype = i32
         L.or_gibbs_normal_gamma_mt.argtypes = [u64, u64, u32, u32, vp, vp, vp, vp, vp, vp, vp, u32, i32]
         L.or_gibbs_normal_gamma_mt.restype = i32
-        L.or_gibbs_lda_mt.argtypes = [u64, u64, u32, u32, u32, vp, vp, vp, vp, u32, i32]
+        L.or_gibbs_lda_mt.argtypes = [u64, u64, u32, u32, u32, vp, vp, vp, vp, vp, vp, u32, i32]
         L.or_gibbs_lda_mt.restype = i32
         L.or_mt_accept.argtypes = [dbl, dbl, dbl]
         L.or_mt_accept.restype = i32
@@ -124,12 +127,20 @@ def new_positions(n_streams):
     return np.zeros(3 * n_streams, dtype=np.uint64)
 
 
-def _bulk(name, seed, S, pos, n, params, buf_len, with_words=True):
+def _bulk(name, seed, S, pos, n, params, buf_len, with_cond=False):
     pos = np.array(pos if pos is not None else new_positions(S), dtype=np.uint64, copy=True)
     out = np.empty(n, dtype=np.float64)
-    words = np.zeros(n, dtype=np.uint32) if with_words else None
+    words = np.zeros(n, dtype=np.uint32)
     ps = [_f32(p) for p in params]
-    st = getattr(lib(), name)(seed, S, _p(pos), n, *[_p(p) for p in ps], _p(out), _p(words), buf_len)
+    extra = []
+    cond = None
+    if name in ("or_gamma", "or_weibull"):
+        cond = np.zeros(n, dtype=np.float64)
+        extra = [_p(cond)]
+    st = getattr(lib(), name)(seed, S, _p(pos), n, *[_p(p) for p in ps], _p(out), _p(words), *extra,
+                              buf_len)
+    if with_cond:
+        return out, words, pos, st, cond
     return out, words, pos, st
 
 
@@ -145,28 +156,33 @@ def exponential(seed, S, lam, pos=None, buf_len=64):
     return _bulk("or_exponential", seed, S, pos, len(lam), [lam], buf_len)
 
 
-def gamma(seed, S, alpha, pos=None, buf_len=64):
-    return _bulk("or_gamma", seed, S, pos, len(alpha), [alpha], buf_len)
+def gamma(seed, S, alpha, pos=None, buf_len=64, with_cond=False):
+    return _bulk("or_gamma", seed, S, pos, len(alpha), [alpha], buf_len, with_cond)
 
 
 def laplace(seed, S, mu, scale, pos=None, buf_len=64):
     return _bulk("or_laplace", seed, S, pos, len(mu), [mu, scale], buf_len)
 
 
-def weibull(seed, S, shape, scale, pos=None, buf_len=64):
-    return _bulk("or_weibull", seed, S, pos, len(shape), [shape, scale], buf_len)
+def weibull(seed, S, shape, scale, pos=None, buf_len=64, with_cond=False):
+    return _bulk("or_weibull", seed, S, pos, len(shape), [shape, scale], buf_len, with_cond)
 
 
-def dirichlet(seed, S, alpha, pos=None, buf_len=64):
+def dirichlet(seed, S, alpha, pos=None, buf_len=64, with_logs=False):
     alpha = _f32(alpha)
     n_rows, K = alpha.shape
     pos = np.array(pos if pos is not None else new_positions(S), dtype=np.uint64, copy=True)
     out = np.empty((n_rows, K), dtype=np.float64)
-    st = lib().or_dirichlet(seed, S, _p(pos), n_rows, K, _p(alpha), _p(out), buf_len)
+    logs = np.empty((n_rows, K), dtype=np.float64)
+    cond = np.zeros((n_rows, K), dtype=np.float64)
+    st = lib().or_dirichlet(seed, S, _p(pos), n_rows, K, _p(alpha), _p(out), _p(logs), _p(cond),
+                            buf_len)
+    if with_logs:
+        return out, pos, st, logs, cond
     return out, pos, st
 
 
-def mixed(seed, S, tag, p0, p1, pos=None, buf_len=64, streams=None, nthreads=1):
+def mixed(seed, S, tag, p0, p1, pos=None, buf_len=64, streams=None, nthreads=1, with_cond=False):
     """Mixed-tag stream; `streams=(s0, s1)` restricts to those streams only
     (the other outputs stay NaN / 0)."""
     tag = np.ascontiguousarray(tag, dtype=np.uint8)
@@ -175,12 +191,15 @@ def mixed(seed, S, tag, p0, p1, pos=None, buf_len=64, streams=None, nthreads=1):
     pos = np.array(pos if pos is not None else new_positions(S), dtype=np.uint64, copy=True)
     out = np.full(n, np.nan, dtype=np.float64)
     words = np.zeros(n, dtype=np.uint32)
+    cond = np.zeros(n, dtype=np.float64)
     if streams is None:
         st = lib().or_mixed_mt(seed, S, _p(pos), n, _p(tag), _p(p0), _p(p1), _p(out), _p(words),
-                               buf_len, _threads(nthreads))
+                               _p(cond), buf_len, _threads(nthreads))
     else:
         st = lib().or_mixed_streams(seed, S, streams[0], streams[1], _p(pos), n, _p(tag), _p(p0),
-                                    _p(p1), _p(out), _p(words), buf_len)
+                                    _p(p1), _p(out), _p(words), _p(cond), buf_len)
+    if with_cond:
+        return out, words, pos, st, cond
     return out, words, pos, st
 
 
@@ -215,8 +234,11 @@ def gibbs_lda(seed, n_sweeps, alpha, doc_offset=0, pos=None, mom=None, buf_len=6
     alpha = _f32(alpha)
     n_docs, K = alpha.shape
     theta = np.zeros((n_docs, K))
+    logs = np.zeros((n_docs, K))
+    cond = np.zeros((n_docs, K))
     pos = np.zeros(2 * n_docs * K, np.uint64) if pos is None else np.array(pos, np.uint64, copy=True)
     mom = np.zeros((n_docs, K)) if mom is None else np.array(mom, np.float64, copy=True)
     st = lib().or_gibbs_lda_mt(seed, doc_offset, n_docs, K, n_sweeps, _p(alpha), _p(theta),
-                               _p(pos), _p(mom), buf_len, _threads(nthreads))
-    return dict(theta=theta, pos=pos.reshape(n_docs, K, 2), mom=mom, status=st)
+                               _p(logs), _p(cond), _p(pos), _p(mom), buf_len, _threads(nthreads))
+    return dict(theta=theta, logs=logs, cond=cond, pos=pos.reshape(n_docs, K, 2), mom=mom,
+                status=st)

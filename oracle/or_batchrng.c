@@ -95,7 +95,7 @@ int or_mt_accept(double alpha, double z, double u_open) {
 }
 
 double or_get_gamma(or_batchrng *g, float alpha_f, uint32_t *first_word, double *log_y,
-                    int *rejected) {
+                    int *rejected, double *cond) {
   double alpha = (double)alpha_f;
   double a = alpha < 1.0 ? alpha + 1.0 : alpha;
   double d = a - 1.0 / 3.0;
@@ -111,17 +111,23 @@ double or_get_gamma(or_batchrng *g, float alpha_f, uint32_t *first_word, double 
     if (or_log(u) < 0.5 * z * z + d * ((1.0 - v) + or_log(v))) {
       double y = d * v;
       double ly = log(y);
+      /* conditioning of d v in the Gaussian z (3 |c z| / t) and of the boost
+       * exponent L = ln(u_b)/alpha: a diagnostic for FP32 comparisons */
+      double kappa = 3.0 * fabs(c * z) / t;
       if (alpha < 1.0) {
         double ub = or_get_uniform_open(g);
         y = y * pow(ub, 1.0 / alpha);
         ly = ly + log(ub) / alpha;
+        kappa += fabs(log(ub) / alpha);
       }
       if (log_y) *log_y = ly;
+      if (cond) *cond = kappa;
       return y;
     }
   }
   if (rejected) *rejected = 1;
   if (log_y) *log_y = NAN;
+  if (cond) *cond = 0.0;
   return NAN;
 }
 
@@ -149,9 +155,9 @@ static void close_stream(or_batchrng *g, uint64_t *pos3) {
  * sets *word to the first raw word it consumed (0 if none), and counts
  * errors. */
 static double draw_tagged(or_batchrng *g, unsigned tag, float p0, float p1, uint32_t *word,
-                          int *n_domain, int *n_reject) {
+                          double *cond, int *n_domain, int *n_reject) {
   uint32_t w = 0;
-  double out = NAN;
+  double out = NAN, kappa = 0.0;
   switch (tag) {
   case 0: /* Uniform[a, b) = a + (b - a) U */
     if (finite_f(p0) && finite_f(p1) && p0 <= p1) {
@@ -174,7 +180,7 @@ static double draw_tagged(or_batchrng *g, unsigned tag, float p0, float p1, uint
   case 3: /* Gamma(alpha, 1) */
     if (finite_f(p0) && p0 > 0.0f) {
       int rej = 0;
-      out = or_get_gamma(g, p0, &w, NULL, &rej);
+      out = or_get_gamma(g, p0, &w, NULL, &rej, &kappa);
       if (rej) ++*n_reject;
     } else ++*n_domain;
     break;
@@ -189,12 +195,14 @@ static double draw_tagged(or_batchrng *g, unsigned tag, float p0, float p1, uint
     if (finite_f(p0) && finite_f(p1) && p0 > 0.0f && p1 > 0.0f) {
       double e = or_get_exponential(g, &w);
       out = (double)p1 * pow(e, 1.0 / (double)p0);
+      kappa = fabs(log(e) / (double)p0);
     } else ++*n_domain;
     break;
   default:
     ++*n_domain;
   }
   if (word) *word = w;
+  if (cond) *cond = kappa;
   return out;
 }
 
@@ -206,7 +214,7 @@ static int status_of(int n_domain, int n_reject) {
 
 int or_mixed_streams(uint64_t seed, uint32_t S, uint32_t s_begin, uint32_t s_end, uint64_t *pos,
                      uint64_t n, const uint8_t *tag, const float *p0, const float *p1,
-                     double *out, uint32_t *words, uint32_t buf_len) {
+                     double *out, uint32_t *words, double *cond, uint32_t buf_len) {
   int n_domain = 0, n_reject = 0;
   if (S == 0 || buf_len == 0) return OR_EINVAL;
   for (uint32_t s = s_begin; s < s_end && s < S; ++s) {
@@ -215,8 +223,10 @@ int or_mixed_streams(uint64_t seed, uint32_t S, uint32_t s_begin, uint32_t s_end
     open_stream(&g, seed, s, pos + 3 * (uint64_t)s, buf_len);
     for (uint64_t i = s; i < n; i += S) {
       uint32_t w;
-      out[i] = draw_tagged(&g, tag[i], p0[i], p1 ? p1[i] : 0.0f, &w, &n_domain, &n_reject);
+      double k;
+      out[i] = draw_tagged(&g, tag[i], p0[i], p1 ? p1[i] : 0.0f, &w, &k, &n_domain, &n_reject);
       if (words) words[i] = w;
+      if (cond) cond[i] = k;
     }
     close_stream(&g, pos + 3 * (uint64_t)s);
   }
@@ -224,13 +234,14 @@ int or_mixed_streams(uint64_t seed, uint32_t S, uint32_t s_begin, uint32_t s_end
 }
 
 int or_mixed(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const uint8_t *tag,
-             const float *p0, const float *p1, double *out, uint32_t *words, uint32_t buf_len) {
-  return or_mixed_streams(seed, S, 0, S, pos, n, tag, p0, p1, out, words, buf_len);
+             const float *p0, const float *p1, double *out, uint32_t *words, double *cond,
+             uint32_t buf_len) {
+  return or_mixed_streams(seed, S, 0, S, pos, n, tag, p0, p1, out, words, cond, buf_len);
 }
 
 /* single-distribution streams: the mixed stream with a constant tag */
 static int single(unsigned tagv, uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n,
-                  const float *p0, const float *p1, double *out, uint32_t *words,
+                  const float *p0, const float *p1, double *out, uint32_t *words, double *cond,
                   uint32_t buf_len) {
   int n_domain = 0, n_reject = 0;
   if (S == 0 || buf_len == 0) return OR_EINVAL;
@@ -239,8 +250,10 @@ static int single(unsigned tagv, uint64_t seed, uint32_t S, uint64_t *pos, uint6
     open_stream(&g, seed, s, pos + 3 * (uint64_t)s, buf_len);
     for (uint64_t i = s; i < n; i += S) {
       uint32_t w;
-      out[i] = draw_tagged(&g, tagv, p0[i], p1 ? p1[i] : 0.0f, &w, &n_domain, &n_reject);
+      double k;
+      out[i] = draw_tagged(&g, tagv, p0[i], p1 ? p1[i] : 0.0f, &w, &k, &n_domain, &n_reject);
       if (words) words[i] = w;
+      if (cond) cond[i] = k;
     }
     close_stream(&g, pos + 3 * (uint64_t)s);
   }
@@ -249,34 +262,34 @@ static int single(unsigned tagv, uint64_t seed, uint32_t S, uint64_t *pos, uint6
 
 int or_uniform(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *a,
                const float *b, double *out, uint32_t *words, uint32_t buf_len) {
-  return single(0, seed, S, pos, n, a, b, out, words, buf_len);
+  return single(0, seed, S, pos, n, a, b, out, words, NULL, buf_len);
 }
 int or_normal(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *mu,
               const float *sigma, double *out, uint32_t *words, uint32_t buf_len) {
-  return single(1, seed, S, pos, n, mu, sigma, out, words, buf_len);
+  return single(1, seed, S, pos, n, mu, sigma, out, words, NULL, buf_len);
 }
 int or_exponential(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *lambda,
                    double *out, uint32_t *words, uint32_t buf_len) {
-  return single(2, seed, S, pos, n, lambda, NULL, out, words, buf_len);
+  return single(2, seed, S, pos, n, lambda, NULL, out, words, NULL, buf_len);
 }
 int or_gamma(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *alpha,
-             double *out, uint32_t *words, uint32_t buf_len) {
-  return single(3, seed, S, pos, n, alpha, NULL, out, words, buf_len);
+             double *out, uint32_t *words, double *cond, uint32_t buf_len) {
+  return single(3, seed, S, pos, n, alpha, NULL, out, words, cond, buf_len);
 }
 int or_laplace(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *mu,
                const float *scale, double *out, uint32_t *words, uint32_t buf_len) {
-  return single(4, seed, S, pos, n, mu, scale, out, words, buf_len);
+  return single(4, seed, S, pos, n, mu, scale, out, words, NULL, buf_len);
 }
 int or_weibull(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *shape,
-               const float *scale, double *out, uint32_t *words, uint32_t buf_len) {
-  return single(5, seed, S, pos, n, shape, scale, out, words, buf_len);
+               const float *scale, double *out, uint32_t *words, double *cond, uint32_t buf_len) {
+  return single(5, seed, S, pos, n, shape, scale, out, words, cond, buf_len);
 }
 
 /* Dirichlet (Sec. 1 footnote): y_k ~ Gamma(alpha_k, 1), x_k = y_k / sum y.
  * The normalisation is taken on log y_k (x_k = exp(l_k - M) / sum exp(l_j - M),
  * M = max l), the same quotient without underflow of tiny y_k. */
 void or_dirichlet_row(or_batchrng *comp, uint32_t K, const float *alpha, double *out,
-                      double *scratch_l, int *n_domain, int *n_reject) {
+                      double *scratch_l, double *cond, int *n_domain, int *n_reject) {
   for (uint32_t k = 0; k < K; ++k) {
     if (!(finite_f(alpha[k]) && alpha[k] > 0.0f)) {
       ++*n_domain;
@@ -285,7 +298,8 @@ void or_dirichlet_row(or_batchrng *comp, uint32_t K, const float *alpha, double 
     }
   }
   int rej = 0;
-  for (uint32_t k = 0; k < K; ++k) or_get_gamma(&comp[k], alpha[k], NULL, &scratch_l[k], &rej);
+  for (uint32_t k = 0; k < K; ++k)
+    or_get_gamma(&comp[k], alpha[k], NULL, &scratch_l[k], &rej, cond ? &cond[k] : NULL);
   if (rej) {
     ++*n_reject;
     for (uint32_t j = 0; j < K; ++j) out[j] = NAN;
@@ -299,7 +313,7 @@ void or_dirichlet_row(or_batchrng *comp, uint32_t K, const float *alpha, double 
 }
 
 int or_dirichlet(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n_rows, uint32_t K,
-                 const float *alpha, double *out, uint32_t buf_len) {
+                 const float *alpha, double *out, double *logs, double *cond, uint32_t buf_len) {
   if (S == 0 || K == 0 || S % K != 0 || buf_len == 0) return OR_EINVAL;
   uint32_t R = S / K;
   int n_domain = 0, n_reject = 0;
@@ -308,8 +322,13 @@ int or_dirichlet(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n_rows, uint
   for (uint32_t r = 0; r < R && (uint64_t)r < n_rows; ++r) {
     for (uint32_t k = 0; k < K; ++k)
       open_stream(&comp[k], seed, r * K + k, pos + 3 * ((uint64_t)r * K + k), buf_len);
-    for (uint64_t i = r; i < n_rows; i += R)
-      or_dirichlet_row(comp, K, alpha + i * K, out + i * K, l, &n_domain, &n_reject);
+    for (uint64_t i = r; i < n_rows; i += R) {
+      for (uint32_t k = 0; k < K; ++k) l[k] = NAN;
+      or_dirichlet_row(comp, K, alpha + i * K, out + i * K, l, cond ? cond + i * K : NULL,
+                       &n_domain, &n_reject);
+      if (logs)
+        for (uint32_t k = 0; k < K; ++k) logs[i * K + k] = l[k];
+    }
     for (uint32_t k = 0; k < K; ++k) close_stream(&comp[k], pos + 3 * ((uint64_t)r * K + k));
   }
   free(comp);

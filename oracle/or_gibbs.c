@@ -77,7 +77,7 @@ int or_gibbs_normal_gamma(uint64_t seed, uint64_t chain_offset, uint32_t n_chain
       double dm = xb - mu;
       double SS = S + n * dm * dm;
       int rej = 0;
-      double G = or_get_gamma(&g, shape, NULL, NULL, &rej);
+      double G = or_get_gamma(&g, shape, NULL, NULL, &rej, NULL);
       n_reject += rej;
       tau = G / (b0 + 0.5 * SS);
       double P = prec0 + n * tau;
@@ -100,8 +100,8 @@ int or_gibbs_normal_gamma(uint64_t seed, uint64_t chain_offset, uint32_t n_chain
 }
 
 int or_gibbs_lda(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K,
-                 uint32_t n_sweeps, const float *alpha, double *theta, uint64_t *pos,
-                 double *mom, uint32_t buf_len) {
+                 uint32_t n_sweeps, const float *alpha, double *theta, double *logs,
+                 double *cond, uint64_t *pos, double *mom, uint32_t buf_len) {
   if (buf_len == 0 || K == 0 || (doc_offset + n_docs) * (uint64_t)K > 0x100000000ull)
     return OR_EINVAL;
   int n_domain = 0, n_reject = 0;
@@ -117,10 +117,14 @@ int or_gibbs_lda(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K
     const float *a = alpha + (uint64_t)d * K;
     double *th = theta + (uint64_t)d * K;
     double *m = mom + (uint64_t)d * K;
+    for (uint32_t k = 0; k < K; ++k) l[k] = NAN;
     for (uint32_t it = 0; it < n_sweeps; ++it) {
-      or_dirichlet_row(comp, K, a, th, l, &n_domain, &n_reject);
+      or_dirichlet_row(comp, K, a, th, l, cond ? cond + (uint64_t)d * K : NULL, &n_domain,
+                       &n_reject);
       for (uint32_t k = 0; k < K; ++k) m[k] += th[k];
     }
+    if (logs)
+      for (uint32_t k = 0; k < K; ++k) logs[(uint64_t)d * K + k] = l[k];
     for (uint32_t k = 0; k < K; ++k) {
       uint64_t idx = (uint64_t)d * K + k;
       uint64_t end[OR_NDOM];
@@ -143,6 +147,7 @@ typedef struct {
   uint32_t n, K, sweeps, buf_len;
   const float *prior, *nobs, *xbar, *sc, *alpha;
   double *a, *b; /* model outputs */
+  double *logs, *cond;
   uint64_t *pos;
   int status;
   /* mixed stream */
@@ -165,12 +170,12 @@ static void *or_run(void *arg) {
                                       j->xbar, j->sc, j->a, j->pos, j->b, j->buf_len);
     break;
   case 2:
-    j->status = or_gibbs_lda(j->seed, j->offset, j->n, j->K, j->sweeps, j->alpha, j->a, j->pos,
-                             j->b, j->buf_len);
+    j->status = or_gibbs_lda(j->seed, j->offset, j->n, j->K, j->sweeps, j->alpha, j->a,
+                             j->logs, j->cond, j->pos, j->b, j->buf_len);
     break;
   default:
     j->status = or_mixed_streams(j->seed, j->S, j->s0, j->s1, j->pos, j->n_draws, j->tag, j->p0,
-                                 j->p1, j->a, j->words, j->buf_len);
+                                 j->p1, j->a, j->words, j->cond, j->buf_len);
   }
   return NULL;
 }
@@ -231,8 +236,8 @@ int or_gibbs_normal_gamma_mt(uint64_t seed, uint64_t chain_offset, uint32_t n_ch
 }
 
 int or_gibbs_lda_mt(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K,
-                    uint32_t n_sweeps, const float *alpha, double *theta, uint64_t *pos,
-                    double *mom, uint32_t buf_len, int nthreads) {
+                    uint32_t n_sweeps, const float *alpha, double *theta, double *logs,
+                    double *cond, uint64_t *pos, double *mom, uint32_t buf_len, int nthreads) {
   if (nthreads < 1) nthreads = 1;
   or_job *jobs = (or_job *)calloc(nthreads, sizeof(or_job));
   for (int t = 0; t < nthreads; ++t) {
@@ -241,7 +246,8 @@ int or_gibbs_lda_mt(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_
     uint64_t o = (uint64_t)b * K;
     jobs[t] = (or_job){.model = 2, .seed = seed, .offset = doc_offset + b, .n = e - b, .K = K,
                        .sweeps = n_sweeps, .buf_len = buf_len, .alpha = alpha + o,
-                       .a = theta + o, .b = mom + o, .pos = pos + 2 * o};
+                       .a = theta + o, .b = mom + o, .pos = pos + 2 * o,
+                       .logs = logs ? logs + o : NULL, .cond = cond ? cond + o : NULL};
   }
   int st = or_spawn(jobs, nthreads);
   free(jobs);
@@ -249,7 +255,7 @@ int or_gibbs_lda_mt(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_
 }
 
 int or_mixed_mt(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const uint8_t *tag,
-                const float *p0, const float *p1, double *out, uint32_t *words,
+                const float *p0, const float *p1, double *out, uint32_t *words, double *cond,
                 uint32_t buf_len, int nthreads) {
   if (nthreads < 1) nthreads = 1;
   or_job *jobs = (or_job *)calloc(nthreads, sizeof(or_job));
@@ -258,7 +264,7 @@ int or_mixed_mt(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const uint
     range_of(S, nthreads, t, &b, &e);
     jobs[t] = (or_job){.model = 3, .seed = seed, .S = S, .s0 = b, .s1 = e, .n_draws = n,
                        .tag = tag, .p0 = p0, .p1 = p1, .a = out, .words = words, .pos = pos,
-                       .buf_len = buf_len};
+                       .buf_len = buf_len, .cond = cond};
   }
   int st = or_spawn(jobs, nthreads);
   free(jobs);

@@ -34,8 +34,8 @@ double or_get_gaussian(or_batchrng *g, uint32_t *word);
 double or_get_exponential(or_batchrng *g, uint32_t *word);
 double or_get_u64(or_batchrng *g);
 double or_get_gamma(or_batchrng *g, float alpha, uint32_t *first_word, double *log_y,
-                    int *rejected);
+                    int *rejected, double *cond);
 void or_dirichlet_row(or_batchrng *comp, uint32_t K, const float *alpha, double *out,
-                      double *scratch_l, int *n_domain, int *n_reject);
+                      double *l, double *cond, int *n_domain, int *n_reject);
 
 #endif

@@ -73,24 +73,27 @@ int or_normal(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float 
               const float *sigma, double *out, uint32_t *words, uint32_t buf_len);
 int or_exponential(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *lambda,
                    double *out, uint32_t *words, uint32_t buf_len);
+/* cond (nullable): per draw 3|c z|/t of the accepted attempt plus |ln(u_b)/alpha|
+ * when boosted -- the relative conditioning of the result, for FP32 checks */
 int or_gamma(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *alpha,
-             double *out, uint32_t *words, uint32_t buf_len);
+             double *out, uint32_t *words, double *cond, uint32_t buf_len);
 int or_laplace(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *mu,
                const float *scale, double *out, uint32_t *words, uint32_t buf_len);
 int or_weibull(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *shape,
-               const float *scale, double *out, uint32_t *words, uint32_t buf_len);
+               const float *scale, double *out, uint32_t *words, double *cond, uint32_t buf_len);
 /* rows of K components; S % K == 0; component k of row i draws from stream
- * (i mod (S/K))*K + k */
+ * (i mod (S/K))*K + k; logs (nullable) gets each component's log-Gamma */
 int or_dirichlet(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n_rows, uint32_t K,
-                 const float *alpha, double *out, uint32_t buf_len);
+                 const float *alpha, double *out, double *logs, double *cond, uint32_t buf_len);
 /* tag 0 U(p0,p1), 1 N(p0,p1), 2 Exp(rate p0), 3 Gamma(p0), 4 Laplace(p0,p1),
  * 5 Weibull(shape p0, scale p1) */
 int or_mixed(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const uint8_t *tag,
-             const float *p0, const float *p1, double *out, uint32_t *words, uint32_t buf_len);
+             const float *p0, const float *p1, double *out, uint32_t *words, double *cond,
+             uint32_t buf_len);
 /* the same, for the streams in [s_begin, s_end) only (sampled parity) */
 int or_mixed_streams(uint64_t seed, uint32_t S, uint32_t s_begin, uint32_t s_end, uint64_t *pos,
                      uint64_t n, const uint8_t *tag, const float *p0, const float *p1,
-                     double *out, uint32_t *words, uint32_t buf_len);
+                     double *out, uint32_t *words, double *cond, uint32_t buf_len);
 
 /* ---- Gibbs models (Markov-dependent consumers) ------------------------ */
 /* Eq. 1 / Fig. 1: xy[2c] = x, xy[2c+1] = y; pos[c] = next U64 element;
@@ -107,10 +110,11 @@ int or_gibbs_normal_gamma(uint64_t seed, uint64_t chain_offset, uint32_t n_chain
                           double *mom, uint32_t buf_len);
 /* LDA-style document-topic draws theta_d ~ Dir(alpha_d) every sweep; component
  * (d, k) is stream (doc_offset + d)*K + k; pos[2(dK+k)] = N, [..+1] = U;
- * theta = last draw; mom[dK+k] += theta_dk per sweep. */
+ * theta = last draw, logs (nullable) = its log-Gammas; mom[dK+k] += theta_dk
+ * per sweep. */
 int or_gibbs_lda(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K,
-                 uint32_t n_sweeps, const float *alpha, double *theta, uint64_t *pos,
-                 double *mom, uint32_t buf_len);
+                 uint32_t n_sweeps, const float *alpha, double *theta, double *logs,
+                 double *cond, uint64_t *pos, double *mom, uint32_t buf_len);
 
 /* the same on `nthreads` host threads over contiguous chain ranges */
 int or_gibbs_triangle_mt(uint64_t seed, uint64_t chain_offset, uint32_t n_chains,
@@ -121,10 +125,10 @@ int or_gibbs_normal_gamma_mt(uint64_t seed, uint64_t chain_offset, uint32_t n_ch
                              const float *xbar, const float *sc, double *state, uint64_t *pos,
                              double *mom, uint32_t buf_len, int nthreads);
 int or_gibbs_lda_mt(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K,
-                    uint32_t n_sweeps, const float *alpha, double *theta, uint64_t *pos,
-                    double *mom, uint32_t buf_len, int nthreads);
+                    uint32_t n_sweeps, const float *alpha, double *theta, double *logs,
+                    double *cond, uint64_t *pos, double *mom, uint32_t buf_len, int nthreads);
 int or_mixed_mt(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const uint8_t *tag,
-                const float *p0, const float *p1, double *out, uint32_t *words,
+                const float *p0, const float *p1, double *out, uint32_t *words, double *cond,
                 uint32_t buf_len, int nthreads);
 
 /* Marsaglia-Tsang acceptance test of one attempt, exactly as the Gamma

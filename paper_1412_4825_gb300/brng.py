@@ -1,0 +1,335 @@
+"""ctypes binding of libbrng.so (include/brng.h), argument marshalling only.
+
+Every ``brng_*`` function here has the name and argument order of the C
+call; device arrays are torch CUDA tensors (their ``data_ptr()`` is passed),
+``stream`` is a ``torch.cuda.Stream`` or None (the current torch stream).
+Every step of the computation runs in the library's CUDA kernels; there is no
+CPU fallback: importing this module fails loudly if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbrng.so")
+
+BRNG_OK, BRNG_EINVAL, BRNG_ENOMEM, BRNG_ECUDA, BRNG_EDOMAIN, BRNG_EREJECT, BRNG_ETIMEOUT, \
+    BRNG_EAGAIN, BRNG_ENOTFOUND = range(9)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EDOMAIN", "EREJECT", "ETIMEOUT", "EAGAIN",
+                "ENOTFOUND"]
+DOMAIN_U, DOMAIN_N, DOMAIN_E, DOMAIN_DATA, DOMAIN_U64 = 0, 1, 2, 3, 4
+TAG_UNIFORM, TAG_NORMAL, TAG_EXPONENTIAL, TAG_GAMMA, TAG_LAPLACE, TAG_WEIBULL = range(6)
+MODEL_TRIANGLE, MODEL_NORMAL_GAMMA, MODEL_LDA = 0, 1, 2
+
+
+class BrngError(RuntimeError):
+    def __init__(self, call, code):
+        super().__init__("%s failed: %s (%d)" % (call, STATUS_NAMES[code] if 0 <= code < 9 else "?", code))
+        self.code = code
+
+
+class brng_tuning_t(C.Structure):
+    _fields_ = [("buf_len", C.c_uint32), ("warps_per_block", C.c_uint32),
+                ("lanes_per_chain", C.c_uint32), ("lookahead", C.c_uint32)]
+
+
+class brng_counters_t(C.Structure):
+    _fields_ = [("n_domain", C.c_uint64), ("n_reject", C.c_uint64), ("n_recheck", C.c_uint64),
+                ("n_flip", C.c_uint64), ("max_flip_ratio", C.c_float), ("pad", C.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+
+
+class brng_normal_gamma_params_t(C.Structure):
+    _fields_ = [("a0", C.c_float), ("b0", C.c_float), ("mu0", C.c_float), ("prec0", C.c_float),
+                ("nobs", C.c_void_p), ("xbar", C.c_void_p), ("sc", C.c_void_p)]
+
+
+class brng_lda_params_t(C.Structure):
+    _fields_ = [("K", C.c_uint32), ("alpha", C.c_void_p)]
+
+
+class brng_lda_state_t(C.Structure):
+    _fields_ = [("theta", C.c_void_p), ("pos", C.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libbrng.so not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    vp, u32, u64, sz, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_size_t, C.c_int
+    sig = {
+        "brng_create": ([u64, u32, u32, C.POINTER(vp)], i32),
+        "brng_destroy": ([vp], i32),
+        "brng_set_tuning": ([vp, C.POINTER(brng_tuning_t)], i32),
+        "brng_get_tuning": ([vp, C.POINTER(brng_tuning_t)], i32),
+        "brng_n_streams": ([vp], u32),
+        "brng_seed": ([vp], u64),
+        "brng_get_positions": ([vp, vp], i32),
+        "brng_set_positions": ([vp, vp], i32),
+        "brng_read_counters": ([vp, vp, C.POINTER(brng_counters_t), i32], i32),
+        "brng_philox_words": ([vp, u32, u32, u64, sz, vp, vp], i32),
+        "brng_fp64_eval": ([u32, sz, vp, vp, vp], i32),
+        "brng_philox_peak": ([u64, u32, u32, vp, vp], i32),
+        "brng_uniform": ([vp, sz, vp, vp, vp, vp, vp], i32),
+        "brng_normal": ([vp, sz, vp, vp, vp, vp, vp], i32),
+        "brng_exponential": ([vp, sz, vp, vp, vp, vp], i32),
+        "brng_gamma": ([vp, sz, vp, vp, vp, vp], i32),
+        "brng_laplace": ([vp, sz, vp, vp, vp, vp, vp], i32),
+        "brng_weibull": ([vp, sz, vp, vp, vp, vp, vp], i32),
+        "brng_mixed": ([vp, sz, vp, vp, vp, vp, vp, vp], i32),
+        "brng_dirichlet": ([vp, sz, u32, vp, vp, vp], i32),
+        "brng_gibbs_run": ([vp, i32, u64, u32, u32, vp, vp, vp, vp], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
+lib = _load()
+
+
+# ---- marshalling helpers ----------------------------------------------------
+
+def _ptr(t, dtype=None, name="array"):
+    """Device pointer of a contiguous torch CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    import torch
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(call, code, ok=(BRNG_OK,)):
+    if code not in ok:
+        raise BrngError(call, code)
+    return code
+
+
+def _f32():
+    import torch
+    return torch.float32
+
+
+# ---- the C calls, same names --------------------------------------------------
+
+def brng_create(seed, n_streams, buf_len=0):
+    h = C.c_void_p()
+    _check("brng_create", lib.brng_create(int(seed) & (2**64 - 1), int(n_streams), int(buf_len), C.byref(h)))
+    return h
+
+
+def brng_destroy(h):
+    return _check("brng_destroy", lib.brng_destroy(h))
+
+
+def brng_set_tuning(h, buf_len=0, warps_per_block=0, lanes_per_chain=0, lookahead=0):
+    t = brng_tuning_t(buf_len, warps_per_block, lanes_per_chain, lookahead)
+    return _check("brng_set_tuning", lib.brng_set_tuning(h, C.byref(t)))
+
+
+def brng_get_tuning(h):
+    t = brng_tuning_t()
+    _check("brng_get_tuning", lib.brng_get_tuning(h, C.byref(t)))
+    return {f: getattr(t, f) for f, _ in t._fields_}
+
+
+def brng_get_positions(h):
+    out = np.zeros(3 * lib.brng_n_streams(h), dtype=np.uint64)
+    _check("brng_get_positions", lib.brng_get_positions(h, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def brng_set_positions(h, pos):
+    pos = np.ascontiguousarray(pos, dtype=np.uint64)
+    return _check("brng_set_positions", lib.brng_set_positions(h, pos.ctypes.data_as(C.c_void_p)))
+
+
+def brng_read_counters(h, stream=None, reset=False):
+    c = brng_counters_t()
+    code = lib.brng_read_counters(h, _stream(stream), C.byref(c), int(bool(reset)))
+    _check("brng_read_counters", code, ok=(BRNG_OK, BRNG_EDOMAIN, BRNG_EREJECT))
+    return code, c.as_dict()
+
+
+def brng_philox_words(h, domain, stream_id, first_block, n_blocks, out, stream=None):
+    import torch
+    return _check("brng_philox_words", lib.brng_philox_words(
+        h, domain, stream_id, first_block, n_blocks, _ptr(out, torch.int32, "out"), _stream(stream)))
+
+
+def brng_philox_peak(iters, blocks, threads, sink, stream=None):
+    import torch
+    return _check("brng_philox_peak", lib.brng_philox_peak(
+        int(iters), int(blocks), int(threads), _ptr(sink, torch.int32, "sink"), _stream(stream)))
+
+
+def brng_fp64_eval(fn, x, out, stream=None):
+    import torch
+    return _check("brng_fp64_eval", lib.brng_fp64_eval(
+        int(fn), x.numel(), _ptr(x, torch.float64, "in"), _ptr(out, torch.float64, "out"), _stream(stream)))
+
+
+def brng_uniform(h, a, b, out, words=None, stream=None):
+    import torch
+    return _check("brng_uniform", lib.brng_uniform(
+        h, out.numel(), _ptr(a, _f32(), "a"), _ptr(b, _f32(), "b"), _ptr(out, _f32(), "out"),
+        _ptr(words, torch.int32, "words"), _stream(stream)))
+
+
+def brng_normal(h, mu, sigma, out, words=None, stream=None):
+    import torch
+    return _check("brng_normal", lib.brng_normal(
+        h, out.numel(), _ptr(mu, _f32(), "mu"), _ptr(sigma, _f32(), "sigma"), _ptr(out, _f32(), "out"),
+        _ptr(words, torch.int32, "words"), _stream(stream)))
+
+
+def brng_exponential(h, lam, out, words=None, stream=None):
+    import torch
+    return _check("brng_exponential", lib.brng_exponential(
+        h, out.numel(), _ptr(lam, _f32(), "lambda"), _ptr(out, _f32(), "out"),
+        _ptr(words, torch.int32, "words"), _stream(stream)))
+
+
+def brng_gamma(h, alpha, out, words=None, stream=None):
+    import torch
+    return _check("brng_gamma", lib.brng_gamma(
+        h, out.numel(), _ptr(alpha, _f32(), "alpha"), _ptr(out, _f32(), "out"),
+        _ptr(words, torch.int32, "words"), _stream(stream)))
+
+
+def brng_laplace(h, mu, b, out, words=None, stream=None):
+    import torch
+    return _check("brng_laplace", lib.brng_laplace(
+        h, out.numel(), _ptr(mu, _f32(), "mu"), _ptr(b, _f32(), "b"), _ptr(out, _f32(), "out"),
+        _ptr(words, torch.int32, "words"), _stream(stream)))
+
+
+def brng_weibull(h, k, lam, out, words=None, stream=None):
+    import torch
+    return _check("brng_weibull", lib.brng_weibull(
+        h, out.numel(), _ptr(k, _f32(), "k"), _ptr(lam, _f32(), "lambda"), _ptr(out, _f32(), "out"),
+        _ptr(words, torch.int32, "words"), _stream(stream)))
+
+
+def brng_mixed(h, tag, p0, p1, out, words=None, stream=None):
+    import torch
+    return _check("brng_mixed", lib.brng_mixed(
+        h, out.numel(), _ptr(tag, torch.uint8, "tag"), _ptr(p0, _f32(), "p0"), _ptr(p1, _f32(), "p1"),
+        _ptr(out, _f32(), "out"), _ptr(words, torch.int32, "words"), _stream(stream)))
+
+
+def brng_dirichlet(h, alpha, out, stream=None):
+    n_rows, K = alpha.shape
+    return _check("brng_dirichlet", lib.brng_dirichlet(
+        h, n_rows, K, _ptr(alpha, _f32(), "alpha"), _ptr(out, _f32(), "out"), _stream(stream)))
+
+
+def brng_gibbs_run(h, model, chain_offset, n_chains, n_sweeps, params, state, moments, stream=None):
+    """`params` / `state`: ctypes structures (passed by reference) or device
+    tensors, as include/brng.h specifies per model."""
+    import torch
+
+    def ref(x):
+        if x is None:
+            return None
+        if isinstance(x, C.Structure):
+            return C.cast(C.byref(x), C.c_void_p)
+        return _ptr(x, None, "state")
+
+    return _check("brng_gibbs_run", lib.brng_gibbs_run(
+        h, int(model), int(chain_offset), int(n_chains), int(n_sweeps), ref(params), ref(state),
+        _ptr(moments, torch.float64, "moments"), _stream(stream)))
+
+
+# ---- state layouts (marshalling of the C structs held in device tensors) ------
+
+def triangle_state(n, x0=0.5, y0=0.5, device="cuda"):
+    """brng_triangle_state_t[n] as a float64 tensor [n, 4]: x, y, pos bits, pad."""
+    import torch
+    s = torch.zeros((n, 4), dtype=torch.float64, device=device)
+    s[:, 0] = x0
+    s[:, 1] = y0
+    return s
+
+
+def triangle_unpack(s):
+    a = s.detach().cpu()
+    return a[:, 0].numpy(), a[:, 1].numpy(), a[:, 2].view(__import__("torch").int64).numpy().view(np.uint64)
+
+
+def normal_gamma_state(n, mu0=0.0, device="cuda"):
+    """brng_normal_gamma_state_t[n] (24 bytes: mu, tau as float32; pos_n, pos_u
+    as uint64) as an int64 tensor [n, 3]."""
+    import torch
+    s = torch.zeros((n, 3), dtype=torch.int64, device=device)
+    f = s.view(torch.float32).view(n, 6)
+    f[:, 0] = mu0
+    return s
+
+
+def normal_gamma_unpack(s):
+    import torch
+    a = s.detach().cpu()
+    f = a.view(torch.float32).view(-1, 6)
+    return (f[:, 0].numpy().copy(), f[:, 1].numpy().copy(),
+            a[:, 1].numpy().view(np.uint64).copy(), a[:, 2].numpy().view(np.uint64).copy())
+
+
+class Handle:
+    """Owns a brng_t*; a convenience wrapper over the brng_* calls."""
+
+    def __init__(self, seed, n_streams, buf_len=0):
+        self.h = brng_create(seed, n_streams, buf_len)
+        self.n_streams = n_streams
+        self.seed = seed
+
+    def close(self):
+        if self.h:
+            brng_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tune(self, **kw):
+        brng_set_tuning(self.h, **kw)
+        return self
+
+    @property
+    def tuning(self):
+        return brng_get_tuning(self.h)
+
+    def positions(self):
+        return brng_get_positions(self.h)
+
+    def set_positions(self, pos):
+        brng_set_positions(self.h, pos)
+
+    def counters(self, stream=None, reset=False):
+        return brng_read_counters(self.h, stream, reset)

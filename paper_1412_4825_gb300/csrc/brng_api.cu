@@ -1,0 +1,331 @@
+// brng_api.cu -- the C ABI (include/brng.h): handle, argument checks,
+// dispatch to the kernels.  Plain pointers and sizes only; all compute runs in
+// the kernels of brng_bulk.cu, brng_dirichlet.cu and brng_gibbs.cu.
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "brng.h"
+#include "brng_gamma.cuh"
+#include "brng_internal.h"
+
+struct brng_handle {
+  uint64_t seed;
+  uint32_t S;
+  brng_tuning_t tune;
+  brng::RoundKeys rk;
+  uint64_t* d_pos;            // SoA [3][S]: U, N, E positions of every stream
+  brng::DevCounters* d_cnt;   // device counters
+  int device;
+};
+
+namespace {
+
+bool pow2_in(uint32_t v, uint32_t lo, uint32_t hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return BRNG_OK;
+  if (e == cudaErrorMemoryAllocation) return BRNG_ENOMEM;
+  if (e == cudaErrorInvalidValue) return BRNG_EINVAL;
+  return BRNG_ECUDA;
+}
+
+brng::Geometry geometry(const brng_t* h) {
+  return brng::Geometry{h->tune.warps_per_block, h->tune.buf_len};
+}
+
+// Shared memory cap check for a per-warp footprint.
+bool smem_fits(size_t per_warp, uint32_t warps) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return per_warp * warps <= static_cast<size_t>(optin);
+}
+
+int bulk(brng_t* h, int tag, size_t n, const uint8_t* tagv, const float* p0, const float* p1,
+         float* out, uint32_t* words, cudaStream_t st) {
+  if (!h) return BRNG_EINVAL;
+  if (n == 0) return BRNG_OK;
+  if (!p0 || !out || (tag == brng::kTagMixed && !tagv)) return BRNG_EINVAL;
+  const bool two = tag == brng::kTagMixed || tag == BRNG_TAG_UNIFORM || tag == BRNG_TAG_NORMAL ||
+                   tag == BRNG_TAG_LAPLACE || tag == BRNG_TAG_WEIBULL;
+  if (two && tag != brng::kTagMixed && !p1) return BRNG_EINVAL;
+  const int ndom = (tag == brng::kTagMixed) ? 3 : (tag == BRNG_TAG_GAMMA || tag == BRNG_TAG_LAPLACE) ? 2 : 1;
+  const size_t per_warp = 128u + static_cast<size_t>(ndom) * h->tune.buf_len * 128u * (words ? 2 : 1);
+  if (!smem_fits(per_warp, h->tune.warps_per_block)) return BRNG_EINVAL;
+  brng::BulkArgs a;
+  a.rk = h->rk;
+  a.n = n;
+  a.S = h->S;
+  a.B = h->tune.buf_len;
+  a.tag = tagv;
+  a.p0 = p0;
+  a.p1 = p1;
+  a.out = out;
+  a.words = words;
+  a.pos = h->d_pos;
+  a.cnt = h->d_cnt;
+  return cuda_status(brng::launch_bulk(tag, a, geometry(h), st));
+}
+
+}  // namespace
+
+extern "C" {
+
+int brng_create(uint64_t seed, uint32_t n_streams, uint32_t buf_len, brng_t** out) {
+  if (!out || n_streams == 0) return BRNG_EINVAL;
+  if (buf_len == 0) buf_len = brng::kDefaultBufLen;
+  if (!pow2_in(buf_len, 4, brng::kMaxBufLen)) return BRNG_EINVAL;
+  brng_t* h = new (std::nothrow) brng_t();
+  if (!h) return BRNG_ENOMEM;
+  h->seed = seed;
+  h->S = n_streams;
+  h->tune.buf_len = buf_len;
+  h->tune.warps_per_block = brng::kDefaultWarpsPerBlock;
+  h->tune.lanes_per_chain = 1;
+  h->tune.lookahead = brng::kDefaultLookahead;
+  h->rk = brng::make_round_keys(seed);
+  cudaGetDevice(&h->device);
+  const size_t pos_bytes = sizeof(uint64_t) * 3ull * n_streams;
+  cudaError_t e = cudaMalloc(&h->d_pos, pos_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_cnt, sizeof(brng::DevCounters));
+  if (e == cudaSuccess) e = cudaMemset(h->d_pos, 0, pos_bytes);
+  if (e == cudaSuccess) e = cudaMemset(h->d_cnt, 0, sizeof(brng::DevCounters));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(h->d_pos);
+    cudaFree(h->d_cnt);
+    delete h;
+    return cuda_status(e);
+  }
+  *out = h;
+  return BRNG_OK;
+}
+
+int brng_destroy(brng_t* h) {
+  if (!h) return BRNG_OK;
+  cudaError_t e1 = cudaFree(h->d_pos);
+  cudaError_t e2 = cudaFree(h->d_cnt);
+  delete h;
+  return e1 != cudaSuccess ? cuda_status(e1) : cuda_status(e2);
+}
+
+int brng_set_tuning(brng_t* h, const brng_tuning_t* t) {
+  if (!h || !t) return BRNG_EINVAL;
+  brng_tuning_t n = h->tune;
+  if (t->buf_len) n.buf_len = t->buf_len;
+  if (t->warps_per_block) n.warps_per_block = t->warps_per_block;
+  if (t->lanes_per_chain) n.lanes_per_chain = t->lanes_per_chain;
+  if (t->lookahead) n.lookahead = t->lookahead;
+  if (!pow2_in(n.buf_len, 4, brng::kMaxBufLen)) return BRNG_EINVAL;
+  if (n.warps_per_block < 1 || n.warps_per_block > 16) return BRNG_EINVAL;
+  if (!pow2_in(n.lanes_per_chain, 1, 32)) return BRNG_EINVAL;
+  if (n.lookahead < 1 || n.lookahead > 16) return BRNG_EINVAL;
+  h->tune = n;
+  return BRNG_OK;
+}
+
+int brng_get_tuning(const brng_t* h, brng_tuning_t* t) {
+  if (!h || !t) return BRNG_EINVAL;
+  *t = h->tune;
+  return BRNG_OK;
+}
+
+uint32_t brng_n_streams(const brng_t* h) { return h ? h->S : 0; }
+uint64_t brng_seed(const brng_t* h) { return h ? h->seed : 0; }
+
+int brng_get_positions(brng_t* h, uint64_t* host_pos) {
+  if (!h || !host_pos) return BRNG_EINVAL;
+  std::vector<uint64_t> soa(3ull * h->S);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(soa.data(), h->d_pos, sizeof(uint64_t) * soa.size(), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  for (uint64_t s = 0; s < h->S; ++s)
+    for (int d = 0; d < 3; ++d) host_pos[3 * s + d] = soa[d * static_cast<uint64_t>(h->S) + s];
+  return BRNG_OK;
+}
+
+int brng_set_positions(brng_t* h, const uint64_t* host_pos) {
+  if (!h || !host_pos) return BRNG_EINVAL;
+  std::vector<uint64_t> soa(3ull * h->S);
+  for (uint64_t s = 0; s < h->S; ++s)
+    for (int d = 0; d < 3; ++d) soa[d * static_cast<uint64_t>(h->S) + s] = host_pos[3 * s + d];
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->d_pos, soa.data(), sizeof(uint64_t) * soa.size(), cudaMemcpyHostToDevice);
+  return cuda_status(e);
+}
+
+int brng_read_counters(brng_t* h, brng_stream_t stream, brng_counters_t* out, int reset) {
+  if (!h) return BRNG_EINVAL;
+  static_assert(sizeof(brng_counters_t) == sizeof(brng::DevCounters), "counter layout");
+  brng_counters_t c;
+  cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaMemcpy(&c, h->d_cnt, sizeof c, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && reset) e = cudaMemset(h->d_cnt, 0, sizeof(brng::DevCounters));
+  if (e == cudaSuccess && reset) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e);
+  if (out) *out = c;
+  if (c.n_domain) return BRNG_EDOMAIN;
+  if (c.n_reject) return BRNG_EREJECT;
+  return BRNG_OK;
+}
+
+int brng_philox_words(brng_t* h, uint32_t domain, uint32_t stream_id, uint64_t first_block,
+                      size_t n_blocks, uint32_t* out, brng_stream_t stream) {
+  if (!h) return BRNG_EINVAL;
+  if (n_blocks == 0) return BRNG_OK;
+  if (!out || (reinterpret_cast<uintptr_t>(out) & 15u)) return BRNG_EINVAL;
+  return cuda_status(brng::launch_philox_words(h->rk, domain, stream_id, first_block, n_blocks, out,
+                                               reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int brng_philox_peak(uint64_t iters, uint32_t blocks, uint32_t threads, uint32_t* sink,
+                     brng_stream_t stream) {
+  if (!sink || blocks == 0 || threads == 0 || threads > 256 || iters == 0) return BRNG_EINVAL;
+  return cuda_status(brng::launch_philox_peak(brng::make_round_keys(0x243F6A8885A308D3ull), iters,
+                                              blocks, threads, sink, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int brng_fp64_eval(uint32_t fn, size_t n, const double* in, double* out, brng_stream_t stream) {
+  if (fn > 2) return BRNG_EINVAL;
+  if (n == 0) return BRNG_OK;
+  if (!in || !out) return BRNG_EINVAL;
+  return cuda_status(brng::launch_fp64_eval(fn, n, in, out, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int brng_uniform(brng_t* h, size_t n, const float* a, const float* b, float* out, uint32_t* words,
+                 brng_stream_t stream) {
+  return bulk(h, BRNG_TAG_UNIFORM, n, nullptr, a, b, out, words, reinterpret_cast<cudaStream_t>(stream));
+}
+int brng_normal(brng_t* h, size_t n, const float* mu, const float* sigma, float* out,
+                uint32_t* words, brng_stream_t stream) {
+  return bulk(h, BRNG_TAG_NORMAL, n, nullptr, mu, sigma, out, words, reinterpret_cast<cudaStream_t>(stream));
+}
+int brng_exponential(brng_t* h, size_t n, const float* lambda, float* out, uint32_t* words,
+                     brng_stream_t stream) {
+  return bulk(h, BRNG_TAG_EXPONENTIAL, n, nullptr, lambda, nullptr, out, words,
+              reinterpret_cast<cudaStream_t>(stream));
+}
+int brng_gamma(brng_t* h, size_t n, const float* alpha, float* out, uint32_t* words,
+               brng_stream_t stream) {
+  return bulk(h, BRNG_TAG_GAMMA, n, nullptr, alpha, nullptr, out, words, reinterpret_cast<cudaStream_t>(stream));
+}
+int brng_laplace(brng_t* h, size_t n, const float* mu, const float* b, float* out, uint32_t* words,
+                 brng_stream_t stream) {
+  return bulk(h, BRNG_TAG_LAPLACE, n, nullptr, mu, b, out, words, reinterpret_cast<cudaStream_t>(stream));
+}
+int brng_weibull(brng_t* h, size_t n, const float* k, const float* lambda, float* out,
+                 uint32_t* words, brng_stream_t stream) {
+  return bulk(h, BRNG_TAG_WEIBULL, n, nullptr, k, lambda, out, words, reinterpret_cast<cudaStream_t>(stream));
+}
+int brng_mixed(brng_t* h, size_t n, const uint8_t* tag, const float* p0, const float* p1,
+               float* out, uint32_t* words, brng_stream_t stream) {
+  if (n && !p1) return BRNG_EINVAL;
+  return bulk(h, brng::kTagMixed, n, tag, p0, p1, out, words, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int brng_dirichlet(brng_t* h, size_t n_rows, uint32_t K, const float* alpha, float* out,
+                   brng_stream_t stream) {
+  if (!h || K == 0 || K > 128 || h->S % K != 0) return BRNG_EINVAL;
+  if (n_rows == 0) return BRNG_OK;
+  if (!alpha || !out) return BRNG_EINVAL;
+  const uint32_t P = K <= 32 ? 1 : K <= 64 ? 2 : 4;
+  const size_t per_warp = 128u + h->tune.lookahead * 32u * P * 4u + 2u * P * h->tune.buf_len * 128u;
+  if (!smem_fits(per_warp, h->tune.warps_per_block)) return BRNG_EINVAL;
+  brng::DirichletArgs a{};
+  a.rk = h->rk;
+  a.K = K;
+  a.B = h->tune.buf_len;
+  a.lookahead = h->tune.lookahead;
+  a.n_rows = n_rows;
+  a.R = h->S / K;
+  a.alpha = alpha;
+  a.out = out;
+  a.pos = h->d_pos;
+  a.S = h->S;
+  a.cnt = h->d_cnt;
+  return cuda_status(brng::launch_dirichlet(a, geometry(h), false, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_t n_chains,
+                   uint32_t n_sweeps, const void* params, void* state, double* moments,
+                   brng_stream_t stream) {
+  if (!h) return BRNG_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n_chains == 0) return BRNG_OK;
+  if (!state || !moments) return BRNG_EINVAL;
+  brng::Geometry g = geometry(h);
+  switch (model) {
+    case BRNG_MODEL_TRIANGLE: {
+      if (chain_offset + n_chains > 0x100000000ull) return BRNG_EINVAL;
+      const uint32_t nc = 32 / h->tune.lanes_per_chain;
+      if (!smem_fits(128u + static_cast<size_t>(h->tune.buf_len) * nc * 8u, g.warps_per_block))
+        return BRNG_EINVAL;
+      brng::TriangleArgs a;
+      a.rk = h->rk;
+      a.chain_offset = chain_offset;
+      a.n_chains = n_chains;
+      a.n_sweeps = n_sweeps;
+      a.B = h->tune.buf_len;
+      a.state = static_cast<brng_triangle_state_t*>(state);
+      a.moments = moments;
+      return cuda_status(brng::launch_triangle(a, g, h->tune.lanes_per_chain, st));
+    }
+    case BRNG_MODEL_NORMAL_GAMMA: {
+      const brng_normal_gamma_params_t* p = static_cast<const brng_normal_gamma_params_t*>(params);
+      if (!p || !p->nobs || !p->xbar || !p->sc) return BRNG_EINVAL;
+      if (chain_offset + n_chains > 0x100000000ull) return BRNG_EINVAL;
+      if (!smem_fits(128u + 2u * static_cast<size_t>(h->tune.buf_len) * 128u, g.warps_per_block))
+        return BRNG_EINVAL;
+      brng::NormalGammaArgs a;
+      a.rk = h->rk;
+      a.chain_offset = chain_offset;
+      a.n_chains = n_chains;
+      a.n_sweeps = n_sweeps;
+      a.B = h->tune.buf_len;
+      a.a0 = p->a0;
+      a.b0 = p->b0;
+      a.mu0 = p->mu0;
+      a.prec0 = p->prec0;
+      a.nobs = p->nobs;
+      a.xbar = p->xbar;
+      a.sc = p->sc;
+      a.state = static_cast<brng_normal_gamma_state_t*>(state);
+      a.moments = moments;
+      a.cnt = h->d_cnt;
+      return cuda_status(brng::launch_normal_gamma(a, g, st));
+    }
+    case BRNG_MODEL_LDA: {
+      const brng_lda_params_t* p = static_cast<const brng_lda_params_t*>(params);
+      const brng_lda_state_t* s = static_cast<const brng_lda_state_t*>(state);
+      if (!p || !p->alpha || p->K == 0 || p->K > 128 || !s->theta || !s->pos) return BRNG_EINVAL;
+      if ((chain_offset + n_chains) * static_cast<uint64_t>(p->K) > 0x100000000ull) return BRNG_EINVAL;
+      const uint32_t P = p->K <= 32 ? 1 : p->K <= 64 ? 2 : 4;
+      const size_t per_warp = 128u + h->tune.lookahead * 32u * P * 4u + 2u * P * h->tune.buf_len * 128u;
+      if (!smem_fits(per_warp, g.warps_per_block)) return BRNG_EINVAL;
+      brng::DirichletArgs a{};
+      a.rk = h->rk;
+      a.K = p->K;
+      a.B = h->tune.buf_len;
+      a.lookahead = h->tune.lookahead;
+      a.alpha = p->alpha;
+      a.out = s->theta;
+      a.pos = s->pos;
+      a.stream_base = chain_offset;
+      a.n_docs = n_chains;
+      a.n_sweeps = n_sweeps;
+      a.moments = moments;
+      a.cnt = h->d_cnt;
+      return cuda_status(brng::launch_dirichlet(a, g, true, st));
+    }
+    default:
+      return BRNG_EINVAL;
+  }
+}
+
+}  // extern "C"

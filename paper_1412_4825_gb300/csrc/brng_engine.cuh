@@ -1,0 +1,89 @@
+// brng_engine.cuh -- core engine and base conversions on the device.
+//
+// Core engine: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random
+// Numbers: As Easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64-bit
+// multiplies by the published multipliers, XOR of the high halves into the
+// other counter words and the round key, key bumped by the published Weyl
+// increments.  It plays the part of the paper's vectorised core engine
+// (Sec. 2.2); being counter-based, element j of any stream is computable
+// directly, so buffers are pure caches of a fixed sequence.
+//
+// The round keys are computed once per launch on the host and passed in the
+// kernel parameter block, so every XOR with a key reads the constant bank.
+#pragma once
+
+#include <cstdint>
+
+namespace brng {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+constexpr uint32_t kDomU = 0, kDomN = 1, kDomE = 2, kDomData = 3, kDomU64 = 4;
+
+// Round keys (k0 + r W0, k1 + r W1), r = 0..9.
+struct RoundKeys {
+  uint32_t k[10][2];
+};
+
+inline RoundKeys make_round_keys(uint64_t seed) {
+  RoundKeys rk;
+  uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k[r][0] = k0;
+    rk.k[r][1] = k1;
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return rk;
+}
+
+__device__ __forceinline__ uint4 philox(uint4 c, const RoundKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+    const uint32_t lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+    const uint32_t lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ rk.k[r][0], lo1, hi0 ^ c.w ^ rk.k[r][1], lo0);
+  }
+  return c;
+}
+
+// counter of block `blk` of (domain, stream)
+__device__ __forceinline__ uint4 philox_ctr(uint64_t blk, uint32_t dom, uint32_t stream) {
+  return make_uint4(static_cast<uint32_t>(blk), dom, stream, static_cast<uint32_t>(blk >> 32));
+}
+
+__device__ __forceinline__ uint4 philox_block(uint64_t blk, uint32_t dom, uint32_t stream,
+                                              const RoundKeys& rk) {
+  return philox(philox_ctr(blk, dom, stream), rk);
+}
+
+// ---- FP32 base conversions (exact where the definition is exact) ----------
+// U = (w >> 8) 2^-24 in [0,1);  U' = U + 2^-24 in (0,1]  (both exact in FP32)
+__device__ __forceinline__ float u01(uint32_t w) { return __uint2float_rn(w >> 8) * 0x1p-24f; }
+__device__ __forceinline__ float u01_open(uint32_t w) {
+  return __uint2float_rn((w >> 8) + 1u) * 0x1p-24f;
+}
+
+// Box-Muller pair from (w0, w1): radius from U'(w0), angle 2 pi U(w1)
+__device__ __forceinline__ float2 box_muller(uint32_t w0, uint32_t w1) {
+  const float r = sqrtf(-2.0f * logf(u01_open(w0)));
+  float s, c;
+  sincospif(2.0f * u01(w1), &s, &c);
+  return make_float2(r * c, r * s);
+}
+
+__device__ __forceinline__ float exp1(uint32_t w) { return -logf(u01_open(w)); }
+
+// 53-bit uniform from two words: ((w0>>5) 2^26 + (w1>>6)) 2^-53, exact
+__device__ __forceinline__ double u53(uint32_t w0, uint32_t w1) {
+  const unsigned long long m =
+      (static_cast<unsigned long long>(w0 >> 5) << 26) | static_cast<unsigned long long>(w1 >> 6);
+  return __dmul_rn(__ull2double_rn(m), 0x1p-53);
+}
+
+}  // namespace brng

@@ -1,0 +1,133 @@
+// brng_fp64.cuh -- FP64 natural log and sin/cos(pi a) for the Gamma accept
+// recheck, written so that each is a fixed sequence of IEEE double
+// operations (explicit __d*_rn intrinsics: never contracted into FMA).
+//
+// Why: a Gamma attempt's accept/reject decision is a comparison of two
+// logarithmic expressions.  The FP32 fast path takes it when its margin is
+// clearly away from zero; otherwise the decision is recomputed in FP64 from
+// the same Philox bits.  For that decision to be the one a reference FP64
+// computation takes, both must evaluate the same expression with the same
+// elementary functions, so these functions are defined by their method, not
+// by a math library:
+//
+//  log(x):  x = m 2^e, m in [sqrt(1/2), sqrt(2)); s = (m - 1)/(m + 1);
+//           ln m = 2 atanh s = 2s + 2s s^2 (1/3 + s^2/5 + ... + s^22/25)
+//           (Horner from the s^22/25 term); ln x = e ln2_hi + (e ln2_lo + ln m)
+//           with ln2_hi holding 32 significant bits of ln 2.
+//  sincospi(a): n = floor(2a + 1/2), r = a - n/2 (exact for dyadic a),
+//           y = pi r, Taylor series of sin y to y^23 and cos y to y^22 by
+//           Horner in y^2, then the quadrant n mod 4 swaps/negates.
+#pragma once
+
+namespace brng {
+
+__device__ __forceinline__ double dlog(double x) {
+  if (!(x > 0.0)) return x == 0.0 ? -__longlong_as_double(0x7ff0000000000000ll)
+                                  : __longlong_as_double(0x7ff8000000000000ll);
+  long long bits = __double_as_longlong(x);
+  if ((bits >> 52) >= 0x7ff) return x;  // +inf
+  int e = 0;
+  if ((bits >> 52) == 0) {  // subnormal: scale by 2^54
+    x = __dmul_rn(x, 0x1p54);
+    bits = __double_as_longlong(x);
+    e = -54;
+  }
+  e += static_cast<int>((bits >> 52) & 0x7ff) - 1022;
+  double m = __longlong_as_double((bits & 0x000fffffffffffffll) | 0x3fe0000000000000ll);
+  if (m < 0x1.6a09e667f3bcdp-1) {
+    m = __dmul_rn(m, 2.0);
+    e -= 1;
+  }
+  const double s = __ddiv_rn(__dadd_rn(m, -1.0), __dadd_rn(m, 1.0));
+  const double s2 = __dmul_rn(s, s);
+  double p = 1.0 / 25.0;
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 23.0);
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 21.0);
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 19.0);
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 17.0);
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 15.0);
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 13.0);
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 11.0);
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 9.0);
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 7.0);
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 5.0);
+  p = __dadd_rn(__dmul_rn(p, s2), 1.0 / 3.0);
+  const double two_s = __dmul_rn(2.0, s);
+  const double lnm = __dadd_rn(two_s, __dmul_rn(two_s, __dmul_rn(s2, p)));
+  const double fe = static_cast<double>(e);
+  return __dadd_rn(__dmul_rn(fe, 0x1.62e42fee00000p-1),
+                   __dadd_rn(__dmul_rn(fe, 0x1.a39ef35793c76p-33), lnm));
+}
+
+__device__ __forceinline__ void dsincospi(double a, double* s_out, double* c_out) {
+  const double n = floor(__dadd_rn(__dmul_rn(2.0, a), 0.5));
+  const double r = __dadd_rn(a, -__dmul_rn(0.5, n));
+  const double y = __dmul_rn(0x1.921fb54442d18p+1, r);
+  const double y2 = __dmul_rn(y, y);
+  double ps = -0x1.761b41316381ap-75;
+  ps = __dadd_rn(__dmul_rn(ps, y2), 0x1.71b8ef6dcf572p-66);
+  ps = __dadd_rn(__dmul_rn(ps, y2), -0x1.2f49b46814157p-57);
+  ps = __dadd_rn(__dmul_rn(ps, y2), 0x1.952c77030ad4ap-49);
+  ps = __dadd_rn(__dmul_rn(ps, y2), -0x1.ae7f3e733b81fp-41);
+  ps = __dadd_rn(__dmul_rn(ps, y2), 0x1.6124613a86d09p-33);
+  ps = __dadd_rn(__dmul_rn(ps, y2), -0x1.ae64567f544e4p-26);
+  ps = __dadd_rn(__dmul_rn(ps, y2), 0x1.71de3a556c734p-19);
+  ps = __dadd_rn(__dmul_rn(ps, y2), -0x1.a01a01a01a01ap-13);
+  ps = __dadd_rn(__dmul_rn(ps, y2), 0x1.1111111111111p-7);
+  ps = __dadd_rn(__dmul_rn(ps, y2), -0x1.5555555555555p-3);
+  const double sn = __dadd_rn(y, __dmul_rn(__dmul_rn(y, y2), ps));
+  double pc = -0x1.0ce396db7f853p-70;
+  pc = __dadd_rn(__dmul_rn(pc, y2), 0x1.e542ba4020225p-62);
+  pc = __dadd_rn(__dmul_rn(pc, y2), -0x1.6827863b97d97p-53);
+  pc = __dadd_rn(__dmul_rn(pc, y2), 0x1.ae7f3e733b81fp-45);
+  pc = __dadd_rn(__dmul_rn(pc, y2), -0x1.93974a8c07c9dp-37);
+  pc = __dadd_rn(__dmul_rn(pc, y2), 0x1.1eed8eff8d898p-29);
+  pc = __dadd_rn(__dmul_rn(pc, y2), -0x1.27e4fb7789f5cp-22);
+  pc = __dadd_rn(__dmul_rn(pc, y2), 0x1.a01a01a01a01ap-16);
+  pc = __dadd_rn(__dmul_rn(pc, y2), -0x1.6c16c16c16c17p-10);
+  pc = __dadd_rn(__dmul_rn(pc, y2), 0x1.5555555555555p-5);
+  pc = __dadd_rn(__dmul_rn(pc, y2), -0.5);
+  const double cs = __dadd_rn(1.0, __dmul_rn(y2, pc));
+  const int q = static_cast<int>(n) & 3;
+  switch (q) {
+    case 0: *s_out = sn; *c_out = cs; break;
+    case 1: *s_out = cs; *c_out = -sn; break;
+    case 2: *s_out = -sn; *c_out = -cs; break;
+    default: *s_out = -cs; *c_out = sn; break;
+  }
+}
+
+// FP64 Gaussian element of a Box-Muller pair (w0, w1); `odd` picks the sin half
+__device__ __forceinline__ double dgauss(uint32_t w0, uint32_t w1, bool odd) {
+  const double u_open = __dmul_rn(static_cast<double>((w0 >> 8) + 1u), 0x1p-24);
+  const double r = __dsqrt_rn(__dmul_rn(-2.0, dlog(u_open)));
+  double s, c;
+  dsincospi(__dmul_rn(static_cast<double>(w1 >> 8), 0x1p-23), &s, &c);
+  return __dmul_rn(r, odd ? s : c);
+}
+
+// FP64 Marsaglia-Tsang decision for shape alpha (FP32 input), Gaussian z and
+// open uniform u: 1 accept, 0 reject, -1 if t <= 0.  Same operations, same
+// order as the reference definition: a = alpha (+1 if alpha < 1),
+// d = a - 1/3, c = 1/sqrt(9d), t = 1 + c z, v = (t t) t,
+// accept iff log(u) < (0.5 z) z + d ((1 - v) + log(v)).
+__device__ __forceinline__ double mt_d64(float alpha_f) {
+  const double alpha = static_cast<double>(alpha_f);
+  const double a = alpha < 1.0 ? __dadd_rn(alpha, 1.0) : alpha;
+  return __dadd_rn(a, -0x1.5555555555555p-2);
+}
+
+__device__ __forceinline__ double mt_t64(double d, double z) {
+  const double c = __ddiv_rn(1.0, __dsqrt_rn(__dmul_rn(9.0, d)));
+  return __dadd_rn(1.0, __dmul_rn(c, z));
+}
+
+__device__ __forceinline__ bool mt_accept64(double d, double z, double t, double u_open) {
+  const double v = __dmul_rn(__dmul_rn(t, t), t);
+  const double lhs = dlog(u_open);
+  const double rhs = __dadd_rn(__dmul_rn(__dmul_rn(0.5, z), z),
+                               __dmul_rn(d, __dadd_rn(__dadd_rn(1.0, -v), dlog(v))));
+  return lhs < rhs;
+}
+
+}  // namespace brng

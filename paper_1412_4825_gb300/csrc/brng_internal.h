@@ -1,0 +1,96 @@
+// brng_internal.h -- declarations shared by the library's translation units
+// (host launchers of the kernels and the handle layout).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "brng.h"
+#include "brng_engine.cuh"
+
+namespace brng {
+
+struct DevCounters;
+
+constexpr uint32_t kDefaultBufLen = 32;
+constexpr uint32_t kMaxBufLen = 512;
+constexpr uint32_t kDefaultWarpsPerBlock = 4;
+constexpr uint32_t kDefaultLookahead = 8;
+constexpr int kTagMixed = -1;
+
+// Launch geometry shared by all kernels: warps per block and ring length.
+struct Geometry {
+  uint32_t warps_per_block;
+  uint32_t buf_len;
+};
+
+// ---- bulk varying-parameter streams (brng_bulk.cu) ----
+struct BulkArgs {
+  RoundKeys rk;
+  uint64_t n;
+  uint32_t S;
+  uint32_t B;
+  const uint8_t* tag;
+  const float* p0;
+  const float* p1;
+  float* out;
+  uint32_t* words;
+  uint64_t* pos;  // SoA: pos[d * S + s], d = U, N, E
+  DevCounters* cnt;
+};
+cudaError_t launch_bulk(int tag, const BulkArgs& a, const Geometry& g, cudaStream_t st);
+cudaError_t launch_philox_words(const RoundKeys& rk, uint32_t dom, uint32_t stream,
+                                uint64_t first_block, size_t n_blocks, uint32_t* out,
+                                cudaStream_t st);
+
+cudaError_t launch_philox_peak(const RoundKeys& rk, uint64_t iters, uint32_t blocks, uint32_t threads,
+                               uint32_t* sink, cudaStream_t st);
+cudaError_t launch_fp64_eval(uint32_t fn, size_t n, const double* in, double* out, cudaStream_t st);
+
+// ---- Dirichlet rows and LDA sweeps (brng_dirichlet.cu) ----
+struct DirichletArgs {
+  RoundKeys rk;
+  uint32_t K;
+  uint32_t B;
+  uint32_t lookahead;
+  // bulk rows: rows i = r + m R of row-stream r, component streams r K + k
+  uint64_t n_rows;
+  uint32_t R;
+  const float* alpha;  // [rows][K]
+  float* out;          // [rows][K] (bulk) or last theta (LDA)
+  uint64_t* pos;       // bulk: SoA [3][S]; LDA: [docs][K][2] (N, U)
+  uint32_t S;          // bulk: stream count
+  // LDA
+  uint64_t stream_base;  // LDA: (chain_offset) -> component stream (base + d) K + k
+  uint32_t n_docs;
+  uint32_t n_sweeps;
+  double* moments;  // LDA: [docs][K]
+  DevCounters* cnt;
+};
+cudaError_t launch_dirichlet(const DirichletArgs& a, const Geometry& g, bool lda, cudaStream_t st);
+
+// ---- Gibbs models (brng_gibbs.cu) ----
+struct TriangleArgs {
+  RoundKeys rk;
+  uint64_t chain_offset;
+  uint32_t n_chains, n_sweeps, B;
+  brng_triangle_state_t* state;
+  double* moments;
+};
+cudaError_t launch_triangle(const TriangleArgs& a, const Geometry& g, uint32_t lanes_per_chain,
+                            cudaStream_t st);
+
+struct NormalGammaArgs {
+  RoundKeys rk;
+  uint64_t chain_offset;
+  uint32_t n_chains, n_sweeps, B;
+  float a0, b0, mu0, prec0;
+  const float *nobs, *xbar, *sc;
+  brng_normal_gamma_state_t* state;
+  double* moments;
+  DevCounters* cnt;
+};
+cudaError_t launch_normal_gamma(const NormalGammaArgs& a, const Geometry& g, cudaStream_t st);
+
+}  // namespace brng

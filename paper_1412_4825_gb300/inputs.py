@@ -75,6 +75,33 @@ def shape_params(n: int, seed: int = 42, lo: float = 0.05, hi: float = 50.0):
     return log_uniform(np.random.default_rng(seed), lo, hi, n)
 
 
+def mixed_stream_torch(n: int, seed: int = 42, n_tags: int = 4, device="cuda"):
+    """The mixed stream's inputs drawn on the device with a seeded torch
+    generator (same distributions as mixed_stream; different draws), for
+    sizes where host generation and transfer would dominate (2^28 draws)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+
+    def logu(lo, hi):
+        u = torch.rand(n, generator=g, device=device, dtype=torch.float32)
+        return torch.exp(np.log(lo) + (np.log(hi) - np.log(lo)) * u)
+
+    tag = torch.randint(0, n_tags, (n,), generator=g, device=device, dtype=torch.uint8)
+    a, b = logu(1e-3, 1e3), logu(1e-3, 1e3)
+    sign = torch.where(torch.rand(n, generator=g, device=device) < 0.5, -1.0, 1.0)
+    p0 = torch.where(tag == TAG_UNIFORM, torch.minimum(a, b), a * sign)
+    p1 = torch.where(tag == TAG_UNIFORM, torch.maximum(a, b), logu(1e-2, 1e2))
+    del a, b, sign
+    p0 = torch.where(tag == TAG_EXPONENTIAL, logu(1e-2, 1e2), p0)
+    p0 = torch.where(tag == TAG_GAMMA, logu(0.05, 50.0), p0)
+    p1 = torch.where((tag == TAG_EXPONENTIAL) | (tag == TAG_GAMMA), torch.zeros_like(p1), p1)
+    if n_tags > TAG_WEIBULL:
+        p0 = torch.where(tag == TAG_WEIBULL, logu(0.5, 5.0), p0)
+    return tag, p0.contiguous(), p1.contiguous()
+
+
 def mixed_stream(n: int, seed: int = 42, n_tags: int = 4):
     """Tag per draw (uniform over the first n_tags distributions) and its
     parameters (p0, p1): U(a,b) a,b log-U[1e-3,1e3] sorted; N(mu, sigma)

@@ -1,0 +1,517 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars:
+  * integer work -- Philox words, first-consumed words, stream positions
+    (hence every Gamma accept decision and attempt count) -- bit-exact;
+  * FP64 paths -- the triangle Gibbs sampler of Eq. 1 and the FP64
+    elementary functions of the Gamma recheck -- bit-exact;
+  * FP32 transforms within 2e-6 relative error of the FP64 oracle fed the same
+    Philox bits.  "Relative" is to the magnitude the FP32 arithmetic works
+    at: |a|+|b| for a+(b-a)U, |mu|+|sigma z| for mu+sigma z, and the result
+    times its conditioning for results built through a power or a
+    logarithm (the oracle reports the Gamma's 3|cz|/t and boost exponent
+    |ln(u_b)/alpha|, the Weibull exponent |ln(E)/k|, the Dirichlet log-Gammas);
+    results below FLT_MIN compare absolutely (2 FLT_MIN).
+Sizes span several warps and a ragged tail; the BASELINE-size workloads are
+checked on sampled streams/chains the oracle recomputes one by one.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1412_4825_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # collected on a CPU host only with -m gpu
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1412_4825_gb300 import brng as B  # noqa: E402
+
+DEV = torch.device("cuda:0")
+FLT_MIN = float(np.finfo(np.float32).tiny)
+RTOL = 2e-6
+NT = os.cpu_count() or 1
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def H(t):
+    return t.detach().cpu().numpy()
+
+
+def words_np(t):
+    return H(t).view(np.uint32)
+
+
+def assert_close(got, want, scale, rtol=RTOL, what=""):
+    got = np.asarray(got, np.float64).ravel()
+    want = np.asarray(want, np.float64).ravel()
+    scale = np.broadcast_to(np.asarray(scale, np.float64), want.shape).ravel()
+    nan_ok = np.isnan(got) & np.isnan(want)
+    err = np.abs(got - want)
+    bound = rtol * scale + 2 * FLT_MIN
+    bad = ~nan_ok & ~(err <= bound)
+    norm = np.where(nan_ok, 0.0, err / np.maximum(bound, 1e-300))
+    print("%s: max err/bound = %.3g over %d values" % (what, np.nanmax(norm) if norm.size else 0, got.size))
+    assert not bad.any(), "%s: %d mismatches, idx %s got %s want %s scale %s" % (
+        what, bad.sum(), np.nonzero(bad)[0][:4], got[bad][:4], want[bad][:4], scale[bad][:4])
+
+
+def handle(seed, S, buf_len=0, **tune):
+    h = B.Handle(seed, S, buf_len)
+    if tune:
+        h.tune(**tune)
+    return h
+
+
+# ---- core engine and FP64 recheck functions ---------------------------------
+
+@pytest.mark.parametrize("domain", [0, 1, 2, 3, 4])
+def test_philox_words_bit_exact(domain):
+    h = handle(0xDEADBEEF12345678, 1)
+    for stream_id, first in [(0, 0), (7, 12345), (2**32 - 1, 2**32 - 3)]:
+        n = 1001
+        out = torch.empty(4 * n, dtype=torch.int32, device=DEV)
+        B.brng_philox_words(h.h, domain, stream_id, first, n, out)
+        ref = O.philox_words(0xDEADBEEF12345678, domain, stream_id, first, n)
+        assert np.array_equal(words_np(out), ref)
+
+
+def test_fp64_log_bit_exact_exhaustive():
+    k = np.arange(1 << 24, dtype=np.float64)
+    rng = np.random.default_rng(1)
+    t = rng.uniform(0.05, 2.5, 1 << 20)
+    x = np.concatenate([(k + 1) * 2.0**-24, t * t * t, np.exp(rng.uniform(-700, 700, 1 << 16)),
+                        [5e-324, 1e-310, 2.2250738585072014e-308, 1.0, 2.0, 0.5]])
+    out = torch.empty(x.size, dtype=torch.float64, device=DEV)
+    B.brng_fp64_eval(0, T(x), out)
+    assert np.array_equal(H(out).view(np.int64), O.log(x).view(np.int64))
+
+
+def test_fp64_sincospi_bit_exact_exhaustive():
+    a = np.arange(1 << 24, dtype=np.float64) * 2.0**-23
+    s_ref, c_ref = O.sincospi(a)
+    out = torch.empty(a.size, dtype=torch.float64, device=DEV)
+    B.brng_fp64_eval(1, T(a), out)
+    assert np.array_equal(H(out).view(np.int64), s_ref.view(np.int64))
+    B.brng_fp64_eval(2, T(a), out)
+    assert np.array_equal(H(out).view(np.int64), c_ref.view(np.int64))
+
+
+# ---- varying-parameter streams ----------------------------------------------
+
+def _params(fn, n, seed):
+    if fn == "uniform":
+        return list(inputs.uniform_params(n, seed))
+    if fn in ("normal", "laplace"):
+        return list(inputs.normal_params(n, seed))
+    if fn == "exponential":
+        return [inputs.rate_params(n, seed)]
+    if fn == "gamma":
+        return [inputs.shape_params(n, seed)]
+    if fn == "weibull":
+        return [inputs.log_uniform(np.random.default_rng(seed), 0.5, 5.0, n), inputs.rate_params(n, seed + 1)]
+    raise ValueError(fn)
+
+
+def _scale(fn, out, params, cond=None):
+    """Magnitude the FP32 arithmetic of `fn` works at (see the module doc)."""
+    out = np.abs(out)
+    if fn == "uniform":
+        return np.maximum(np.abs(params[0]), np.abs(params[1])).astype(np.float64)
+    if fn in ("normal", "laplace"):
+        mu = np.abs(params[0].astype(np.float64))
+        return mu + np.abs(out - mu)
+    if fn == "exponential":
+        return out
+    return out * np.maximum(1.0, cond)
+
+
+def _run_bulk(fn, h, params, n, words=True):
+    out = torch.empty(n, dtype=torch.float32, device=DEV)
+    w = torch.empty(n, dtype=torch.int32, device=DEV) if words else None
+    getattr(B, "brng_" + fn)(h.h, *[T(p) for p in params], out, w)
+    return out, w
+
+
+BULK = ["uniform", "normal", "exponential", "gamma", "laplace", "weibull"]
+
+
+@pytest.mark.parametrize("fn", BULK)
+def test_bulk_parity(fn):
+    seed, S, n = 42, 1000, 20011  # 31.25 warps of streams; 20 or 21 draws each
+    params = _params(fn, n, 7)
+    h = handle(seed, S)
+    out, w = _run_bulk(fn, h, params, n)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    res = getattr(O, fn)(seed, S, *params, **({"with_cond": True} if fn in ("gamma", "weibull") else {}))
+    ro, rw, rpos = res[0], res[1], res[2]
+    cond = res[4] if fn in ("gamma", "weibull") else None
+    assert np.array_equal(words_np(w), rw)
+    assert np.array_equal(h.positions(), rpos)
+    g = H(out).astype(np.float64)
+    if fn in ("normal", "laplace"):
+        mu = params[0].astype(np.float64)
+        scale = np.abs(mu) + np.abs(ro - mu)
+    else:
+        scale = _scale(fn, ro, params, cond)
+    assert_close(g, ro, scale, what=fn)
+
+
+def test_gamma_decisions_many():
+    """4M Gamma draws over alpha in [0.05, 500] and near 1: every attempt
+    count (hence every accept decision) equals the oracle's."""
+    seed, S, n = 9, 1 << 14, 1 << 22
+    rng = np.random.default_rng(3)
+    alpha = np.exp(rng.uniform(np.log(0.05), np.log(500.0), n)).astype(np.float32)
+    alpha[::7] = np.float32(1.0)
+    alpha[1::7] = np.nextafter(np.float32(1.0), np.float32(0.0))
+    h = handle(seed, S)
+    out, w = _run_bulk("gamma", h, [alpha], n)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK
+    ro, rw, rpos, _, cond = O.gamma(seed, S, alpha, with_cond=True)
+    assert np.array_equal(h.positions(), rpos)
+    assert np.array_equal(words_np(w), rw)
+    assert_close(H(out), ro, np.abs(ro) * np.maximum(1.0, cond), what="gamma 4M")
+    print("rechecks", cnt)
+    # FP32 decisions overturned in FP64 lie deep inside the tolerance band
+    assert cnt["n_flip"] == 0 or cnt["max_flip_ratio"] < 0.25
+
+
+@pytest.mark.parametrize("buf_len,wpb", [(4, 1), (16, 16), (128, 2), (256, 1)])
+def test_bulk_tuning_invariance(buf_len, wpb):
+    seed, S, n = 5, 333, 10000
+    tag, p0, p1 = inputs.mixed_stream(n, seed=5, n_tags=6)
+    outs = []
+    for tune in [dict(), dict(buf_len=buf_len, warps_per_block=wpb)]:
+        h = handle(seed, S, **tune)
+        out = torch.empty(n, dtype=torch.float32, device=DEV)
+        w = torch.empty(n, dtype=torch.int32, device=DEV)
+        B.brng_mixed(h.h, T(tag), T(p0), T(p1), out, w)
+        outs.append((H(out), words_np(w), h.positions()))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a.view(np.uint32) if a.dtype == np.float32 else a,
+                              b.view(np.uint32) if b.dtype == np.float32 else b)
+
+
+def test_call_splitting():
+    seed, S = 11, 64
+    n1, n2 = 64 * 7 + 5, 64 * 9 + 33
+    alpha = inputs.shape_params(n1 + n2, seed=2)
+    h = handle(seed, S)
+    o1, w1 = _run_bulk("gamma", h, [alpha[:n1]], n1)
+    o2, w2 = _run_bulk("gamma", h, [alpha[n1:]], n2)
+    pos1 = O.new_positions(S)
+    r1 = O.gamma(seed, S, alpha[:n1])
+    r2 = O.gamma(seed, S, alpha[n1:], pos=r1[2])
+    assert np.array_equal(words_np(w1), r1[1]) and np.array_equal(words_np(w2), r2[1])
+    assert np.array_equal(h.positions(), r2[2])
+    # checkpoint / resume of positions
+    h2 = handle(seed, S)
+    h2.set_positions(r1[2])
+    o2b, w2b = _run_bulk("gamma", h2, [alpha[n1:]], n2)
+    assert np.array_equal(words_np(w2b), r2[1])
+    assert np.array_equal(H(o2b).view(np.uint32), H(o2).view(np.uint32))
+    del pos1
+
+
+def _mixed_scale(tag, p0, p1, ro, cond):
+    p0 = p0.astype(np.float64)
+    p1 = p1.astype(np.float64)
+    sc = np.abs(ro) * np.maximum(1.0, cond)
+    sc = np.where(tag == 0, np.maximum(np.abs(p0), np.abs(p1)), sc)
+    sc = np.where((tag == 1) | (tag == 4), np.abs(p0) + np.abs(ro - p0), sc)
+    sc = np.where(tag == 2, np.abs(ro), sc)
+    return sc
+
+
+def test_mixed_parity():
+    seed, S, n = 42, 2048, 200003
+    tag, p0, p1 = inputs.mixed_stream(n, seed=seed, n_tags=6)
+    h = handle(seed, S)
+    out = torch.empty(n, dtype=torch.float32, device=DEV)
+    w = torch.empty(n, dtype=torch.int32, device=DEV)
+    B.brng_mixed(h.h, T(tag), T(p0), T(p1), out, w)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    ro, rw, rpos, _, cond = O.mixed(seed, S, tag, p0, p1, nthreads=NT, with_cond=True)
+    assert np.array_equal(words_np(w), rw)
+    assert np.array_equal(h.positions(), rpos)
+    assert_close(H(out), ro, _mixed_scale(tag, p0, p1, ro, cond), what="mixed")
+
+
+def test_mixed_full_size_sampled():
+    """2^28 draws over 2^20 streams (the mixed-stream workload); 128 whole
+    streams recomputed by the oracle."""
+    seed, S, n = 42, 1 << 20, 1 << 28
+    tag, p0, p1 = inputs.mixed_stream_torch(n, seed=seed, device=DEV)
+    h = handle(seed, S)
+    out = torch.empty(n, dtype=torch.float32, device=DEV)
+    w = torch.empty(n, dtype=torch.int32, device=DEV)
+    B.brng_mixed(h.h, tag, p0, p1, out, w)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    tag_h, p0_h, p1_h = H(tag), H(p0), H(p1)
+    out_h, w_h = H(out), words_np(w)
+    pos_gpu = h.positions().reshape(S, 3)
+    for s0, s1 in [(0, 64), (S - 64, S)]:
+        ro, rw, rpos, _, cond = O.mixed(seed, S, tag_h, p0_h, p1_h, streams=(s0, s1), with_cond=True)
+        idx = np.concatenate([np.arange(s, n, S) for s in range(s0, s1)])
+        assert np.array_equal(w_h[idx], rw[idx])
+        assert np.array_equal(pos_gpu[s0:s1], rpos.reshape(S, 3)[s0:s1])
+        assert_close(out_h[idx], ro[idx], _mixed_scale(tag_h[idx], p0_h[idx], p1_h[idx], ro[idx], cond[idx]),
+                     what="mixed 2^28 streams %d..%d" % (s0, s1))
+
+
+# ---- Dirichlet --------------------------------------------------------------
+
+def _dir_scale(th, logs, cond):
+    mag = np.abs(logs) + np.nanmax(np.abs(logs), axis=1, keepdims=True)
+    kap = cond + np.nanmax(cond, axis=1, keepdims=True)
+    return np.abs(th) * (1.0 + mag + kap)
+
+
+@pytest.mark.parametrize("K,rows,R", [(1, 100, 100), (5, 333, 333), (64, 500, 100), (100, 40, 7),
+                                      (128, 64, 64), (64, 2000, 2000)])
+def test_dirichlet_parity(K, rows, R):
+    seed = 13
+    rng = np.random.default_rng(K)
+    alpha = np.exp(rng.uniform(np.log(0.05), np.log(20.0), (rows, K))).astype(np.float32)
+    h = handle(seed, R * K)
+    out = torch.empty((rows, K), dtype=torch.float32, device=DEV)
+    B.brng_dirichlet(h.h, T(alpha), out)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    th, rpos, st, logs, cond = O.dirichlet(seed, R * K, alpha, with_logs=True)
+    assert np.array_equal(h.positions(), rpos)
+    g = H(out).astype(np.float64)
+    assert_close(g, th, _dir_scale(th, logs, cond), what="dirichlet K=%d" % K)
+    assert np.max(np.abs(g.sum(axis=1) - 1.0)) < 1e-5
+
+
+def test_dirichlet_invalid_rows():
+    seed, K, rows = 3, 40, 30
+    alpha = np.full((rows, K), 0.7, dtype=np.float32)
+    alpha[4, 7] = -1.0
+    alpha[9, 39] = np.nan
+    h = handle(seed, 10 * K)  # R = 10: row-streams serve 3 rows each
+    out = torch.empty((rows, K), dtype=torch.float32, device=DEV)
+    B.brng_dirichlet(h.h, T(alpha), out)
+    code, cnt = h.counters()
+    assert code == B.BRNG_EDOMAIN and cnt["n_domain"] == 2
+    th, rpos, st = O.dirichlet(seed, 10 * K, alpha)
+    assert st == O.EDOMAIN
+    g = H(out)
+    assert np.all(np.isnan(g[4])) and np.all(np.isnan(g[9]))
+    assert np.array_equal(h.positions(), rpos)
+
+
+# ---- Gibbs models -----------------------------------------------------------
+
+def _triangle_gpu(n_chains, n_sweeps, lanes=1, buf_len=256, wpb=4, state=None, mom=None, offset=0):
+    h = handle(42, 1, buf_len, lanes_per_chain=lanes, warps_per_block=wpb)
+    st = B.triangle_state(n_chains, device=DEV) if state is None else state
+    m = torch.zeros((n_chains, 5), dtype=torch.float64, device=DEV) if mom is None else mom
+    B.brng_gibbs_run(h.h, B.MODEL_TRIANGLE, offset, n_chains, n_sweeps, None, st, m)
+    torch.cuda.synchronize()
+    return st, m
+
+
+def test_triangle_full_size_bit_exact():
+    """Eq. 1 / Fig. 1 workload: 1,024 chains x 10,000 sweeps, FP64, bit-exact."""
+    n_chains, n_sweeps = 1024, 10000
+    st, m = _triangle_gpu(n_chains, n_sweeps)
+    x, y, pos = B.triangle_unpack(st)
+    ref = O.gibbs_triangle(42, n_chains, n_sweeps, nthreads=NT)
+    assert np.array_equal(x.view(np.int64), ref["xy"][:, 0].view(np.int64))
+    assert np.array_equal(y.view(np.int64), ref["xy"][:, 1].view(np.int64))
+    assert np.array_equal(pos, ref["pos"])
+    assert np.array_equal(H(m).view(np.int64), ref["mom"].view(np.int64))
+
+
+@pytest.mark.parametrize("lanes,buf_len,wpb", [(2, 64, 4), (4, 4, 16), (32, 512, 1), (8, 256, 2)])
+def test_triangle_layout_invariance(lanes, buf_len, wpb):
+    a, ma = _triangle_gpu(300, 777)
+    b, mb = _triangle_gpu(300, 777, lanes=lanes, buf_len=buf_len, wpb=wpb)
+    assert torch.equal(a, b) and torch.equal(ma, mb)
+
+
+def test_triangle_resume_and_shard():
+    whole, mw = _triangle_gpu(100, 500)
+    st, m = _triangle_gpu(100, 123)
+    st, m = _triangle_gpu(100, 377, state=st, mom=m, buf_len=8)
+    assert torch.equal(st, whole) and torch.equal(m, mw)
+    a, ma = _triangle_gpu(40, 500)
+    b, mb = _triangle_gpu(60, 500, offset=40)
+    assert torch.equal(torch.cat([a, b]), whole) and torch.equal(torch.cat([ma, mb]), mw)
+
+
+def _ng_gpu(nobs, xbar, sc, n_sweeps, offset=0, state=None, mom=None, **tune):
+    n = nobs.size
+    h = handle(42, 1, **tune)
+    t = [T(nobs), T(xbar), T(sc)]
+    params = B.brng_normal_gamma_params_t(2.0, 1.0, 0.0, 0.01, *[x.data_ptr() for x in t])
+    st = B.normal_gamma_state(n, device=DEV) if state is None else state
+    m = torch.zeros((n, 4), dtype=torch.float64, device=DEV) if mom is None else mom
+    B.brng_gibbs_run(h.h, B.MODEL_NORMAL_GAMMA, offset, n, n_sweeps, params, st, m)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    return st, m, cnt
+
+
+def _ng_check(st, m, ref, n_sweeps, what):
+    mu, tau, pn, pu = B.normal_gamma_unpack(st)
+    assert np.array_equal(pn, ref["pos"][:, 0]) and np.array_equal(pu, ref["pos"][:, 1])
+    rmu, rtau = ref["state"][:, 0], ref["state"][:, 1]
+    # the last sweep's mu = mean + z / sqrt(P): FP32 at the scale |mean| + |z|/sqrt(P),
+    # tau = G / rate; the chain contracts, so earlier sweeps' FP32 errors do not grow
+    sd = 1.0 / np.sqrt(0.01 + 100.0 * rtau)
+    assert_close(mu, rmu, np.abs(rmu) + 4 * sd, rtol=1e-5, what=what + " mu")
+    assert_close(tau, rtau, np.abs(rtau), rtol=1e-5, what=what + " tau")
+    g = H(m)
+    rm = ref["mom"]
+    assert_close(g[:, 0], rm[:, 0], np.abs(rm[:, 0]) + n_sweeps * 4 * sd.mean(), rtol=1e-5, what=what + " sum mu")
+    assert_close(g[:, 1], rm[:, 1], np.abs(rm[:, 1]), rtol=1e-5, what=what + " sum tau")
+    assert_close(g[:, 2], rm[:, 2], np.abs(rm[:, 2]), rtol=2e-5, what=what + " sum mu^2")
+    assert_close(g[:, 3], rm[:, 3], np.abs(rm[:, 3]), rtol=2e-5, what=what + " sum tau^2")
+
+
+def test_normal_gamma_parity_small():
+    nobs, xbar, sc = inputs.normal_gamma_data(1000, seed=5)
+    st, m, cnt = _ng_gpu(nobs, xbar, sc, 300)
+    ref = O.gibbs_normal_gamma(42, 300, nobs, xbar, sc, nthreads=NT)
+    _ng_check(st, m, ref, 300, "normal-gamma 1000x300")
+
+
+def test_normal_gamma_full_size_sampled():
+    """65,536 chains x 2,000 sweeps; 256 chains recomputed by the oracle."""
+    n_chains, n_sweeps = 65536, 2000
+    nobs, xbar, sc = inputs.normal_gamma_data(n_chains, seed=42)
+    st, m, cnt = _ng_gpu(nobs, xbar, sc, n_sweeps)
+    print("counters", cnt)
+    for c0, c1 in [(0, 128), (n_chains - 128, n_chains)]:
+        ref = O.gibbs_normal_gamma(42, n_sweeps, nobs[c0:c1], xbar[c0:c1], sc[c0:c1], chain_offset=c0,
+                                   nthreads=NT)
+        _ng_check(st[c0:c1], m[c0:c1], ref, n_sweeps, "normal-gamma chains %d..%d" % (c0, c1))
+
+
+def test_normal_gamma_invariance_and_resume():
+    nobs, xbar, sc = inputs.normal_gamma_data(200, seed=6)
+    a, ma, _ = _ng_gpu(nobs, xbar, sc, 100)
+    b, mb, _ = _ng_gpu(nobs, xbar, sc, 100, buf_len=4, warps_per_block=16)
+    assert torch.equal(a, b) and torch.equal(ma, mb)
+    c, mc, _ = _ng_gpu(nobs, xbar, sc, 37)
+    c, mc, _ = _ng_gpu(nobs, xbar, sc, 63, state=c, mom=mc, buf_len=128)
+    assert torch.equal(a[:, 1:], c[:, 1:])  # positions identical
+    mu_a, tau_a, _, _ = B.normal_gamma_unpack(a)
+    mu_c, tau_c, _, _ = B.normal_gamma_unpack(c)
+    assert np.array_equal(mu_a, mu_c) and np.array_equal(tau_a, tau_c)
+
+
+def _lda_gpu(alpha, n_sweeps, offset=0, **tune):
+    n_docs, K = alpha.shape
+    h = handle(42, 1, **tune)
+    a = T(alpha)
+    theta = torch.zeros((n_docs, K), dtype=torch.float32, device=DEV)
+    pos = torch.zeros((n_docs, K, 2), dtype=torch.int64, device=DEV)
+    mom = torch.zeros((n_docs, K), dtype=torch.float64, device=DEV)
+    params = B.brng_lda_params_t(K, a.data_ptr())
+    state = B.brng_lda_state_t(theta.data_ptr(), pos.data_ptr())
+    B.brng_gibbs_run(h.h, B.MODEL_LDA, offset, n_docs, n_sweeps, params, state, mom)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    return theta, pos, mom
+
+
+def _lda_check(theta, pos, mom, ref, what):
+    assert np.array_equal(H(pos).view(np.uint64), ref["pos"])
+    assert_close(H(theta), ref["theta"], _dir_scale(ref["theta"], ref["logs"], ref["cond"]),
+                 what=what + " theta")
+    # accumulated theta: every sweep within the per-draw bound; log-Gammas of
+    # these documents stay below ~60 in magnitude
+    assert_close(H(mom), ref["mom"], np.abs(ref["mom"]) * 250.0, what=what + " sum theta")
+
+
+def test_lda_parity_small():
+    alpha, _, _ = inputs.lda_alpha(96, K=64, seed=7)
+    theta, pos, mom = _lda_gpu(alpha, 40)
+    ref = O.gibbs_lda(42, 40, alpha, nthreads=NT)
+    _lda_check(theta, pos, mom, ref, "lda 96x64x40")
+
+
+def test_lda_full_size_sampled():
+    """16,384 documents x K=64 x 500 sweeps; 8 documents recomputed."""
+    alpha, _, _ = inputs.lda_alpha(16384, K=64, seed=42)
+    theta, pos, mom = _lda_gpu(alpha, 500)
+    for d0, d1 in [(0, 4), (16380, 16384)]:
+        ref = O.gibbs_lda(42, 500, alpha[d0:d1], doc_offset=d0, nthreads=NT)
+        _lda_check(theta[d0:d1], pos[d0:d1], mom[d0:d1], ref, "lda docs %d..%d" % (d0, d1))
+
+
+@pytest.mark.parametrize("tune", [dict(lookahead=1), dict(lookahead=16, buf_len=4), dict(warps_per_block=1, buf_len=128)])
+def test_lda_tuning_invariance(tune):
+    alpha, _, _ = inputs.lda_alpha(50, K=64, seed=8)
+    a = _lda_gpu(alpha, 25)
+    b = _lda_gpu(alpha, 25, **tune)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+# ---- edge cases and errors --------------------------------------------------
+
+def test_edge_cases():
+    h = handle(1, 10)
+    empty = torch.empty(0, dtype=torch.float32, device=DEV)
+    assert B.brng_gamma(h.h, empty, empty) == B.BRNG_OK
+    # fewer draws than streams; single stream
+    for S, n in [(10, 3), (1, 257)]:
+        h = handle(2, S)
+        alpha = np.full(n, 0.5, np.float32)
+        out, w = _run_bulk("gamma", h, [alpha], n)
+        ro, rw, rpos, _ = O.gamma(2, S, alpha)
+        assert np.array_equal(words_np(w), rw) and np.array_equal(h.positions(), rpos)
+    # invalid parameters: NaN, nothing consumed, counted
+    h = handle(3, 4)
+    a = np.array([0, 1, np.nan, 2, 5, 5], np.float32)
+    b = np.array([1, 0.5, 1, np.inf, 5, 6], np.float32)
+    out, w = _run_bulk("uniform", h, [a, b], 6)
+    code, cnt = h.counters(reset=True)
+    assert code == B.BRNG_EDOMAIN and cnt["n_domain"] == 3
+    ro, rw, rpos, st = O.uniform(3, 4, a, b)
+    g = H(out)
+    assert np.array_equal(np.isnan(g), np.isnan(ro)) and np.array_equal(h.positions(), rpos)
+    assert g[4] == 5.0
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK and cnt["n_domain"] == 0
+    # unknown tag
+    tag = np.array([0, 9, 3], np.uint8)
+    p = np.ones(3, np.float32)
+    o = torch.empty(3, dtype=torch.float32, device=DEV)
+    B.brng_mixed(h.h, T(tag), T(p), T(p + 1), o)
+    code, cnt = h.counters()
+    assert code == B.BRNG_EDOMAIN and np.isnan(H(o)[1])
+
+
+def test_argument_errors():
+    with pytest.raises(B.BrngError):
+        B.brng_create(1, 0)
+    with pytest.raises(B.BrngError):
+        B.brng_create(1, 4, 48)  # not a power of two
+    h = handle(1, 10)
+    with pytest.raises(B.BrngError):
+        h.tune(warps_per_block=17)
+    with pytest.raises(B.BrngError):
+        B.brng_dirichlet(h.h, torch.ones((2, 3), device=DEV), torch.empty((2, 3), device=DEV))  # 10 % 3
+    with pytest.raises(B.BrngError):
+        h.tune(buf_len=512, warps_per_block=16)
+        a = torch.ones(100, device=DEV)
+        B.brng_mixed(h.h, torch.zeros(100, dtype=torch.uint8, device=DEV), a, a, torch.empty(100, device=DEV),
+                     torch.empty(100, dtype=torch.int32, device=DEV))  # shared memory too large
