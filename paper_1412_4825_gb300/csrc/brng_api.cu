@@ -33,16 +33,17 @@ int cuda_status(cudaError_t e) {
   return BRNG_ECUDA;
 }
 
-brng::Geometry geometry(const brng_t* h) {
-  return brng::Geometry{h->tune.warps_per_block, h->tune.buf_len};
-}
-
-// Shared memory cap check for a per-warp footprint.
-bool smem_fits(size_t per_warp, uint32_t warps) {
+// Launch geometry for a kernel needing `per_warp` bytes of shared memory per
+// warp: the tuned warps per block, reduced until a block fits the device's
+// opt-in shared memory (values never depend on it).  warps_per_block = 0 if
+// not even one warp fits.
+brng::Geometry geometry(const brng_t* h, size_t per_warp) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return per_warp * warps <= static_cast<size_t>(optin);
+  uint32_t w = h->tune.warps_per_block;
+  while (w > 0 && per_warp * w > static_cast<size_t>(optin)) --w;
+  return brng::Geometry{w, h->tune.buf_len};
 }
 
 int bulk(brng_t* h, int tag, size_t n, const uint8_t* tagv, const float* p0, const float* p1,
@@ -55,7 +56,8 @@ int bulk(brng_t* h, int tag, size_t n, const uint8_t* tagv, const float* p0, con
   if (two && tag != brng::kTagMixed && !p1) return BRNG_EINVAL;
   const int ndom = (tag == brng::kTagMixed) ? 3 : (tag == BRNG_TAG_GAMMA || tag == BRNG_TAG_LAPLACE) ? 2 : 1;
   const size_t per_warp = 128u + static_cast<size_t>(ndom) * h->tune.buf_len * 128u * (words ? 2 : 1);
-  if (!smem_fits(per_warp, h->tune.warps_per_block)) return BRNG_EINVAL;
+  const brng::Geometry g = geometry(h, per_warp);
+  if (g.warps_per_block == 0) return BRNG_EINVAL;
   brng::BulkArgs a;
   a.rk = h->rk;
   a.n = n;
@@ -68,7 +70,7 @@ int bulk(brng_t* h, int tag, size_t n, const uint8_t* tagv, const float* p0, con
   a.words = words;
   a.pos = h->d_pos;
   a.cnt = h->d_cnt;
-  return cuda_status(brng::launch_bulk(tag, a, geometry(h), st));
+  return cuda_status(brng::launch_bulk(tag, a, g, st));
 }
 
 }  // namespace
@@ -236,7 +238,8 @@ int brng_dirichlet(brng_t* h, size_t n_rows, uint32_t K, const float* alpha, flo
   if (!alpha || !out) return BRNG_EINVAL;
   const uint32_t P = K <= 32 ? 1 : K <= 64 ? 2 : 4;
   const size_t per_warp = 128u + h->tune.lookahead * 32u * P * 4u + 2u * P * h->tune.buf_len * 128u;
-  if (!smem_fits(per_warp, h->tune.warps_per_block)) return BRNG_EINVAL;
+  const brng::Geometry g = geometry(h, per_warp);
+  if (g.warps_per_block == 0) return BRNG_EINVAL;
   brng::DirichletArgs a{};
   a.rk = h->rk;
   a.K = K;
@@ -249,7 +252,7 @@ int brng_dirichlet(brng_t* h, size_t n_rows, uint32_t K, const float* alpha, flo
   a.pos = h->d_pos;
   a.S = h->S;
   a.cnt = h->d_cnt;
-  return cuda_status(brng::launch_dirichlet(a, geometry(h), false, reinterpret_cast<cudaStream_t>(stream)));
+  return cuda_status(brng::launch_dirichlet(a, g, false, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_t n_chains,
@@ -259,13 +262,12 @@ int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (n_chains == 0) return BRNG_OK;
   if (!state || !moments) return BRNG_EINVAL;
-  brng::Geometry g = geometry(h);
   switch (model) {
     case BRNG_MODEL_TRIANGLE: {
       if (chain_offset + n_chains > 0x100000000ull) return BRNG_EINVAL;
       const uint32_t nc = 32 / h->tune.lanes_per_chain;
-      if (!smem_fits(128u + static_cast<size_t>(h->tune.buf_len) * nc * 8u, g.warps_per_block))
-        return BRNG_EINVAL;
+      const brng::Geometry g = geometry(h, 128u + static_cast<size_t>(h->tune.buf_len) * nc * 8u);
+      if (g.warps_per_block == 0) return BRNG_EINVAL;
       brng::TriangleArgs a;
       a.rk = h->rk;
       a.chain_offset = chain_offset;
@@ -280,8 +282,8 @@ int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_
       const brng_normal_gamma_params_t* p = static_cast<const brng_normal_gamma_params_t*>(params);
       if (!p || !p->nobs || !p->xbar || !p->sc) return BRNG_EINVAL;
       if (chain_offset + n_chains > 0x100000000ull) return BRNG_EINVAL;
-      if (!smem_fits(128u + 2u * static_cast<size_t>(h->tune.buf_len) * 128u, g.warps_per_block))
-        return BRNG_EINVAL;
+      const brng::Geometry g = geometry(h, 128u + 2u * static_cast<size_t>(h->tune.buf_len) * 128u);
+      if (g.warps_per_block == 0) return BRNG_EINVAL;
       brng::NormalGammaArgs a;
       a.rk = h->rk;
       a.chain_offset = chain_offset;
@@ -307,7 +309,8 @@ int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_
       if ((chain_offset + n_chains) * static_cast<uint64_t>(p->K) > 0x100000000ull) return BRNG_EINVAL;
       const uint32_t P = p->K <= 32 ? 1 : p->K <= 64 ? 2 : 4;
       const size_t per_warp = 128u + h->tune.lookahead * 32u * P * 4u + 2u * P * h->tune.buf_len * 128u;
-      if (!smem_fits(per_warp, g.warps_per_block)) return BRNG_EINVAL;
+      const brng::Geometry g = geometry(h, per_warp);
+      if (g.warps_per_block == 0) return BRNG_EINVAL;
       brng::DirichletArgs a{};
       a.rk = h->rk;
       a.K = p->K;

@@ -52,7 +52,8 @@ def words_np(t):
 def assert_close(got, want, scale, rtol=RTOL, what=""):
     got = np.asarray(got, np.float64).ravel()
     want = np.asarray(want, np.float64).ravel()
-    scale = np.broadcast_to(np.asarray(scale, np.float64), want.shape).ravel()
+    scale = np.asarray(scale, np.float64)
+    scale = scale.ravel() if scale.size == want.size else np.broadcast_to(scale, want.shape)
     nan_ok = np.isnan(got) & np.isnan(want)
     err = np.abs(got - want)
     bound = rtol * scale + 2 * FLT_MIN
@@ -513,5 +514,6 @@ def test_argument_errors():
     with pytest.raises(B.BrngError):
         h.tune(buf_len=512, warps_per_block=16)
         a = torch.ones(100, device=DEV)
+        # 3 rings x 512 elements x 32 lanes x (value + word): not even one warp fits
         B.brng_mixed(h.h, torch.zeros(100, dtype=torch.uint8, device=DEV), a, a, torch.empty(100, device=DEV),
-                     torch.empty(100, dtype=torch.int32, device=DEV))  # shared memory too large
+                     torch.empty(100, dtype=torch.int32, device=DEV))
