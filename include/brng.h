@@ -183,6 +183,34 @@ int brng_weibull(brng_t *h, size_t n, const float *k, const float *lambda, float
  * Unknown tags give NaN (n_domain).  tag: device uint8[n]. */
 int brng_mixed(brng_t *h, size_t n, const uint8_t *tag, const float *p0, const float *p1,
                float *out, uint32_t *words, brng_stream_t stream);
+/* ---- Gamma draws without device allocation ----------------------------------
+ * No counterpart in the paper: this entry point exists for callers that cannot
+ * call cudaMalloc -- code running inside another framework's memory pool,
+ * which must own every device allocation, or a loop that must not stall on the
+ * device-wide synchronisation that cudaMalloc/cudaFree imply.
+ * brng_gamma_static(seed, n_streams, n, alpha, out, words, stream) gives what
+ * brng_create(seed, n_streams, 0, &h); brng_gamma(h, n, alpha, out, words,
+ * stream); brng_destroy(h) would give -- every stream starting at its first
+ * element -- but allocates nothing: its per-stream positions and counters live
+ * in one fixed array in the library's device memory, which every GPU that
+ * loads the library holds (about 1.5 MB) until the process exits.
+ * Limits and rules:
+ *   - 1 <= n_streams <= BRNG_STATIC_MAX_STREAMS, else BRNG_EINVAL (nothing is
+ *     enqueued);
+ *   - alpha, out (and words, if not NULL) are caller-owned device arrays of n
+ *     elements, as for brng_gamma; invalid alpha gives NaN in out (no counter
+ *     can be read back through this entry point);
+ *   - the first call on a device looks up the array's device address (a
+ *     one-time set-up per device); make that first call before any stream
+ *     capture;
+ *   - every call clears the array on `stream` before its kernel, and all calls
+ *     share it: calls whose work overlaps on the GPU (other streams, other
+ *     host threads) race and give wrong results.  Order them on one stream.
+ * Enqueued on `stream`; returns BRNG_OK, BRNG_EINVAL or BRNG_ECUDA. */
+#define BRNG_STATIC_MAX_STREAMS 65536u
+int brng_gamma_static(uint64_t seed, uint32_t n_streams, size_t n, const float *alpha,
+                      float *out, uint32_t *words, brng_stream_t stream);
+
 /* Dirichlet rows (Sec. 1 footnote: K Gammas, normalised).  alpha and out are
  * device float32 [n_rows][K].  Needs K >= 1, K <= 128 and n_streams % K == 0:
  * component k of row i draws its Gamma from stream (i mod (n_streams/K))*K + k.

@@ -83,6 +83,7 @@ def _load():
         "brng_weibull": ([vp, sz, vp, vp, vp, vp, vp], i32),
         "brng_mixed": ([vp, sz, vp, vp, vp, vp, vp, vp], i32),
         "brng_dirichlet": ([vp, sz, u32, vp, vp, vp], i32),
+        "brng_gamma_static": ([u64, u32, sz, vp, vp, vp, vp], i32),
         "brng_gibbs_run": ([vp, i32, u64, u32, u32, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
@@ -238,6 +239,16 @@ def brng_mixed(h, tag, p0, p1, out, words=None, stream=None):
     import torch
     return _check("brng_mixed", lib.brng_mixed(
         h, out.numel(), _ptr(tag, torch.uint8, "tag"), _ptr(p0, _f32(), "p0"), _ptr(p1, _f32(), "p1"),
+        _ptr(out, _f32(), "out"), _ptr(words, torch.int32, "words"), _stream(stream)))
+
+
+def brng_gamma_static(seed, n_streams, alpha, out, words=None, stream=None):
+    """Gamma draws with no device allocation (see include/brng.h): for
+    callers that must not call cudaMalloc.  Streams start at their first
+    element on every call; calls must not overlap on the GPU."""
+    import torch
+    return _check("brng_gamma_static", lib.brng_gamma_static(
+        int(seed) & (2**64 - 1), int(n_streams), out.numel(), _ptr(alpha, _f32(), "alpha"),
         _ptr(out, _f32(), "out"), _ptr(words, torch.int32, "words"), _stream(stream)))
 
 
