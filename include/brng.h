@@ -135,6 +135,14 @@ int brng_philox_words(brng_t *h, uint32_t domain, uint32_t stream_id, uint64_t f
 int brng_philox_peak(uint64_t iters, uint32_t blocks, uint32_t threads, uint32_t *sink,
                      brng_stream_t stream);
 
+/* ---- FP32 elementary functions of the base conversions ----------------------
+ * out[i] = f(in[i]) on the device for fn = 0: natural log (the FP32 log of
+ * the exponential and Box-Muller buffers and of the Gamma test), 1: sin and
+ * 2: cos of pi k 2^-23 for the integer k = in[i] in [0, 2^24) (the Box-Muller
+ * angle).  Written without integer/float conversion instructions; exposed so
+ * their error can be bounded against a reference.  in, out: device float[n]. */
+int brng_fp32_eval(uint32_t fn, size_t n, const float *in, float *out, brng_stream_t stream);
+
 /* ---- FP64 elementary functions of the Gamma accept recheck ----------------
  * out[i] = f(in[i]) on the device for fn = 0: log, 1: sin(pi x), 2: cos(pi x),
  * the fixed-operation-order FP64 functions the Gamma sampler uses when it

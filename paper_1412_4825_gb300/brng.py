@@ -74,6 +74,7 @@ def _load():
         "brng_read_counters": ([vp, vp, C.POINTER(brng_counters_t), i32], i32),
         "brng_philox_words": ([vp, u32, u32, u64, sz, vp, vp], i32),
         "brng_fp64_eval": ([u32, sz, vp, vp, vp], i32),
+        "brng_fp32_eval": ([u32, sz, vp, vp, vp], i32),
         "brng_philox_peak": ([u64, u32, u32, vp, vp], i32),
         "brng_uniform": ([vp, sz, vp, vp, vp, vp, vp], i32),
         "brng_normal": ([vp, sz, vp, vp, vp, vp, vp], i32),
@@ -185,6 +186,11 @@ def brng_philox_peak(iters, blocks, threads, sink, stream=None):
     import torch
     return _check("brng_philox_peak", lib.brng_philox_peak(
         int(iters), int(blocks), int(threads), _ptr(sink, torch.int32, "sink"), _stream(stream)))
+
+
+def brng_fp32_eval(fn, x, out, stream=None):
+    return _check("brng_fp32_eval", lib.brng_fp32_eval(
+        int(fn), x.numel(), _ptr(x, _f32(), "in"), _ptr(out, _f32(), "out"), _stream(stream)))
 
 
 def brng_fp64_eval(fn, x, out, stream=None):

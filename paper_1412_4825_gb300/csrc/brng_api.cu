@@ -193,6 +193,13 @@ int brng_philox_peak(uint64_t iters, uint32_t blocks, uint32_t threads, uint32_t
                                               blocks, threads, sink, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+int brng_fp32_eval(uint32_t fn, size_t n, const float* in, float* out, brng_stream_t stream) {
+  if (fn > 2) return BRNG_EINVAL;
+  if (n == 0) return BRNG_OK;
+  if (!in || !out) return BRNG_EINVAL;
+  return cuda_status(brng::launch_fp32_eval(fn, n, in, out, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 int brng_fp64_eval(uint32_t fn, size_t n, const double* in, double* out, brng_stream_t stream) {
   if (fn > 2) return BRNG_EINVAL;
   if (n == 0) return BRNG_OK;

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(512) bulk_kernel(const BulkArgs a) {
       if (w) {
         word = wd;
         if (tag == BRNG_TAG_EXPONENTIAL) out = e / p0;
-        if (tag == BRNG_TAG_WEIBULL) out = p1 * expf(logf(e) / p0);
+        if (tag == BRNG_TAG_WEIBULL) out = p1 * expf(flog(e) / p0);
       }
     }
     if constexpr (D::kN && D::kU && (TAG < 0 || TAG == BRNG_TAG_GAMMA)) {
@@ -140,11 +140,14 @@ __global__ void __launch_bounds__(512) bulk_kernel(const BulkArgs a) {
         const bool acc = mt_attempt(pending, g, RN, RU, s, a.rk, a.cnt, &dv, &zw);
         if (pending && attempts == 0) word = zw;
         const bool boost_now = pending && acc && g.boost;
-        const float ub = RU.get(boost_now, s, a.rk);
+        if (__any_sync(kFull, boost_now)) {  // warp-uniform: shapes below 1 only
+          const float ub = RU.get(boost_now, s, a.rk);
+          if (boost_now) dv *= expf(flog(ub + 0x1p-24f) / g.alpha);
+        }
         if (pending) {
           ++attempts;
           if (acc) {
-            out = g.boost ? dv * expf(logf(ub + 0x1p-24f) / g.alpha) : dv;
+            out = dv;
             pending = false;
           } else if (attempts >= kGammaMaxAttempts) {
             pending = false;
@@ -238,6 +241,28 @@ __global__ void __launch_bounds__(256) philox_peak_kernel(const RoundKeys rk, ui
 cudaError_t launch_philox_peak(const RoundKeys& rk, uint64_t iters, uint32_t blocks, uint32_t threads,
                                uint32_t* sink, cudaStream_t st) {
   philox_peak_kernel<<<blocks, threads, 0, st>>>(rk, iters, sink);
+  return cudaGetLastError();
+}
+
+// ---- the FP32 base-conversion functions, one element per thread ----------
+__global__ void fp32_eval_kernel(uint32_t fn, uint64_t n, const float* in, float* out) {
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    if (fn == 0) {
+      out[i] = flog(in[i]);
+    } else {
+      float s, c;
+      fsincospi_k(static_cast<uint32_t>(in[i]), &s, &c);
+      out[i] = fn == 1 ? s : c;
+    }
+  }
+}
+
+cudaError_t launch_fp32_eval(uint32_t fn, size_t n, const float* in, float* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  fp32_eval_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(fn, n, in, out);
   return cudaGetLastError();
 }
 

@@ -19,8 +19,9 @@
 // order; a row whose alpha has an invalid entry is all NaN and consumes
 // nothing (validity is voted by the warp for each row entering the window).
 // LDA (brng_gibbs_run): the row is the document and every sweep redraws it
-// with the same alpha; the warp accumulates theta in FP32 partials flushed to
-// FP64 every 16 sweeps.
+// with the same alpha; the warp accumulates theta in compensated (Kahan) FP32
+// sums, added to the FP64 moments at the end (no FP64 instruction in the loop:
+// GB300's FP64 pipe is narrow).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -30,7 +31,6 @@
 
 namespace brng {
 
-constexpr uint32_t kMaxLookahead = 16;
 
 __host__ __device__ inline uint32_t dirichlet_warp_bytes(uint32_t P, uint32_t B, uint32_t Q) {
   return 128u + Q * 32u * P * 4u + 2u * P * B * 32u * 4u;
@@ -72,8 +72,7 @@ __global__ void __launch_bounds__(512) dirichlet_kernel(const DirichletArgs a) {
   uint32_t stream[P], done[P];
   int att[P];
   bool kvalid[P], fresh[P];
-  float acc32[P], last[P];
-  double acc64[P];
+  float acc32[P], comp32[P], last[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     const uint32_t k = lane + 32u * p;
@@ -96,7 +95,7 @@ __global__ void __launch_bounds__(512) dirichlet_kernel(const DirichletArgs a) {
     att[p] = 0;
     fresh[p] = true;
     acc32[p] = 0.0f;
-    acc64[p] = 0.0;
+    comp32[p] = 0.0f;
     last[p] = 0.0f;
     g[p] = gamma_setup(1.0f);
   }
@@ -144,15 +143,18 @@ __global__ void __launch_bounds__(512) dirichlet_kernel(const DirichletArgs a) {
       uint32_t zw;
       const bool acc = mt_attempt(run, g[p], RN[p], RU[p], stream[p], a.rk, a.cnt, &dv, &zw);
       const bool boost_now = run && acc && g[p].boost;
-      const float ub = RU[p].get(boost_now, stream[p], a.rk);
+      float lb = 0.0f;  // log of the boost factor u_b^(1/alpha)
+      if (__any_sync(kFull, boost_now)) {  // warp-uniform: shapes below 1 only
+        const float ub = RU[p].get(boost_now, stream[p], a.rk);
+        if (boost_now) lb = flog(ub + 0x1p-24f) / g[p].alpha;
+      }
       bool rejected = false;
       if (run) {
         ++att[p];
         if (acc || att[p] >= kGammaMaxAttempts) {
           float l = __int_as_float(0x7fc00000);
           if (acc) {
-            l = logf(dv);
-            if (g[p].boost) l += logf(ub + 0x1p-24f) / g[p].alpha;
+            l = flog(dv) + lb;
           } else {
             rejected = true;
           }
@@ -194,19 +196,15 @@ __global__ void __launch_bounds__(512) dirichlet_kernel(const DirichletArgs a) {
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         const float th = e[p] * inv;
-        if (LDA) {
-          acc32[p] += th;
+        if (LDA) {  // compensated (Kahan) FP32 sum: no FP64 in the loop
+          const float yk = th - comp32[p];
+          const float tk = acc32[p] + yk;
+          comp32[p] = (tk - acc32[p]) - yk;
+          acc32[p] = tk;
           last[p] = th;
         } else if (kvalid[p]) {
           const uint64_t row = unit + static_cast<uint64_t>(tn) * a.R;
           a.out[row * K + lane + 32u * p] = th;
-        }
-      }
-      if (LDA && ((tn & 15u) == 15u || tn + 1 == nrows)) {
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          acc64[p] += static_cast<double>(acc32[p]);
-          acc32[p] = 0.0f;
         }
       }
       ++tn;
@@ -229,7 +227,7 @@ __global__ void __launch_bounds__(512) dirichlet_kernel(const DirichletArgs a) {
       a.pos[idx * 2] = RN[p].pos();
       a.pos[idx * 2 + 1] = RU[p].pos();
       a.out[idx] = last[p];
-      a.moments[idx] += acc64[p];
+      a.moments[idx] += static_cast<double>(acc32[p]) - static_cast<double>(comp32[p]);
     } else {
       const uint64_t sid = unit * K + k;
       a.pos[static_cast<uint64_t>(a.S) + sid] = RN[p].pos();

@@ -14,6 +14,8 @@
 
 #include <cstdint>
 
+#include "brng_fp32.cuh"
+
 namespace brng {
 
 constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
@@ -62,22 +64,18 @@ __device__ __forceinline__ uint4 philox_block(uint64_t blk, uint32_t dom, uint32
   return philox(philox_ctr(blk, dom, stream), rk);
 }
 
-// ---- FP32 base conversions (exact where the definition is exact) ----------
-// U = (w >> 8) 2^-24 in [0,1);  U' = U + 2^-24 in (0,1]  (both exact in FP32)
-__device__ __forceinline__ float u01(uint32_t w) { return __uint2float_rn(w >> 8) * 0x1p-24f; }
-__device__ __forceinline__ float u01_open(uint32_t w) {
-  return __uint2float_rn((w >> 8) + 1u) * 0x1p-24f;
-}
-
-// Box-Muller pair from (w0, w1): radius from U'(w0), angle 2 pi U(w1)
+// ---- FP32 base conversions (brng_fp32.cuh: no conversion instructions) ----
+// Box-Muller pair from (w0, w1): radius from U'(w0), angle 2 pi U(w1) =
+// pi (w1 >> 8) 2^-23
 __device__ __forceinline__ float2 box_muller(uint32_t w0, uint32_t w1) {
-  const float r = sqrtf(-2.0f * logf(u01_open(w0)));
+  const float q = -2.0f * flog(u01_open(w0));  // >= 0; 0 only for U' = 1
+  const float r = q > 0.0f ? q * rsqrtf(q) : 0.0f;
   float s, c;
-  sincospif(2.0f * u01(w1), &s, &c);
+  fsincospi_k(w1 >> 8, &s, &c);
   return make_float2(r * c, r * s);
 }
 
-__device__ __forceinline__ float exp1(uint32_t w) { return -logf(u01_open(w)); }
+__device__ __forceinline__ float exp1(uint32_t w) { return -flog(u01_open(w)); }
 
 // 53-bit uniform from two words: ((w0>>5) 2^26 + (w1>>6)) 2^-53, exact
 __device__ __forceinline__ double u53(uint32_t w0, uint32_t w1) {

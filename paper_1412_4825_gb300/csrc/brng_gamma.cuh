@@ -7,16 +7,21 @@
 // which lets lanes that accepted move on to their next draw instead of
 // idling while a neighbour retries.
 //
-// Precision: the attempt is computed in FP32 with the cancellation-free forms
-//   1 - v = -x (3 + x (3 + x)),  ln v = 3 log1p(x),  x = c z,
-// and its margin m = z^2/2 + d (1 - v + ln v) - ln u' decides when
-// |m| > tol = 1e-5 (1 + S), S the sum of the magnitudes of the terms
-// (plus d 3|x|/t for the sensitivity to z near t = 0).  The FP32 error of m is
-// a few ulp of S (~1e-6 S), so the FP64 decision agrees whenever |m| > tol;
-// otherwise the decision is recomputed in FP64 (brng_fp64.cuh) from the same
-// Philox bits, in the reference operation order.  The sign of t is treated
-// the same way when |t| <= 1e-5.  Both rechecks are counted; a recheck that
-// overturns the FP32 sign records |m| / tol (which must stay below 1).
+// Precision: the attempt is computed in FP32 and decided there when its
+// margin m = ln-test right side minus ln u' is clearly away from zero.  With
+// x = c z (c = 1/sqrt(9d)) the margin is exactly
+//     m = -ln u' - 3 d x^4 (1/4 - x/5 + x^2/6 - ... ),
+// since z^2/2 = 9 d x^2 / 2 cancels the quadratic term of d (1 - v + ln v);
+// for |x| <= 1/4 this series (12 terms, truncation < 2e-8 relative) is used,
+// free of the cancellation the textbook form suffers at large shapes.  For
+// |x| > 1/4 the form z^2/2 + d (1 - v + 3 ln t) - ln u' with
+// 1 - v = -x (3 + x (3 + x)) is used.  The FP32 error of m is a few ulp of the
+// magnitudes S of its terms, so the decision is taken in FP32 when
+// |m| > tol = 1e-5 (1 + S), and otherwise recomputed in FP64
+// (brng_fp64.cuh) from the same Philox bits, in the reference operation
+// order.  The sign of t = 1 + x is treated the same way when |t| <= 1e-5.
+// Rechecks are counted; a recheck that overturns the FP32 sign records
+// |m| / tol (which stays far below 1 if the error bound holds).
 #pragma once
 
 #include <cstdint>
@@ -29,6 +34,7 @@ namespace brng {
 constexpr int kGammaMaxAttempts = 64;
 constexpr float kTauT = 1e-5f;
 constexpr float kTauM = 1e-5f;
+constexpr float kSeriesMaxX = 0.25f;
 
 // Device counters (layout = brng_counters_t).
 struct DevCounters {
@@ -63,11 +69,46 @@ __device__ __forceinline__ bool gamma_param_ok(float alpha) {
   return isfinite(alpha) && alpha > 0.0f;
 }
 
-// FP64 value of N element `idx` of `stream` (Box-Muller from its word pair)
-__device__ __forceinline__ double gauss64_at(uint64_t idx, uint32_t stream, const RoundKeys& rk) {
-  const uint4 w = philox_block(idx / 4, kDomN, stream, rk);
-  const uint32_t slot = static_cast<uint32_t>(idx % 4);
-  return slot < 2 ? dgauss(w.x, w.y, slot & 1) : dgauss(w.z, w.w, slot & 1);
+// Philox with the key schedule computed on the fly from the seed words (for
+// the rare out-of-line paths, which then need no round-key table)
+__device__ __forceinline__ uint4 philox_keyed(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += kPhiloxW0;
+      k1 += kPhiloxW1;
+    }
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+    const uint32_t lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+    const uint32_t lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+struct Recheck {
+  float t;   // t = 1 + c z from the FP64 values (for the output d t^3)
+  int pass;  // mode 0: t > 0;  mode 1: the attempt accepts
+};
+
+// The FP64 re-decision of one attempt, from the same Philox bits: z of N
+// element `zi` (Box-Muller in FP64), d, c, t, then either the sign of t
+// (mode 0) or the accept test with U' = uo (mode 1; t > 0 is known).  Kept
+// out of line on purpose: GB300's FP64 pipe is narrow, and FP64 code the
+// compiler predicated into the attempt instead of branching around would
+// occupy it on every attempt rather than on the rare ones that need it.
+static __device__ __noinline__ Recheck mt_recheck64(float alpha, uint64_t zi, uint32_t stream,
+                                                    uint32_t k0, uint32_t k1, float uo, int mode) {
+  const uint4 w = philox_keyed(philox_ctr(zi / 4, kDomN, stream), k0, k1);
+  const uint32_t slot = static_cast<uint32_t>(zi % 4);
+  const double z64 = slot < 2 ? dgauss(w.x, w.y, slot & 1) : dgauss(w.z, w.w, slot & 1);
+  const double d64 = mt_d64(alpha);
+  const double t64 = mt_t64(d64, z64);
+  Recheck r;
+  r.t = static_cast<float>(t64);
+  r.pass = mode == 0 ? (t64 > 0.0) : mt_accept64(d64, z64, t64, static_cast<double>(uo));
+  return r;
 }
 
 static __device__ __noinline__ void record_flip(DevCounters* cnt, float ratio) {
@@ -81,51 +122,70 @@ template <class RN, class RU>
 __device__ __forceinline__ bool mt_attempt(bool run, const GammaState& g, RN& N, RU& U,
                                            uint32_t stream, const RoundKeys& rk,
                                            DevCounters* cnt, float* dv, uint32_t* zword) {
-  uint64_t zi = 0;
-  const float z = N.get(run, stream, rk, zword, &zi);
+  const float z = N.get(run, stream, rk, zword);
   const float x = g.c * z;
+  const bool series = fabsf(x) <= kSeriesMaxX;
   float t = 1.0f + x;
   bool tpos = t > 0.0f;
-  double z64 = 0.0, d64 = 0.0, t64 = 0.0;
-  bool have64 = false;
-  const bool tclose = run && fabsf(t) <= kTauT;
-  if (tclose) {  // rare: the sign of t is re-decided in FP64
-    z64 = gauss64_at(zi, stream, rk);
-    d64 = mt_d64(g.alpha);
-    t64 = mt_t64(d64, z64);
-    tpos = t64 > 0.0;
-    have64 = true;
-    t = static_cast<float>(t64);
+  const bool tclose = run && !series && fabsf(t) <= kTauT;
+  if (tclose) {  // rare: the sign of t is re-decided in FP64 (z is N element pos-1)
+    const Recheck r = mt_recheck64(g.alpha, N.pos() - 1, stream, rk.k[0][0], rk.k[0][1], 0.0f, 0);
+    tpos = r.pass != 0;
+    t = r.t;
   }
-  count_warp(&cnt->n_recheck, tclose);
   const bool needu = run && tpos;
   const float u = U.get(needu, stream, rk);
   bool acc = false;
   bool recheck = false;
   if (needu) {
     const float uo = u + 0x1p-24f;  // U' = U + 2^-24, exact
-    const float lnu = logf(uo);
-    const float lnv = 3.0f * log1pf(x);
-    const float omv = -x * fmaf(x, x + 3.0f, 3.0f);  // 1 - (1 + x)^3
-    const float h = 0.5f * z * z;
-    const float m = h + g.d * (omv + lnv) - lnu;
-    const float S = h + g.d * (fabsf(omv) + fabsf(lnv) + 3.0f * fabsf(x) / t) + fabsf(lnu);
-    const float tol = kTauM * (1.0f + S);
-    if (fabsf(m) > tol) {
-      acc = m > 0.0f;
+    // q = 3 d x^4 (1/4 - x/5 + x^2/6 - ...) >= 0: the margin is -ln U' - q
+    float p = -0x1.111112p-4f;         // -1/15
+    p = fmaf(p, x, 0x1.24924ap-4f);    //  1/14
+    p = fmaf(p, x, -0x1.3b13b2p-4f);   // -1/13
+    p = fmaf(p, x, 0x1.555556p-4f);    //  1/12
+    p = fmaf(p, x, -0x1.745d18p-4f);   // -1/11
+    p = fmaf(p, x, 0x1.99999ap-4f);    //  1/10
+    p = fmaf(p, x, -0x1.c71c72p-4f);   // -1/9
+    p = fmaf(p, x, 0.125f);            //  1/8
+    p = fmaf(p, x, -0x1.24924ap-3f);   // -1/7
+    p = fmaf(p, x, 0x1.555556p-3f);    //  1/6
+    p = fmaf(p, x, -0x1.99999ap-3f);   // -1/5
+    p = fmaf(p, x, 0.25f);             //  1/4
+    const float x2 = x * x;
+    const float q = (3.0f * g.d) * (x2 * x2) * p;
+    // Log-free accept: e^-q >= 1 - q, so U' + q < 1 implies ln U' < -q.  The
+    // factor 1.00001 covers q's FP32 error (a few 1e-7 relative) and the bound
+    // 1 - 2^-22 the rounding of the sum with room to spare, so a fast accept
+    // is also an accept of the exact (and FP64) test.
+    if (series && fmaf(q, 1.00001f, uo) < 0x1.fffff8p-1f) {
+      acc = true;
     } else {
-      recheck = true;
-      if (!have64) {
-        z64 = gauss64_at(zi, stream, rk);
-        d64 = mt_d64(g.alpha);
-        t64 = mt_t64(d64, z64);
+      const float lnu = flog(uo);
+      float m, tol;
+      if (series) {
+        m = -lnu - q;
+        tol = kTauM * (1.0f + fabsf(lnu) + q);
+      } else {
+        const float lnv = 3.0f * flog(t);
+        const float omv = -x * fmaf(x, x + 3.0f, 3.0f);  // 1 - (1 + x)^3
+        const float h = 0.5f * z * z;
+        m = h + g.d * (omv + lnv) - lnu;
+        const float S =
+            h + g.d * (fabsf(omv) + fabsf(lnv) + __fdividef(3.0f * fabsf(x), t)) + fabsf(lnu);
+        tol = kTauM * (1.0f + S);
       }
-      acc = mt_accept64(d64, z64, t64, static_cast<double>(uo));
-      if (isfinite(m) && acc != (m > 0.0f)) record_flip(cnt, fabsf(m) / tol);
+      if (fabsf(m) > tol) {
+        acc = m > 0.0f;
+      } else {
+        recheck = true;
+        acc = mt_recheck64(g.alpha, N.pos() - 1, stream, rk.k[0][0], rk.k[0][1], uo, 1).pass != 0;
+        if (isfinite(m) && acc != (m > 0.0f)) record_flip(cnt, fabsf(m) / tol);
+      }
     }
     *dv = g.d * (t * t * t);
   }
-  count_warp(&cnt->n_recheck, recheck);
+  count_warp(&cnt->n_recheck, tclose || recheck);
   return acc;
 }
 

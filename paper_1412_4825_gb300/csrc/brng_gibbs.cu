@@ -152,51 +152,56 @@ __global__ void __launch_bounds__(512) normal_gamma_kernel(const NormalGammaArgs
   const float nxb = n * xb;
 
   float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
-  uint32_t sweep = 0, it = 0;
+  uint32_t sweep = 0;
   int att = 0;
   bool rejected = false;
-  while (true) {
-    const bool run = active && sweep < a.n_sweeps;
-    if (!__any_sync(kFull, run)) break;
-    float dv = 0.0f;
-    uint32_t zw;
-    const bool acc = mt_attempt(run, g, RN, RU, stream, a.rk, a.cnt, &dv, &zw);
-    const bool boost_now = run && acc && g.boost;
-    const float ub = RU.get(boost_now, stream, a.rk);
-    bool finish = false;
-    float G = 0.0f;
-    if (run) {
-      ++att;
-      if (acc) {
-        G = g.boost ? dv * expf(logf(ub + 0x1p-24f) / g.alpha) : dv;
-        finish = true;
-      } else if (att >= kGammaMaxAttempts) {
-        G = __int_as_float(0x7fc00000);
-        finish = true;
-        rejected = true;
+  bool more = true;
+  while (more) {
+    // at most 64 attempts per lane into the FP32 partials, then one FP64 flush
+    // outside the inner loop (so no FP64 instruction sits in the hot loop)
+    for (uint32_t j = 0; j < 64; ++j) {
+      const bool run = active && sweep < a.n_sweeps;
+      more = __any_sync(kFull, run);
+      if (!more) break;
+      float dv = 0.0f;
+      uint32_t zw;
+      const bool acc = mt_attempt(run, g, RN, RU, stream, a.rk, a.cnt, &dv, &zw);
+      const bool boost_now = run && acc && g.boost;
+      float G = dv;
+      if (__any_sync(kFull, boost_now)) {  // warp-uniform: shapes below 1 only
+        const float ub = RU.get(boost_now, stream, a.rk);
+        if (boost_now) G = dv * expf(flog(ub + 0x1p-24f) / g.alpha);
+      }
+      bool finish = false;
+      if (run) {
+        ++att;
+        if (acc) {
+          finish = true;
+        } else if (att >= kGammaMaxAttempts) {
+          G = __int_as_float(0x7fc00000);
+          finish = true;
+          rejected = true;
+        }
+      }
+      const float z = RN.get(finish, stream, a.rk);
+      if (finish) {
+        const float dm = xb - mu;
+        const float SS = fmaf(n * dm, dm, S);
+        tau = __fdividef(G, fmaf(0.5f, SS, a.b0));
+        const float P = fmaf(n, tau, a.prec0);
+        const float mean = __fdividef(fmaf(tau, nxb, prior_num), P);
+        mu = fmaf(z, rsqrtf(P), mean);
+        p0 += mu;
+        p1 += tau;
+        p2 = fmaf(mu, mu, p2);
+        p3 = fmaf(tau, tau, p3);
+        ++sweep;
+        att = 0;
       }
     }
-    const float z = RN.get(finish, stream, a.rk);
-    if (finish) {
-      const float dm = xb - mu;
-      const float SS = fmaf(n * dm, dm, S);
-      tau = G / fmaf(0.5f, SS, a.b0);
-      const float P = fmaf(n, tau, a.prec0);
-      const float mean = fmaf(tau, nxb, prior_num) / P;
-      mu = fmaf(z, rsqrtf(P), mean);
-      p0 += mu;
-      p1 += tau;
-      p2 = fmaf(mu, mu, p2);
-      p3 = fmaf(tau, tau, p3);
-      ++sweep;
-      att = 0;
-    }
-    if ((++it & 63u) == 0) {
-      d0 += p0; d1 += p1; d2 += p2; d3 += p3;
-      p0 = p1 = p2 = p3 = 0.0f;
-    }
+    d0 += p0; d1 += p1; d2 += p2; d3 += p3;
+    p0 = p1 = p2 = p3 = 0.0f;
   }
-  d0 += p0; d1 += p1; d2 += p2; d3 += p3;
   count_warp(&a.cnt->n_reject, rejected);
   if (active) {
     brng_normal_gamma_state_t s;

@@ -46,6 +46,7 @@ cudaError_t launch_philox_words(const RoundKeys& rk, uint32_t dom, uint32_t stre
 
 cudaError_t launch_philox_peak(const RoundKeys& rk, uint64_t iters, uint32_t blocks, uint32_t threads,
                                uint32_t* sink, cudaStream_t st);
+cudaError_t launch_fp32_eval(uint32_t fn, size_t n, const float* in, float* out, cudaStream_t st);
 cudaError_t launch_fp64_eval(uint32_t fn, size_t n, const double* in, double* out, cudaStream_t st);
 
 // ---- Dirichlet rows and LDA sweeps (brng_dirichlet.cu) ----

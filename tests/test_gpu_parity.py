@@ -105,6 +105,44 @@ def test_fp64_sincospi_bit_exact_exhaustive():
     assert np.array_equal(H(out).view(np.int64), c_ref.view(np.int64))
 
 
+def _ulp32(v):
+    return np.spacing(np.abs(v).astype(np.float32)).astype(np.float64)
+
+
+def test_fp32_log_error_bound():
+    """The FP32 log of the base conversions (no conversion instructions):
+    within 4 ulp of the true value over every U' the buffers produce and over
+    the t = 1 + cz and d v ranges of the Gamma test."""
+    k = np.arange(1 << 24, dtype=np.float64)
+    rng = np.random.default_rng(2)
+    x = np.concatenate([(k + 1) * 2.0**-24, rng.uniform(0.05, 3.0, 1 << 20),
+                        np.exp(rng.uniform(-30, 30, 1 << 18))]).astype(np.float32)
+    out = torch.empty(x.size, dtype=torch.float32, device=DEV)
+    B.brng_fp32_eval(0, T(x), out)
+    ref = O.log(x.astype(np.float64))
+    err = np.abs(H(out).astype(np.float64) - ref)
+    ratio = err / np.maximum(_ulp32(ref), 1e-45)
+    print("flog max error %.2f ulp" % ratio.max())
+    assert ratio.max() <= 4.0
+    assert H(out)[(1 << 24) - 1] == 0.0  # log 1 = 0 exactly
+
+
+def test_fp32_sincospi_error_bound():
+    """sin/cos of pi k 2^-23 over every 24-bit k (every Box-Muller angle):
+    within 2 ulp of the true value; exact at multiples of pi/2."""
+    k = np.arange(1 << 24, dtype=np.float32)
+    s_ref, c_ref = O.sincospi(np.arange(1 << 24, dtype=np.float64) * 2.0**-23)
+    out = torch.empty(k.size, dtype=torch.float32, device=DEV)
+    for fn, ref in ((1, s_ref), (2, c_ref)):
+        B.brng_fp32_eval(fn, T(k), out)
+        g = H(out).astype(np.float64)
+        ratio = np.abs(g - ref) / np.maximum(_ulp32(ref), 1e-45)
+        print("sincospi fn %d max error %.2f ulp" % (fn, ratio.max()))
+        assert ratio.max() <= 2.0
+        for q in range(4):
+            assert g[q << 22] == np.round(ref[q << 22])
+
+
 # ---- varying-parameter streams ----------------------------------------------
 
 def _params(fn, n, seed):
