@@ -281,6 +281,46 @@ int brng_gibbs_run(brng_t *h, brng_model_t model, uint64_t chain_offset, uint32_
                    uint32_t n_sweeps, const void *params, void *state, double *moments,
                    brng_stream_t stream);
 
+/* ---- batched Gibbs jobs: uneven ensembles in one persistent kernel ---------
+ * Batching/serving (the paper's asynchronous-service idea, Sec. 3 item 3): a
+ * job is the argument list of one brng_gibbs_run plus its own seed.  All jobs
+ * of a batch run in ONE launch: each job splits into units of one warp (32
+ * triangle or normal-gamma chains, one LDA document); resident warps claim
+ * units from a counter, longest units first.  Every job's results are
+ * identical to brng_gibbs_run on a handle created with the job's seed and the
+ * same tuning (lanes_per_chain is 1 inside a batch), because each unit runs
+ * the same code on the same streams.  Jobs of one batch must not share state
+ * or output memory. */
+typedef struct {
+  brng_model_t model;
+  uint32_t n_chains;     /* chains (documents for LDA); 0 = empty job      */
+  uint32_t n_sweeps;
+  uint32_t pad;
+  uint64_t seed;         /* the job's Philox key                             */
+  uint64_t chain_offset; /* global chain id of the job's first chain         */
+  const void *params;    /* as brng_gibbs_run (host struct or NULL), read at */
+  void *state;           /*   planning time; device state / moments as       */
+  double *moments;       /*   brng_gibbs_run                                  */
+} brng_job_t;
+
+typedef struct brng_batch brng_batch_t;
+
+/* brng_batch_create: validate the jobs and upload their table (synchronous;
+ * allocates device memory); brng_batch_launch: reset the unit counter and
+ * launch the persistent kernel on `stream` (two stream operations, no host
+ * synchronisation: it can be captured in a CUDA graph and replayed, each
+ * replay continuing every job's chains); brng_batch_destroy frees it (no
+ * launch may be in flight).  Errors: BRNG_EINVAL for a bad job (the first
+ * one found), else CUDA errors. */
+int brng_batch_create(brng_t *h, const brng_job_t *jobs, uint32_t n_jobs, brng_batch_t **out);
+int brng_batch_launch(brng_batch_t *b, brng_stream_t stream);
+int brng_batch_destroy(brng_batch_t *b);
+
+/* brng_gibbs_batch: plan + launch in one call, using table memory owned by
+ * the handle (grown as needed); asynchronous on `stream`.  Calls on one
+ * handle must be ordered (one stream). */
+int brng_gibbs_batch(brng_t *h, const brng_job_t *jobs, uint32_t n_jobs, brng_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,12 @@ class brng_lda_state_t(C.Structure):
     _fields_ = [("theta", C.c_void_p), ("pos", C.c_void_p)]
 
 
+class brng_job_t(C.Structure):
+    _fields_ = [("model", C.c_int), ("n_chains", C.c_uint32), ("n_sweeps", C.c_uint32),
+                ("pad", C.c_uint32), ("seed", C.c_uint64), ("chain_offset", C.c_uint64),
+                ("params", C.c_void_p), ("state", C.c_void_p), ("moments", C.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libbrng.so not built (%s); run __graft_entry__.build()" % LIB_PATH)
@@ -86,6 +92,10 @@ def _load():
         "brng_dirichlet": ([vp, sz, u32, vp, vp, vp], i32),
         "brng_gamma_static": ([u64, u32, sz, vp, vp, vp, vp], i32),
         "brng_gibbs_run": ([vp, i32, u64, u32, u32, vp, vp, vp, vp], i32),
+        "brng_batch_create": ([vp, vp, u32, C.POINTER(vp)], i32),
+        "brng_batch_launch": ([vp, vp], i32),
+        "brng_batch_destroy": ([vp], i32),
+        "brng_gibbs_batch": ([vp, vp, u32, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -279,6 +289,47 @@ def brng_gibbs_run(h, model, chain_offset, n_chains, n_sweeps, params, state, mo
     return _check("brng_gibbs_run", lib.brng_gibbs_run(
         h, int(model), int(chain_offset), int(n_chains), int(n_sweeps), ref(params), ref(state),
         _ptr(moments, torch.float64, "moments"), _stream(stream)))
+
+
+def make_job(model, n_chains, n_sweeps, seed, params, state, moments, chain_offset=0):
+    """A brng_job_t; `params` / `state` as for brng_gibbs_run (a ctypes
+    structure is referenced by address, so keep it alive while the job is
+    used).  Returns (job, keepalive)."""
+    def addr(x):
+        if x is None:
+            return None
+        if isinstance(x, C.Structure):
+            return C.addressof(x)
+        return _ptr(x, None, "state")
+    j = brng_job_t(int(model), int(n_chains), int(n_sweeps), 0, int(seed) & (2**64 - 1),
+                   int(chain_offset), addr(params), addr(state), _ptr(moments, None, "moments"))
+    return j, (params, state, moments)
+
+
+def _job_array(jobs):
+    arr = (brng_job_t * len(jobs))(*jobs)
+    return arr
+
+
+def brng_gibbs_batch(h, jobs, stream=None):
+    arr = _job_array(jobs)
+    return _check("brng_gibbs_batch", lib.brng_gibbs_batch(h, C.cast(arr, C.c_void_p), len(jobs),
+                                                           _stream(stream)))
+
+
+def brng_batch_create(h, jobs):
+    arr = _job_array(jobs)
+    b = C.c_void_p()
+    _check("brng_batch_create", lib.brng_batch_create(h, C.cast(arr, C.c_void_p), len(jobs), C.byref(b)))
+    return b
+
+
+def brng_batch_launch(b, stream=None):
+    return _check("brng_batch_launch", lib.brng_batch_launch(b, _stream(stream)))
+
+
+def brng_batch_destroy(b):
+    return _check("brng_batch_destroy", lib.brng_batch_destroy(b))
 
 
 # ---- state layouts (marshalling of the C structs held in device tensors) ------

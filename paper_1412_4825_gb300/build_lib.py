@@ -19,7 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbrng.so")
-SOURCES = ["brng_api.cu", "brng_bulk.cu", "brng_dirichlet.cu", "brng_gibbs.cu", "brng_static.cu"]
+SOURCES = ["brng_api.cu", "brng_bulk.cu", "brng_dirichlet.cu", "brng_gibbs.cu", "brng_static.cu",
+           "brng_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -3,6 +3,7 @@
 // the kernels of brng_bulk.cu, brng_dirichlet.cu and brng_gibbs.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -20,6 +21,9 @@ struct brng_handle {
   uint64_t* d_pos;            // SoA [3][S]: U, N, E positions of every stream
   brng::DevCounters* d_cnt;   // device counters
   int device;
+  brng::BatchJob* d_batch_jobs = nullptr;        // brng_gibbs_batch job table
+  size_t batch_cap = 0;
+  unsigned long long* d_batch_counter = nullptr;  // brng_gibbs_batch unit counter
 };
 
 namespace {
@@ -109,6 +113,8 @@ int brng_create(uint64_t seed, uint32_t n_streams, uint32_t buf_len, brng_t** ou
 
 int brng_destroy(brng_t* h) {
   if (!h) return BRNG_OK;
+  cudaFree(h->d_batch_jobs);
+  cudaFree(h->d_batch_counter);
   cudaError_t e1 = cudaFree(h->d_pos);
   cudaError_t e2 = cudaFree(h->d_cnt);
   delete h;
@@ -262,37 +268,39 @@ int brng_dirichlet(brng_t* h, size_t n_rows, uint32_t K, const float* alpha, flo
   return cuda_status(brng::launch_dirichlet(a, g, false, reinterpret_cast<cudaStream_t>(stream)));
 }
 
-int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_t n_chains,
-                   uint32_t n_sweeps, const void* params, void* state, double* moments,
-                   brng_stream_t stream) {
-  if (!h) return BRNG_EINVAL;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (n_chains == 0) return BRNG_OK;
+}  // extern "C"
+
+namespace {
+
+// Validates one Gibbs job and fills its kernel arguments (model args of a
+// BatchJob; the other two model slots are left zero).  `seed_rk`: the job's
+// round keys.
+int make_job(const brng_t* h, brng_model_t model, const brng::RoundKeys& rk, uint64_t chain_offset,
+             uint32_t n_chains, uint32_t n_sweeps, const void* params, void* state, double* moments,
+             brng::BatchJob* j) {
   if (!state || !moments) return BRNG_EINVAL;
+  *j = brng::BatchJob{};
+  j->model = static_cast<uint32_t>(model);
   switch (model) {
     case BRNG_MODEL_TRIANGLE: {
       if (chain_offset + n_chains > 0x100000000ull) return BRNG_EINVAL;
-      const uint32_t nc = 32 / h->tune.lanes_per_chain;
-      const brng::Geometry g = geometry(h, 128u + static_cast<size_t>(h->tune.buf_len) * nc * 8u);
-      if (g.warps_per_block == 0) return BRNG_EINVAL;
-      brng::TriangleArgs a;
-      a.rk = h->rk;
+      brng::TriangleArgs& a = j->tri;
+      a.rk = rk;
       a.chain_offset = chain_offset;
       a.n_chains = n_chains;
       a.n_sweeps = n_sweeps;
       a.B = h->tune.buf_len;
       a.state = static_cast<brng_triangle_state_t*>(state);
       a.moments = moments;
-      return cuda_status(brng::launch_triangle(a, g, h->tune.lanes_per_chain, st));
+      j->n_units = (static_cast<uint64_t>(n_chains) + 31) / 32;
+      return BRNG_OK;
     }
     case BRNG_MODEL_NORMAL_GAMMA: {
       const brng_normal_gamma_params_t* p = static_cast<const brng_normal_gamma_params_t*>(params);
       if (!p || !p->nobs || !p->xbar || !p->sc) return BRNG_EINVAL;
       if (chain_offset + n_chains > 0x100000000ull) return BRNG_EINVAL;
-      const brng::Geometry g = geometry(h, 128u + 2u * static_cast<size_t>(h->tune.buf_len) * 128u);
-      if (g.warps_per_block == 0) return BRNG_EINVAL;
-      brng::NormalGammaArgs a;
-      a.rk = h->rk;
+      brng::NormalGammaArgs& a = j->ng;
+      a.rk = rk;
       a.chain_offset = chain_offset;
       a.n_chains = n_chains;
       a.n_sweeps = n_sweeps;
@@ -307,19 +315,16 @@ int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_
       a.state = static_cast<brng_normal_gamma_state_t*>(state);
       a.moments = moments;
       a.cnt = h->d_cnt;
-      return cuda_status(brng::launch_normal_gamma(a, g, st));
+      j->n_units = (static_cast<uint64_t>(n_chains) + 31) / 32;
+      return BRNG_OK;
     }
     case BRNG_MODEL_LDA: {
       const brng_lda_params_t* p = static_cast<const brng_lda_params_t*>(params);
       const brng_lda_state_t* s = static_cast<const brng_lda_state_t*>(state);
       if (!p || !p->alpha || p->K == 0 || p->K > 128 || !s->theta || !s->pos) return BRNG_EINVAL;
       if ((chain_offset + n_chains) * static_cast<uint64_t>(p->K) > 0x100000000ull) return BRNG_EINVAL;
-      const uint32_t P = p->K <= 32 ? 1 : p->K <= 64 ? 2 : 4;
-      const size_t per_warp = 128u + h->tune.lookahead * 32u * P * 4u + 2u * P * h->tune.buf_len * 128u;
-      const brng::Geometry g = geometry(h, per_warp);
-      if (g.warps_per_block == 0) return BRNG_EINVAL;
-      brng::DirichletArgs a{};
-      a.rk = h->rk;
+      brng::DirichletArgs& a = j->lda;
+      a.rk = rk;
       a.K = p->K;
       a.B = h->tune.buf_len;
       a.lookahead = h->tune.lookahead;
@@ -331,11 +336,205 @@ int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_
       a.n_sweeps = n_sweeps;
       a.moments = moments;
       a.cnt = h->d_cnt;
-      return cuda_status(brng::launch_dirichlet(a, g, true, st));
+      j->n_units = n_chains;
+      return BRNG_OK;
     }
     default:
       return BRNG_EINVAL;
   }
+}
+
+uint32_t lda_p(uint32_t K) { return K <= 32 ? 1 : K <= 64 ? 2 : 4; }
+
+// relative cost of one unit-sweep by model (orders the batch: longest first)
+double unit_cost(const brng::BatchJob& j) {
+  switch (j.model) {
+    case BRNG_MODEL_TRIANGLE: return 1.0 * j.tri.n_sweeps;
+    case BRNG_MODEL_NORMAL_GAMMA: return 3.0 * j.ng.n_sweeps;
+    default: return 0.25 * j.lda.K * j.lda.n_sweeps;
+  }
+}
+
+}  // namespace
+
+struct brng_batch {
+  brng::BatchJob* d_jobs;
+  unsigned long long* d_counter;
+  brng::BatchArgs args;
+  uint32_t P;
+  uint32_t warps_per_block;
+  uint32_t blocks;  // grid, fixed when planned
+};
+
+namespace {
+
+// Builds the ordered job table of a batch on the host.
+int plan_batch(const brng_t* h, const brng_job_t* jobs, uint32_t n_jobs,
+               std::vector<brng::BatchJob>* table, uint32_t* P, uint32_t* wpb, uint32_t* warp_bytes) {
+  if (!h || (n_jobs && !jobs)) return BRNG_EINVAL;
+  table->clear();
+  table->reserve(n_jobs);
+  bool tri = false, ng = false, lda = false;
+  uint32_t maxP = 1;
+  for (uint32_t i = 0; i < n_jobs; ++i) {
+    const brng_job_t& jb = jobs[i];
+    if (jb.n_chains == 0) continue;
+    brng::BatchJob j;
+    const int st = make_job(h, jb.model, brng::make_round_keys(jb.seed), jb.chain_offset, jb.n_chains,
+                            jb.n_sweeps, jb.params, jb.state, jb.moments, &j);
+    if (st != BRNG_OK) return st;
+    tri |= jb.model == BRNG_MODEL_TRIANGLE;
+    ng |= jb.model == BRNG_MODEL_NORMAL_GAMMA;
+    if (jb.model == BRNG_MODEL_LDA) {
+      lda = true;
+      maxP = std::max(maxP, lda_p(j.lda.K));
+    }
+    table->push_back(j);
+  }
+  std::stable_sort(table->begin(), table->end(), [](const brng::BatchJob& a, const brng::BatchJob& b) {
+    return unit_cost(a) > unit_cost(b);
+  });
+  uint64_t first = 0;
+  for (auto& j : *table) {
+    j.first_unit = first;
+    first += j.n_units;
+  }
+  const size_t per_warp = brng::batch_warp_bytes(tri, ng, lda, h->tune.buf_len, maxP, h->tune.lookahead);
+  const brng::Geometry g = geometry(h, per_warp);
+  if (g.warps_per_block == 0) return BRNG_EINVAL;
+  *P = maxP;
+  *wpb = g.warps_per_block;
+  *warp_bytes = static_cast<uint32_t>(per_warp);
+  return BRNG_OK;
+}
+
+uint64_t total_units(const std::vector<brng::BatchJob>& t) {
+  return t.empty() ? 0 : t.back().first_unit + t.back().n_units;
+}
+
+}  // namespace
+
+extern "C" {
+
+int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_t n_chains,
+                   uint32_t n_sweeps, const void* params, void* state, double* moments,
+                   brng_stream_t stream) {
+  if (!h) return BRNG_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n_chains == 0) return BRNG_OK;
+  brng::BatchJob j;
+  const int rc = make_job(h, model, h->rk, chain_offset, n_chains, n_sweeps, params, state, moments, &j);
+  if (rc != BRNG_OK) return rc;
+  switch (model) {
+    case BRNG_MODEL_TRIANGLE: {
+      const uint32_t nc = 32 / h->tune.lanes_per_chain;
+      const brng::Geometry g = geometry(h, 128u + static_cast<size_t>(h->tune.buf_len) * nc * 8u);
+      if (g.warps_per_block == 0) return BRNG_EINVAL;
+      return cuda_status(brng::launch_triangle(j.tri, g, h->tune.lanes_per_chain, st));
+    }
+    case BRNG_MODEL_NORMAL_GAMMA: {
+      const brng::Geometry g = geometry(h, 128u + 2u * static_cast<size_t>(h->tune.buf_len) * 128u);
+      if (g.warps_per_block == 0) return BRNG_EINVAL;
+      return cuda_status(brng::launch_normal_gamma(j.ng, g, st));
+    }
+    default: {
+      const uint32_t P = lda_p(j.lda.K);
+      const size_t per_warp = 128u + h->tune.lookahead * 32u * P * 4u + 2u * P * h->tune.buf_len * 128u;
+      const brng::Geometry g = geometry(h, per_warp);
+      if (g.warps_per_block == 0) return BRNG_EINVAL;
+      return cuda_status(brng::launch_dirichlet(j.lda, g, true, st));
+    }
+  }
+}
+
+int brng_batch_create(brng_t* h, const brng_job_t* jobs, uint32_t n_jobs, brng_batch_t** out) {
+  if (!out) return BRNG_EINVAL;
+  std::vector<brng::BatchJob> table;
+  uint32_t P = 1, wpb = 1, wbytes = 128;
+  const int rc = plan_batch(h, jobs, n_jobs, &table, &P, &wpb, &wbytes);
+  if (rc != BRNG_OK) return rc;
+  brng_batch_t* b = new (std::nothrow) brng_batch_t();
+  if (!b) return BRNG_ENOMEM;
+  cudaError_t e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
+  if (e == cudaSuccess && !table.empty())
+    e = cudaMalloc(&b->d_jobs, sizeof(brng::BatchJob) * table.size());
+  if (e == cudaSuccess && !table.empty())
+    e = cudaMemcpy(b->d_jobs, table.data(), sizeof(brng::BatchJob) * table.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(b->d_counter);
+    cudaFree(b->d_jobs);
+    delete b;
+    return cuda_status(e);
+  }
+  b->args.jobs = b->d_jobs;
+  b->args.n_jobs = static_cast<uint32_t>(table.size());
+  b->args.warp_bytes = wbytes;
+  b->args.total_units = total_units(table);
+  b->args.counter = b->d_counter;
+  b->P = P;
+  b->warps_per_block = wpb;
+  e = brng::batch_grid(b->args, P, wpb, &b->blocks);
+  if (e != cudaSuccess) {
+    brng_batch_destroy(b);
+    return cuda_status(e);
+  }
+  *out = b;
+  return BRNG_OK;
+}
+
+int brng_batch_launch(brng_batch_t* b, brng_stream_t stream) {
+  if (!b) return BRNG_EINVAL;
+  if (b->args.total_units == 0) return BRNG_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = brng::launch_batch(b->args, b->P, b->warps_per_block, b->blocks, st);
+  return cuda_status(e);
+}
+
+int brng_batch_destroy(brng_batch_t* b) {
+  if (!b) return BRNG_OK;
+  cudaError_t e1 = cudaFree(b->d_jobs);
+  cudaError_t e2 = cudaFree(b->d_counter);
+  delete b;
+  return e1 != cudaSuccess ? cuda_status(e1) : cuda_status(e2);
+}
+
+int brng_gibbs_batch(brng_t* h, const brng_job_t* jobs, uint32_t n_jobs, brng_stream_t stream) {
+  std::vector<brng::BatchJob> table;
+  uint32_t P = 1, wpb = 1, wbytes = 128;
+  const int rc = plan_batch(h, jobs, n_jobs, &table, &P, &wpb, &wbytes);
+  if (rc != BRNG_OK) return rc;
+  if (table.empty()) return BRNG_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (table.size() > h->batch_cap) {  // grow the handle's table (cudaFree waits for the device)
+    cudaFree(h->d_batch_jobs);
+    h->d_batch_jobs = nullptr;
+    h->batch_cap = 0;
+    e = cudaMalloc(&h->d_batch_jobs, sizeof(brng::BatchJob) * table.size());
+    if (e != cudaSuccess) return cuda_status(e);
+    h->batch_cap = table.size();
+  }
+  if (!h->d_batch_counter) {
+    e = cudaMalloc(&h->d_batch_counter, sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  // from pageable memory: the call returns once the table is staged, so the
+  // vector may go; the copy is ordered on `stream` before the kernel
+  e = cudaMemcpyAsync(h->d_batch_jobs, table.data(), sizeof(brng::BatchJob) * table.size(),
+                      cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_batch_counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return cuda_status(e);
+  brng::BatchArgs a;
+  a.jobs = h->d_batch_jobs;
+  a.n_jobs = static_cast<uint32_t>(table.size());
+  a.warp_bytes = wbytes;
+  a.total_units = total_units(table);
+  a.counter = h->d_batch_counter;
+  uint32_t blocks = 0;
+  e = brng::batch_grid(a, P, wpb, &blocks);
+  if (e != cudaSuccess) return cuda_status(e);
+  return cuda_status(brng::launch_batch(a, P, wpb, blocks, st));
 }
 
 }  // extern "C"

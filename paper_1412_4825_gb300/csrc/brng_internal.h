@@ -94,4 +94,26 @@ struct NormalGammaArgs {
 };
 cudaError_t launch_normal_gamma(const NormalGammaArgs& a, const Geometry& g, cudaStream_t st);
 
+// ---- batched persistent kernel (brng_batch.cu) ----
+struct BatchJob {
+  uint32_t model;       // brng_model_t
+  uint32_t pad;
+  uint64_t first_unit;  // global index of the job's first unit (prefix sum)
+  uint64_t n_units;
+  TriangleArgs tri;
+  NormalGammaArgs ng;
+  DirichletArgs lda;
+};
+struct BatchArgs {
+  const BatchJob* jobs;  // device, ordered by first_unit
+  uint32_t n_jobs;
+  uint32_t warp_bytes;   // shared memory per warp (max over the models present)
+  uint64_t total_units;
+  unsigned long long* counter;  // device, zeroed before each launch
+};
+size_t batch_warp_bytes(bool tri, bool ng, bool lda, uint32_t B, uint32_t P, uint32_t Q);
+cudaError_t batch_grid(const BatchArgs& a, uint32_t P, uint32_t warps_per_block, uint32_t* blocks);
+cudaError_t launch_batch(const BatchArgs& a, uint32_t P, uint32_t warps_per_block, uint32_t blocks,
+                         cudaStream_t st);
+
 }  // namespace brng
