@@ -133,6 +133,149 @@ def run_reference(args):
     return 0
 
 
+def _time_s(fn, stream, reps=3, warm=1):
+    """Median seconds of `fn` (which enqueues on `stream`), CUDA events."""
+    import torch
+    for _ in range(warm):
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev) / 1e3
+
+
+def extras(dev, stream, peaks, args):
+    """Secondary workloads of the method (not the headline): the triangle
+    Gibbs sampler of Eq. 1 (1,024 chains x 10,000 sweeps, FP64), the LDA
+    document-topic step (16,384 documents x K=64 x 500 sweeps), the mixed
+    varying-parameter stream (2^28 draws over 2^20 streams, with its HBM
+    roofline), one uneven ensemble run batched vs one kernel per job, and the
+    served Poisson mix (2,000 jobs/s and a sub-capacity rate)."""
+    import numpy as np
+    import torch
+
+    from paper_1412_4825_gb300 import brng as B
+    from paper_1412_4825_gb300 import inputs, serve
+
+    out = {}
+    # -- triangle (Eq. 1, Fig. 1): buffers of 256 FP64 uniforms per chain
+    h = B.Handle(SEED, 1)
+    rec = {}
+    for lanes in (1, 4, 32):
+        h.tune(buf_len=256, lanes_per_chain=lanes)
+        st = B.triangle_state(1024, device=dev)
+        mom = torch.zeros((1024, 5), dtype=torch.float64, device=dev)
+        t = _time_s(lambda: B.brng_gibbs_run(h.h, B.MODEL_TRIANGLE, 0, 1024, 10000, None, st, mom, stream), stream)
+        rec[lanes] = 2 * 1024 * 10000 / t
+    best = max(rec, key=rec.get)
+    out["triangle_1024x10000"] = {"updates_per_s": rec[best], "ms": 2 * 1024 * 10000 / rec[best] * 1e3,
+                                  "lanes_per_chain": best, "by_lanes_per_chain": rec}
+    h.close()
+    # -- LDA document-topic Dirichlet step
+    alpha, _, _ = inputs.lda_alpha(16384, K=64, seed=SEED)
+    a = torch.from_numpy(alpha).to(dev)
+    theta = torch.zeros((16384, 64), dtype=torch.float32, device=dev)
+    pos = torch.zeros((16384, 64, 2), dtype=torch.int64, device=dev)
+    mom = torch.zeros((16384, 64), dtype=torch.float64, device=dev)
+    h = B.Handle(SEED, 1)
+    lp = B.brng_lda_params_t(64, a.data_ptr())
+    ls = B.brng_lda_state_t(theta.data_ptr(), pos.data_ptr())
+    t = _time_s(lambda: B.brng_gibbs_run(h.h, B.MODEL_LDA, 0, 16384, 500, lp, ls, mom, stream), stream)
+    out["lda_16384x64x500"] = {"dirichlet_updates_per_s": 16384 * 500 / t,
+                               "gamma_deviates_per_s": 16384 * 64 * 500 / t, "ms": t * 1e3,
+                               "tuning": h.tuning}
+    h.close()
+    del a, theta, pos, mom
+    # -- mixed varying-parameter stream, 17 B per draw through HBM
+    n, S = 1 << 28, 1 << 20
+    tag, p0, p1 = inputs.mixed_stream_torch(n, seed=SEED, device=dev)
+    o = torch.empty(n, dtype=torch.float32, device=dev)
+    w = torch.empty(n, dtype=torch.int32, device=dev)
+    hm = B.Handle(SEED, S)
+    rec = {}
+    for bl in (8, 16, 32):
+        hm.tune(buf_len=bl)
+        rec[bl] = _time_s(lambda: B.brng_mixed(hm.h, tag, p0, p1, o, w, stream), stream)
+    bl = min(rec, key=rec.get)
+    t = rec[bl]
+    gbs = 17.0 * n / t / 1e9
+    out["mixed_2^28"] = {"deviates_per_s": n / t, "ms": t * 1e3, "buf_len": bl,
+                         "ms_by_buf_len": {k: v * 1e3 for k, v in rec.items()},
+                         "hbm_achieved_gbs": gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                         "hbm_frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None}
+    hm.close()
+    del tag, p0, p1, o, w
+    torch.cuda.empty_cache()
+    # -- uneven ensemble: batched (one persistent launch) vs one kernel per job
+    rng = np.random.default_rng(SEED)
+    pool = serve.InputPool(65536, 64, SEED)
+    specs = []
+    for i in range(48):
+        model = int(rng.integers(0, 3))
+        nch = int(min(65536, max(1, np.exp(rng.uniform(0, np.log(65537))))))
+        specs.append((model, nch, int(rng.integers(100, 10001)), SEED + 1 + i))
+    d_nobs, d_xbar, d_sc = (torch.from_numpy(x).to(dev) for x in (pool.nobs, pool.xbar, pool.sc))
+    d_alpha = torch.from_numpy(pool.alpha).to(dev)
+    keep = []
+
+    def fresh_jobs():
+        jobs = []
+        for model, nch, sw, seed in specs:
+            if model == B.MODEL_TRIANGLE:
+                st, mm, prm = B.triangle_state(nch, device=dev), torch.zeros((nch, 5), dtype=torch.float64, device=dev), None
+                sarg = st
+            elif model == B.MODEL_NORMAL_GAMMA:
+                st, mm = B.normal_gamma_state(nch, device=dev), torch.zeros((nch, 4), dtype=torch.float64, device=dev)
+                prm = B.brng_normal_gamma_params_t(2.0, 1.0, 0.0, 0.01, d_nobs.data_ptr(), d_xbar.data_ptr(),
+                                                   d_sc.data_ptr())
+                sarg = st
+            else:
+                th = torch.zeros((nch, 64), dtype=torch.float32, device=dev)
+                ps = torch.zeros((nch, 64, 2), dtype=torch.int64, device=dev)
+                mm = torch.zeros((nch, 64), dtype=torch.float64, device=dev)
+                prm = B.brng_lda_params_t(64, d_alpha.data_ptr())
+                sarg = B.brng_lda_state_t(th.data_ptr(), ps.data_ptr())
+                keep.append((th, ps))
+            keep.append((sarg, mm, prm))
+            jobs.append((model, nch, sw, seed, prm, sarg, mm))
+        return jobs
+
+    upd = sum((1 if m == B.MODEL_LDA else 2) * c * s for m, c, s, _ in specs)
+    hb = B.Handle(SEED, 1)
+    handles = {seed: B.Handle(seed, 1) for _, _, _, seed in specs}
+    jobs = fresh_jobs()
+
+    def plain():
+        for model, nch, sw, seed, prm, sarg, mm in jobs:
+            B.brng_gibbs_run(handles[seed].h, model, 0, nch, sw, prm, sarg, mm, stream)
+
+    t_plain = _time_s(plain, stream, reps=2, warm=1)
+    jobs = fresh_jobs()
+    bjobs = [B.make_job(m, c, s, seed, prm, sarg, mm)[0] for m, c, s, seed, prm, sarg, mm in jobs]
+    t_batch = _time_s(lambda: B.brng_gibbs_batch(hb.h, bjobs, stream), stream, reps=2, warm=1)
+    out["ensemble_48_jobs"] = {"jobs": len(specs), "updates": upd, "plain_updates_per_s": upd / t_plain,
+                               "batched_updates_per_s": upd / t_batch, "batched_over_plain": t_plain / t_batch,
+                               "plain_ms": t_plain * 1e3, "batched_ms": t_batch * 1e3}
+    for hh in handles.values():
+        hh.close()
+    hb.close()
+    keep.clear()
+    jobs = bjobs = None
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    # -- served Poisson mix: the 2,000 jobs/s rate for a bounded window, and a sub-capacity rate
+    full = serve.run_mix(serve.MixSpec(rate=2000.0, duration=args.serve_seconds, seed=SEED), pool=pool,
+                         drain_s=args.serve_seconds)
+    sub = serve.run_mix(serve.MixSpec(rate=10.0, duration=max(2.0, args.serve_seconds / 2), seed=SEED + 1),
+                        pool=pool, drain_s=60.0)
+    out["served_2000_per_s"] = full.summary()
+    out["served_10_per_s"] = sub.summary()
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -149,10 +292,13 @@ def run_gpu(args):
     from paper_1412_4825_gb300 import build_lib
     build_lib.build()
     from paper_1412_4825_gb300 import brng as B
-    from paper_1412_4825_gb300 import inputs
+    from paper_1412_4825_gb300 import inputs, shard
 
-    chain_offset = rank * N_CHAINS
-    nobs, xbar, sc = inputs.normal_gamma_data(N_CHAINS, n_obs=N_OBS, seed=SEED + rank)
+    # weak scaling: rank r runs global chains [r*N, (r+1)*N) on its slice of
+    # one global data set, so any rank count reproduces the one-GPU chains
+    chain_offset, _ = shard.weak_range(N_CHAINS, rank)
+    nobs, xbar, sc = (a[chain_offset:chain_offset + N_CHAINS] for a in
+                      inputs.normal_gamma_data(chain_offset + N_CHAINS, n_obs=N_OBS, seed=SEED))
     stream = torch.cuda.Stream(device=dev)
     h = B.Handle(SEED, 1)
     if args.buf_len or args.warps_per_block:
@@ -207,10 +353,9 @@ def run_gpu(args):
     wall = time.perf_counter() - wall0
     clocks = _clock_summary(sampler) if rank == 0 else None
     ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = torch.tensor([sum(ms)], dtype=torch.float64, device=dev)
+    total_s = sum(ms) / 1e3
     if pg is not None:
-        pg.all_reduce(total_ms, op=pg.ReduceOp.MAX)
-    total_s = float(total_ms.item()) / 1e3
+        total_s = shard.max_over_ranks(pg, total_s, device=dev)
     value = world * UPDATES_PER_STEP * args.steps / total_s
 
     # end to end through the public API: host inputs -> device -> run -> host results
@@ -237,10 +382,10 @@ def run_gpu(args):
             h_mom.copy_(mom, non_blocking=True)
             e_ev[k][1].record(stream)
     barrier()
-    e_ms = torch.tensor([sum(a.elapsed_time(b) for a, b in e_ev)], dtype=torch.float64, device=dev)
+    e_s = sum(a.elapsed_time(b) for a, b in e_ev) / 1e3
     if pg is not None:
-        pg.all_reduce(e_ms, op=pg.ReduceOp.MAX)
-    e2e_value = world * UPDATES_PER_STEP * args.steps / (float(e_ms.item()) / 1e3)
+        e_s = shard.max_over_ranks(pg, e_s, device=dev)
+    e2e_value = world * UPDATES_PER_STEP * args.steps / e_s
 
     # integer-pipe roofline: Philox blocks the step consumed / kernel time,
     # against 152 SMs x (64 32-bit multiply results per clock per SM / 2 per
@@ -289,6 +434,11 @@ def run_gpu(args):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+    if world == 1 and not args.no_extras:
+        try:
+            line["extra"] = extras(dev, stream, peaks, args)
+        except Exception as exc:  # the headline line is printed regardless
+            line["extra"] = {"error": repr(exc)}
     print(json.dumps(line), flush=True)
     if pg is not None:
         pg.barrier()
@@ -304,6 +454,10 @@ def main():
     ap.add_argument("--buf-len", type=int, default=0)
     ap.add_argument("--warps-per-block", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary workloads (triangle, LDA, mixed stream, batched vs plain, served mix)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="arrival window of the served mix at 2,000 jobs/s")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

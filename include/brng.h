@@ -321,6 +321,67 @@ int brng_batch_destroy(brng_batch_t *b);
  * handle must be ordered (one stream). */
 int brng_gibbs_batch(brng_t *h, const brng_job_t *jobs, uint32_t n_jobs, brng_stream_t stream);
 
+/* ---- serving: continuous batching of Gibbs jobs ------------------------------
+ * A server owns a scheduler thread on the current device.  brng_serve_submit
+ * queues a job (copying its host inputs) and returns at once.  The scheduler
+ * admits queued jobs in arrival order while their device memory (state,
+ * moments, inputs) fits `mem_budget` bytes, and launches every admitted job
+ * not yet running as one batch on one of `max_inflight` streams, so work that
+ * arrives while earlier batches run starts at once and overlaps with them on
+ * the device.  A served job gives exactly the results of brng_gibbs_run for
+ * it alone (its own seed, start state x = y = 0.5 / mu = mu0 / empty LDA
+ * positions, zero moments).  Results stay on the device until
+ * brng_serve_result copies them to the host (state as in brng_gibbs_run; for
+ * LDA the last theta, float [n][K]) and returns the memory to the budget:
+ * collect every job, or admission stalls.  A job larger than the whole budget
+ * fails with BRNG_ENOMEM. */
+typedef struct brng_server brng_server_t;
+
+typedef struct {
+  brng_model_t model;
+  uint32_t n_chains;     /* chains (documents for LDA), >= 1                  */
+  uint32_t n_sweeps;
+  uint32_t K;            /* LDA topics                                        */
+  uint64_t seed;
+  uint64_t chain_offset;
+  const float *nobs;     /* host [n] (NORMAL_GAMMA), copied at submit          */
+  const float *xbar;     /* host [n]                                          */
+  const float *sc;       /* host [n]                                          */
+  const float *alpha;    /* host [n][K] (LDA), copied at submit               */
+  float a0, b0, mu0, prec0; /* NORMAL_GAMMA priors                             */
+  uint32_t flags;        /* BRNG_SERVE_BORROW_INPUTS: the host arrays stay valid */
+  uint32_t pad;          /*   until the job finishes and are read at admission  */
+} brng_request_t;        /*   instead of being copied at submit                  */
+
+#define BRNG_SERVE_BORROW_INPUTS 1u
+
+typedef struct {
+  uint64_t submitted_ns, admitted_ns, launched_ns, completed_ns; /* steady clock */
+  uint64_t device_bytes;
+  int32_t status;
+  uint32_t pad;
+} brng_job_info_t;
+
+typedef struct {
+  uint64_t submitted, admitted, completed, refused, batches, queued, device_bytes_in_use;
+} brng_serve_stats_t;
+
+int brng_serve_open(uint64_t mem_budget, uint32_t max_inflight, const brng_tuning_t *tuning,
+                    brng_server_t **out);
+int brng_serve_submit(brng_server_t *s, const brng_request_t *req, uint64_t *job_id);
+/* *done = 1 once finished (or failed; the return value is then its status) */
+int brng_serve_poll(brng_server_t *s, uint64_t job_id, int *done);
+/* blocks up to timeout_s; BRNG_EAGAIN on timeout */
+int brng_serve_wait(brng_server_t *s, uint64_t job_id, double timeout_s);
+/* host_state / host_moments may be NULL; BRNG_EAGAIN if not finished; the
+ * job is forgotten afterwards (BRNG_ENOTFOUND on a second call) */
+int brng_serve_result(brng_server_t *s, uint64_t job_id, void *host_state, double *host_moments,
+                      brng_job_info_t *info);
+int brng_serve_stats(brng_server_t *s, brng_serve_stats_t *out);
+/* cancels jobs still waiting for memory, finishes the admitted ones, frees
+ * everything; uncollected results are lost */
+int brng_serve_close(brng_server_t *s);
+
 #ifdef __cplusplus
 }
 #endif

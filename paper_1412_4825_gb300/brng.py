@@ -63,6 +63,29 @@ class brng_job_t(C.Structure):
                 ("params", C.c_void_p), ("state", C.c_void_p), ("moments", C.c_void_p)]
 
 
+class brng_request_t(C.Structure):
+    _fields_ = [("model", C.c_int), ("n_chains", C.c_uint32), ("n_sweeps", C.c_uint32), ("K", C.c_uint32),
+                ("seed", C.c_uint64), ("chain_offset", C.c_uint64), ("nobs", C.c_void_p),
+                ("xbar", C.c_void_p), ("sc", C.c_void_p), ("alpha", C.c_void_p), ("a0", C.c_float),
+                ("b0", C.c_float), ("mu0", C.c_float), ("prec0", C.c_float), ("flags", C.c_uint32),
+                ("pad", C.c_uint32)]
+
+
+SERVE_BORROW_INPUTS = 1
+
+
+class brng_job_info_t(C.Structure):
+    _fields_ = [("submitted_ns", C.c_uint64), ("admitted_ns", C.c_uint64), ("launched_ns", C.c_uint64),
+                ("completed_ns", C.c_uint64), ("device_bytes", C.c_uint64), ("status", C.c_int32),
+                ("pad", C.c_uint32)]
+
+
+class brng_serve_stats_t(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
+                ("refused", C.c_uint64), ("batches", C.c_uint64), ("queued", C.c_uint64),
+                ("device_bytes_in_use", C.c_uint64)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libbrng.so not built (%s); run __graft_entry__.build()" % LIB_PATH)
@@ -96,6 +119,13 @@ def _load():
         "brng_batch_launch": ([vp, vp], i32),
         "brng_batch_destroy": ([vp], i32),
         "brng_gibbs_batch": ([vp, vp, u32, vp], i32),
+        "brng_serve_open": ([u64, u32, vp, C.POINTER(vp)], i32),
+        "brng_serve_submit": ([vp, C.POINTER(brng_request_t), C.POINTER(u64)], i32),
+        "brng_serve_poll": ([vp, u64, C.POINTER(C.c_int)], i32),
+        "brng_serve_wait": ([vp, u64, C.c_double], i32),
+        "brng_serve_result": ([vp, u64, vp, vp, C.POINTER(brng_job_info_t)], i32),
+        "brng_serve_stats": ([vp, C.POINTER(brng_serve_stats_t)], i32),
+        "brng_serve_close": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -330,6 +360,49 @@ def brng_batch_launch(b, stream=None):
 
 def brng_batch_destroy(b):
     return _check("brng_batch_destroy", lib.brng_batch_destroy(b))
+
+
+def brng_serve_open(mem_budget, max_inflight=4, buf_len=0, warps_per_block=0, lookahead=0):
+    s = C.c_void_p()
+    t = brng_tuning_t(buf_len, warps_per_block, 0, lookahead)
+    _check("brng_serve_open", lib.brng_serve_open(int(mem_budget), int(max_inflight), C.byref(t), C.byref(s)))
+    return s
+
+
+def brng_serve_submit(s, req):
+    """`req`: a brng_request_t whose host arrays stay alive until the call returns."""
+    jid = C.c_uint64()
+    _check("brng_serve_submit", lib.brng_serve_submit(s, C.byref(req), C.byref(jid)))
+    return jid.value
+
+
+def brng_serve_poll(s, job_id):
+    done = C.c_int()
+    code = lib.brng_serve_poll(s, job_id, C.byref(done))
+    return code, bool(done.value)
+
+
+def brng_serve_wait(s, job_id, timeout_s):
+    return lib.brng_serve_wait(s, job_id, float(timeout_s))
+
+
+def brng_serve_result(s, job_id, host_state=None, host_moments=None):
+    """host_state / host_moments: writable numpy arrays (or None)."""
+    info = brng_job_info_t()
+    ps = None if host_state is None else host_state.ctypes.data_as(C.c_void_p)
+    pm = None if host_moments is None else host_moments.ctypes.data_as(C.c_void_p)
+    code = lib.brng_serve_result(s, job_id, ps, pm, C.byref(info))
+    return code, {f: getattr(info, f) for f, _ in info._fields_ if f != "pad"}
+
+
+def brng_serve_stats(s):
+    st = brng_serve_stats_t()
+    code = lib.brng_serve_stats(s, C.byref(st))
+    return code, {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def brng_serve_close(s):
+    return _check("brng_serve_close", lib.brng_serve_close(s))
 
 
 # ---- state layouts (marshalling of the C structs held in device tensors) ------

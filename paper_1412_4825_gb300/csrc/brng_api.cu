@@ -500,41 +500,51 @@ int brng_batch_destroy(brng_batch_t* b) {
 }
 
 int brng_gibbs_batch(brng_t* h, const brng_job_t* jobs, uint32_t n_jobs, brng_stream_t stream) {
-  std::vector<brng::BatchJob> table;
+  if (!h) return BRNG_EINVAL;
+  return brng::batch_launch_into(h, jobs, n_jobs, &h->d_batch_jobs, &h->batch_cap,
+                                 &h->d_batch_counter, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+namespace brng {
+
+int batch_launch_into(brng_t* h, const brng_job_t* jobs, uint32_t n_jobs, BatchJob** d_table,
+                      size_t* cap, unsigned long long** d_counter, cudaStream_t st) {
+  std::vector<BatchJob> table;
   uint32_t P = 1, wpb = 1, wbytes = 128;
   const int rc = plan_batch(h, jobs, n_jobs, &table, &P, &wpb, &wbytes);
   if (rc != BRNG_OK) return rc;
   if (table.empty()) return BRNG_OK;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
-  if (table.size() > h->batch_cap) {  // grow the handle's table (cudaFree waits for the device)
-    cudaFree(h->d_batch_jobs);
-    h->d_batch_jobs = nullptr;
-    h->batch_cap = 0;
-    e = cudaMalloc(&h->d_batch_jobs, sizeof(brng::BatchJob) * table.size());
+  if (table.size() > *cap) {  // grow the table (cudaFree waits for the device)
+    cudaFree(*d_table);
+    *d_table = nullptr;
+    *cap = 0;
+    e = cudaMalloc(d_table, sizeof(BatchJob) * table.size());
     if (e != cudaSuccess) return cuda_status(e);
-    h->batch_cap = table.size();
+    *cap = table.size();
   }
-  if (!h->d_batch_counter) {
-    e = cudaMalloc(&h->d_batch_counter, sizeof(unsigned long long));
+  if (!*d_counter) {
+    e = cudaMalloc(d_counter, sizeof(unsigned long long));
     if (e != cudaSuccess) return cuda_status(e);
   }
   // from pageable memory: the call returns once the table is staged, so the
-  // vector may go; the copy is ordered on `stream` before the kernel
-  e = cudaMemcpyAsync(h->d_batch_jobs, table.data(), sizeof(brng::BatchJob) * table.size(),
-                      cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_batch_counter, 0, sizeof(unsigned long long), st);
+  // vector may go; the copy is ordered on `st` before the kernel
+  e = cudaMemcpyAsync(*d_table, table.data(), sizeof(BatchJob) * table.size(), cudaMemcpyHostToDevice,
+                      st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(*d_counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return cuda_status(e);
-  brng::BatchArgs a;
-  a.jobs = h->d_batch_jobs;
+  BatchArgs a;
+  a.jobs = *d_table;
   a.n_jobs = static_cast<uint32_t>(table.size());
   a.warp_bytes = wbytes;
   a.total_units = total_units(table);
-  a.counter = h->d_batch_counter;
+  a.counter = *d_counter;
   uint32_t blocks = 0;
-  e = brng::batch_grid(a, P, wpb, &blocks);
+  e = batch_grid(a, P, wpb, &blocks);
   if (e != cudaSuccess) return cuda_status(e);
-  return cuda_status(brng::launch_batch(a, P, wpb, blocks, st));
+  return cuda_status(launch_batch(a, P, wpb, blocks, st));
 }
 
-}  // extern "C"
+}  // namespace brng

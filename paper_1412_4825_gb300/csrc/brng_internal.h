@@ -113,6 +113,10 @@ struct BatchArgs {
 };
 size_t batch_warp_bytes(bool tri, bool ng, bool lda, uint32_t B, uint32_t P, uint32_t Q);
 cudaError_t batch_grid(const BatchArgs& a, uint32_t P, uint32_t warps_per_block, uint32_t* blocks);
+// Plans `jobs` with the handle's tuning and launches them as one batch on
+// `st`, using (and growing) the caller's device table and counter.
+int batch_launch_into(brng_t* h, const brng_job_t* jobs, uint32_t n_jobs, BatchJob** d_table,
+                      size_t* cap, unsigned long long** d_counter, cudaStream_t st);
 cudaError_t launch_batch(const BatchArgs& a, uint32_t P, uint32_t warps_per_block, uint32_t blocks,
                          cudaStream_t st);
 
