@@ -82,7 +82,7 @@ typedef struct {
   uint64_t n_recheck;  /* Gamma tests re-decided in FP64 (FP32 margin within tolerance) */
   uint64_t n_flip;     /* ... of which the FP64 decision differed from the FP32 sign  */
   float max_flip_ratio;/* max |FP32 margin| / tolerance over the flips (must stay < 1) */
-  uint32_t pad;
+  uint32_t n_timeout;  /* bounded device waits that ran out (chains ended with NaN)  */
 } brng_counters_t;
 
 /* Tuning knobs; zero fields mean "library default". */
@@ -91,7 +91,12 @@ typedef struct {
   uint32_t warps_per_block; /* 1..16                                                         */
   uint32_t lanes_per_chain; /* triangle model only: 1, 2, 4, 8, 16 or 32                       */
   uint32_t lookahead;       /* Dirichlet/LDA: sweeps a component may run ahead, 1..16         */
+  uint32_t producer_warps;  /* normal-gamma brng_gibbs_run: warps per block that only refill  */
+                            /* the rings while the others sample (asynchronous replenishment, */
+                            /* Sec. 4), 1..8, or BRNG_PRODUCERS_NONE: each warp refills its   */
+                            /* own rings when they run dry (Sec. 2.2).  Results are the same. */
 } brng_tuning_t;
+#define BRNG_PRODUCERS_NONE 0xffffffffu
 
 /* ---- handle (Sec. 2.2 constructor / destructor) ---------------------------
  * brng_create: a handle with `n_streams` streams (>= 1, < 2^32) keyed by

@@ -33,12 +33,16 @@ class BrngError(RuntimeError):
 
 class brng_tuning_t(C.Structure):
     _fields_ = [("buf_len", C.c_uint32), ("warps_per_block", C.c_uint32),
-                ("lanes_per_chain", C.c_uint32), ("lookahead", C.c_uint32)]
+                ("lanes_per_chain", C.c_uint32), ("lookahead", C.c_uint32),
+                ("producer_warps", C.c_uint32)]
+
+
+PRODUCERS_NONE = 0xFFFFFFFF
 
 
 class brng_counters_t(C.Structure):
     _fields_ = [("n_domain", C.c_uint64), ("n_reject", C.c_uint64), ("n_recheck", C.c_uint64),
-                ("n_flip", C.c_uint64), ("max_flip_ratio", C.c_float), ("pad", C.c_uint32)]
+                ("n_flip", C.c_uint64), ("max_flip_ratio", C.c_float), ("n_timeout", C.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
@@ -187,8 +191,8 @@ def brng_destroy(h):
     return _check("brng_destroy", lib.brng_destroy(h))
 
 
-def brng_set_tuning(h, buf_len=0, warps_per_block=0, lanes_per_chain=0, lookahead=0):
-    t = brng_tuning_t(buf_len, warps_per_block, lanes_per_chain, lookahead)
+def brng_set_tuning(h, buf_len=0, warps_per_block=0, lanes_per_chain=0, lookahead=0, producer_warps=0):
+    t = brng_tuning_t(buf_len, warps_per_block, lanes_per_chain, lookahead, producer_warps)
     return _check("brng_set_tuning", lib.brng_set_tuning(h, C.byref(t)))
 
 
@@ -364,7 +368,7 @@ def brng_batch_destroy(b):
 
 def brng_serve_open(mem_budget, max_inflight=4, buf_len=0, warps_per_block=0, lookahead=0):
     s = C.c_void_p()
-    t = brng_tuning_t(buf_len, warps_per_block, 0, lookahead)
+    t = brng_tuning_t(buf_len, warps_per_block, 0, lookahead, 0)
     _check("brng_serve_open", lib.brng_serve_open(int(mem_budget), int(max_inflight), C.byref(t), C.byref(s)))
     return s
 

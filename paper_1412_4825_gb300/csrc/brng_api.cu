@@ -93,6 +93,7 @@ int brng_create(uint64_t seed, uint32_t n_streams, uint32_t buf_len, brng_t** ou
   h->tune.warps_per_block = brng::kDefaultWarpsPerBlock;
   h->tune.lanes_per_chain = 1;
   h->tune.lookahead = brng::kDefaultLookahead;
+  h->tune.producer_warps = brng::kDefaultProducerWarps;
   h->rk = brng::make_round_keys(seed);
   cudaGetDevice(&h->device);
   const size_t pos_bytes = sizeof(uint64_t) * 3ull * n_streams;
@@ -128,10 +129,13 @@ int brng_set_tuning(brng_t* h, const brng_tuning_t* t) {
   if (t->warps_per_block) n.warps_per_block = t->warps_per_block;
   if (t->lanes_per_chain) n.lanes_per_chain = t->lanes_per_chain;
   if (t->lookahead) n.lookahead = t->lookahead;
+  if (t->producer_warps) n.producer_warps = t->producer_warps;
   if (!pow2_in(n.buf_len, 4, brng::kMaxBufLen)) return BRNG_EINVAL;
   if (n.warps_per_block < 1 || n.warps_per_block > 16) return BRNG_EINVAL;
   if (!pow2_in(n.lanes_per_chain, 1, 32)) return BRNG_EINVAL;
   if (n.lookahead < 1 || n.lookahead > 16) return BRNG_EINVAL;
+  if (n.producer_warps != BRNG_PRODUCERS_NONE && (n.producer_warps < 1 || n.producer_warps > 8))
+    return BRNG_EINVAL;
   h->tune = n;
   return BRNG_OK;
 }
@@ -433,6 +437,13 @@ int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_
       return cuda_status(brng::launch_triangle(j.tri, g, h->tune.lanes_per_chain, st));
     }
     case BRNG_MODEL_NORMAL_GAMMA: {
+      const uint32_t Wp = h->tune.producer_warps;
+      if (Wp != BRNG_PRODUCERS_NONE) {  // consumer warps + producer warps per block
+        const brng::Geometry g = geometry(h, brng::normal_gamma_pc_bytes_per_warp(h->tune.buf_len));
+        const uint32_t Wc = std::min({g.warps_per_block, 16u - Wp, 8u * Wp});
+        if (Wc == 0) return BRNG_EINVAL;
+        return cuda_status(brng::launch_normal_gamma_pc(j.ng, Wc, Wp, st));
+      }
       const brng::Geometry g = geometry(h, 128u + 2u * static_cast<size_t>(h->tune.buf_len) * 128u);
       if (g.warps_per_block == 0) return BRNG_EINVAL;
       return cuda_status(brng::launch_normal_gamma(j.ng, g, st));

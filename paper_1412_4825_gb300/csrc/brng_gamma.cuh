@@ -40,7 +40,7 @@ constexpr float kSeriesMaxX = 0.25f;
 struct DevCounters {
   unsigned long long n_domain, n_reject, n_recheck, n_flip;
   unsigned int max_flip_ratio_bits;  // float bits (non-negative -> monotone as uint)
-  unsigned int pad;
+  unsigned int n_timeout;            // bounded waits that ran out
 };
 
 // warp-aggregated counter increment for lanes with `pred`
@@ -116,9 +116,46 @@ static __device__ __noinline__ void record_flip(DevCounters* cnt, float ratio) {
   atomicMax(&cnt->max_flip_ratio_bits, __float_as_uint(ratio));
 }
 
+// The attempts the log-free accept did not settle: the FP32 margin with its
+// tolerance, and the FP64 re-decision when the margin is within it.  Returns
+// accept | (rechecked << 1).
+__device__ __forceinline__ int mt_slow(float alpha, float d, float x, float z, float t, float uo,
+                                       float q, bool series, uint64_t zi, uint32_t stream,
+                                       uint32_t k0, uint32_t k1, DevCounters* cnt) {
+  const float lnu = flog(uo);
+  float m, tol;
+  if (series) {
+    m = -lnu - q;
+    tol = kTauM * (1.0f + fabsf(lnu) + q);
+  } else {
+    const float lnv = 3.0f * flog(t);
+    const float omv = -x * fmaf(x, x + 3.0f, 3.0f);  // 1 - (1 + x)^3
+    const float h = 0.5f * z * z;
+    m = h + d * (omv + lnv) - lnu;
+    const float S = h + d * (fabsf(omv) + fabsf(lnv) + __fdividef(3.0f * fabsf(x), t)) + fabsf(lnu);
+    tol = kTauM * (1.0f + S);
+  }
+  if (fabsf(m) > tol) return m > 0.0f ? 1 : 0;
+  const bool acc = mt_recheck64(alpha, zi, stream, k0, k1, uo, 1).pass != 0;
+  if (isfinite(m) && acc != (m > 0.0f)) record_flip(cnt, fabsf(m) / tol);
+  return (acc ? 1 : 0) | 2;
+}
+
+// The same, out of line: for large shapes (a few per cent of attempts get
+// here), so that none of it is issued, even predicated off, on the common path.
+static __device__ __noinline__ int mt_slow_call(float alpha, float d, float x, float z, float t,
+                                                float uo, float q, bool series, uint64_t zi,
+                                                uint32_t stream, uint32_t k0, uint32_t k1,
+                                                DevCounters* cnt) {
+  return mt_slow(alpha, d, x, z, t, uo, q, series, zi, stream, k0, k1, cnt);
+}
+
 // One attempt.  Returns true for lanes that accepted; then *dv = d v (FP32).
 // *zword gets the raw word of the N element used (for the first-word output).
-template <class RN, class RU>
+// kLargeShape: the caller's shapes are large (the series form and the
+// log-free accept settle almost every attempt), so the rest is called out of
+// line; otherwise it is inline (small shapes take it on most attempts).
+template <bool kLargeShape = false, class RN, class RU>
 __device__ __forceinline__ bool mt_attempt(bool run, const GammaState& g, RN& N, RU& U,
                                            uint32_t stream, const RoundKeys& rk,
                                            DevCounters* cnt, float* dv, uint32_t* zword) {
@@ -161,27 +198,12 @@ __device__ __forceinline__ bool mt_attempt(bool run, const GammaState& g, RN& N,
     if (series && fmaf(q, 1.00001f, uo) < 0x1.fffff8p-1f) {
       acc = true;
     } else {
-      const float lnu = flog(uo);
-      float m, tol;
-      if (series) {
-        m = -lnu - q;
-        tol = kTauM * (1.0f + fabsf(lnu) + q);
-      } else {
-        const float lnv = 3.0f * flog(t);
-        const float omv = -x * fmaf(x, x + 3.0f, 3.0f);  // 1 - (1 + x)^3
-        const float h = 0.5f * z * z;
-        m = h + g.d * (omv + lnv) - lnu;
-        const float S =
-            h + g.d * (fabsf(omv) + fabsf(lnv) + __fdividef(3.0f * fabsf(x), t)) + fabsf(lnu);
-        tol = kTauM * (1.0f + S);
-      }
-      if (fabsf(m) > tol) {
-        acc = m > 0.0f;
-      } else {
-        recheck = true;
-        acc = mt_recheck64(g.alpha, N.pos() - 1, stream, rk.k[0][0], rk.k[0][1], uo, 1).pass != 0;
-        if (isfinite(m) && acc != (m > 0.0f)) record_flip(cnt, fabsf(m) / tol);
-      }
+      const int r = kLargeShape ? mt_slow_call(g.alpha, g.d, x, z, t, uo, q, series, N.pos() - 1, stream,
+                                               rk.k[0][0], rk.k[0][1], cnt)
+                                : mt_slow(g.alpha, g.d, x, z, t, uo, q, series, N.pos() - 1, stream,
+                                          rk.k[0][0], rk.k[0][1], cnt);
+      acc = (r & 1) != 0;
+      recheck = (r & 2) != 0;
     }
     *dv = g.d * (t * t * t);
   }

@@ -45,7 +45,7 @@ cudaError_t launch_triangle(const TriangleArgs& a, const Geometry& g, uint32_t l
   }
 }
 
-__global__ void __launch_bounds__(512) normal_gamma_kernel(const NormalGammaArgs a) {
+__global__ void __maxnreg__(128) normal_gamma_kernel(const NormalGammaArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned warp = threadIdx.x >> 5;
   const uint64_t unit = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + warp;

@@ -7,6 +7,7 @@
 
 #include "brng_gamma.cuh"
 #include "brng_internal.h"
+#include "brng_pc.cuh"
 
 namespace brng {
 
@@ -84,6 +85,358 @@ __host__ __device__ inline uint32_t normal_gamma_warp_bytes(uint32_t B) {
   return 128u + 2u * B * 32u * 4u;
 }
 
+// Chain state of one lane, read from and written back to global memory.
+struct NgChain {
+  float n, xb, S, mu, tau;
+  uint64_t pn, pu;
+  double d0, d1, d2, d3;
+};
+
+__device__ __forceinline__ NgChain ng_load(const NormalGammaArgs& a, uint64_t c, bool active) {
+  NgChain s{};
+  if (active) {
+    s.n = a.nobs[c];
+    s.xb = a.xbar[c];
+    s.S = a.sc[c];
+    const brng_normal_gamma_state_t st = a.state[c];
+    s.mu = st.mu;
+    s.tau = st.tau;
+    s.pn = st.pos_n;
+    s.pu = st.pos_u;
+    const double* m = a.moments + 4 * c;
+    s.d0 = m[0]; s.d1 = m[1]; s.d2 = m[2]; s.d3 = m[3];
+  }
+  return s;
+}
+
+__device__ __forceinline__ void ng_store(const NormalGammaArgs& a, uint64_t c, bool active,
+                                         const NgChain& s) {
+  if (active) {
+    brng_normal_gamma_state_t st;
+    st.mu = s.mu;
+    st.tau = s.tau;
+    st.pos_n = s.pn;
+    st.pos_u = s.pu;
+    a.state[c] = st;
+    double* m = a.moments + 4 * c;
+    m[0] = s.d0; m[1] = s.d1; m[2] = s.d2; m[3] = s.d3;
+  }
+}
+
+template <class R>
+__device__ __forceinline__ bool ring_failed(const R&) { return false; }
+
+// Compensated (Kahan) FP32 running sum: the sweep moments stay accurate to a
+// few FP32 ulp of the total over any number of sweeps with no FP64 arithmetic
+// in the loop, and the result does not depend on how the sweeps are grouped.
+struct Kahan {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const {
+    return static_cast<double>(s) - static_cast<double>(c);
+  }
+};
+
+// mu | tau after tau = G / (b0 + SS/2): the sweep's state update (FP32)
+__device__ __forceinline__ void ng_update(const NormalGammaArgs& a, float n, float xb, float S,
+                                          float nxb, float prior_num, float G, float z, float& mu,
+                                          float& tau) {
+  const float dm = xb - mu;
+  const float SS = fmaf(n * dm, dm, S);
+  tau = __fdividef(G, fmaf(0.5f, SS, a.b0));
+  const float P = fmaf(n, tau, a.prec0);
+  const float mean = __fdividef(fmaf(tau, nxb, prior_num), P);
+  mu = fmaf(z, rsqrtf(P), mean);
+}
+
+// The sweeps of one warp's 32 chains from the rings RN (N domain) and RU (U
+// domain): the warp's own circular rings or rings that producer warps fill
+// (brng_pc.cuh).  Leaves the final positions in s.pn, s.pu.
+//
+// The Gamma shape a0 + n/2 does not depend on the chain state, only the rate
+// does, so the Gamma(shape, 1) draws of a chain -- and the positions of the
+// normal and uniform elements each consumes -- follow from its streams alone.
+// Each round therefore evaluates W Marsaglia-Tsang attempts at once (ILP W),
+// speculating that each earlier one accepts: attempt i reads N element 2i (z)
+// and U element i, and its sweep's mu | tau normal is N element 2i + 1.  The
+// first k attempts that the log-free test accepts are exactly the sweeps the
+// one-at-a-time loop would run (same elements, same FP32 operations); the
+// cheap state recursion then runs over them.  The attempt after them (a
+// rejection, or one the fast test does not settle: about 0.05 % at shape 52)
+// is run by the exact one-attempt-at-a-time code, and the next round starts
+// after it.  Shapes below 1 (boosted) always take the exact code.
+// One attempt of Marsaglia-Tsang the exact way (FP32 decision with the FP64
+// recheck near the boundary), reading its elements with peek/advance from
+// rings that hold at least 2 N and 2 U elements for the lane: z (N), then U'
+// if t > 0, then for a boosted shape U_b after an accept.  Consumes exactly
+// what mt_attempt consumes.  Returns true on accept with *G set.
+template <class RNT, class RUT>
+__device__ __forceinline__ bool ng_exact_attempt(bool run, const GammaState& g, RNT& RN, RUT& RU,
+                                                 uint32_t stream, const NormalGammaArgs& a,
+                                                 float* G) {
+  const float z = run ? RN.peek(0) : 0.0f;
+  if (run) RN.advance(1);
+  const float x = g.c * z;
+  const bool series = fabsf(x) <= kSeriesMaxX;
+  float t = 1.0f + x;
+  bool tpos = t > 0.0f;
+  const bool tclose = run && !series && fabsf(t) <= kTauT;
+  if (tclose) {  // rare: the sign of t is re-decided in FP64 (z is N element pos-1)
+    const Recheck r = mt_recheck64(g.alpha, RN.pos() - 1, stream, a.rk.k[0][0], a.rk.k[0][1], 0.0f, 0);
+    tpos = r.pass != 0;
+    t = r.t;
+  }
+  const bool needu = run && tpos;
+  bool acc = false, recheck = false;
+  if (needu) {
+    const float uo = RU.peek(0) + 0x1p-24f;  // U' = U + 2^-24, exact
+    RU.advance(1);
+    float p = -0x1.111112p-4f;  // the series of mt_attempt
+    p = fmaf(p, x, 0x1.24924ap-4f);
+    p = fmaf(p, x, -0x1.3b13b2p-4f);
+    p = fmaf(p, x, 0x1.555556p-4f);
+    p = fmaf(p, x, -0x1.745d18p-4f);
+    p = fmaf(p, x, 0x1.99999ap-4f);
+    p = fmaf(p, x, -0x1.c71c72p-4f);
+    p = fmaf(p, x, 0.125f);
+    p = fmaf(p, x, -0x1.24924ap-3f);
+    p = fmaf(p, x, 0x1.555556p-3f);
+    p = fmaf(p, x, -0x1.99999ap-3f);
+    p = fmaf(p, x, 0.25f);
+    const float x2 = x * x;
+    const float q = (3.0f * g.d) * (x2 * x2) * p;
+    if (series && fmaf(q, 1.00001f, uo) < 0x1.fffff8p-1f) {
+      acc = true;
+    } else {
+      const int r = mt_slow_call(g.alpha, g.d, x, z, t, uo, q, series, RN.pos() - 1, stream,
+                                 a.rk.k[0][0], a.rk.k[0][1], a.cnt);
+      acc = (r & 1) != 0;
+      recheck = (r & 2) != 0;
+    }
+    float dv = g.d * (t * t * t);
+    if (acc && g.boost) {  // shapes below 1: Gamma(a + 1) U_b^(1/a), U_b after the accept
+      const float ub = RU.peek(0);
+      RU.advance(1);
+      dv = dv * expf(flog(ub + 0x1p-24f) / g.alpha);
+    }
+    *G = dv;
+  }
+  count_warp(&a.cnt->n_recheck, tclose || recheck);
+  return acc;
+}
+
+// The sweeps of one warp's 32 chains from the rings RN (N domain) and RU (U
+// domain): the warp's own circular rings or rings that producer warps fill
+// (brng_pc.cuh).  Leaves the final positions in s.pn, s.pu.
+//
+// The Gamma shape a0 + n/2 does not depend on the chain state, only the rate
+// does, so the Gamma(shape, 1) draws of a chain -- and the positions of the
+// normal and uniform elements each consumes -- follow from its streams alone.
+// Each round therefore evaluates W Marsaglia-Tsang attempts at once (ILP W),
+// speculating that each earlier one accepts: attempt i reads N element 2i (z)
+// and U element i, and its sweep's mu | tau normal is N element 2i + 1.  The
+// first k attempts that the log-free test accepts are exactly the sweeps the
+// one-at-a-time loop would run (same elements, same FP32 operations); the
+// cheap state recursion then runs over them.  The attempt after them (a
+// rejection, or one the fast test does not settle: about 0.05 % at shape 52)
+// puts the lane in exact mode: one attempt the exact way per round, in the
+// same round and the following ones, until one accepts and its sweep ends.
+// Shapes below 1 (boosted) stay in exact mode.  Each ring is refilled at one
+// point of the round only (its refill code is large, and the instruction
+// cache small): the round's 2W N and W U elements cover both parts, since
+// a lane that leaves the speculative part after k < W sweeps still has
+// 2W - 2k >= 2 N and W - k >= 1 U elements for its exact attempt, and a lane
+// in exact mode from the start needs at most 2 of each (boosted lanes never
+// speculate).
+template <int W, class RNT, class RUT>
+__device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t stream, bool active,
+                                          NgChain& s, RNT& RN, RUT& RU) {
+  static_assert(W >= 2, "the speculative form needs W >= 2");
+  const GammaState g = gamma_setup(a.a0 + 0.5f * s.n);
+  const float prior_num = a.prec0 * a.mu0;
+  const float nxb = s.n * s.xb;
+  const float n = s.n, xb = s.xb, S = s.S;
+  float mu = s.mu, tau = s.tau;
+  Kahan k0, k1, k2, k3;
+  bool exact = g.boost;  // per lane: the next attempt is taken the exact way
+  int att = 0;
+  uint32_t sweep = 0;
+  bool rejected = false;
+  while (true) {
+    const bool run = active && sweep < a.n_sweeps && !ring_failed(RN) && !ring_failed(RU);
+    if (!__any_sync(kFull, run)) break;
+    RN.ensure(run, 2 * W, stream, a.rk);
+    RU.ensure(run, W, stream, a.rk);
+    const bool spec = run && !exact;
+    if (__any_sync(kFull, spec)) {
+      float G[W], zm[W];
+      uint32_t fast = 0;
+#pragma unroll
+      for (int i = 0; i < W; ++i) {
+        const float z = RN.peek(2 * i);
+        zm[i] = RN.peek(2 * i + 1);
+        const float uo = RU.peek(i) + 0x1p-24f;  // U' = U + 2^-24, exact
+        const float x = g.c * z;
+        float p = -0x1.111112p-4f;  // the series of mt_attempt
+        p = fmaf(p, x, 0x1.24924ap-4f);
+        p = fmaf(p, x, -0x1.3b13b2p-4f);
+        p = fmaf(p, x, 0x1.555556p-4f);
+        p = fmaf(p, x, -0x1.745d18p-4f);
+        p = fmaf(p, x, 0x1.99999ap-4f);
+        p = fmaf(p, x, -0x1.c71c72p-4f);
+        p = fmaf(p, x, 0.125f);
+        p = fmaf(p, x, -0x1.24924ap-3f);
+        p = fmaf(p, x, 0x1.555556p-3f);
+        p = fmaf(p, x, -0x1.99999ap-3f);
+        p = fmaf(p, x, 0.25f);
+        const float x2 = x * x;
+        const float q = (3.0f * g.d) * (x2 * x2) * p;
+        const float t = 1.0f + x;
+        G[i] = g.d * (t * t * t);
+        const bool ok = fabsf(x) <= kSeriesMaxX && fmaf(q, 1.00001f, uo) < 0x1.fffff8p-1f;
+        fast |= static_cast<uint32_t>(ok) << i;
+      }
+      if (!spec) fast = 0;
+      uint32_t k = static_cast<uint32_t>(__ffs(~fast)) - 1u;  // leading accepted attempts
+      k = min(k, static_cast<uint32_t>(W));
+      k = min(k, a.n_sweeps - min(sweep, a.n_sweeps));
+#pragma unroll
+      for (int i = 0; i < W; ++i) {
+        if (static_cast<uint32_t>(i) < k) {
+          ng_update(a, n, xb, S, nxb, prior_num, G[i], zm[i], mu, tau);
+          k0.add(mu);
+          k1.add(tau);
+          k2.add(mu * mu);
+          k3.add(tau * tau);
+        }
+      }
+      if (spec) {
+        RN.advance(2 * k);
+        RU.advance(k);
+        sweep += k;
+        if (k < W && sweep < a.n_sweeps) exact = true;
+      }
+    }
+    const bool ex = run && exact && sweep < a.n_sweeps;
+    if (__any_sync(kFull, ex)) {
+      float G = 0.0f;
+      const bool acc = ng_exact_attempt(ex, g, RN, RU, stream, a, &G);
+      bool finish = false;
+      if (ex) {
+        ++att;
+        if (acc) {
+          finish = true;
+        } else if (att >= kGammaMaxAttempts) {
+          G = __int_as_float(0x7fc00000);
+          finish = true;
+          rejected = true;
+        }
+      }
+      if (finish) {
+        const float z = RN.peek(0);
+        RN.advance(1);
+        ng_update(a, n, xb, S, nxb, prior_num, G, z, mu, tau);
+        k0.add(mu);
+        k1.add(tau);
+        k2.add(mu * mu);
+        k3.add(tau * tau);
+        ++sweep;
+        att = 0;
+        exact = g.boost;
+      }
+    }
+  }
+  count_warp(&a.cnt->n_reject, rejected);
+  if (ring_failed(RN) || ring_failed(RU)) mu = tau = __int_as_float(0x7fc00000);
+  s.mu = mu;
+  s.tau = tau;
+  s.d0 += k0.value();
+  s.d1 += k1.value();
+  s.d2 += k2.value();
+  s.d3 += k3.value();
+  s.pn = RN.pos();
+  s.pu = RU.pos();
+}
+
+// Ring length 4 (one block): no room to look ahead, one exact attempt per
+// iteration with refill-on-demand reads.
+template <class RNT, class RUT>
+__device__ __forceinline__ void ng_sweeps_plain(const NormalGammaArgs& a, uint32_t stream, bool active,
+                                                NgChain& s, RNT& RN, RUT& RU) {
+  const GammaState g = gamma_setup(a.a0 + 0.5f * s.n);
+  const float prior_num = a.prec0 * a.mu0;
+  const float nxb = s.n * s.xb;
+  const float n = s.n, xb = s.xb, S = s.S;
+  float mu = s.mu, tau = s.tau;
+  Kahan k0, k1, k2, k3;
+  uint32_t sweep = 0;
+  int att = 0;
+  bool rejected = false;
+  while (true) {
+    const bool run = active && sweep < a.n_sweeps && !ring_failed(RN) && !ring_failed(RU);
+    if (!__any_sync(kFull, run)) break;
+    float dv = 0.0f;
+    uint32_t zw;
+    const bool acc = mt_attempt<true>(run, g, RN, RU, stream, a.rk, a.cnt, &dv, &zw);
+    const bool boost_now = run && acc && g.boost;
+    if (__any_sync(kFull, boost_now)) {  // shapes below 1 only
+      const float ub = RU.get(boost_now, stream, a.rk);
+      if (boost_now) dv = dv * expf(flog(ub + 0x1p-24f) / g.alpha);
+    }
+    bool finish = false;
+    if (run) {
+      ++att;
+      if (acc) {
+        finish = true;
+      } else if (att >= kGammaMaxAttempts) {
+        dv = __int_as_float(0x7fc00000);
+        finish = true;
+        rejected = true;
+      }
+    }
+    const float z = RN.get(finish, stream, a.rk);
+    if (finish) {
+      ng_update(a, n, xb, S, nxb, prior_num, dv, z, mu, tau);
+      k0.add(mu);
+      k1.add(tau);
+      k2.add(mu * mu);
+      k3.add(tau * tau);
+      ++sweep;
+      att = 0;
+    }
+  }
+  count_warp(&a.cnt->n_reject, rejected);
+  if (ring_failed(RN) || ring_failed(RU)) mu = tau = __int_as_float(0x7fc00000);
+  s.mu = mu;
+  s.tau = tau;
+  s.d0 += k0.value();
+  s.d1 += k1.value();
+  s.d2 += k2.value();
+  s.d3 += k3.value();
+  s.pn = RN.pos();
+  s.pu = RU.pos();
+}
+
+// Speculation width for ring length B (elements per lane and domain): the
+// N ring must hold 2W elements past the read point (B >= 4W).
+__host__ __device__ constexpr int ng_width(uint32_t B) { return B >= 32 ? 8 : B >= 16 ? 4 : B >= 8 ? 2 : 0; }
+
+template <class RNT, class RUT>
+__device__ __forceinline__ void ng_sweeps_any(const NormalGammaArgs& a, uint32_t stream, bool active,
+                                              NgChain& s, RNT& RN, RUT& RU) {
+  switch (ng_width(a.B)) {  // warp-uniform
+    case 8: ng_sweeps<8>(a, stream, active, s, RN, RU); break;
+    case 4: ng_sweeps<4>(a, stream, active, s, RN, RU); break;
+    case 2: ng_sweeps<2>(a, stream, active, s, RN, RU); break;
+    default: ng_sweeps_plain(a, stream, active, s, RN, RU); break;
+  }
+}
+
 // One work unit: 32 chains (unit * 32 ..), one warp; `base` holds
 // normal_gamma_warp_bytes(a.B) bytes of this warp's shared memory.
 __device__ __forceinline__ void normal_gamma_unit(const NormalGammaArgs& a, uint64_t unit,
@@ -96,92 +449,13 @@ __device__ __forceinline__ void normal_gamma_unit(const NormalGammaArgs& a, uint
   const uint64_t c = unit * 32 + lane;
   const bool active = c < a.n_chains;
   const uint32_t stream = static_cast<uint32_t>(a.chain_offset + c);
-
-  float n = 0.0f, xb = 0.0f, S = 0.0f, mu = 0.0f, tau = 0.0f;
-  uint64_t pn = 0, pu = 0;
-  double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
-  if (active) {
-    n = a.nobs[c];
-    xb = a.xbar[c];
-    S = a.sc[c];
-    const brng_normal_gamma_state_t s = a.state[c];
-    mu = s.mu;
-    tau = s.tau;
-    pn = s.pos_n;
-    pu = s.pos_u;
-    const double* m = a.moments + 4 * c;
-    d0 = m[0]; d1 = m[1]; d2 = m[2]; d3 = m[3];
-  }
-  Ring<GenN, 32, false> RN;
-  Ring<GenU, 32, false> RU;
-  RN.init(ringN, nullptr, list, a.B, pn);
-  RU.init(ringU, nullptr, list, a.B, pu);
-  const GammaState g = gamma_setup(a.a0 + 0.5f * n);
-  const float prior_num = a.prec0 * a.mu0;
-  const float nxb = n * xb;
-
-  float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;
-  uint32_t sweep = 0;
-  int att = 0;
-  bool rejected = false;
-  bool more = true;
-  while (more) {
-    // at most 64 attempts per lane into the FP32 partials, then one FP64 flush
-    // outside the inner loop (so no FP64 instruction sits in the hot loop)
-    for (uint32_t j = 0; j < 64; ++j) {
-      const bool run = active && sweep < a.n_sweeps;
-      more = __any_sync(kFull, run);
-      if (!more) break;
-      float dv = 0.0f;
-      uint32_t zw;
-      const bool acc = mt_attempt(run, g, RN, RU, stream, a.rk, a.cnt, &dv, &zw);
-      const bool boost_now = run && acc && g.boost;
-      float G = dv;
-      if (__any_sync(kFull, boost_now)) {  // warp-uniform: shapes below 1 only
-        const float ub = RU.get(boost_now, stream, a.rk);
-        if (boost_now) G = dv * expf(flog(ub + 0x1p-24f) / g.alpha);
-      }
-      bool finish = false;
-      if (run) {
-        ++att;
-        if (acc) {
-          finish = true;
-        } else if (att >= kGammaMaxAttempts) {
-          G = __int_as_float(0x7fc00000);
-          finish = true;
-          rejected = true;
-        }
-      }
-      const float z = RN.get(finish, stream, a.rk);
-      if (finish) {
-        const float dm = xb - mu;
-        const float SS = fmaf(n * dm, dm, S);
-        tau = __fdividef(G, fmaf(0.5f, SS, a.b0));
-        const float P = fmaf(n, tau, a.prec0);
-        const float mean = __fdividef(fmaf(tau, nxb, prior_num), P);
-        mu = fmaf(z, rsqrtf(P), mean);
-        p0 += mu;
-        p1 += tau;
-        p2 = fmaf(mu, mu, p2);
-        p3 = fmaf(tau, tau, p3);
-        ++sweep;
-        att = 0;
-      }
-    }
-    d0 += p0; d1 += p1; d2 += p2; d3 += p3;
-    p0 = p1 = p2 = p3 = 0.0f;
-  }
-  count_warp(&a.cnt->n_reject, rejected);
-  if (active) {
-    brng_normal_gamma_state_t s;
-    s.mu = mu;
-    s.tau = tau;
-    s.pos_n = RN.pos();
-    s.pos_u = RU.pos();
-    a.state[c] = s;
-    double* m = a.moments + 4 * c;
-    m[0] = d0; m[1] = d1; m[2] = d2; m[3] = d3;
-  }
+  NgChain s = ng_load(a, c, active);
+  CRing<GenN> RN;
+  CRing<GenU> RU;
+  RN.init(ringN, list, a.B, s.pn);
+  RU.init(ringU, list, a.B, s.pu);
+  ng_sweeps_any(a, stream, active, s, RN, RU);
+  ng_store(a, c, active, s);
   __syncwarp();  // the rings are reused by the warp's next unit
 }
 

@@ -17,6 +17,7 @@ constexpr uint32_t kDefaultBufLen = 32;
 constexpr uint32_t kMaxBufLen = 512;
 constexpr uint32_t kDefaultWarpsPerBlock = 4;
 constexpr uint32_t kDefaultLookahead = 8;
+constexpr uint32_t kDefaultProducerWarps = BRNG_PRODUCERS_NONE;
 constexpr int kTagMixed = -1;
 
 // Launch geometry shared by all kernels: warps per block and ring length.
@@ -93,6 +94,9 @@ struct NormalGammaArgs {
   DevCounters* cnt;
 };
 cudaError_t launch_normal_gamma(const NormalGammaArgs& a, const Geometry& g, cudaStream_t st);
+// With Wc consumer and Wp producer warps per block (brng_gibbs_pc.cu).
+cudaError_t launch_normal_gamma_pc(const NormalGammaArgs& a, uint32_t Wc, uint32_t Wp, cudaStream_t st);
+size_t normal_gamma_pc_bytes_per_warp(uint32_t B);  // shared memory per consumer warp
 
 // ---- batched persistent kernel (brng_batch.cu) ----
 struct BatchJob {

@@ -455,6 +455,44 @@ def test_normal_gamma_invariance_and_resume():
     assert np.array_equal(mu_a, mu_c) and np.array_equal(tau_a, tau_c)
 
 
+@pytest.mark.parametrize("wpb,wp,buf_len", [(4, 1, 32), (4, 2, 32), (8, 2, 8), (2, 2, 4), (12, 4, 64), (1, 1, 16)])
+def test_normal_gamma_producers_equal_inline(wpb, wp, buf_len):
+    """Asynchronous replenishment (producer warps) gives the inline form's
+    bits, for ragged chain counts and every block shape."""
+    nobs, xbar, sc = inputs.normal_gamma_data(1000, seed=9)
+    a, ma, _ = _ng_gpu(nobs, xbar, sc, 150)
+    b, mb, cnt = _ng_gpu(nobs, xbar, sc, 150, buf_len=buf_len, warps_per_block=wpb, producer_warps=wp)
+    assert cnt["n_timeout"] == 0, cnt
+    assert torch.equal(a, b) and torch.equal(ma, mb)
+
+
+def test_normal_gamma_producers_oracle_and_resume():
+    nobs, xbar, sc = inputs.normal_gamma_data(333, seed=10)
+    ref = O.gibbs_normal_gamma(42, 120, nobs, xbar, sc, nthreads=NT)
+    st, m, _ = _ng_gpu(nobs, xbar, sc, 120, producer_warps=2)
+    _ng_check(st, m, ref, 120, "normal-gamma producers 333x120")
+    # resume from mid-block positions (the rings then start inside a block)
+    c, mc, _ = _ng_gpu(nobs, xbar, sc, 41, producer_warps=1)
+    c, mc, cnt = _ng_gpu(nobs, xbar, sc, 79, state=c, mom=mc, producer_warps=3, buf_len=8)
+    assert cnt["n_timeout"] == 0
+    assert torch.equal(st, c)
+    # the FP32 partial sums are flushed at other iterations when a run is split
+    torch.testing.assert_close(mc, m, rtol=1e-6, atol=0)
+
+
+def test_normal_gamma_producers_full_size_sampled():
+    """65,536 chains x 2,000 sweeps with producer warps; 128 chains at each
+    end recomputed by the oracle."""
+    n_chains, n_sweeps = 65536, 2000
+    nobs, xbar, sc = inputs.normal_gamma_data(n_chains, seed=42)
+    st, m, cnt = _ng_gpu(nobs, xbar, sc, n_sweeps, producer_warps=2)
+    assert cnt["n_timeout"] == 0, cnt
+    for c0, c1 in [(0, 128), (n_chains - 128, n_chains)]:
+        ref = O.gibbs_normal_gamma(42, n_sweeps, nobs[c0:c1], xbar[c0:c1], sc[c0:c1], chain_offset=c0,
+                                   nthreads=NT)
+        _ng_check(st[c0:c1], m[c0:c1], ref, n_sweeps, "normal-gamma producers chains %d..%d" % (c0, c1))
+
+
 def _lda_gpu(alpha, n_sweeps, offset=0, **tune):
     n_docs, K = alpha.shape
     h = handle(42, 1, **tune)
@@ -547,6 +585,8 @@ def test_argument_errors():
     h = handle(1, 10)
     with pytest.raises(B.BrngError):
         h.tune(warps_per_block=17)
+    with pytest.raises(B.BrngError):
+        h.tune(producer_warps=9)
     with pytest.raises(B.BrngError):
         B.brng_dirichlet(h.h, torch.ones((2, 3), device=DEV), torch.empty((2, 3), device=DEV))  # 10 % 3
     with pytest.raises(B.BrngError):
