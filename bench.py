@@ -452,7 +452,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--buf-len", type=int, default=0)
-    ap.add_argument("--warps-per-block", type=int, default=0)
+    ap.add_argument("--warps-per-block", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary workloads (triangle, LDA, mixed stream, batched vs plain, served mix)")

@@ -59,7 +59,8 @@ int bulk(brng_t* h, int tag, size_t n, const uint8_t* tagv, const float* p0, con
                    tag == BRNG_TAG_LAPLACE || tag == BRNG_TAG_WEIBULL;
   if (two && tag != brng::kTagMixed && !p1) return BRNG_EINVAL;
   const int ndom = (tag == brng::kTagMixed) ? 3 : (tag == BRNG_TAG_GAMMA || tag == BRNG_TAG_LAPLACE) ? 2 : 1;
-  const size_t per_warp = 128u + static_cast<size_t>(ndom) * h->tune.buf_len * 128u * (words ? 2 : 1);
+  const size_t per_warp =
+      128u + static_cast<size_t>(ndom) * std::max(h->tune.buf_len, brng::kBulkMinRing) * 128u * (words ? 2 : 1);
   const brng::Geometry g = geometry(h, per_warp);
   if (g.warps_per_block == 0) return BRNG_EINVAL;
   brng::BulkArgs a;

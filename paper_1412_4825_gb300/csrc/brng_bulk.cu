@@ -43,123 +43,154 @@ __device__ __forceinline__ bool param_ok(int tag, float p0, float p1) {
   }
 }
 
+// Per lane, one step per iteration: the lane's current draw, or for a Gamma
+// draw one Marsaglia-Tsang attempt (a rejected attempt leaves the lane on the
+// same draw for the next iteration, while its neighbours move on).  Each ring
+// is topped up at one point of the iteration, for the most a step can take
+// (U: 2 = attempt + boost; N: 1; E: 1), and every read is a peek, so each
+// domain's generator code appears once in the kernel.  The next draw's tag
+// and parameters are loaded one step ahead.
 template <int TAG, bool WORDS>
-__global__ void __launch_bounds__(512) bulk_kernel(const BulkArgs a) {
+__global__ void __maxnreg__(128) bulk_kernel(const BulkArgs a) {
   using D = BulkDomains<TAG>;
   extern __shared__ __align__(16) unsigned char smem[];
-  const unsigned lane = lane_id();
   const unsigned warp = threadIdx.x >> 5;
   const uint32_t wbytes = bulk_warp_bytes(D::kCount, a.B, WORDS);
-  unsigned char* base = smem + warp * wbytes;
-  uint32_t* list = reinterpret_cast<uint32_t*>(base);
-  base += 128;
+  unsigned char* base = smem + warp * wbytes + 128;
   const uint32_t ring_bytes = a.B * 32u * 4u;
 
   const uint64_t gwarp = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + warp;
-  const uint64_t s64 = gwarp * 32u + lane;
+  const uint64_t s64 = gwarp * 32u + lane_id();
   const bool has_stream = s64 < a.S;
   const uint32_t s = static_cast<uint32_t>(s64);
 
-  Ring<GenU, 32, WORDS> RU;
-  Ring<GenN, 32, WORDS> RN;
-  Ring<GenE, 32, WORDS> RE;
+  CRing<GenU, WORDS> RU;
+  CRing<GenN, WORDS> RN;
+  CRing<GenE, WORDS> RE;
   if constexpr (D::kU) {
     RU.init(reinterpret_cast<float*>(base), WORDS ? reinterpret_cast<uint32_t*>(base + ring_bytes) : nullptr,
-            list, a.B, has_stream ? a.pos[s] : 0);
+            a.B, has_stream ? a.pos[s] : 0);
     base += ring_bytes * (WORDS ? 2 : 1);
   }
   if constexpr (D::kN) {
     RN.init(reinterpret_cast<float*>(base), WORDS ? reinterpret_cast<uint32_t*>(base + ring_bytes) : nullptr,
-            list, a.B, has_stream ? a.pos[static_cast<uint64_t>(a.S) + s] : 0);
+            a.B, has_stream ? a.pos[static_cast<uint64_t>(a.S) + s] : 0);
     base += ring_bytes * (WORDS ? 2 : 1);
   }
   if constexpr (D::kE) {
     RE.init(reinterpret_cast<float*>(base), WORDS ? reinterpret_cast<uint32_t*>(base + ring_bytes) : nullptr,
-            list, a.B, has_stream ? a.pos[2ull * a.S + s] : 0);
+            a.B, has_stream ? a.pos[2ull * a.S + s] : 0);
   }
 
-  for (uint64_t m = 0;; ++m) {
-    const uint64_t i = s64 + m * a.S;
+  // current draw (i, tag, p0, p1) and the next one's inputs, loaded ahead
+  uint64_t i = s64;
+  int tag = TAG, tag_n = TAG;
+  float p0 = 0.0f, p1 = 0.0f, p0_n = 0.0f, p1_n = 0.0f;
+  auto load = [&](uint64_t k, int& t, float& q0, float& q1) {
+    if constexpr (TAG < 0) t = a.tag[k];
+    q0 = a.p0[k];
+    if (a.p1) q1 = a.p1[k];
+  };
+  if (has_stream && i < a.n) load(i, tag, p0, p1);
+  if (has_stream && i + a.S < a.n) load(i + a.S, tag_n, p0_n, p1_n);
+  bool ok = has_stream && i < a.n && param_ok(tag, p0, p1);
+  count_warp(&a.cnt->n_domain, has_stream && i < a.n && !ok);
+  GammaState g = gamma_setup(ok && tag == BRNG_TAG_GAMMA ? p0 : 1.0f);
+  int attempts = 0;
+  uint32_t word = 0;
+
+  while (true) {
     const bool active = has_stream && i < a.n;
     if (!__any_sync(kFull, active)) break;
-    int tag = TAG;
-    float p0 = 0.0f, p1 = 0.0f;
-    if (active) {
-      if constexpr (TAG < 0) tag = a.tag[i];
-      p0 = a.p0[i];
-      if (a.p1) p1 = a.p1[i];
-    }
-    const bool ok = active && param_ok(tag, p0, p1);
-    count_warp(&a.cnt->n_domain, active && !ok);
-    float out = __int_as_float(0x7fc00000);  // NaN unless drawn
-    uint32_t word = 0;
+    const bool isU = ok && tag == BRNG_TAG_UNIFORM;
+    const bool isN = ok && tag == BRNG_TAG_NORMAL;
+    const bool isE = ok && (tag == BRNG_TAG_EXPONENTIAL || tag == BRNG_TAG_LAPLACE || tag == BRNG_TAG_WEIBULL);
+    const bool isL = ok && tag == BRNG_TAG_LAPLACE;
+    const bool isG = ok && tag == BRNG_TAG_GAMMA;
+    // a stream with draws left is topped up whenever a ring of its warp runs dry
+    if constexpr (D::kU) RU.ensure(isU || isL || isG, 2, active, s, a.rk);
+    if constexpr (D::kN) RN.ensure(isN || isG, 1, active, s, a.rk);
+    if constexpr (D::kE) RE.ensure(isE, 1, active, s, a.rk);
 
+    bool done = active && !ok;  // an invalid parameter: NaN, nothing consumed
+    float out = __int_as_float(0x7fc00000);
     if constexpr (D::kU && (TAG < 0 || TAG == BRNG_TAG_UNIFORM)) {
-      const bool w = ok && tag == BRNG_TAG_UNIFORM;
-      uint32_t wd = 0;
-      const float u = RU.get(w, s, a.rk, &wd);
-      if (w) {
+      if (isU) {
+        const float u = RU.peek(0);
+        if (WORDS) word = RU.peek_word(0);
+        RU.advance(1);
         out = fmaf(p1 - p0, u, p0);
-        word = wd;
+        done = true;
       }
     }
     if constexpr (D::kN && (TAG < 0 || TAG == BRNG_TAG_NORMAL)) {
-      const bool w = ok && tag == BRNG_TAG_NORMAL;
-      uint32_t wd = 0;
-      const float z = RN.get(w, s, a.rk, &wd);
-      if (w) {
+      if (isN) {
+        const float z = RN.peek(0);
+        if (WORDS) word = RN.peek_word(0);
+        RN.advance(1);
         out = fmaf(p1, z, p0);
-        word = wd;
+        done = true;
       }
     }
-    if constexpr (D::kE && (TAG < 0 || TAG == BRNG_TAG_EXPONENTIAL || TAG == BRNG_TAG_LAPLACE ||
-                            TAG == BRNG_TAG_WEIBULL)) {
-      const bool w = ok && (tag == BRNG_TAG_EXPONENTIAL || tag == BRNG_TAG_LAPLACE ||
-                            tag == BRNG_TAG_WEIBULL);
-      uint32_t wd = 0;
-      const float e = RE.get(w, s, a.rk, &wd);
-      if constexpr (TAG < 0 || TAG == BRNG_TAG_LAPLACE) {
-        const bool wl = ok && tag == BRNG_TAG_LAPLACE;
-        const float u = RU.get(wl, s, a.rk);
-        if (wl) out = u < 0.5f ? fmaf(-p1, e, p0) : fmaf(p1, e, p0);
-      }
-      if (w) {
-        word = wd;
+    if constexpr (D::kE) {
+      if (isE) {
+        const float e = RE.peek(0);
+        if (WORDS) word = RE.peek_word(0);
+        RE.advance(1);
         if (tag == BRNG_TAG_EXPONENTIAL) out = e / p0;
-        if (tag == BRNG_TAG_WEIBULL) out = p1 * expf(flog(e) / p0);
+        if constexpr (TAG < 0 || TAG == BRNG_TAG_WEIBULL)
+          if (tag == BRNG_TAG_WEIBULL) out = p1 * expf(flog(e) / p0);
+        if constexpr (D::kU && (TAG < 0 || TAG == BRNG_TAG_LAPLACE)) {
+          if (isL) {
+            const float u = RU.peek(0);
+            RU.advance(1);
+            out = u < 0.5f ? fmaf(-p1, e, p0) : fmaf(p1, e, p0);
+          }
+        }
+        done = true;
       }
     }
     if constexpr (D::kN && D::kU && (TAG < 0 || TAG == BRNG_TAG_GAMMA)) {
-      bool pending = ok && tag == BRNG_TAG_GAMMA;
-      GammaState g = gamma_setup(pending ? p0 : 1.0f);
-      int attempts = 0;
-      bool rejected = false;
-      while (__any_sync(kFull, pending)) {
+      bool gdone = false, rej = false;
+      if (__any_sync(kFull, isG)) {
         float dv = 0.0f;
         uint32_t zw = 0;
-        const bool acc = mt_attempt(pending, g, RN, RU, s, a.rk, a.cnt, &dv, &zw);
-        if (pending && attempts == 0) word = zw;
-        const bool boost_now = pending && acc && g.boost;
-        if (__any_sync(kFull, boost_now)) {  // warp-uniform: shapes below 1 only
-          const float ub = RU.get(boost_now, s, a.rk);
-          if (boost_now) dv *= expf(flog(ub + 0x1p-24f) / g.alpha);
-        }
-        if (pending) {
+        const bool acc = mt_attempt_peek<false, WORDS>(isG, g, RN, RU, s, a.rk, a.cnt, &dv, &zw);
+        if (isG) {
+          if (attempts == 0) word = zw;
           ++attempts;
           if (acc) {
             out = dv;
-            pending = false;
+            gdone = true;
           } else if (attempts >= kGammaMaxAttempts) {
-            pending = false;
-            rejected = true;
+            gdone = true;  // NaN
+            rej = true;
           }
         }
       }
-      count_warp(&a.cnt->n_reject, rejected);
+      count_warp(&a.cnt->n_reject, rej);
+      done = done || gdone;
     }
-    if (active) {
+    if (done) {  // finish the draw, move to the stream's next one
       a.out[i] = out;
       if (WORDS) a.words[i] = word;
+      i += a.S;
+      tag = tag_n;
+      p0 = p0_n;
+      p1 = p1_n;
+      if (i + a.S < a.n) load(i + a.S, tag_n, p0_n, p1_n);
+      word = 0;
+      attempts = 0;
+    }
+    const bool fresh = done && i < a.n;
+    if (__any_sync(kFull, done)) {
+      const bool okn = fresh && param_ok(tag, p0, p1);
+      count_warp(&a.cnt->n_domain, fresh && !okn);
+      if (done) {
+        ok = okn;
+        if constexpr (D::kN && D::kU && (TAG < 0 || TAG == BRNG_TAG_GAMMA))
+          if (ok && tag == BRNG_TAG_GAMMA) g = gamma_setup(p0);
+      }
     }
   }
   if (has_stream) {
@@ -172,14 +203,16 @@ __global__ void __launch_bounds__(512) bulk_kernel(const BulkArgs a) {
 template <int TAG, bool WORDS>
 static cudaError_t launch_bulk_t(const BulkArgs& a, const Geometry& g, cudaStream_t st) {
   using D = BulkDomains<TAG>;
+  BulkArgs b = a;
+  b.B = a.B < kBulkMinRing ? kBulkMinRing : a.B;  // a step may take 2 U elements: B - 3 >= 2
   const uint32_t threads = 32u * g.warps_per_block;
-  const size_t smem = static_cast<size_t>(g.warps_per_block) * bulk_warp_bytes(D::kCount, a.B, WORDS);
+  const size_t smem = static_cast<size_t>(g.warps_per_block) * bulk_warp_bytes(D::kCount, b.B, WORDS);
   const uint64_t warps = (static_cast<uint64_t>(a.S) + 31) / 32;
   const uint64_t blocks = (warps + g.warps_per_block - 1) / g.warps_per_block;
   cudaError_t e = cudaFuncSetAttribute(bulk_kernel<TAG, WORDS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  bulk_kernel<TAG, WORDS><<<static_cast<unsigned>(blocks), threads, smem, st>>>(a);
+  bulk_kernel<TAG, WORDS><<<static_cast<unsigned>(blocks), threads, smem, st>>>(b);
   return cudaGetLastError();
 }
 

@@ -211,4 +211,71 @@ __device__ __forceinline__ bool mt_attempt(bool run, const GammaState& g, RN& N,
   return acc;
 }
 
+// One attempt (as mt_attempt) reading its elements with peek/advance from
+// rings that already hold, for each lane with `run`, at least 1 N and 2 U
+// elements: z (N), then U' if t > 0, then for a boosted shape U_b after an
+// accept, which it folds in: on accept *dv = Gamma(alpha) (FP32).  *zword
+// gets z's raw word when the N ring keeps words.  Consumes exactly what
+// mt_attempt plus the caller's boost draw consume.
+template <bool kLargeShape, bool kZWord, class RNT, class RUT>
+__device__ __forceinline__ bool mt_attempt_peek(bool run, const GammaState& g, RNT& N, RUT& U,
+                                                uint32_t stream, const RoundKeys& rk,
+                                                DevCounters* cnt, float* dv, uint32_t* zword) {
+  float z = 0.0f;
+  if (run) {
+    z = N.peek(0);
+    if constexpr (kZWord) *zword = N.peek_word(0);
+    N.advance(1);
+  }
+  const float x = g.c * z;
+  const bool series = fabsf(x) <= kSeriesMaxX;
+  float t = 1.0f + x;
+  bool tpos = t > 0.0f;
+  const bool tclose = run && !series && fabsf(t) <= kTauT;
+  if (tclose) {  // rare: the sign of t is re-decided in FP64 (z is N element pos-1)
+    const Recheck r = mt_recheck64(g.alpha, N.pos() - 1, stream, rk.k[0][0], rk.k[0][1], 0.0f, 0);
+    tpos = r.pass != 0;
+    t = r.t;
+  }
+  const bool needu = run && tpos;
+  bool acc = false, recheck = false;
+  if (needu) {
+    const float uo = U.peek(0) + 0x1p-24f;  // U' = U + 2^-24, exact
+    U.advance(1);
+    float p = -0x1.111112p-4f;  // the series of mt_attempt
+    p = fmaf(p, x, 0x1.24924ap-4f);
+    p = fmaf(p, x, -0x1.3b13b2p-4f);
+    p = fmaf(p, x, 0x1.555556p-4f);
+    p = fmaf(p, x, -0x1.745d18p-4f);
+    p = fmaf(p, x, 0x1.99999ap-4f);
+    p = fmaf(p, x, -0x1.c71c72p-4f);
+    p = fmaf(p, x, 0.125f);
+    p = fmaf(p, x, -0x1.24924ap-3f);
+    p = fmaf(p, x, 0x1.555556p-3f);
+    p = fmaf(p, x, -0x1.99999ap-3f);
+    p = fmaf(p, x, 0.25f);
+    const float x2 = x * x;
+    const float q = (3.0f * g.d) * (x2 * x2) * p;
+    if (series && fmaf(q, 1.00001f, uo) < 0x1.fffff8p-1f) {
+      acc = true;
+    } else {
+      const int r = kLargeShape ? mt_slow_call(g.alpha, g.d, x, z, t, uo, q, series, N.pos() - 1, stream,
+                                               rk.k[0][0], rk.k[0][1], cnt)
+                                : mt_slow(g.alpha, g.d, x, z, t, uo, q, series, N.pos() - 1, stream,
+                                          rk.k[0][0], rk.k[0][1], cnt);
+      acc = (r & 1) != 0;
+      recheck = (r & 2) != 0;
+    }
+    float v = g.d * (t * t * t);
+    if (acc && g.boost) {  // shapes below 1: Gamma(a + 1) U_b^(1/a), U_b after the accept
+      const float ub = U.peek(0);
+      U.advance(1);
+      v = v * expf(flog(ub + 0x1p-24f) / g.alpha);
+    }
+    *dv = v;
+  }
+  count_warp(&cnt->n_recheck, tclose || recheck);
+  return acc;
+}
+
 }  // namespace brng

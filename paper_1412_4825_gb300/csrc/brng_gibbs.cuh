@@ -168,82 +168,6 @@ __device__ __forceinline__ void ng_update(const NormalGammaArgs& a, float n, flo
 // one-at-a-time loop would run (same elements, same FP32 operations); the
 // cheap state recursion then runs over them.  The attempt after them (a
 // rejection, or one the fast test does not settle: about 0.05 % at shape 52)
-// is run by the exact one-attempt-at-a-time code, and the next round starts
-// after it.  Shapes below 1 (boosted) always take the exact code.
-// One attempt of Marsaglia-Tsang the exact way (FP32 decision with the FP64
-// recheck near the boundary), reading its elements with peek/advance from
-// rings that hold at least 2 N and 2 U elements for the lane: z (N), then U'
-// if t > 0, then for a boosted shape U_b after an accept.  Consumes exactly
-// what mt_attempt consumes.  Returns true on accept with *G set.
-template <class RNT, class RUT>
-__device__ __forceinline__ bool ng_exact_attempt(bool run, const GammaState& g, RNT& RN, RUT& RU,
-                                                 uint32_t stream, const NormalGammaArgs& a,
-                                                 float* G) {
-  const float z = run ? RN.peek(0) : 0.0f;
-  if (run) RN.advance(1);
-  const float x = g.c * z;
-  const bool series = fabsf(x) <= kSeriesMaxX;
-  float t = 1.0f + x;
-  bool tpos = t > 0.0f;
-  const bool tclose = run && !series && fabsf(t) <= kTauT;
-  if (tclose) {  // rare: the sign of t is re-decided in FP64 (z is N element pos-1)
-    const Recheck r = mt_recheck64(g.alpha, RN.pos() - 1, stream, a.rk.k[0][0], a.rk.k[0][1], 0.0f, 0);
-    tpos = r.pass != 0;
-    t = r.t;
-  }
-  const bool needu = run && tpos;
-  bool acc = false, recheck = false;
-  if (needu) {
-    const float uo = RU.peek(0) + 0x1p-24f;  // U' = U + 2^-24, exact
-    RU.advance(1);
-    float p = -0x1.111112p-4f;  // the series of mt_attempt
-    p = fmaf(p, x, 0x1.24924ap-4f);
-    p = fmaf(p, x, -0x1.3b13b2p-4f);
-    p = fmaf(p, x, 0x1.555556p-4f);
-    p = fmaf(p, x, -0x1.745d18p-4f);
-    p = fmaf(p, x, 0x1.99999ap-4f);
-    p = fmaf(p, x, -0x1.c71c72p-4f);
-    p = fmaf(p, x, 0.125f);
-    p = fmaf(p, x, -0x1.24924ap-3f);
-    p = fmaf(p, x, 0x1.555556p-3f);
-    p = fmaf(p, x, -0x1.99999ap-3f);
-    p = fmaf(p, x, 0.25f);
-    const float x2 = x * x;
-    const float q = (3.0f * g.d) * (x2 * x2) * p;
-    if (series && fmaf(q, 1.00001f, uo) < 0x1.fffff8p-1f) {
-      acc = true;
-    } else {
-      const int r = mt_slow_call(g.alpha, g.d, x, z, t, uo, q, series, RN.pos() - 1, stream,
-                                 a.rk.k[0][0], a.rk.k[0][1], a.cnt);
-      acc = (r & 1) != 0;
-      recheck = (r & 2) != 0;
-    }
-    float dv = g.d * (t * t * t);
-    if (acc && g.boost) {  // shapes below 1: Gamma(a + 1) U_b^(1/a), U_b after the accept
-      const float ub = RU.peek(0);
-      RU.advance(1);
-      dv = dv * expf(flog(ub + 0x1p-24f) / g.alpha);
-    }
-    *G = dv;
-  }
-  count_warp(&a.cnt->n_recheck, tclose || recheck);
-  return acc;
-}
-
-// The sweeps of one warp's 32 chains from the rings RN (N domain) and RU (U
-// domain): the warp's own circular rings or rings that producer warps fill
-// (brng_pc.cuh).  Leaves the final positions in s.pn, s.pu.
-//
-// The Gamma shape a0 + n/2 does not depend on the chain state, only the rate
-// does, so the Gamma(shape, 1) draws of a chain -- and the positions of the
-// normal and uniform elements each consumes -- follow from its streams alone.
-// Each round therefore evaluates W Marsaglia-Tsang attempts at once (ILP W),
-// speculating that each earlier one accepts: attempt i reads N element 2i (z)
-// and U element i, and its sweep's mu | tau normal is N element 2i + 1.  The
-// first k attempts that the log-free test accepts are exactly the sweeps the
-// one-at-a-time loop would run (same elements, same FP32 operations); the
-// cheap state recursion then runs over them.  The attempt after them (a
-// rejection, or one the fast test does not settle: about 0.05 % at shape 52)
 // puts the lane in exact mode: one attempt the exact way per round, in the
 // same round and the following ones, until one accepts and its sweep ends.
 // Shapes below 1 (boosted) stay in exact mode.  Each ring is refilled at one
@@ -270,8 +194,8 @@ __device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t str
   while (true) {
     const bool run = active && sweep < a.n_sweeps && !ring_failed(RN) && !ring_failed(RU);
     if (!__any_sync(kFull, run)) break;
-    RN.ensure(run, 2 * W, stream, a.rk);
-    RU.ensure(run, W, stream, a.rk);
+    RN.ensure(run, 2 * W, run, stream, a.rk);
+    RU.ensure(run, W, run, stream, a.rk);
     const bool spec = run && !exact;
     if (__any_sync(kFull, spec)) {
       float G[W], zm[W];
@@ -325,7 +249,7 @@ __device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t str
     const bool ex = run && exact && sweep < a.n_sweeps;
     if (__any_sync(kFull, ex)) {
       float G = 0.0f;
-      const bool acc = ng_exact_attempt(ex, g, RN, RU, stream, a, &G);
+      const bool acc = mt_attempt_peek<true, false>(ex, g, RN, RU, stream, a.rk, a.cnt, &G, nullptr);
       bool finish = false;
       if (ex) {
         ++att;
@@ -450,10 +374,11 @@ __device__ __forceinline__ void normal_gamma_unit(const NormalGammaArgs& a, uint
   const bool active = c < a.n_chains;
   const uint32_t stream = static_cast<uint32_t>(a.chain_offset + c);
   NgChain s = ng_load(a, c, active);
+  (void)list;
   CRing<GenN> RN;
   CRing<GenU> RU;
-  RN.init(ringN, list, a.B, s.pn);
-  RU.init(ringU, list, a.B, s.pu);
+  RN.init(ringN, nullptr, a.B, s.pn);
+  RU.init(ringU, nullptr, a.B, s.pu);
   ng_sweeps_any(a, stream, active, s, RN, RU);
   ng_store(a, c, active, s);
   __syncwarp();  // the rings are reused by the warp's next unit

@@ -19,6 +19,7 @@ constexpr uint32_t kDefaultWarpsPerBlock = 4;
 constexpr uint32_t kDefaultLookahead = 8;
 constexpr uint32_t kDefaultProducerWarps = BRNG_PRODUCERS_NONE;
 constexpr int kTagMixed = -1;
+constexpr uint32_t kBulkMinRing = 8;  // bulk streams use rings of at least this length
 
 // Launch geometry shared by all kernels: warps per block and ring length.
 struct Geometry {

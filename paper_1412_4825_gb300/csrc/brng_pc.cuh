@@ -107,7 +107,7 @@ struct PcRing {
 
   // Waits until k elements are available to every lane with `want` (all 32
   // lanes call this; k <= B - 3, since the producer writes whole blocks).
-  __device__ __forceinline__ void ensure(bool want, uint32_t k, uint32_t = 0,
+  __device__ __forceinline__ void ensure(bool want, uint32_t k, bool = false, uint32_t = 0,
                                          const RoundKeys& = RoundKeys{}) {
     bool need = want && static_cast<int32_t>(seen - static_cast<uint32_t>(p)) < static_cast<int32_t>(k);
     if (!__any_sync(kFull, need)) return;

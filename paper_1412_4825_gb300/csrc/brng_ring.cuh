@@ -164,34 +164,44 @@ struct Ring {
 // Element r (counted from the first element of Philox block b0) of a lane
 // lives in slot r mod B.  Unlike Ring, a refill appends blocks after the
 // last one generated instead of restarting the ring, so nothing is thrown
-// away, and a consumer may read (peek) any of the next `avail()` elements
-// before it commits to consuming them (advance).  ensure(want, k) makes at
-// least k elements available to lanes with `want`: each lane short of k
-// gets nb = (B - k + 1) / 4 >= 1 new blocks per round, which always fit (it
-// has at least B - k + 1 free slots; callers keep k <= B - 3).  When every lane is short
-// at once, as happens when the lanes consume in step, each lane generates
-// its own blocks, two at a time; otherwise the warp shares the work
-// round-robin as in Ring.
-template <class Gen>
+// away, and a consumer may read (peek) any of the next avail = filled - rp
+// elements before it commits to consuming them (advance).
+//
+// Refill is a top-up: when any lane with `want` has fewer than k elements
+// (ensure), every live lane appends as many whole blocks as its free slots
+// hold, nb = floor((rp + B - filled) / 4), generating its own column (no
+// shuffles, no lists).  Afterwards every live lane has at least B - 3
+// elements, so k <= B - 3 is always met by one top-up, even for a ring that
+// starts inside a block (rp > filled = 0).  Lanes that consume at different
+// rates (tags of a mixed stream, rejections) are thus refilled together, and
+// each refill does nearly a full ring of work per lane instead of a few
+// blocks for the few lanes that ran dry.  kWords: also keep each element's
+// raw Philox word.
+template <class Gen, bool kWords = false>
 struct CRing {
   using T = typename Gen::T;
   static constexpr uint32_t kEPB = Gen::kEPB;
   static_assert(kEPB == 4, "four elements per block");
   T* val;          // shared: [B][32]
-  uint32_t* list;  // shared: 32 entries
+  uint32_t* wrd;   // shared: [B][32] when kWords
   uint64_t b0;     // Philox block of relative element 0
   uint32_t rp;     // next relative element to consume
   uint32_t filled; // relative elements generated (multiple of 4)
   uint32_t mask;   // B - 1
+  bool live = false;  // get(): also top up this lane when another runs dry
 
-  __device__ __forceinline__ void init(T* v, uint32_t* l, uint32_t len, uint64_t pos) {
-    val = v; list = l; mask = len - 1;
+  __device__ __forceinline__ void init(T* v, uint32_t* w, uint32_t len, uint64_t pos) {
+    val = v; wrd = w; mask = len - 1;
     b0 = pos / kEPB;
     rp = static_cast<uint32_t>(pos % kEPB);
     filled = 0;
   }
   __device__ __forceinline__ uint64_t pos() const { return b0 * kEPB + rp; }
+  __device__ __forceinline__ int32_t avail() const { return static_cast<int32_t>(filled - rp); }
   __device__ __forceinline__ T peek(uint32_t i) const { return val[((rp + i) & mask) * 32u + lane_id()]; }
+  __device__ __forceinline__ uint32_t peek_word(uint32_t i) const {
+    return wrd[((rp + i) & mask) * 32u + lane_id()];
+  }
   __device__ __forceinline__ void advance(uint32_t n) { rp += n; }
 
   __device__ __forceinline__ void gen_own(uint64_t blk, uint32_t slot, uint32_t stream,
@@ -200,88 +210,57 @@ struct CRing {
     T v[kEPB];
     Gen::gen(w, v);
 #pragma unroll
-    for (uint32_t i = 0; i < kEPB; ++i) val[(slot + i) * 32u + lane_id()] = v[i];
+    for (uint32_t i = 0; i < kEPB; ++i) {
+      val[(slot + i) * 32u + lane_id()] = v[i];
+      if (kWords) wrd[(slot + i) * 32u + lane_id()] = word_of(w, i);
+    }
   }
 
-  // (inline: the round keys stay kernel parameters, read from the constant bank)
-  __device__ __forceinline__ void refill(unsigned m, bool need, uint32_t k, uint32_t stream,
-                                         const RoundKeys& rk) {
-    const uint32_t B = mask + 1;
-    const uint32_t nb = (B - k + 1) / kEPB;
-    if (need && filled >= rp) {  // keep the relative counters small: drop whole rings already read
+  // Lanes with `live` fill every free slot (inline: the round keys stay
+  // kernel parameters, read from the constant bank).
+  __device__ __forceinline__ void topup(bool live, uint32_t stream, const RoundKeys& rk) {
+    if (!live) return;
+    if (filled >= rp) {  // keep the relative counters small: drop whole rings already read
       const uint32_t D = rp & ~mask;
       b0 += D / kEPB;
       rp -= D;
       filled -= D;
     }
-    if (m == kFull) {  // every lane short: each fills its own column
-      const uint64_t first = b0 + filled / kEPB;
-      uint32_t j = 0;
-      for (; j + 2 <= nb; j += 2) {
-        gen_own(first + j, (filled + j * kEPB) & mask, stream, rk);
-        gen_own(first + j + 1, (filled + (j + 1) * kEPB) & mask, stream, rk);
-      }
-      if (j < nb) gen_own(first + j, (filled + j * kEPB) & mask, stream, rk);
-      filled += nb * kEPB;
-      return;  // each lane wrote only its own column
+    const uint32_t nb = (rp + mask + 1u - filled) / kEPB;
+    const uint64_t first = b0 + filled / kEPB;
+    uint32_t j = 0;
+    for (; j + 2 <= nb; j += 2) {  // two blocks in flight
+      gen_own(first + j, (filled + j * kEPB) & mask, stream, rk);
+      gen_own(first + j + 1, (filled + (j + 1) * kEPB) & mask, stream, rk);
     }
-    const unsigned lane = lane_id();
-    if (need) list[__popc(m & ((1u << lane) - 1u))] = lane;
-    __syncwarp();
-    const uint32_t kk = __popc(m);
-    const uint32_t total = kk * nb;
-    uint32_t rank = lane % kk, b = lane / kk;
-    const uint32_t step_r = 32u % kk, step_b = 32u / kk;
-    const uint64_t next = b0 + filled / kEPB;
-    for (uint32_t q0 = 0; q0 < total; q0 += 32) {
-      const uint32_t tgt = list[rank];
-      const uint64_t tblk = shfl_u64(next, static_cast<int>(tgt));
-      const uint32_t tfill = __shfl_sync(kFull, filled, static_cast<int>(tgt));
-      const uint32_t tstream = __shfl_sync(kFull, stream, static_cast<int>(tgt));
-      if (q0 + lane < total) {
-        const uint4 w = philox_block(tblk + b, Gen::kDom, tstream, rk);
-        T v[kEPB];
-        Gen::gen(w, v);
-        const uint32_t slot = (tfill + b * kEPB) & mask;
-#pragma unroll
-        for (uint32_t i = 0; i < kEPB; ++i) val[(slot + i) * 32u + tgt] = v[i];
-      }
-      rank += step_r;
-      b += step_b;
-      if (rank >= kk) {
-        rank -= kk;
-        b += 1;
-      }
-    }
-    __syncwarp();
-    if (need) filled += nb * kEPB;
+    if (j < nb) gen_own(first + j, (filled + j * kEPB) & mask, stream, rk);
+    filled += nb * kEPB;
   }
 
-  // At least k elements available for every lane with `want` (all 32 lanes
-  // call).  Availability is signed: a ring that starts inside a block has
-  // rp > filled = 0 until its first refill, so a lane can fall short of k
-  // once more after one refill; each round adds at least one block to every
-  // short lane, so this ends within a few rounds (bounded all the same).
-  __device__ __forceinline__ void ensure(bool want, uint32_t k, uint32_t stream, const RoundKeys& rk) {
-    for (int round = 0; round < 64; ++round) {
-      const bool need = want && static_cast<int32_t>(filled - rp) < static_cast<int32_t>(k);
-      const unsigned m = __ballot_sync(kFull, need);
-      if (!m) break;
-      refill(m, need, k, stream, rk);
-    }
+  // At least k <= B - 3 elements for every lane with `want` (all 32 lanes call).
+  __device__ __forceinline__ void ensure(bool want, uint32_t k, bool live, uint32_t stream,
+                                         const RoundKeys& rk) {
+    const bool need = want && avail() < static_cast<int32_t>(k);
+    if (__any_sync(kFull, need)) topup(live || need, stream, rk);
   }
 
-  // Next element for lanes with `want` (all 32 lanes call this); same call
-  // shape as Ring::get.
-  __device__ __forceinline__ T get(bool want, uint32_t stream, const RoundKeys& rk,
-                                   uint32_t* = nullptr, uint64_t* = nullptr) {
-    ensure(want, 1, stream, rk);
+  // Next element for lanes with `want` (all 32 lanes call this); `live`: the
+  // lane's stream is still in use (topped up along with the needy ones).
+  __device__ __forceinline__ T take(bool want, bool live, uint32_t stream, const RoundKeys& rk,
+                                    uint32_t* word = nullptr) {
+    ensure(want, 1, live, stream, rk);
     T v = T(0);
     if (want) {
       v = peek(0);
+      if (kWords && word) *word = peek_word(0);
       ++rp;
     }
     return v;
+  }
+  // Ring::get's call shape; the lane is topped up when it wants or is `live`.
+  __device__ __forceinline__ T get(bool want, uint32_t stream, const RoundKeys& rk,
+                                   uint32_t* word = nullptr, uint64_t* = nullptr) {
+    return take(want, want || live, stream, rk, word);
   }
 };
 
