@@ -40,6 +40,11 @@ METRIC = "Gibbs updates/s (normal-gamma, varying-parameter Gamma+Normal draws)"
 UNIT = "updates/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 PHILOX_MULS_PER_BLOCK = 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one normal_gamma_kernel
+# launch at this workload, from a full ncu capture of the current kernel
+# (profiles/normal_gamma_kernel_65536x2000.md); the data, state and moment
+# arrays only -- the rings live in shared memory
+NG_DRAM_BYTES_PER_LAUNCH = 4564992
 
 
 def _clock_sampler(uuid):
@@ -196,8 +201,8 @@ def extras(dev, stream, peaks, args):
     w = torch.empty(n, dtype=torch.int32, device=dev)
     hm = B.Handle(SEED, S)
     rec = {}
-    for bl in (8, 16, 32):
-        hm.tune(buf_len=bl)
+    for bl in (8, 16):
+        hm.tune(buf_len=bl, warps_per_block=2)
         rec[bl] = _time_s(lambda: B.brng_mixed(hm.h, tag, p0, p1, o, w, stream), stream)
     bl = min(rec, key=rec.get)
     t = rec[bl]
@@ -425,7 +430,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_blocks / 1e9,
-                     "unit": "GPhilox-block/s", "frac": achieved / peak_blocks, "traffic": None,
+                     "unit": "GPhilox-block/s", "frac": achieved / peak_blocks, "traffic": NG_DRAM_BYTES_PER_LAUNCH,
                      "kernel": "normal_gamma_kernel",
                      "probe_measured": probe_blocks_s / 1e9,
                      "note": "integer pipe: 20 32x32->64 multiplies per Philox4x32-10 block; blocks = "
@@ -445,6 +450,66 @@ def run_gpu(args):
     return 0
 
 
+def run_case(args):
+    """One secondary workload at a chosen size, timed with CUDA events (for
+    profiling commands): prints {"case", "ms": [...], ...}."""
+    import numpy as np
+    import torch
+
+    from paper_1412_4825_gb300 import build_lib
+    build_lib.build()
+    from paper_1412_4825_gb300 import brng as B
+    from paper_1412_4825_gb300 import inputs
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    reps = max(1, args.steps)
+    info = {"case": args.case}
+    if args.case == "mixed":
+        n, S = 1 << args.log2n, 1 << args.log2s
+        tag, p0, p1 = inputs.mixed_stream_torch(n, seed=SEED, device=dev)
+        o = torch.empty(n, dtype=torch.float32, device=dev)
+        w = torch.empty(n, dtype=torch.int32, device=dev)
+        h = B.Handle(SEED, S)
+        h.tune(buf_len=args.buf_len or 8, warps_per_block=args.warps_per_block)
+        fn = lambda: B.brng_mixed(h.h, tag, p0, p1, o, w, stream)  # noqa: E731
+        info.update(draws=n, streams=S, bytes_per_launch=17 * n)
+    elif args.case == "lda":
+        alpha, _, _ = inputs.lda_alpha(args.docs, K=64, seed=SEED)
+        a = torch.from_numpy(alpha).to(dev)
+        theta = torch.zeros((args.docs, 64), dtype=torch.float32, device=dev)
+        pos = torch.zeros((args.docs, 64, 2), dtype=torch.int64, device=dev)
+        mom = torch.zeros((args.docs, 64), dtype=torch.float64, device=dev)
+        h = B.Handle(SEED, 1)
+        if args.buf_len:
+            h.tune(buf_len=args.buf_len)
+        lp = B.brng_lda_params_t(64, a.data_ptr())
+        ls = B.brng_lda_state_t(theta.data_ptr(), pos.data_ptr())
+        fn = lambda: B.brng_gibbs_run(h.h, B.MODEL_LDA, 0, args.docs, args.sweeps, lp, ls, mom, stream)  # noqa: E731
+        info.update(docs=args.docs, sweeps=args.sweeps, K=64)
+    elif args.case == "triangle":
+        h = B.Handle(SEED, 1)
+        h.tune(buf_len=256, lanes_per_chain=4)
+        st = B.triangle_state(1024, device=dev)
+        mom = torch.zeros((1024, 5), dtype=torch.float64, device=dev)
+        fn = lambda: B.brng_gibbs_run(h.h, B.MODEL_TRIANGLE, 0, 1024, args.sweeps, None, st, mom, stream)  # noqa: E731
+        info.update(chains=1024, sweeps=args.sweeps)
+    else:
+        raise SystemExit("unknown case %r" % args.case)
+    for _ in range(args.warmup):
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a0, a1 in ev:
+        a0.record(stream)
+        fn()
+        a1.record(stream)
+    torch.cuda.synchronize()
+    info["ms"] = [round(a0.elapsed_time(a1), 4) for a0, a1 in ev]
+    info["counters"] = h.counters()[1]
+    print(json.dumps(info), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -458,7 +523,15 @@ def main():
                     help="skip the secondary workloads (triangle, LDA, mixed stream, batched vs plain, served mix)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="arrival window of the served mix at 2,000 jobs/s")
+    ap.add_argument("--case", choices=["mixed", "lda", "triangle"], default=None,
+                    help="time one secondary workload instead (profiling): mixed, lda or triangle")
+    ap.add_argument("--log2n", type=int, default=28, help="--case mixed: log2 of the draws")
+    ap.add_argument("--log2s", type=int, default=20, help="--case mixed: log2 of the streams")
+    ap.add_argument("--docs", type=int, default=16384, help="--case lda: documents")
+    ap.add_argument("--sweeps", type=int, default=500, help="--case lda/triangle: sweeps")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
