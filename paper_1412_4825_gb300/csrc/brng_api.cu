@@ -255,13 +255,14 @@ int brng_dirichlet(brng_t* h, size_t n_rows, uint32_t K, const float* alpha, flo
   if (n_rows == 0) return BRNG_OK;
   if (!alpha || !out) return BRNG_EINVAL;
   const uint32_t P = K <= 32 ? 1 : K <= 64 ? 2 : 4;
-  const size_t per_warp = 128u + h->tune.lookahead * 32u * P * 4u + 2u * P * h->tune.buf_len * 128u;
+  const uint32_t B = brng::ring_len_min8(h->tune.buf_len);
+  const size_t per_warp = 128u + h->tune.lookahead * 32u * P * 4u + 2u * P * B * 128u;
   const brng::Geometry g = geometry(h, per_warp);
   if (g.warps_per_block == 0) return BRNG_EINVAL;
   brng::DirichletArgs a{};
   a.rk = h->rk;
   a.K = K;
-  a.B = h->tune.buf_len;
+  a.B = B;
   a.lookahead = h->tune.lookahead;
   a.n_rows = n_rows;
   a.R = h->S / K;
@@ -331,7 +332,7 @@ int make_job(const brng_t* h, brng_model_t model, const brng::RoundKeys& rk, uin
       brng::DirichletArgs& a = j->lda;
       a.rk = rk;
       a.K = p->K;
-      a.B = h->tune.buf_len;
+      a.B = brng::ring_len_min8(h->tune.buf_len);
       a.lookahead = h->tune.lookahead;
       a.alpha = p->alpha;
       a.out = s->theta;
@@ -451,7 +452,7 @@ int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_
     }
     default: {
       const uint32_t P = lda_p(j.lda.K);
-      const size_t per_warp = 128u + h->tune.lookahead * 32u * P * 4u + 2u * P * h->tune.buf_len * 128u;
+      const size_t per_warp = 128u + h->tune.lookahead * 32u * P * 4u + 2u * P * j.lda.B * 128u;
       const brng::Geometry g = geometry(h, per_warp);
       if (g.warps_per_block == 0) return BRNG_EINVAL;
       return cuda_status(brng::launch_dirichlet(j.lda, g, true, st));

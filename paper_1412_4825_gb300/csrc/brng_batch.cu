@@ -62,7 +62,7 @@ size_t batch_warp_bytes(bool tri, bool ng, bool lda, uint32_t B, uint32_t P, uin
   size_t w = 128;
   if (tri && triangle_warp_bytes(32, B) > w) w = triangle_warp_bytes(32, B);
   if (ng && normal_gamma_warp_bytes(B) > w) w = normal_gamma_warp_bytes(B);
-  if (lda && dirichlet_warp_bytes(P, B, Q) > w) w = dirichlet_warp_bytes(P, B, Q);
+  if (lda && dirichlet_warp_bytes(P, ring_len_min8(B), Q) > w) w = dirichlet_warp_bytes(P, ring_len_min8(B), Q);
   return w;
 }
 

@@ -7,7 +7,7 @@
 namespace brng {
 
 template <int P, bool LDA>
-__global__ void __launch_bounds__(512) dirichlet_kernel(const DirichletArgs a) {
+__global__ void __maxnreg__(128) dirichlet_kernel(const DirichletArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned warp = threadIdx.x >> 5;
   const uint64_t unit = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + warp;

@@ -32,8 +32,6 @@
 
 namespace brng {
 
-
-
 __host__ __device__ inline uint32_t dirichlet_warp_bytes(uint32_t P, uint32_t B, uint32_t Q) {
   return 128u + Q * 32u * P * 4u + 2u * P * B * 32u * 4u;
 }
@@ -57,8 +55,7 @@ __device__ __forceinline__ void dirichlet_unit(const DirichletArgs& a, uint64_t 
   const unsigned lane = lane_id();
   const uint32_t Q = a.lookahead;
   const uint32_t KP = 32u * P;
-  uint32_t* list = reinterpret_cast<uint32_t*>(base);
-  float* q = reinterpret_cast<float*>(base + 128);
+  float* q = reinterpret_cast<float*>(base + 128);  // (the first 128 bytes are unused)
   float* rings = reinterpret_cast<float*>(base + 128 + Q * KP * 4u);
   const uint64_t n_units = LDA ? a.n_docs : (a.n_rows < a.R ? a.n_rows : a.R);
   if (unit >= n_units) return;  // whole warp
@@ -66,8 +63,8 @@ __device__ __forceinline__ void dirichlet_unit(const DirichletArgs& a, uint64_t 
   const uint32_t nrows = LDA ? a.n_sweeps
                              : static_cast<uint32_t>((a.n_rows - unit + a.R - 1) / a.R);
 
-  Ring<GenN, 32, false> RN[P];
-  Ring<GenU, 32, false> RU[P];
+  CRing<GenN> RN[P];
+  CRing<GenU> RU[P];
   GammaState g[P];
   uint32_t stream[P], done[P];
   int att[P];
@@ -89,8 +86,8 @@ __device__ __forceinline__ void dirichlet_unit(const DirichletArgs& a, uint64_t 
         pu = a.pos[sid];
       }
     }
-    RN[p].init(rings + (2 * p) * a.B * 32u, nullptr, list, a.B, pn);
-    RU[p].init(rings + (2 * p + 1) * a.B * 32u, nullptr, list, a.B, pu);
+    RN[p].init(rings + (2 * p) * a.B * 32u, nullptr, a.B, pn);
+    RU[p].init(rings + (2 * p + 1) * a.B * 32u, nullptr, a.B, pu);
     done[p] = 0;
     att[p] = 0;
     fresh[p] = true;
@@ -124,6 +121,7 @@ __device__ __forceinline__ void dirichlet_unit(const DirichletArgs& a, uint64_t 
 
   uint32_t tn = 0;
   while (tn < nrows) {
+    bool run[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       const bool work = kvalid[p] && done[p] < nrows && done[p] < tn + Q;
@@ -133,23 +131,31 @@ __device__ __forceinline__ void dirichlet_unit(const DirichletArgs& a, uint64_t 
         ++done[p];
         fresh[p] = true;
       }
-      const bool run = work && rowok;
-      if (run && fresh[p]) {
+      run[p] = work && rowok;
+      if (run[p] && fresh[p]) {
         const uint64_t row = LDA ? unit : unit + static_cast<uint64_t>(done[p]) * a.R;
         g[p] = gamma_setup(a.alpha[row * K + lane + 32u * p]);
         fresh[p] = false;
       }
+    }
+    // one top-up point per ring: an attempt takes at most 1 N and 2 U (u, u_b)
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const bool live = kvalid[p] && done[p] < nrows;
+      RN[p].ensure(run[p], 1, live, stream[p], a.rk);
+      RU[p].ensure(run[p], 2, live, stream[p], a.rk);
+    }
+    // the P attempts of a lane are independent: no warp vote between them
+    bool rejected = false, rechecked = false;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
       float dv = 0.0f;
-      uint32_t zw;
-      const bool acc = mt_attempt(run, g[p], RN[p], RU[p], stream[p], a.rk, a.cnt, &dv, &zw);
-      const bool boost_now = run && acc && g[p].boost;
       float lb = 0.0f;  // log of the boost factor u_b^(1/alpha)
-      if (__any_sync(kFull, boost_now)) {  // warp-uniform: shapes below 1 only
-        const float ub = RU[p].get(boost_now, stream[p], a.rk);
-        if (boost_now) lb = flog(ub + 0x1p-24f) / g[p].alpha;
-      }
-      bool rejected = false;
-      if (run) {
+      bool rc = false;
+      const bool acc = mt_attempt_peek<false, false, true>(run[p], g[p], RN[p], RU[p], stream[p], a.rk,
+                                                           a.cnt, &dv, nullptr, &lb, &rc);
+      rechecked = rechecked || rc;
+      if (run[p]) {
         ++att[p];
         if (acc || att[p] >= kGammaMaxAttempts) {
           float l = __int_as_float(0x7fc00000);
@@ -164,8 +170,9 @@ __device__ __forceinline__ void dirichlet_unit(const DirichletArgs& a, uint64_t 
           fresh[p] = !LDA;
         }
       }
-      count_warp(&a.cnt->n_reject, rejected);
     }
+    count_warp(&a.cnt->n_recheck, rechecked);
+    count_warp(&a.cnt->n_reject, rejected);
     // normalise every row all components have finished
     uint32_t mn = 0xffffffffu;
 #pragma unroll

@@ -217,10 +217,15 @@ __device__ __forceinline__ bool mt_attempt(bool run, const GammaState& g, RN& N,
 // accept, which it folds in: on accept *dv = Gamma(alpha) (FP32).  *zword
 // gets z's raw word when the N ring keeps words.  Consumes exactly what
 // mt_attempt plus the caller's boost draw consume.
-template <bool kLargeShape, bool kZWord, class RNT, class RUT>
+// kLogBoost: leave *dv = d v and return the boost in log form in *lboost
+// (ln U_b / alpha, 0 without boost) for callers that work in log space.
+// rechecked != nullptr: no warp vote inside (the caller counts the rechecks,
+// e.g. after several independent attempts, which then overlap).
+template <bool kLargeShape, bool kZWord, bool kLogBoost = false, class RNT, class RUT>
 __device__ __forceinline__ bool mt_attempt_peek(bool run, const GammaState& g, RNT& N, RUT& U,
                                                 uint32_t stream, const RoundKeys& rk,
-                                                DevCounters* cnt, float* dv, uint32_t* zword) {
+                                                DevCounters* cnt, float* dv, uint32_t* zword,
+                                                float* lboost = nullptr, bool* rechecked = nullptr) {
   float z = 0.0f;
   if (run) {
     z = N.peek(0);
@@ -270,11 +275,14 @@ __device__ __forceinline__ bool mt_attempt_peek(bool run, const GammaState& g, R
     if (acc && g.boost) {  // shapes below 1: Gamma(a + 1) U_b^(1/a), U_b after the accept
       const float ub = U.peek(0);
       U.advance(1);
-      v = v * expf(flog(ub + 0x1p-24f) / g.alpha);
+      const float lb = __fdividef(flog(ub + 0x1p-24f), g.alpha);
+      if constexpr (kLogBoost) *lboost = lb;
+      else v = v * expf(lb);
     }
     *dv = v;
   }
-  count_warp(&cnt->n_recheck, tclose || recheck);
+  if (rechecked) *rechecked = tclose || recheck;
+  else count_warp(&cnt->n_recheck, tclose || recheck);
   return acc;
 }
 
