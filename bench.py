@@ -166,18 +166,16 @@ def extras(dev, stream, peaks, args):
     from paper_1412_4825_gb300 import inputs, serve
 
     out = {}
-    # -- triangle (Eq. 1, Fig. 1): buffers of 256 FP64 uniforms per chain
+    from paper_1412_4825_gb300 import autotune as AT
+    # -- triangle (Eq. 1, Fig. 1): FP64, 1,024 chains; tuning chosen by the autotuner
     h = B.Handle(SEED, 1)
-    rec = {}
-    for lanes in (1, 4, 32):
-        h.tune(buf_len=256, lanes_per_chain=lanes)
-        st = B.triangle_state(1024, device=dev)
-        mom = torch.zeros((1024, 5), dtype=torch.float64, device=dev)
-        t = _time_s(lambda: B.brng_gibbs_run(h.h, B.MODEL_TRIANGLE, 0, 1024, 10000, None, st, mom, stream), stream)
-        rec[lanes] = 2 * 1024 * 10000 / t
-    best = max(rec, key=rec.get)
-    out["triangle_1024x10000"] = {"updates_per_s": rec[best], "ms": 2 * 1024 * 10000 / rec[best] * 1e3,
-                                  "lanes_per_chain": best, "by_lanes_per_chain": rec}
+    st = B.triangle_state(1024, device=dev)
+    mom = torch.zeros((1024, 5), dtype=torch.float64, device=dev)
+    run_tri = lambda: B.brng_gibbs_run(h.h, B.MODEL_TRIANGLE, 0, 1024, 10000, None, st, mom, stream)  # noqa: E731
+    tune, _, table = AT.autotune(h, run_tri, AT.SPACES["triangle"], stream, "triangle-1024x10000")
+    t = _time_s(run_tri, stream)
+    out["triangle_1024x10000"] = {"updates_per_s": 2 * 1024 * 10000 / t, "ms": t * 1e3, "tuning": tune,
+                                  "autotune_ms": table}
     h.close()
     # -- LDA document-topic Dirichlet step
     alpha, _, _ = inputs.lda_alpha(16384, K=64, seed=SEED)
@@ -188,10 +186,12 @@ def extras(dev, stream, peaks, args):
     h = B.Handle(SEED, 1)
     lp = B.brng_lda_params_t(64, a.data_ptr())
     ls = B.brng_lda_state_t(theta.data_ptr(), pos.data_ptr())
-    t = _time_s(lambda: B.brng_gibbs_run(h.h, B.MODEL_LDA, 0, 16384, 500, lp, ls, mom, stream), stream)
+    run_lda = lambda: B.brng_gibbs_run(h.h, B.MODEL_LDA, 0, 16384, 500, lp, ls, mom, stream)  # noqa: E731
+    tune, _, table = AT.autotune(h, run_lda, AT.SPACES["lda"], stream, "lda-16384x64x500", reps=2)
+    t = _time_s(run_lda, stream)
     out["lda_16384x64x500"] = {"dirichlet_updates_per_s": 16384 * 500 / t,
                                "gamma_deviates_per_s": 16384 * 64 * 500 / t, "ms": t * 1e3,
-                               "tuning": h.tuning}
+                               "tuning": tune, "autotune_ms": table}
     h.close()
     del a, theta, pos, mom
     # -- mixed varying-parameter stream, 17 B per draw through HBM
@@ -200,15 +200,11 @@ def extras(dev, stream, peaks, args):
     o = torch.empty(n, dtype=torch.float32, device=dev)
     w = torch.empty(n, dtype=torch.int32, device=dev)
     hm = B.Handle(SEED, S)
-    rec = {}
-    for bl in (8, 16):
-        hm.tune(buf_len=bl, warps_per_block=2)
-        rec[bl] = _time_s(lambda: B.brng_mixed(hm.h, tag, p0, p1, o, w, stream), stream)
-    bl = min(rec, key=rec.get)
-    t = rec[bl]
+    run_mixed = lambda: B.brng_mixed(hm.h, tag, p0, p1, o, w, stream)  # noqa: E731
+    tune, _, table = AT.autotune(hm, run_mixed, AT.SPACES["mixed"], stream, "mixed-2^28-2^20", reps=2)
+    t = _time_s(run_mixed, stream)
     gbs = 17.0 * n / t / 1e9
-    out["mixed_2^28"] = {"deviates_per_s": n / t, "ms": t * 1e3, "buf_len": bl,
-                         "ms_by_buf_len": {k: v * 1e3 for k, v in rec.items()},
+    out["mixed_2^28"] = {"deviates_per_s": n / t, "ms": t * 1e3, "tuning": tune, "autotune_ms": table,
                          "hbm_achieved_gbs": gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"),
                          "hbm_frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None}
     hm.close()
@@ -306,7 +302,8 @@ def run_gpu(args):
                       inputs.normal_gamma_data(chain_offset + N_CHAINS, n_obs=N_OBS, seed=SEED))
     stream = torch.cuda.Stream(device=dev)
     h = B.Handle(SEED, 1)
-    if args.buf_len or args.warps_per_block:
+    fixed = bool(args.buf_len or args.warps_per_block)
+    if fixed:
         h.tune(buf_len=args.buf_len, warps_per_block=args.warps_per_block)
     d_nobs, d_xbar, d_sc = (torch.from_numpy(a).to(dev) for a in (nobs, xbar, sc))
     params = B.brng_normal_gamma_params_t(*PRIOR, d_nobs.data_ptr(), d_xbar.data_ptr(), d_sc.data_ptr())
@@ -324,6 +321,11 @@ def run_gpu(args):
             pg.barrier()
         torch.cuda.synchronize(dev)
 
+    autotune_table = None
+    if not fixed:  # launch knobs picked by measurement (results do not depend on them)
+        from paper_1412_4825_gb300 import autotune as AT
+        _, _, autotune_table = AT.autotune(h, step, AT.SPACES["normal_gamma"], stream,
+                                           "normal-gamma-%dx%d" % (N_CHAINS, N_SWEEPS))
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
@@ -425,7 +427,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "chains_per_gpu": N_CHAINS, "sweeps": N_SWEEPS,
                    "updates_per_step_per_gpu": UPDATES_PER_STEP, "parallelism": "chains sharded by rank",
-                   "l2": "flushed between timed steps (512 MB write)", "tuning": h.tuning},
+                   "l2": "flushed between timed steps (512 MB write)", "tuning": h.tuning,
+                   "autotune_ms": autotune_table},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
@@ -517,7 +520,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--buf-len", type=int, default=0)
-    ap.add_argument("--warps-per-block", type=int, default=8)
+    ap.add_argument("--warps-per-block", type=int, default=0,
+                    help="fix the warps per block (with --buf-len: no autotuning of the headline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary workloads (triangle, LDA, mixed stream, batched vs plain, served mix)")

@@ -77,11 +77,20 @@ __device__ __forceinline__ float2 box_muller(uint32_t w0, uint32_t w1) {
 
 __device__ __forceinline__ float exp1(uint32_t w) { return -flog(u01_open(w)); }
 
-// 53-bit uniform from two words: ((w0>>5) 2^26 + (w1>>6)) 2^-53, exact
+// 53-bit uniform from two words: ((w0>>5) 2^26 + (w1>>6)) 2^-53, exact.
+// Built from the bits with integer operations only (normalise the 53-bit
+// integer m, then set the exponent), since GB300's FP64 pipe is narrow: the
+// value m 2^-53 is exactly representable, so this is the same double a
+// conversion and a multiply would give.
 __device__ __forceinline__ double u53(uint32_t w0, uint32_t w1) {
   const unsigned long long m =
       (static_cast<unsigned long long>(w0 >> 5) << 26) | static_cast<unsigned long long>(w1 >> 6);
-  return __dmul_rn(__ull2double_rn(m), 0x1p-53);
+  if (m == 0) return 0.0;
+  const int sh = __clzll(m) - 11;  // bit 52 becomes the leading one
+  const unsigned long long mant = m << sh;
+  const unsigned long long bits =
+      (static_cast<unsigned long long>(1022 - sh) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double(static_cast<long long>(bits));
 }
 
 }  // namespace brng

@@ -24,50 +24,81 @@ __host__ __device__ inline uint32_t triangle_warp_bytes(uint32_t NC, uint32_t B)
 
 // One work unit: NC chains (unit * NC .. unit * NC + NC - 1), one warp.
 // `base`: this warp's shared memory (triangle_warp_bytes(NC, a.B) bytes).
+//
+// With L = 32 / NC lanes per chain, the L lanes of a chain (one per group
+// g = lane / NC) all read the chain's U64 elements (a shared-memory broadcast)
+// and run the same x, y updates, and group g keeps the running sums
+// m_g, m_{g+L}, ... of the five moments (x, y, x^2, y^2, x y).  On GB300 the
+// FP64 pipe issues a warp instruction over many cycles, so what counts is FP64
+// warp instructions per sweep: 4 for the updates plus 2 per moment slot --
+// 5 slots with one lane per chain, 1 with eight or more.  Group 0 owns the
+// ring refills (the other groups read its columns in step).
 template <int NC>
 __device__ __forceinline__ void triangle_unit(const TriangleArgs& a, uint64_t unit,
                                               unsigned char* base) {
+  constexpr int L = 32 / NC;                  // lanes per chain
+  constexpr int SLOTS = (5 + L - 1) / L;      // moments per lane
   const unsigned lane = lane_id();
+  const unsigned col = lane % NC;
+  const unsigned grp = lane / NC;
   uint32_t* list = reinterpret_cast<uint32_t*>(base);
   double* ring = reinterpret_cast<double*>(base + 128);
   if (unit * NC >= a.n_chains) return;  // whole warp
-  const uint64_t c = unit * NC + lane;
-  const bool consumer = lane < static_cast<unsigned>(NC) && c < a.n_chains;
+  const uint64_t c = unit * NC + col;
+  const bool live = c < a.n_chains;
+  const bool owner = live && grp == 0;
   const uint32_t stream = static_cast<uint32_t>(a.chain_offset + c);
 
   double x = 0.0, y = 0.0;
-  double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0, m4 = 0.0;
+  double m[SLOTS];
   uint64_t pos = 0;
-  if (consumer) {
+  if (live) {
     const brng_triangle_state_t s = a.state[c];
     x = s.x;
     y = s.y;
     pos = s.pos;
-    const double* m = a.moments + 5 * c;
-    m0 = m[0]; m1 = m[1]; m2 = m[2]; m3 = m[3]; m4 = m[4];
+  }
+#pragma unroll
+  for (int k = 0; k < SLOTS; ++k) {
+    const unsigned j = grp + k * L;  // moment index of this slot
+    m[k] = (live && j < 5) ? a.moments[5 * c + j] : 0.0;
   }
   Ring<GenU64, NC, false> R;
   R.init(ring, nullptr, list, a.B, pos);
   for (uint32_t it = 0; it < a.n_sweeps; ++it) {
-    const double ux = R.get(consumer, stream, a.rk);
+    const double ux = R.get(live, stream, a.rk, nullptr, nullptr, grp == 0);
     x = __dmul_rn(__dadd_rn(1.0, -y), ux);
-    const double uy = R.get(consumer, stream, a.rk);
+    const double uy = R.get(live, stream, a.rk, nullptr, nullptr, grp == 0);
     y = __dmul_rn(__dadd_rn(1.0, -x), uy);
-    m0 = __dadd_rn(m0, x);
-    m1 = __dadd_rn(m1, y);
-    m2 = __dadd_rn(m2, __dmul_rn(x, x));
-    m3 = __dadd_rn(m3, __dmul_rn(y, y));
-    m4 = __dadd_rn(m4, __dmul_rn(x, y));
+    if constexpr (L == 1) {  // one lane per chain: all five sums here
+      m[0] = __dadd_rn(m[0], x);
+      m[1] = __dadd_rn(m[1], y);
+      m[2] = __dadd_rn(m[2], __dmul_rn(x, x));
+      m[3] = __dadd_rn(m[3], __dmul_rn(y, y));
+      m[4] = __dadd_rn(m[4], __dmul_rn(x, y));
+    } else {
+#pragma unroll
+      for (int k = 0; k < SLOTS; ++k) {
+        // moment j = grp + k L: x*1, y*1, x*x, y*y, x*y (times 1.0 is exact)
+        const unsigned j = grp + k * L;
+        const double f0 = (j == 1 || j == 3) ? y : x;
+        const double f1 = j < 2 ? 1.0 : (j == 2 ? x : y);
+        m[k] = __dadd_rn(m[k], __dmul_rn(f0, f1));
+      }
+    }
   }
-  if (consumer) {
+  if (owner) {
     brng_triangle_state_t s;
     s.x = x;
     s.y = y;
     s.pos = R.pos();
     s.pad = 0;
     a.state[c] = s;
-    double* m = a.moments + 5 * c;
-    m[0] = m0; m[1] = m1; m[2] = m2; m[3] = m3; m[4] = m4;
+  }
+#pragma unroll
+  for (int k = 0; k < SLOTS; ++k) {
+    const unsigned j = grp + k * L;
+    if (live && j < 5) a.moments[5 * c + j] = m[k];
   }
   __syncwarp();  // the ring is reused by the warp's next unit
 }
@@ -75,11 +106,8 @@ __device__ __forceinline__ void triangle_unit(const TriangleArgs& a, uint64_t un
 // ---------------------------------------------------------------------------
 // Normal-gamma Gibbs: per sweep tau | mu ~ Gamma(a0 + n/2, rate b0 + SS/2),
 // SS = S + n (xbar - mu)^2, then mu | tau ~ N((prec0 mu0 + tau n xbar)/P, 1/P),
-// P = prec0 + n tau.  The Gamma shape does not depend on the state, so a lane
-// runs one Marsaglia-Tsang attempt per loop iteration and, when it accepts,
-// finishes its sweep (draws mu) in the same iteration: lanes never idle while
-// a neighbour retries.  Moments: FP32 partials over 64 iterations (the warp
-// flushes together) added into FP64 accumulators.
+// P = prec0 + n tau.  The sweeps run in speculative rounds (ng_sweeps below);
+// moments are compensated FP32 sums added into FP64 at the end.
 // ---------------------------------------------------------------------------
 __host__ __device__ inline uint32_t normal_gamma_warp_bytes(uint32_t B) {
   return 128u + 2u * B * 32u * 4u;

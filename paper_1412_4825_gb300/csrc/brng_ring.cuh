@@ -100,19 +100,22 @@ struct Ring {
   }
   __device__ __forceinline__ uint64_t pos() const { return blk * kEPB + rp; }
 
-  // Refill the rings of the columns in `mask` (all 32 lanes call this).
-  // `col` is this lane's column (== lane for lane < NC), `stream` its stream.
-  __device__ __forceinline__ void refill(unsigned mask, bool need, uint32_t stream,
-                                      const RoundKeys& rk) {
+  // Refill the rings of the needy columns (all 32 lanes call this).  Lanes
+  // with `need` restart their ring; those that also have `gen` (one lane per
+  // column, lane == column) put their column on the list to generate.
+  // `stream` is this lane's stream.
+  __device__ __forceinline__ void refill(bool need, bool gen, uint32_t stream, const RoundKeys& rk) {
     const unsigned lane = lane_id();
+    const unsigned mask = __ballot_sync(kFull, need && gen);
     if (need) {
       blk += rp / kEPB;
       rp %= kEPB;
       valid = B;
-      list[__popc(mask & ((1u << lane) - 1u))] = lane;
+      if (gen) list[__popc(mask & ((1u << lane) - 1u))] = lane;
     }
     __syncwarp();
     const uint32_t k = __popc(mask);
+    if (k == 0) return;
     const uint32_t nblk = B / kEPB;
     const uint32_t total = k * nblk;
     uint32_t rank = lane % k, b = lane / k;
@@ -142,17 +145,19 @@ struct Ring {
   }
 
   // Next element for lanes with `want` (all 32 lanes call this).  Optional
-  // outputs: the element's raw word and its index in the stream.
+  // outputs: the element's raw word and its index in the stream.  `gen`:
+  // this lane generates its column when it runs dry (false for lanes that
+  // read a column another lane of the warp owns, in step with it).
   __device__ __forceinline__ T get(bool want, uint32_t stream, const RoundKeys& rk,
-                                   uint32_t* word = nullptr, uint64_t* index = nullptr) {
+                                   uint32_t* word = nullptr, uint64_t* index = nullptr,
+                                   bool gen = true) {
     const bool need = want && rp >= valid;
-    const unsigned mask = __ballot_sync(kFull, need);
-    if (mask) refill(mask, need, stream, rk);
+    if (__any_sync(kFull, need)) refill(need, gen, stream, rk);
     T v = T(0);
     if (want) {
       const unsigned lane = lane_id();
-      v = val[rp * NC + lane];
-      if (kWords && word) *word = wrd[rp * NC + lane];
+      v = val[rp * NC + (lane % NC)];
+      if (kWords && word) *word = wrd[rp * NC + (lane % NC)];
       if (index) *index = blk * kEPB + rp;
       ++rp;
     }
