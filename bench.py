@@ -484,15 +484,14 @@ def run_case(args):
         pos = torch.zeros((args.docs, 64, 2), dtype=torch.int64, device=dev)
         mom = torch.zeros((args.docs, 64), dtype=torch.float64, device=dev)
         h = B.Handle(SEED, 1)
-        if args.buf_len:
-            h.tune(buf_len=args.buf_len)
+        h.tune(buf_len=args.buf_len or 16, lookahead=16, warps_per_block=args.warps_per_block or 4)
         lp = B.brng_lda_params_t(64, a.data_ptr())
         ls = B.brng_lda_state_t(theta.data_ptr(), pos.data_ptr())
         fn = lambda: B.brng_gibbs_run(h.h, B.MODEL_LDA, 0, args.docs, args.sweeps, lp, ls, mom, stream)  # noqa: E731
         info.update(docs=args.docs, sweeps=args.sweeps, K=64)
     elif args.case == "triangle":
         h = B.Handle(SEED, 1)
-        h.tune(buf_len=256, lanes_per_chain=4)
+        h.tune(buf_len=256, lanes_per_chain=16)
         st = B.triangle_state(1024, device=dev)
         mom = torch.zeros((1024, 5), dtype=torch.float64, device=dev)
         fn = lambda: B.brng_gibbs_run(h.h, B.MODEL_TRIANGLE, 0, 1024, args.sweeps, None, st, mom, stream)  # noqa: E731
