@@ -210,62 +210,68 @@ def extras(dev, stream, peaks, args):
     hm.close()
     del tag, p0, p1, o, w
     torch.cuda.empty_cache()
-    # -- uneven ensemble: batched (one persistent launch) vs one kernel per job
-    rng = np.random.default_rng(SEED)
+    # -- uneven ensembles: batched (one persistent launch) vs one kernel per job
     pool = serve.InputPool(65536, 64, SEED)
-    specs = []
-    for i in range(48):
-        model = int(rng.integers(0, 3))
-        nch = int(min(65536, max(1, np.exp(rng.uniform(0, np.log(65537))))))
-        specs.append((model, nch, int(rng.integers(100, 10001)), SEED + 1 + i))
     d_nobs, d_xbar, d_sc = (torch.from_numpy(x).to(dev) for x in (pool.nobs, pool.xbar, pool.sc))
     d_alpha = torch.from_numpy(pool.alpha).to(dev)
-    keep = []
 
-    def fresh_jobs():
-        jobs = []
-        for model, nch, sw, seed in specs:
-            if model == B.MODEL_TRIANGLE:
-                st, mm, prm = B.triangle_state(nch, device=dev), torch.zeros((nch, 5), dtype=torch.float64, device=dev), None
-                sarg = st
-            elif model == B.MODEL_NORMAL_GAMMA:
-                st, mm = B.normal_gamma_state(nch, device=dev), torch.zeros((nch, 4), dtype=torch.float64, device=dev)
-                prm = B.brng_normal_gamma_params_t(2.0, 1.0, 0.0, 0.01, d_nobs.data_ptr(), d_xbar.data_ptr(),
-                                                   d_sc.data_ptr())
-                sarg = st
-            else:
-                th = torch.zeros((nch, 64), dtype=torch.float32, device=dev)
-                ps = torch.zeros((nch, 64, 2), dtype=torch.int64, device=dev)
-                mm = torch.zeros((nch, 64), dtype=torch.float64, device=dev)
-                prm = B.brng_lda_params_t(64, d_alpha.data_ptr())
-                sarg = B.brng_lda_state_t(th.data_ptr(), ps.data_ptr())
-                keep.append((th, ps))
-            keep.append((sarg, mm, prm))
-            jobs.append((model, nch, sw, seed, prm, sarg, mm))
-        return jobs
+    def ensemble(n_jobs, max_chains, sweeps, seed):
+        rng = np.random.default_rng(seed)
+        specs = []
+        for i in range(n_jobs):
+            model = int(rng.integers(0, 3))
+            nch = int(min(max_chains, max(1, np.exp(rng.uniform(0, np.log(max_chains + 1))))))
+            specs.append((model, nch, int(rng.integers(sweeps[0], sweeps[1] + 1)), seed + 1 + i))
+        keep = []
 
-    upd = sum((1 if m == B.MODEL_LDA else 2) * c * s for m, c, s, _ in specs)
-    hb = B.Handle(SEED, 1)
-    handles = {seed: B.Handle(seed, 1) for _, _, _, seed in specs}
-    jobs = fresh_jobs()
+        def fresh_jobs():
+            jobs = []
+            for model, nch, sw, sd in specs:
+                if model == B.MODEL_TRIANGLE:
+                    st = B.triangle_state(nch, device=dev)
+                    mm, prm, sarg = torch.zeros((nch, 5), dtype=torch.float64, device=dev), None, st
+                elif model == B.MODEL_NORMAL_GAMMA:
+                    st = B.normal_gamma_state(nch, device=dev)
+                    mm = torch.zeros((nch, 4), dtype=torch.float64, device=dev)
+                    prm = B.brng_normal_gamma_params_t(2.0, 1.0, 0.0, 0.01, d_nobs.data_ptr(), d_xbar.data_ptr(),
+                                                       d_sc.data_ptr())
+                    sarg = st
+                else:
+                    th = torch.zeros((nch, 64), dtype=torch.float32, device=dev)
+                    ps = torch.zeros((nch, 64, 2), dtype=torch.int64, device=dev)
+                    mm = torch.zeros((nch, 64), dtype=torch.float64, device=dev)
+                    prm = B.brng_lda_params_t(64, d_alpha.data_ptr())
+                    sarg = B.brng_lda_state_t(th.data_ptr(), ps.data_ptr())
+                    keep.append((th, ps))
+                keep.append((sarg, mm, prm))
+                jobs.append((model, nch, sw, sd, prm, sarg, mm))
+            return jobs
 
-    def plain():
-        for model, nch, sw, seed, prm, sarg, mm in jobs:
-            B.brng_gibbs_run(handles[seed].h, model, 0, nch, sw, prm, sarg, mm, stream)
+        upd = sum((1 if m == B.MODEL_LDA else 2) * c * sw for m, c, sw, _ in specs)
+        hb = B.Handle(SEED, 1)
+        handles = {sd: B.Handle(sd, 1) for _, _, _, sd in specs}
+        jobs = fresh_jobs()
 
-    t_plain = _time_s(plain, stream, reps=2, warm=1)
-    jobs = fresh_jobs()
-    bjobs = [B.make_job(m, c, s, seed, prm, sarg, mm)[0] for m, c, s, seed, prm, sarg, mm in jobs]
-    t_batch = _time_s(lambda: B.brng_gibbs_batch(hb.h, bjobs, stream), stream, reps=2, warm=1)
-    out["ensemble_48_jobs"] = {"jobs": len(specs), "updates": upd, "plain_updates_per_s": upd / t_plain,
-                               "batched_updates_per_s": upd / t_batch, "batched_over_plain": t_plain / t_batch,
-                               "plain_ms": t_plain * 1e3, "batched_ms": t_batch * 1e3}
-    for hh in handles.values():
-        hh.close()
-    hb.close()
-    keep.clear()
-    jobs = bjobs = None
-    torch.cuda.synchronize()
+        def plain():
+            for model, nch, sw, sd, prm, sarg, mm in jobs:
+                B.brng_gibbs_run(handles[sd].h, model, 0, nch, sw, prm, sarg, mm, stream)
+
+        t_plain = _time_s(plain, stream, reps=2, warm=1)
+        jobs = fresh_jobs()
+        bjobs = [B.make_job(m, c, sw, sd, prm, sarg, mm)[0] for m, c, sw, sd, prm, sarg, mm in jobs]
+        t_batch = _time_s(lambda: B.brng_gibbs_batch(hb.h, bjobs, stream), stream, reps=2, warm=1)
+        for hh in handles.values():
+            hh.close()
+        hb.close()
+        keep.clear()
+        torch.cuda.synchronize()
+        return {"jobs": len(specs), "chains": "log-uniform [1, %d]" % max_chains,
+                "sweeps": "uniform [%d, %d]" % sweeps, "updates": upd,
+                "plain_updates_per_s": upd / t_plain, "batched_updates_per_s": upd / t_batch,
+                "batched_over_plain": t_plain / t_batch, "plain_ms": t_plain * 1e3, "batched_ms": t_batch * 1e3}
+
+    out["ensemble_48_jobs"] = ensemble(48, 65536, (100, 10000), SEED)
+    out["ensemble_256_small_jobs"] = ensemble(256, 2048, (100, 1000), SEED + 1000)
     torch.cuda.empty_cache()
     # -- served Poisson mix: the 2,000 jobs/s rate for a bounded window, and a sub-capacity rate
     full = serve.run_mix(serve.MixSpec(rate=2000.0, duration=args.serve_seconds, seed=SEED), pool=pool,
