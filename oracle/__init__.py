@@ -20,6 +20,8 @@ from . import build as _build
 DOM_U, DOM_N, DOM_E, DOM_DATA, DOM_U64 = 0, 1, 2, 3, 4
 OK, EINVAL, EDOMAIN, EREJECT = 0, 1, 4, 5
 GAMMA_MAX_ATTEMPTS = 64
+POISSON_MAX_LAMBDA = 64.0
+POISSON_MAX_K = 1024
 
 _lib = None
 
@@ -36,6 +38,11 @@ def lib():
         L.or_log.argtypes = [dbl]
         L.or_log.restype = dbl
         L.or_log_many.argtypes = [u64, vp, vp]
+        L.or_exp_many.argtypes = [u64, vp, vp]
+        L.or_poisson_inv.argtypes = [dbl, dbl]
+        L.or_poisson_inv.restype = dbl
+        L.or_poisson.argtypes = [u64, u32, vp, u64, vp, vp, vp, u32]
+        L.or_poisson.restype = i32
         L.or_sincospi_many.argtypes = [u64, vp, vp, vp]
         L.or_elem_values.argtypes = [u64, u32, u32, u64, u64, vp, vp]
         for name in ("or_uniform", "or_normal", "or_laplace"):
@@ -99,6 +106,17 @@ def log(x):
     out = np.empty_like(x)
     lib().or_log_many(x.size, _p(x), _p(out))
     return out
+
+
+def exp(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    lib().or_exp_many(x.size, _p(x), _p(out))
+    return out
+
+
+def poisson_inv(lam, u):
+    return lib().or_poisson_inv(float(lam), float(u))
 
 
 def sincospi(a):
@@ -166,6 +184,10 @@ def laplace(seed, S, mu, scale, pos=None, buf_len=64):
 
 def weibull(seed, S, shape, scale, pos=None, buf_len=64, with_cond=False):
     return _bulk("or_weibull", seed, S, pos, len(shape), [shape, scale], buf_len, with_cond)
+
+
+def poisson(seed, S, lam, pos=None, buf_len=64):
+    return _bulk("or_poisson", seed, S, pos, len(lam), [lam], buf_len)
 
 
 def dirichlet(seed, S, alpha, pos=None, buf_len=64, with_logs=False):

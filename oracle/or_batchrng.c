@@ -198,12 +198,31 @@ static double draw_tagged(or_batchrng *g, unsigned tag, float p0, float p1, uint
       kappa = fabs(log(e) / (double)p0);
     } else ++*n_domain;
     break;
+  case 6: /* Poisson(lambda) by inversion of one U */
+    if (finite_f(p0) && p0 > 0.0f && p0 <= OR_POISSON_MAX_LAMBDA) {
+      double u = or_get_uniform(g, &w);
+      out = or_poisson_inv((double)p0, u);
+    } else ++*n_domain;
+    break;
   default:
     ++*n_domain;
   }
   if (word) *word = w;
   if (cond) *cond = kappa;
   return out;
+}
+
+double or_poisson_inv(double lambda, double u) {
+  double p = or_exp(-lambda);
+  double F = p;
+  int k = 0;
+  while (!(u < F) && k < OR_POISSON_MAX_K) {
+    ++k;
+    p = (p * lambda) / (double)k;
+    if (p == 0.0) break; /* the tail underflowed: nothing left to add */
+    F = F + p;
+  }
+  return (double)k;
 }
 
 static int status_of(int n_domain, int n_reject) {
@@ -283,6 +302,11 @@ int or_laplace(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float
 int or_weibull(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *shape,
                const float *scale, double *out, uint32_t *words, double *cond, uint32_t buf_len) {
   return single(5, seed, S, pos, n, shape, scale, out, words, cond, buf_len);
+}
+
+int or_poisson(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *lambda,
+               double *out, uint32_t *words, uint32_t buf_len) {
+  return single(6, seed, S, pos, n, lambda, NULL, out, words, NULL, buf_len);
 }
 
 /* Dirichlet (Sec. 1 footnote): y_k ~ Gamma(alpha_k, 1), x_k = y_k / sum y.

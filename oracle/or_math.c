@@ -14,6 +14,11 @@
  *       ln m = 2 atanh s = 2 (s + s^3/3 + s^5/5 + ...), series through s^25
  *       (|s| <= 0.1716, so the first dropped term is below 2^-60 relative);
  *       ln x = e*ln2_hi + (e*ln2_lo + ln m), ln2 split so e*ln2_hi is exact.
+ * exp:  (for the Poisson inversion's e^-lambda) x = k ln2 + r with
+ *       k = floor(x (1/ln2) + 1/2), r = (x - k ln2_hi) - k ln2_lo
+ *       (k ln2_hi exact), |r| <= 0.35; e^r by its Taylor series through
+ *       r^16/16! (first dropped term below 2^-74 relative), Horner in r;
+ *       times 2^k (exact for results in the normal range).
  * sincospi: a reduced exactly by multiples of 1/2 to r in [-1/4, 1/4];
  *       y = pi*r; Taylor series of sin y through y^23 and cos y through y^22
  *       (|y| <= pi/4), evaluated by Horner in y^2; quadrant swap/sign.
@@ -68,6 +73,37 @@ double or_log(double x) {
   double lnm = 2.0 * s + (2.0 * s) * (s2 * p);
   double fe = (double)e;
   return fe * OR_LN2_HI + (fe * OR_LN2_LO + lnm);
+}
+
+/* e^x for -708 <= x <= 709 (NaN for NaN; 0 below, inf above) */
+double or_exp(double x) {
+  if (isnan(x)) return x;
+  if (x < -708.0) return 0.0;
+  if (x > 709.0) return INFINITY;
+  const double k = floor(x * 0x1.71547652b82fep+0 + 0.5); /* nearest multiple of ln 2 */
+  const double r = (x - k * OR_LN2_HI) - k * OR_LN2_LO;
+  double p = 0x1.ae7f3e733b81fp-45;      /* 1/16! */
+  p = p * r + 0x1.ae7f3e733b81fp-41;     /* 1/15! */
+  p = p * r + 0x1.93974a8c07c9dp-37;     /* 1/14! */
+  p = p * r + 0x1.6124613a86d09p-33;     /* 1/13! */
+  p = p * r + 0x1.1eed8eff8d898p-29;     /* 1/12! */
+  p = p * r + 0x1.ae64567f544e4p-26;     /* 1/11! */
+  p = p * r + 0x1.27e4fb7789f5cp-22;     /* 1/10! */
+  p = p * r + 0x1.71de3a556c734p-19;     /* 1/9!  */
+  p = p * r + 0x1.a01a01a01a01ap-16;     /* 1/8!  */
+  p = p * r + 0x1.a01a01a01a01ap-13;     /* 1/7!  */
+  p = p * r + 0x1.6c16c16c16c17p-10;     /* 1/6!  */
+  p = p * r + 0x1.1111111111111p-7;      /* 1/5!  */
+  p = p * r + 0x1.5555555555555p-5;      /* 1/4!  */
+  p = p * r + 0x1.5555555555555p-3;      /* 1/3!  */
+  p = p * r + 0.5;                       /* 1/2!  */
+  p = p * r + 1.0;
+  p = p * r + 1.0;
+  return ldexp(p, (int)k);
+}
+
+void or_exp_many(uint64_t n, const double *x, double *out) {
+  for (uint64_t i = 0; i < n; ++i) out[i] = or_exp(x[i]);
 }
 
 /* sin y and cos y for |y| <= pi/4 by their Taylor series */

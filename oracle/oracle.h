@@ -46,6 +46,10 @@ extern "C" {
 
 /* Marsaglia-Tsang attempts before a Gamma draw gives up (NaN + EREJECT) */
 #define OR_GAMMA_MAX_ATTEMPTS 64
+/* Poisson by inversion (sequential search, O(lambda) steps): 0 < lambda <= this */
+#define OR_POISSON_MAX_LAMBDA 64.0f
+/* the search stops here at the latest (far beyond any 24-bit uniform's reach) */
+#define OR_POISSON_MAX_K 1024
 
 /* ---- core engine ------------------------------------------------------ */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -54,6 +58,8 @@ void or_philox_words(uint64_t seed, uint32_t domain, uint32_t stream,
 
 /* ---- FP64 elementary functions written for the oracle ----------------- */
 double or_log(double x);
+double or_exp(double x);
+void or_exp_many(uint64_t n, const double *x, double *out);
 void or_sincospi(double a, double *s, double *c);
 void or_log_many(uint64_t n, const double *x, double *out);
 void or_sincospi_many(uint64_t n, const double *a, double *s, double *c);
@@ -85,8 +91,14 @@ int or_weibull(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float
  * (i mod (S/K))*K + k; logs (nullable) gets each component's log-Gamma */
 int or_dirichlet(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n_rows, uint32_t K,
                  const float *alpha, double *out, double *logs, double *cond, uint32_t buf_len);
+/* Poisson(lambda = p0) by inversion of one U: the smallest k with U < F(k),
+ * F(k) = sum_{j<=k} p_j, p_0 = e^-lambda (or_exp), p_j = (p_{j-1} lambda) / j,
+ * F accumulated left to right, all in FP64 (the draw's value is k) */
+double or_poisson_inv(double lambda, double u);
+int or_poisson(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *lambda,
+               double *out, uint32_t *words, uint32_t buf_len);
 /* tag 0 U(p0,p1), 1 N(p0,p1), 2 Exp(rate p0), 3 Gamma(p0), 4 Laplace(p0,p1),
- * 5 Weibull(shape p0, scale p1) */
+ * 5 Weibull(shape p0, scale p1), 6 Poisson(p0) */
 int or_mixed(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const uint8_t *tag,
              const float *p0, const float *p1, double *out, uint32_t *words, double *cond,
              uint32_t buf_len);
