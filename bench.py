@@ -210,6 +210,23 @@ def extras(dev, stream, peaks, args):
     hm.close()
     del tag, p0, p1, o, w
     torch.cuda.empty_cache()
+    # -- Poisson draws (discrete, by inversion of one U), lambda log-uniform in [0.05, 64]
+    n, S = 1 << 26, 1 << 20
+    g = torch.Generator(device=dev)
+    g.manual_seed(SEED)
+    lam = torch.exp(np.log(0.05) + (np.log(64.0) - np.log(0.05)) *
+                    torch.rand(n, generator=g, device=dev, dtype=torch.float32))
+    o = torch.empty(n, dtype=torch.float32, device=dev)
+    w = torch.empty(n, dtype=torch.int32, device=dev)
+    hp = B.Handle(SEED, S)
+    run_p = lambda: B.brng_poisson(hp.h, lam, o, w, stream)  # noqa: E731
+    tune, _, table = AT.autotune(hp, run_p, AT.SPACES["mixed"], stream, "poisson-2^26-2^20", reps=2)
+    t = _time_s(run_p, stream)
+    out["poisson_2^26"] = {"deviates_per_s": n / t, "ms": t * 1e3, "lambda": "log-uniform [0.05, 64]",
+                           "tuning": tune, "rechecks": hp.counters()[1]["n_recheck"]}
+    hp.close()
+    del lam, o, w
+    torch.cuda.empty_cache()
     # -- uneven ensembles: batched (one persistent launch) vs one kernel per job
     pool = serve.InputPool(65536, 64, SEED)
     d_nobs, d_xbar, d_sc = (torch.from_numpy(x).to(dev) for x in (pool.nobs, pool.xbar, pool.sc))

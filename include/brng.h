@@ -66,7 +66,8 @@ enum { BRNG_DOMAIN_U = 0, BRNG_DOMAIN_N = 1, BRNG_DOMAIN_E = 2, BRNG_DOMAIN_DATA
 
 /* distribution tags of the mixed stream */
 enum { BRNG_TAG_UNIFORM = 0, BRNG_TAG_NORMAL = 1, BRNG_TAG_EXPONENTIAL = 2, BRNG_TAG_GAMMA = 3,
-       BRNG_TAG_LAPLACE = 4, BRNG_TAG_WEIBULL = 5 };
+       BRNG_TAG_LAPLACE = 4, BRNG_TAG_WEIBULL = 5, BRNG_TAG_POISSON = 6 };
+#define BRNG_POISSON_MAX_LAMBDA 64.0f
 
 /* Gibbs models */
 typedef enum {
@@ -93,8 +94,8 @@ typedef struct {
   uint32_t lookahead;       /* Dirichlet/LDA: sweeps a component may run ahead, 1..16         */
   uint32_t producer_warps;  /* normal-gamma brng_gibbs_run: warps per block that only refill  */
                             /* the rings while the others sample (asynchronous replenishment, */
-                            /* Sec. 4), 1..8, or BRNG_PRODUCERS_NONE: each warp refills its   */
-                            /* own rings when they run dry (Sec. 2.2).  Results are the same. */
+                            /* Sec. 3 item 3), 1..8, or BRNG_PRODUCERS_NONE: each warp refills */
+                            /* its own rings when they run dry (Sec. 2.2).  Same results.    */
 } brng_tuning_t;
 #define BRNG_PRODUCERS_NONE 0xffffffffu
 
@@ -148,8 +149,9 @@ int brng_philox_peak(uint64_t iters, uint32_t blocks, uint32_t threads, uint32_t
  * their error can be bounded against a reference.  in, out: device float[n]. */
 int brng_fp32_eval(uint32_t fn, size_t n, const float *in, float *out, brng_stream_t stream);
 
-/* ---- FP64 elementary functions of the Gamma accept recheck ----------------
+/* ---- FP64 elementary functions of the Gamma and Poisson rechecks ----------
  * out[i] = f(in[i]) on the device for fn = 0: log, 1: sin(pi x), 2: cos(pi x),
+ * 3: exp (Taylor through r^16 after reduction by ln 2),
  * the fixed-operation-order FP64 functions the Gamma sampler uses when it
  * re-decides an accept test in FP64 (log by the atanh series, sin/cos(pi x) by
  * exact reduction and Taylor series).  Exposed so that their bits can be
@@ -191,8 +193,19 @@ int brng_laplace(brng_t *h, size_t n, const float *mu, const float *b, float *ou
 /* Weibull(shape k, scale lambda): lambda E^(1/k).  Needs finite k, lambda > 0. */
 int brng_weibull(brng_t *h, size_t n, const float *k, const float *lambda, float *out,
                  uint32_t *words, brng_stream_t stream);
+/* Poisson(lambda), a discrete distribution of the expanded library (Sec. 3
+ * item 1), drawn from the same U buffer: one U element u per draw, the result
+ * the smallest k with u < F(k), F the Poisson CDF summed left to right from
+ * p_0 = e^-lambda, p_k = p_{k-1} lambda / k (inversion by sequential search,
+ * O(lambda) steps).  The search runs in FP32 and is redone in FP64 (own exp,
+ * fixed operation order) when u lies within the FP32 error bound of a CDF
+ * step, so every k equals the FP64 reference's.  out gets k as a float
+ * (exact).  Needs finite 0 < lambda <= BRNG_POISSON_MAX_LAMBDA; FP64 redraws
+ * count in n_recheck. */
+int brng_poisson(brng_t *h, size_t n, const float *lambda, float *out, uint32_t *words,
+                 brng_stream_t stream);
 /* Mixed stream: draw i is distribution tag[i] (BRNG_TAG_*) with parameters
- * (p0[i], p1[i]) as in the calls above (Gamma, Exponential ignore p1).
+ * (p0[i], p1[i]) as in the calls above (Gamma, Exponential, Poisson ignore p1).
  * Unknown tags give NaN (n_domain).  tag: device uint8[n]. */
 int brng_mixed(brng_t *h, size_t n, const uint8_t *tag, const float *p0, const float *p1,
                float *out, uint32_t *words, brng_stream_t stream);

@@ -21,7 +21,8 @@ BRNG_OK, BRNG_EINVAL, BRNG_ENOMEM, BRNG_ECUDA, BRNG_EDOMAIN, BRNG_EREJECT, BRNG_
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EDOMAIN", "EREJECT", "ETIMEOUT", "EAGAIN",
                 "ENOTFOUND"]
 DOMAIN_U, DOMAIN_N, DOMAIN_E, DOMAIN_DATA, DOMAIN_U64 = 0, 1, 2, 3, 4
-TAG_UNIFORM, TAG_NORMAL, TAG_EXPONENTIAL, TAG_GAMMA, TAG_LAPLACE, TAG_WEIBULL = range(6)
+TAG_UNIFORM, TAG_NORMAL, TAG_EXPONENTIAL, TAG_GAMMA, TAG_LAPLACE, TAG_WEIBULL, TAG_POISSON = range(7)
+POISSON_MAX_LAMBDA = 64.0
 MODEL_TRIANGLE, MODEL_NORMAL_GAMMA, MODEL_LDA = 0, 1, 2
 
 
@@ -115,6 +116,7 @@ def _load():
         "brng_gamma": ([vp, sz, vp, vp, vp, vp], i32),
         "brng_laplace": ([vp, sz, vp, vp, vp, vp, vp], i32),
         "brng_weibull": ([vp, sz, vp, vp, vp, vp, vp], i32),
+        "brng_poisson": ([vp, sz, vp, vp, vp, vp], i32),
         "brng_mixed": ([vp, sz, vp, vp, vp, vp, vp, vp], i32),
         "brng_dirichlet": ([vp, sz, u32, vp, vp, vp], i32),
         "brng_gamma_static": ([u64, u32, sz, vp, vp, vp, vp], i32),
@@ -254,6 +256,13 @@ def brng_normal(h, mu, sigma, out, words=None, stream=None):
     import torch
     return _check("brng_normal", lib.brng_normal(
         h, out.numel(), _ptr(mu, _f32(), "mu"), _ptr(sigma, _f32(), "sigma"), _ptr(out, _f32(), "out"),
+        _ptr(words, torch.int32, "words"), _stream(stream)))
+
+
+def brng_poisson(h, lam, out, words=None, stream=None):
+    import torch
+    return _check("brng_poisson", lib.brng_poisson(
+        h, out.numel(), _ptr(lam, _f32(), "lambda"), _ptr(out, _f32(), "out"),
         _ptr(words, torch.int32, "words"), _stream(stream)))
 
 

@@ -205,14 +205,14 @@ int brng_philox_peak(uint64_t iters, uint32_t blocks, uint32_t threads, uint32_t
 }
 
 int brng_fp32_eval(uint32_t fn, size_t n, const float* in, float* out, brng_stream_t stream) {
-  if (fn > 2) return BRNG_EINVAL;
+  if (fn > 3) return BRNG_EINVAL;
   if (n == 0) return BRNG_OK;
   if (!in || !out) return BRNG_EINVAL;
   return cuda_status(brng::launch_fp32_eval(fn, n, in, out, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 int brng_fp64_eval(uint32_t fn, size_t n, const double* in, double* out, brng_stream_t stream) {
-  if (fn > 2) return BRNG_EINVAL;
+  if (fn > 3) return BRNG_EINVAL;
   if (n == 0) return BRNG_OK;
   if (!in || !out) return BRNG_EINVAL;
   return cuda_status(brng::launch_fp64_eval(fn, n, in, out, reinterpret_cast<cudaStream_t>(stream)));
@@ -242,6 +242,11 @@ int brng_laplace(brng_t* h, size_t n, const float* mu, const float* b, float* ou
 int brng_weibull(brng_t* h, size_t n, const float* k, const float* lambda, float* out,
                  uint32_t* words, brng_stream_t stream) {
   return bulk(h, BRNG_TAG_WEIBULL, n, nullptr, k, lambda, out, words, reinterpret_cast<cudaStream_t>(stream));
+}
+int brng_poisson(brng_t* h, size_t n, const float* lambda, float* out, uint32_t* words,
+                 brng_stream_t stream) {
+  return bulk(h, BRNG_TAG_POISSON, n, nullptr, lambda, nullptr, out, words,
+              reinterpret_cast<cudaStream_t>(stream));
 }
 int brng_mixed(brng_t* h, size_t n, const uint8_t* tag, const float* p0, const float* p1,
                float* out, uint32_t* words, brng_stream_t stream) {

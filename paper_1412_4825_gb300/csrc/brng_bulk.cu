@@ -20,7 +20,7 @@ namespace brng {
 template <int TAG>
 struct BulkDomains {
   static constexpr bool kU = TAG < 0 || TAG == BRNG_TAG_UNIFORM || TAG == BRNG_TAG_GAMMA ||
-                             TAG == BRNG_TAG_LAPLACE;
+                             TAG == BRNG_TAG_LAPLACE || TAG == BRNG_TAG_POISSON;
   static constexpr bool kN = TAG < 0 || TAG == BRNG_TAG_NORMAL || TAG == BRNG_TAG_GAMMA;
   static constexpr bool kE = TAG < 0 || TAG == BRNG_TAG_EXPONENTIAL ||
                              TAG == BRNG_TAG_LAPLACE || TAG == BRNG_TAG_WEIBULL;
@@ -39,6 +39,7 @@ __device__ __forceinline__ bool param_ok(int tag, float p0, float p1) {
     case BRNG_TAG_EXPONENTIAL:
     case BRNG_TAG_GAMMA: return isfinite(p0) && p0 > 0.0f;
     case BRNG_TAG_WEIBULL: return isfinite(p0) && isfinite(p1) && p0 > 0.0f && p1 > 0.0f;
+    case BRNG_TAG_POISSON: return isfinite(p0) && p0 > 0.0f && p0 <= kPoissonMaxLambda;
     default: return false;
   }
 }
@@ -50,6 +51,46 @@ __device__ __forceinline__ bool param_ok(int tag, float p0, float p1) {
 // (U: 2 = attempt + boost; N: 1; E: 1), and every read is a peek, so each
 // domain's generator code appears once in the kernel.  The next draw's tag
 // and parameters are loaded one step ahead.
+// Poisson(lambda) from one U element u (a multiple of 2^-24): the smallest k
+// with u < F(k), searched in FP32 with p_0 = e^-lambda (library expf, within
+// 2 ulp) and p_k = (p_{k-1} lambda) / k (IEEE), F summed left to right.  The
+// FP32 F(k) is within (4 + 3k) 2^-24 of the exact CDF (2^-24 the unit
+// roundoff: 4 for the exp, one per multiply and divide, one per sum), so the
+// two comparisons that fix k -- u < F(k) and u >= F(k-1) -- are taken in FP32
+// when u lies farther than (16 + 8k) 2^-24 from the bound; otherwise (and if
+// the FP32 search ran out) the draw is redone in FP64 in the reference
+// operation order (poisson_inv64), whose decisions are the reference's.
+static __device__ __noinline__ float poisson_recheck(float lambda, float u) {
+  return static_cast<float>(poisson_inv64(static_cast<double>(lambda), static_cast<double>(u),
+                                          kPoissonMaxK));
+}
+
+__device__ __forceinline__ float poisson_draw(float lambda, float u, bool* rechecked) {
+  float p = expf(-lambda);
+  float F = p, Fprev = 0.0f;
+  int k = 0;
+  bool ran_out = false;
+  while (!(u < F)) {
+    if (k >= kPoissonMaxK) {
+      ran_out = true;
+      break;
+    }
+    ++k;
+    p = (p * lambda) / static_cast<float>(k);
+    Fprev = F;
+    if (p == 0.0f) {
+      ran_out = true;
+      break;
+    }
+    F = F + p;
+  }
+  const float kf = static_cast<float>(k);
+  const bool sure = !ran_out && (F - u > (16.0f + 8.0f * kf) * 0x1p-24f) &&
+                    (k == 0 || u - Fprev > (8.0f + 8.0f * kf) * 0x1p-24f);
+  *rechecked = !sure;
+  return sure ? kf : poisson_recheck(lambda, u);
+}
+
 template <int TAG, bool WORDS>
 __global__ void __maxnreg__(128) bulk_kernel(const BulkArgs a) {
   using D = BulkDomains<TAG>;
@@ -107,8 +148,9 @@ __global__ void __maxnreg__(128) bulk_kernel(const BulkArgs a) {
     const bool isE = ok && (tag == BRNG_TAG_EXPONENTIAL || tag == BRNG_TAG_LAPLACE || tag == BRNG_TAG_WEIBULL);
     const bool isL = ok && tag == BRNG_TAG_LAPLACE;
     const bool isG = ok && tag == BRNG_TAG_GAMMA;
+    const bool isP = ok && tag == BRNG_TAG_POISSON;
     // a stream with draws left is topped up whenever a ring of its warp runs dry
-    if constexpr (D::kU) RU.ensure(isU || isL || isG, 2, active, s, a.rk);
+    if constexpr (D::kU) RU.ensure(isU || isL || isG || isP, 2, active, s, a.rk);
     if constexpr (D::kN) RN.ensure(isN || isG, 1, active, s, a.rk);
     if constexpr (D::kE) RE.ensure(isE, 1, active, s, a.rk);
 
@@ -148,6 +190,19 @@ __global__ void __maxnreg__(128) bulk_kernel(const BulkArgs a) {
           }
         }
         done = true;
+      }
+    }
+    if constexpr (D::kU && (TAG < 0 || TAG == BRNG_TAG_POISSON)) {
+      if (__any_sync(kFull, isP)) {  // (a warp without Poisson tags skips this)
+        bool rc = false;
+        if (isP) {
+          const float u = RU.peek(0);
+          if (WORDS) word = RU.peek_word(0);
+          RU.advance(1);
+          out = poisson_draw(p0, u, &rc);
+          done = true;
+        }
+        count_warp(&a.cnt->n_recheck, rc);
       }
     }
     if constexpr (D::kN && D::kU && (TAG < 0 || TAG == BRNG_TAG_GAMMA)) {
@@ -226,6 +281,7 @@ cudaError_t launch_bulk(int tag, const BulkArgs& a, const Geometry& g, cudaStrea
     case BRNG_TAG_GAMMA: return w ? launch_bulk_t<3, true>(a, g, st) : launch_bulk_t<3, false>(a, g, st);
     case BRNG_TAG_LAPLACE: return w ? launch_bulk_t<4, true>(a, g, st) : launch_bulk_t<4, false>(a, g, st);
     case BRNG_TAG_WEIBULL: return w ? launch_bulk_t<5, true>(a, g, st) : launch_bulk_t<5, false>(a, g, st);
+    case BRNG_TAG_POISSON: return w ? launch_bulk_t<6, true>(a, g, st) : launch_bulk_t<6, false>(a, g, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -306,6 +362,8 @@ __global__ void fp64_eval_kernel(uint32_t fn, uint64_t n, const double* in, doub
     double s, c;
     if (fn == 0) {
       out[i] = dlog(in[i]);
+    } else if (fn == 3) {
+      out[i] = dexp(in[i]);
     } else {
       dsincospi(in[i], &s, &c);
       out[i] = fn == 1 ? s : c;

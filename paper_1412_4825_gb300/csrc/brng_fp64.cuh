@@ -17,6 +17,9 @@
 //  sincospi(a): n = floor(2a + 1/2), r = a - n/2 (exact for dyadic a),
 //           y = pi r, Taylor series of sin y to y^23 and cos y to y^22 by
 //           Horner in y^2, then the quadrant n mod 4 swaps/negates.
+//  exp(x):  (the Poisson inversion's e^-lambda) k = floor(x (1/ln2) + 1/2),
+//           r = (x - k ln2_hi) - k ln2_lo, e^r by Taylor through r^16/16!
+//           (Horner in r), times 2^k.
 #pragma once
 
 namespace brng {
@@ -57,6 +60,50 @@ __device__ __forceinline__ double dlog(double x) {
   const double fe = static_cast<double>(e);
   return __dadd_rn(__dmul_rn(fe, 0x1.62e42fee00000p-1),
                    __dadd_rn(__dmul_rn(fe, 0x1.a39ef35793c76p-33), lnm));
+}
+
+// e^x for -708 <= x <= 709 (NaN for NaN; 0 below, inf above)
+__device__ __forceinline__ double dexp(double x) {
+  if (x != x) return x;
+  if (x < -708.0) return 0.0;
+  if (x > 709.0) return __longlong_as_double(0x7ff0000000000000ll);
+  const double k = floor(__dadd_rn(__dmul_rn(x, 0x1.71547652b82fep+0), 0.5));
+  const double r = __dadd_rn(__dadd_rn(x, -__dmul_rn(k, 0x1.62e42fee00000p-1)),
+                             -__dmul_rn(k, 0x1.a39ef35793c76p-33));
+  double p = 0x1.ae7f3e733b81fp-45;                      // 1/16!
+  p = __dadd_rn(__dmul_rn(p, r), 0x1.ae7f3e733b81fp-41);  // 1/15!
+  p = __dadd_rn(__dmul_rn(p, r), 0x1.93974a8c07c9dp-37);  // 1/14!
+  p = __dadd_rn(__dmul_rn(p, r), 0x1.6124613a86d09p-33);  // 1/13!
+  p = __dadd_rn(__dmul_rn(p, r), 0x1.1eed8eff8d898p-29);  // 1/12!
+  p = __dadd_rn(__dmul_rn(p, r), 0x1.ae64567f544e4p-26);  // 1/11!
+  p = __dadd_rn(__dmul_rn(p, r), 0x1.27e4fb7789f5cp-22);  // 1/10!
+  p = __dadd_rn(__dmul_rn(p, r), 0x1.71de3a556c734p-19);  // 1/9!
+  p = __dadd_rn(__dmul_rn(p, r), 0x1.a01a01a01a01ap-16);  // 1/8!
+  p = __dadd_rn(__dmul_rn(p, r), 0x1.a01a01a01a01ap-13);  // 1/7!
+  p = __dadd_rn(__dmul_rn(p, r), 0x1.6c16c16c16c17p-10);  // 1/6!
+  p = __dadd_rn(__dmul_rn(p, r), 0x1.1111111111111p-7);   // 1/5!
+  p = __dadd_rn(__dmul_rn(p, r), 0x1.5555555555555p-5);   // 1/4!
+  p = __dadd_rn(__dmul_rn(p, r), 0x1.5555555555555p-3);   // 1/3!
+  p = __dadd_rn(__dmul_rn(p, r), 0.5);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0);
+  p = __dadd_rn(__dmul_rn(p, r), 1.0);
+  return ldexp(p, static_cast<int>(k));
+}
+
+// Poisson(lambda) by inversion of u in FP64: the smallest k with u < F(k),
+// F(k) = p_0 + ... + p_k left to right, p_0 = e^-lambda, p_j = (p_{j-1} lambda) / j;
+// the search stops when p underflows or at k = kmax.
+__device__ __forceinline__ double poisson_inv64(double lambda, double u, int kmax) {
+  double p = dexp(-lambda);
+  double F = p;
+  int k = 0;
+  while (!(u < F) && k < kmax) {
+    ++k;
+    p = __ddiv_rn(__dmul_rn(p, lambda), static_cast<double>(k));
+    if (p == 0.0) break;
+    F = __dadd_rn(F, p);
+  }
+  return static_cast<double>(k);
 }
 
 __device__ __forceinline__ void dsincospi(double a, double* s_out, double* c_out) {

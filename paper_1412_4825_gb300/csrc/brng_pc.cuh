@@ -1,6 +1,6 @@
 // brng_pc.cuh -- asynchronous replenishment of the buffers: producer warps
 // keep the rings filled while consumer warps run the sampler (the paper's
-// closing idea of refilling the buffers in the background, Sec. 4, in its
+// closing idea of refilling the buffers in the background, Sec. 3 item 3, in its
 // GPU form: warp specialisation inside one block).
 //
 // A block holds Wc consumer warps (32 chains each, as in the inline form) and

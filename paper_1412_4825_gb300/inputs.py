@@ -19,7 +19,7 @@ from __future__ import annotations
 
 import numpy as np
 
-TAG_UNIFORM, TAG_NORMAL, TAG_EXPONENTIAL, TAG_GAMMA, TAG_LAPLACE, TAG_WEIBULL = 0, 1, 2, 3, 4, 5
+TAG_UNIFORM, TAG_NORMAL, TAG_EXPONENTIAL, TAG_GAMMA, TAG_LAPLACE, TAG_WEIBULL, TAG_POISSON = 0, 1, 2, 3, 4, 5, 6
 
 
 def log_uniform(rng: np.random.Generator, lo: float, hi: float, n: int) -> np.ndarray:
@@ -99,6 +99,9 @@ def mixed_stream_torch(n: int, seed: int = 42, n_tags: int = 4, device="cuda"):
     p1 = torch.where((tag == TAG_EXPONENTIAL) | (tag == TAG_GAMMA), torch.zeros_like(p1), p1)
     if n_tags > TAG_WEIBULL:
         p0 = torch.where(tag == TAG_WEIBULL, logu(0.5, 5.0), p0)
+    if n_tags > TAG_POISSON:
+        p0 = torch.where(tag == TAG_POISSON, logu(0.05, 64.0), p0)
+        p1 = torch.where(tag == TAG_POISSON, torch.zeros_like(p1), p1)
     return tag, p0.contiguous(), p1.contiguous()
 
 
@@ -107,7 +110,7 @@ def mixed_stream(n: int, seed: int = 42, n_tags: int = 4):
     parameters (p0, p1): U(a,b) a,b log-U[1e-3,1e3] sorted; N(mu, sigma)
     mu = +-log-U[1e-3,1e3], sigma log-U[1e-2,1e2]; Exp(rate) log-U[1e-2,1e2];
     Gamma(alpha) log-U[0.05, 50]; Laplace(mu, b) like Normal; Weibull(k, lambda)
-    k log-U[0.5, 5], lambda log-U[1e-2, 1e2]."""
+    k log-U[0.5, 5], lambda log-U[1e-2, 1e2]; Poisson(lambda) log-U[0.05, 64]."""
     rng = np.random.default_rng(seed)
     tag = rng.integers(0, n_tags, size=n, dtype=np.uint8)
     p0 = np.empty(n, dtype=np.float32)
@@ -130,4 +133,10 @@ def mixed_stream(n: int, seed: int = 42, n_tags: int = 4):
         elif t == TAG_WEIBULL:
             p0[idx] = log_uniform(rng, 0.5, 5.0, m)
             p1[idx] = log_uniform(rng, 1e-2, 1e2, m)
+        elif t == TAG_POISSON:
+            p0[idx] = log_uniform(rng, 0.05, 64.0, m)
     return tag, p0, p1
+
+
+def poisson_params(n: int, seed: int = 42, lo: float = 0.05, hi: float = 64.0):
+    return log_uniform(np.random.default_rng(seed), lo, hi, n)

@@ -262,6 +262,99 @@ def test_call_splitting():
     del pos1
 
 
+# ---- Poisson (discrete; counts must equal the oracle's exactly) -------------
+
+def test_fp64_exp_bit_exact():
+    rng = np.random.default_rng(12)
+    x = np.concatenate([rng.uniform(-708.0, 0.0, 1 << 16), -rng.uniform(0.0, 64.0, 1 << 16),
+                        [0.0, -1e-300, -64.0, -708.0]])
+    out = torch.empty(x.size, dtype=torch.float64, device=DEV)
+    B.brng_fp64_eval(3, T(x), out)
+    assert np.array_equal(H(out).view(np.uint64), O.exp(x).view(np.uint64))
+
+
+@pytest.mark.parametrize("lo,hi", [(0.05, 64.0), (0.001, 0.5), (30.0, 64.0)])
+def test_poisson_parity(lo, hi):
+    seed, S, n = 42, 1000, 200011
+    lam = inputs.poisson_params(n, seed=3, lo=lo, hi=hi)
+    h = handle(seed, S)
+    out, w = _run_bulk("poisson", h, [lam], n)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    ro, rw, rpos, _ = O.poisson(seed, S, lam)
+    assert np.array_equal(H(out).astype(np.float64), ro)
+    assert np.array_equal(words_np(w), rw)
+    assert np.array_equal(h.positions(), rpos)
+    print("poisson rechecks", cnt["n_recheck"])
+
+
+def test_poisson_near_cdf_steps_redraw_in_fp64():
+    """Lambdas chosen so that each draw's uniform sits next to a step of the
+    Poisson CDF (within a few 2^-24): the FP32 search cannot certify those
+    comparisons and redraws in FP64; every count still equals the oracle's."""
+    from scipy import stats
+    seed, S, per = 77, 32, 8
+    n = S * per
+    rng = np.random.default_rng(1)
+    lam = np.empty(n, np.float32)
+    for i in range(n):
+        s_, m = i % S, i // S
+        u = float(O.elements(seed, O.DOM_U, s_, m, 1)[0][0])
+        k = int(rng.integers(0, 12))
+        if not (stats.poisson.cdf(k, 64.0) < u < stats.poisson.cdf(k, 1e-3)):
+            lam[i] = np.float32(3.0)
+            continue
+        lo, hi = 1e-3, 64.0  # F(k; lambda) falls from ~1 to ~0 as lambda grows
+        for _ in range(80):
+            mid = 0.5 * (lo + hi)
+            if stats.poisson.cdf(k, mid) > u:
+                lo = mid
+            else:
+                hi = mid
+        lam[i] = np.float32(lo)
+    h = handle(seed, S)
+    out, w = _run_bulk("poisson", h, [lam], n)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    ro, rw, rpos, _ = O.poisson(seed, S, lam)
+    assert np.array_equal(H(out).astype(np.float64), ro)
+    assert np.array_equal(words_np(w), rw)
+    assert np.array_equal(h.positions(), rpos)
+    assert cnt["n_recheck"] > n // 4, cnt  # the FP64 path ran
+
+
+def test_mixed_with_poisson_tags():
+    seed, S, n = 42, 2048, 100003
+    tag, p0, p1 = inputs.mixed_stream(n, seed=seed, n_tags=7)
+    assert (tag == 6).any()
+    h = handle(seed, S)
+    out = torch.empty(n, dtype=torch.float32, device=DEV)
+    w = torch.empty(n, dtype=torch.int32, device=DEV)
+    B.brng_mixed(h.h, T(tag), T(p0), T(p1), out, w)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    ro, rw, rpos, _, cond = O.mixed(seed, S, tag, p0, p1, nthreads=NT, with_cond=True)
+    assert np.array_equal(words_np(w), rw)
+    assert np.array_equal(h.positions(), rpos)
+    pois = tag == 6
+    assert np.array_equal(H(out)[pois].astype(np.float64), ro[pois])
+    rest = ~pois
+    assert_close(H(out)[rest], ro[rest], _mixed_scale(tag[rest], p0[rest], p1[rest], ro[rest], cond[rest]),
+                 what="mixed with Poisson")
+
+
+def test_poisson_invalid_lambda():
+    lam = np.array([1.0, 0.0, -2.0, np.nan, np.inf, 64.5, 3.0], np.float32)
+    h = handle(2, 1)
+    out, w = _run_bulk("poisson", h, [lam], lam.size)
+    code, cnt = h.counters()
+    assert code == B.BRNG_EDOMAIN and cnt["n_domain"] == 5
+    ro, rw, rpos, _ = O.poisson(2, 1, lam)
+    g = H(out).astype(np.float64)
+    assert np.isnan(g[1:6]).all() and np.array_equal(g[[0, 6]], ro[[0, 6]])
+    assert np.array_equal(h.positions(), rpos)
+
+
 def _mixed_scale(tag, p0, p1, ro, cond):
     p0 = p0.astype(np.float64)
     p1 = p1.astype(np.float64)
