@@ -22,6 +22,7 @@ OK, EINVAL, EDOMAIN, EREJECT = 0, 1, 4, 5
 GAMMA_MAX_ATTEMPTS = 64
 POISSON_MAX_LAMBDA = 64.0
 POISSON_MAX_K = 1024
+BINOMIAL_MAX_MEAN = 64.0
 
 _lib = None
 
@@ -43,6 +44,10 @@ def lib():
         L.or_poisson_inv.restype = dbl
         L.or_poisson.argtypes = [u64, u32, vp, u64, vp, vp, vp, u32]
         L.or_poisson.restype = i32
+        L.or_binomial_inv.argtypes = [dbl, dbl, dbl]
+        L.or_binomial_inv.restype = dbl
+        L.or_binomial.argtypes = [u64, u32, vp, u64, vp, vp, vp, vp, u32]
+        L.or_binomial.restype = i32
         L.or_sincospi_many.argtypes = [u64, vp, vp, vp]
         L.or_elem_values.argtypes = [u64, u32, u32, u64, u64, vp, vp]
         for name in ("or_uniform", "or_normal", "or_laplace"):
@@ -188,6 +193,14 @@ def weibull(seed, S, shape, scale, pos=None, buf_len=64, with_cond=False):
 
 def poisson(seed, S, lam, pos=None, buf_len=64):
     return _bulk("or_poisson", seed, S, pos, len(lam), [lam], buf_len)
+
+
+def binomial_inv(n, p, u):
+    return lib().or_binomial_inv(float(n), float(p), float(u))
+
+
+def binomial(seed, S, trials, prob, pos=None, buf_len=64):
+    return _bulk("or_binomial", seed, S, pos, len(trials), [trials, prob], buf_len)
 
 
 def dirichlet(seed, S, alpha, pos=None, buf_len=64, with_logs=False):

@@ -204,6 +204,13 @@ static double draw_tagged(or_batchrng *g, unsigned tag, float p0, float p1, uint
       out = or_poisson_inv((double)p0, u);
     } else ++*n_domain;
     break;
+  case 7: /* Binomial(n, p) by inversion of one U */
+    if (finite_f(p0) && p0 >= 0.0f && p0 == floorf(p0) && p0 <= 16777216.0f && finite_f(p1) &&
+        p1 >= 0.0f && p1 <= 1.0f && (double)p0 * fmin((double)p1, 1.0 - (double)p1) <= OR_BINOMIAL_MAX_MEAN) {
+      double u = or_get_uniform(g, &w);
+      out = or_binomial_inv((double)p0, (double)p1, u);
+    } else ++*n_domain;
+    break;
   default:
     ++*n_domain;
   }
@@ -223,6 +230,22 @@ double or_poisson_inv(double lambda, double u) {
     F = F + p;
   }
   return (double)k;
+}
+
+double or_binomial_inv(double n, double p, double u) {
+  const int flip = p > 0.5;
+  const double q = flip ? 1.0 - p : p;
+  double pk = or_exp(n * or_log(1.0 - q));
+  const double r = q / (1.0 - q);
+  double F = pk;
+  int k = 0;
+  while (!(u < F) && (double)k < n) {
+    ++k;
+    pk = (pk * (((n - (double)k) + 1.0) * r)) / (double)k;
+    if (pk == 0.0) break; /* the tail underflowed: nothing left to add */
+    F = F + pk;
+  }
+  return flip ? n - (double)k : (double)k;
 }
 
 static int status_of(int n_domain, int n_reject) {
@@ -307,6 +330,10 @@ int or_weibull(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float
 int or_poisson(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *lambda,
                double *out, uint32_t *words, uint32_t buf_len) {
   return single(6, seed, S, pos, n, lambda, NULL, out, words, NULL, buf_len);
+}
+int or_binomial(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *trials,
+                const float *prob, double *out, uint32_t *words, uint32_t buf_len) {
+  return single(7, seed, S, pos, n, trials, prob, out, words, NULL, buf_len);
 }
 
 /* Dirichlet (Sec. 1 footnote): y_k ~ Gamma(alpha_k, 1), x_k = y_k / sum y.

@@ -50,6 +50,8 @@ extern "C" {
 #define OR_POISSON_MAX_LAMBDA 64.0f
 /* the search stops here at the latest (far beyond any 24-bit uniform's reach) */
 #define OR_POISSON_MAX_K 1024
+/* Binomial by inversion: integer 0 <= n <= 2^24, 0 <= p <= 1, n min(p, 1-p) <= this */
+#define OR_BINOMIAL_MAX_MEAN 64.0
 
 /* ---- core engine ------------------------------------------------------ */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -97,8 +99,15 @@ int or_dirichlet(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n_rows, uint
 double or_poisson_inv(double lambda, double u);
 int or_poisson(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *lambda,
                double *out, uint32_t *words, uint32_t buf_len);
+/* Binomial(n = p0, p = p1) by inversion of one U on q = min(p, 1-p): the
+ * smallest k with U < F(k), F the Binomial(n, q) CDF summed left to right from
+ * p_0 = exp(n log(1 - q)) (or_exp, or_log), p_k = (p_{k-1} ((n - k + 1) r)) / k,
+ * r = q / (1 - q), all FP64; the draw is k, or n - k when p > 1/2 */
+double or_binomial_inv(double n, double p, double u);
+int or_binomial(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *trials,
+                const float *prob, double *out, uint32_t *words, uint32_t buf_len);
 /* tag 0 U(p0,p1), 1 N(p0,p1), 2 Exp(rate p0), 3 Gamma(p0), 4 Laplace(p0,p1),
- * 5 Weibull(shape p0, scale p1), 6 Poisson(p0) */
+ * 5 Weibull(shape p0, scale p1), 6 Poisson(p0), 7 Binomial(n = p0, p = p1) */
 int or_mixed(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const uint8_t *tag,
              const float *p0, const float *p1, double *out, uint32_t *words, double *cond,
              uint32_t buf_len);
