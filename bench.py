@@ -224,8 +224,20 @@ def extras(dev, stream, peaks, args):
     t = _time_s(run_p, stream)
     out["poisson_2^26"] = {"deviates_per_s": n / t, "ms": t * 1e3, "lambda": "log-uniform [0.05, 64]",
                            "tuning": tune, "rechecks": hp.counters()[1]["n_recheck"]}
+    # -- Binomial draws: trials log-uniform integers in [1, 1000], p uniform, mean <= 64
+    tr = torch.floor(torch.exp(np.log(1001.0) * torch.rand(n, generator=g, device=dev)))
+    pr = torch.rand(n, generator=g, device=dev)
+    q = torch.minimum(pr, 1.0 - pr)
+    cap = 0.999 * 64.0 / torch.clamp(tr, min=1.0)
+    pr = torch.where(tr * q > 64.0, torch.where(pr <= 0.5, cap, 1.0 - cap), pr).contiguous()
+    del q, cap
+    run_b = lambda: B.brng_binomial(hp.h, tr, pr, o, w, stream)  # noqa: E731
+    t = _time_s(run_b, stream)
+    out["binomial_2^26"] = {"deviates_per_s": n / t, "ms": t * 1e3,
+                            "params": "n log-uniform integers [1, 1000], p uniform, n min(p, 1-p) <= 64",
+                            "tuning": hp.tuning, "rechecks": hp.counters()[1]["n_recheck"]}
     hp.close()
-    del lam, o, w
+    del lam, o, w, tr, pr
     torch.cuda.empty_cache()
     # -- uneven ensembles: batched (one persistent launch) vs one kernel per job
     pool = serve.InputPool(65536, 64, SEED)

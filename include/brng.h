@@ -66,8 +66,9 @@ enum { BRNG_DOMAIN_U = 0, BRNG_DOMAIN_N = 1, BRNG_DOMAIN_E = 2, BRNG_DOMAIN_DATA
 
 /* distribution tags of the mixed stream */
 enum { BRNG_TAG_UNIFORM = 0, BRNG_TAG_NORMAL = 1, BRNG_TAG_EXPONENTIAL = 2, BRNG_TAG_GAMMA = 3,
-       BRNG_TAG_LAPLACE = 4, BRNG_TAG_WEIBULL = 5, BRNG_TAG_POISSON = 6 };
+       BRNG_TAG_LAPLACE = 4, BRNG_TAG_WEIBULL = 5, BRNG_TAG_POISSON = 6, BRNG_TAG_BINOMIAL = 7 };
 #define BRNG_POISSON_MAX_LAMBDA 64.0f
+#define BRNG_BINOMIAL_MAX_MEAN 64.0f
 
 /* Gibbs models */
 typedef enum {
@@ -204,6 +205,17 @@ int brng_weibull(brng_t *h, size_t n, const float *k, const float *lambda, float
  * count in n_recheck. */
 int brng_poisson(brng_t *h, size_t n, const float *lambda, float *out, uint32_t *words,
                  brng_stream_t stream);
+/* Binomial(n, p), the second discrete distribution of the expanded library
+ * (Sec. 3 item 1): one U element u per draw; with q = min(p, 1 - p), the
+ * smallest k with u < F(k), F the Binomial(n, q) CDF summed left to right
+ * from (1 - q)^n, p_k = p_{k-1} (n - k + 1) q / ((1 - q) k); the draw is k, or
+ * n - k when p > 1/2.  FP32 search, redone in FP64 (own log and exp, fixed
+ * operation order) near a CDF step, so every count equals the FP64
+ * reference's.  trials: device float[n] holding integers 0 <= n <= 2^24;
+ * prob: device float[n] in [0, 1]; needs n min(p, 1-p) <=
+ * BRNG_BINOMIAL_MAX_MEAN (O(mean) search). */
+int brng_binomial(brng_t *h, size_t n, const float *trials, const float *prob, float *out,
+                  uint32_t *words, brng_stream_t stream);
 /* Mixed stream: draw i is distribution tag[i] (BRNG_TAG_*) with parameters
  * (p0[i], p1[i]) as in the calls above (Gamma, Exponential, Poisson ignore p1).
  * Unknown tags give NaN (n_domain).  tag: device uint8[n]. */

@@ -21,8 +21,9 @@ BRNG_OK, BRNG_EINVAL, BRNG_ENOMEM, BRNG_ECUDA, BRNG_EDOMAIN, BRNG_EREJECT, BRNG_
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EDOMAIN", "EREJECT", "ETIMEOUT", "EAGAIN",
                 "ENOTFOUND"]
 DOMAIN_U, DOMAIN_N, DOMAIN_E, DOMAIN_DATA, DOMAIN_U64 = 0, 1, 2, 3, 4
-TAG_UNIFORM, TAG_NORMAL, TAG_EXPONENTIAL, TAG_GAMMA, TAG_LAPLACE, TAG_WEIBULL, TAG_POISSON = range(7)
+TAG_UNIFORM, TAG_NORMAL, TAG_EXPONENTIAL, TAG_GAMMA, TAG_LAPLACE, TAG_WEIBULL, TAG_POISSON, TAG_BINOMIAL = range(8)
 POISSON_MAX_LAMBDA = 64.0
+BINOMIAL_MAX_MEAN = 64.0
 MODEL_TRIANGLE, MODEL_NORMAL_GAMMA, MODEL_LDA = 0, 1, 2
 
 
@@ -117,6 +118,7 @@ def _load():
         "brng_laplace": ([vp, sz, vp, vp, vp, vp, vp], i32),
         "brng_weibull": ([vp, sz, vp, vp, vp, vp, vp], i32),
         "brng_poisson": ([vp, sz, vp, vp, vp, vp], i32),
+        "brng_binomial": ([vp, sz, vp, vp, vp, vp, vp], i32),
         "brng_mixed": ([vp, sz, vp, vp, vp, vp, vp, vp], i32),
         "brng_dirichlet": ([vp, sz, u32, vp, vp, vp], i32),
         "brng_gamma_static": ([u64, u32, sz, vp, vp, vp, vp], i32),
@@ -263,6 +265,13 @@ def brng_poisson(h, lam, out, words=None, stream=None):
     import torch
     return _check("brng_poisson", lib.brng_poisson(
         h, out.numel(), _ptr(lam, _f32(), "lambda"), _ptr(out, _f32(), "out"),
+        _ptr(words, torch.int32, "words"), _stream(stream)))
+
+
+def brng_binomial(h, trials, prob, out, words=None, stream=None):
+    import torch
+    return _check("brng_binomial", lib.brng_binomial(
+        h, out.numel(), _ptr(trials, _f32(), "trials"), _ptr(prob, _f32(), "prob"), _ptr(out, _f32(), "out"),
         _ptr(words, torch.int32, "words"), _stream(stream)))
 
 

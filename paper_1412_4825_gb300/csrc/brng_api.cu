@@ -56,7 +56,7 @@ int bulk(brng_t* h, int tag, size_t n, const uint8_t* tagv, const float* p0, con
   if (n == 0) return BRNG_OK;
   if (!p0 || !out || (tag == brng::kTagMixed && !tagv)) return BRNG_EINVAL;
   const bool two = tag == brng::kTagMixed || tag == BRNG_TAG_UNIFORM || tag == BRNG_TAG_NORMAL ||
-                   tag == BRNG_TAG_LAPLACE || tag == BRNG_TAG_WEIBULL;
+                   tag == BRNG_TAG_LAPLACE || tag == BRNG_TAG_WEIBULL || tag == BRNG_TAG_BINOMIAL;
   if (two && tag != brng::kTagMixed && !p1) return BRNG_EINVAL;
   const int ndom = (tag == brng::kTagMixed) ? 3 : (tag == BRNG_TAG_GAMMA || tag == BRNG_TAG_LAPLACE) ? 2 : 1;
   const size_t per_warp =
@@ -246,6 +246,11 @@ int brng_weibull(brng_t* h, size_t n, const float* k, const float* lambda, float
 int brng_poisson(brng_t* h, size_t n, const float* lambda, float* out, uint32_t* words,
                  brng_stream_t stream) {
   return bulk(h, BRNG_TAG_POISSON, n, nullptr, lambda, nullptr, out, words,
+              reinterpret_cast<cudaStream_t>(stream));
+}
+int brng_binomial(brng_t* h, size_t n, const float* trials, const float* prob, float* out,
+                  uint32_t* words, brng_stream_t stream) {
+  return bulk(h, BRNG_TAG_BINOMIAL, n, nullptr, trials, prob, out, words,
               reinterpret_cast<cudaStream_t>(stream));
 }
 int brng_mixed(brng_t* h, size_t n, const uint8_t* tag, const float* p0, const float* p1,

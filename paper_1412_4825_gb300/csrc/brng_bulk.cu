@@ -20,7 +20,8 @@ namespace brng {
 template <int TAG>
 struct BulkDomains {
   static constexpr bool kU = TAG < 0 || TAG == BRNG_TAG_UNIFORM || TAG == BRNG_TAG_GAMMA ||
-                             TAG == BRNG_TAG_LAPLACE || TAG == BRNG_TAG_POISSON;
+                             TAG == BRNG_TAG_LAPLACE || TAG == BRNG_TAG_POISSON ||
+                             TAG == BRNG_TAG_BINOMIAL;
   static constexpr bool kN = TAG < 0 || TAG == BRNG_TAG_NORMAL || TAG == BRNG_TAG_GAMMA;
   static constexpr bool kE = TAG < 0 || TAG == BRNG_TAG_EXPONENTIAL ||
                              TAG == BRNG_TAG_LAPLACE || TAG == BRNG_TAG_WEIBULL;
@@ -40,6 +41,11 @@ __device__ __forceinline__ bool param_ok(int tag, float p0, float p1) {
     case BRNG_TAG_GAMMA: return isfinite(p0) && p0 > 0.0f;
     case BRNG_TAG_WEIBULL: return isfinite(p0) && isfinite(p1) && p0 > 0.0f && p1 > 0.0f;
     case BRNG_TAG_POISSON: return isfinite(p0) && p0 > 0.0f && p0 <= kPoissonMaxLambda;
+    case BRNG_TAG_BINOMIAL:
+      return isfinite(p0) && p0 >= 0.0f && p0 == floorf(p0) && p0 <= 16777216.0f && isfinite(p1) &&
+             p1 >= 0.0f && p1 <= 1.0f &&
+             static_cast<double>(p0) * fmin(static_cast<double>(p1), 1.0 - static_cast<double>(p1)) <=
+                 static_cast<double>(kBinomialMaxMean);
     default: return false;
   }
 }
@@ -89,6 +95,51 @@ __device__ __forceinline__ float poisson_draw(float lambda, float u, bool* reche
                     (k == 0 || u - Fprev > (8.0f + 8.0f * kf) * 0x1p-24f);
   *rechecked = !sure;
   return sure ? kf : poisson_recheck(lambda, u);
+}
+
+// Binomial(n, p) from one U element u, by inversion on q = min(p, 1 - p)
+// (then n - k when p > 1/2), searched in FP32: p_0 = exp(a), a = n log1p(-q)
+// (library log1pf and expf, within 1 and 2 ulp), r = q / (1 - q),
+// p_k = (p_{k-1} ((n - k + 1) r)) / k.  With u the unit roundoff 2^-24:
+// p_0 is within (5|a| + 4) u relative, each p_k adds 5 u (r, the product with
+// (n - k + 1), the multiply and the divide), each sum u, so F(k) is within
+// (5|a| + 4 + 6k) u of the reference; the two comparisons that fix k are
+// taken in FP32 beyond twice that, and otherwise the draw is redone in FP64
+// in the reference operation order (binomial_inv64).
+static __device__ __noinline__ float binomial_recheck(float n, float p, float u) {
+  return static_cast<float>(binomial_inv64(static_cast<double>(n), static_cast<double>(p),
+                                           static_cast<double>(u)));
+}
+
+__device__ __forceinline__ float binomial_draw(float n, float p, float u, bool* rechecked) {
+  const bool flip = p > 0.5f;
+  const float q = flip ? 1.0f - p : p;  // exact for p in (1/2, 1]
+  const float a = n * log1pf(-q);
+  const float r = q / (1.0f - q);
+  float pk = expf(a);
+  float F = pk, Fprev = 0.0f;
+  float k = 0.0f;
+  bool ran_out = false;
+  while (!(u < F)) {
+    if (k >= n) {
+      ran_out = true;
+      break;
+    }
+    k += 1.0f;
+    pk = (pk * (((n - k) + 1.0f) * r)) / k;
+    Fprev = F;
+    if (pk == 0.0f) {
+      ran_out = true;
+      break;
+    }
+    F = F + pk;
+  }
+  const float base = 10.0f * fabsf(a) + 8.0f;
+  const bool sure = !ran_out && (F - u > (base + 12.0f * k) * 0x1p-24f) &&
+                    (k == 0.0f || u - Fprev > (base + 12.0f * (k - 1.0f)) * 0x1p-24f);
+  *rechecked = !sure;
+  if (!sure) return binomial_recheck(n, p, u);
+  return flip ? n - k : k;
 }
 
 template <int TAG, bool WORDS>
@@ -149,8 +200,9 @@ __global__ void __maxnreg__(128) bulk_kernel(const BulkArgs a) {
     const bool isL = ok && tag == BRNG_TAG_LAPLACE;
     const bool isG = ok && tag == BRNG_TAG_GAMMA;
     const bool isP = ok && tag == BRNG_TAG_POISSON;
+    const bool isB = ok && tag == BRNG_TAG_BINOMIAL;
     // a stream with draws left is topped up whenever a ring of its warp runs dry
-    if constexpr (D::kU) RU.ensure(isU || isL || isG || isP, 2, active, s, a.rk);
+    if constexpr (D::kU) RU.ensure(isU || isL || isG || isP || isB, 2, active, s, a.rk);
     if constexpr (D::kN) RN.ensure(isN || isG, 1, active, s, a.rk);
     if constexpr (D::kE) RE.ensure(isE, 1, active, s, a.rk);
 
@@ -200,6 +252,19 @@ __global__ void __maxnreg__(128) bulk_kernel(const BulkArgs a) {
           if (WORDS) word = RU.peek_word(0);
           RU.advance(1);
           out = poisson_draw(p0, u, &rc);
+          done = true;
+        }
+        count_warp(&a.cnt->n_recheck, rc);
+      }
+    }
+    if constexpr (D::kU && (TAG < 0 || TAG == BRNG_TAG_BINOMIAL)) {
+      if (__any_sync(kFull, isB)) {  // (a warp without Binomial tags skips this)
+        bool rc = false;
+        if (isB) {
+          const float u = RU.peek(0);
+          if (WORDS) word = RU.peek_word(0);
+          RU.advance(1);
+          out = binomial_draw(p0, p1, u, &rc);
           done = true;
         }
         count_warp(&a.cnt->n_recheck, rc);
@@ -282,6 +347,7 @@ cudaError_t launch_bulk(int tag, const BulkArgs& a, const Geometry& g, cudaStrea
     case BRNG_TAG_LAPLACE: return w ? launch_bulk_t<4, true>(a, g, st) : launch_bulk_t<4, false>(a, g, st);
     case BRNG_TAG_WEIBULL: return w ? launch_bulk_t<5, true>(a, g, st) : launch_bulk_t<5, false>(a, g, st);
     case BRNG_TAG_POISSON: return w ? launch_bulk_t<6, true>(a, g, st) : launch_bulk_t<6, false>(a, g, st);
+    case BRNG_TAG_BINOMIAL: return w ? launch_bulk_t<7, true>(a, g, st) : launch_bulk_t<7, false>(a, g, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -106,6 +106,26 @@ __device__ __forceinline__ double poisson_inv64(double lambda, double u, int kma
   return static_cast<double>(k);
 }
 
+// Binomial(n, p) by inversion of u in FP64 on q = min(p, 1 - p): the smallest
+// k with u < F(k), F summed left to right from p_0 = exp(n log(1 - q)),
+// p_k = (p_{k-1} ((n - k + 1) r)) / k, r = q / (1 - q); n - k when p > 1/2.
+__device__ __forceinline__ double binomial_inv64(double n, double p, double u) {
+  const bool flip = p > 0.5;
+  const double q = flip ? __dadd_rn(1.0, -p) : p;
+  const double omq = __dadd_rn(1.0, -q);
+  double pk = dexp(__dmul_rn(n, dlog(omq)));
+  const double r = __ddiv_rn(q, omq);
+  double F = pk;
+  double k = 0.0;
+  while (!(u < F) && k < n) {
+    k = k + 1.0;
+    pk = __ddiv_rn(__dmul_rn(pk, __dmul_rn(__dadd_rn(__dadd_rn(n, -k), 1.0), r)), k);
+    if (pk == 0.0) break;
+    F = __dadd_rn(F, pk);
+  }
+  return flip ? __dadd_rn(n, -k) : k;
+}
+
 __device__ __forceinline__ void dsincospi(double a, double* s_out, double* c_out) {
   const double n = floor(__dadd_rn(__dmul_rn(2.0, a), 0.5));
   const double r = __dadd_rn(a, -__dmul_rn(0.5, n));

@@ -19,7 +19,8 @@ from __future__ import annotations
 
 import numpy as np
 
-TAG_UNIFORM, TAG_NORMAL, TAG_EXPONENTIAL, TAG_GAMMA, TAG_LAPLACE, TAG_WEIBULL, TAG_POISSON = 0, 1, 2, 3, 4, 5, 6
+TAG_UNIFORM, TAG_NORMAL, TAG_EXPONENTIAL, TAG_GAMMA, TAG_LAPLACE, TAG_WEIBULL, TAG_POISSON, TAG_BINOMIAL = (
+    0, 1, 2, 3, 4, 5, 6, 7)
 
 
 def log_uniform(rng: np.random.Generator, lo: float, hi: float, n: int) -> np.ndarray:
@@ -110,7 +111,8 @@ def mixed_stream(n: int, seed: int = 42, n_tags: int = 4):
     parameters (p0, p1): U(a,b) a,b log-U[1e-3,1e3] sorted; N(mu, sigma)
     mu = +-log-U[1e-3,1e3], sigma log-U[1e-2,1e2]; Exp(rate) log-U[1e-2,1e2];
     Gamma(alpha) log-U[0.05, 50]; Laplace(mu, b) like Normal; Weibull(k, lambda)
-    k log-U[0.5, 5], lambda log-U[1e-2, 1e2]; Poisson(lambda) log-U[0.05, 64]."""
+    k log-U[0.5, 5], lambda log-U[1e-2, 1e2]; Poisson(lambda) log-U[0.05, 64];
+    Binomial(n, p) as binomial_params."""
     rng = np.random.default_rng(seed)
     tag = rng.integers(0, n_tags, size=n, dtype=np.uint8)
     p0 = np.empty(n, dtype=np.float32)
@@ -135,8 +137,24 @@ def mixed_stream(n: int, seed: int = 42, n_tags: int = 4):
             p1[idx] = log_uniform(rng, 1e-2, 1e2, m)
         elif t == TAG_POISSON:
             p0[idx] = log_uniform(rng, 0.05, 64.0, m)
+        elif t == TAG_BINOMIAL:
+            p0[idx], p1[idx] = binomial_params(m, rng=rng)
     return tag, p0, p1
 
 
 def poisson_params(n: int, seed: int = 42, lo: float = 0.05, hi: float = 64.0):
     return log_uniform(np.random.default_rng(seed), lo, hi, n)
+
+
+def binomial_params(n: int, seed: int = 42, max_trials: int = 1000, rng=None):
+    """(trials, prob): trials log-uniform integers in [1, max_trials] (some 0),
+    prob uniform in [0, 1], clipped so that trials * min(p, 1-p) <= 64."""
+    rng = rng if rng is not None else np.random.default_rng(seed)
+    trials = np.floor(np.exp(rng.uniform(0.0, np.log(max_trials + 1), n))).astype(np.float32)
+    trials[rng.random(n) < 0.02] = 0.0
+    prob = rng.random(n).astype(np.float32)
+    q = np.minimum(prob, 1.0 - prob)
+    over = trials.astype(np.float64) * q > 64.0
+    cap = (64.0 / np.maximum(trials, 1.0)).astype(np.float32) * np.float32(0.999)
+    prob = np.where(over, np.where(prob <= 0.5, cap, np.float32(1.0) - cap), prob).astype(np.float32)
+    return trials, prob

@@ -323,10 +323,10 @@ def test_poisson_near_cdf_steps_redraw_in_fp64():
     assert cnt["n_recheck"] > n // 4, cnt  # the FP64 path ran
 
 
-def test_mixed_with_poisson_tags():
+def test_mixed_with_discrete_tags():
     seed, S, n = 42, 2048, 100003
-    tag, p0, p1 = inputs.mixed_stream(n, seed=seed, n_tags=7)
-    assert (tag == 6).any()
+    tag, p0, p1 = inputs.mixed_stream(n, seed=seed, n_tags=8)
+    assert (tag == 6).any() and (tag == 7).any()
     h = handle(seed, S)
     out = torch.empty(n, dtype=torch.float32, device=DEV)
     w = torch.empty(n, dtype=torch.int32, device=DEV)
@@ -336,7 +336,7 @@ def test_mixed_with_poisson_tags():
     ro, rw, rpos, _, cond = O.mixed(seed, S, tag, p0, p1, nthreads=NT, with_cond=True)
     assert np.array_equal(words_np(w), rw)
     assert np.array_equal(h.positions(), rpos)
-    pois = tag == 6
+    pois = (tag == 6) | (tag == 7)  # discrete: counts exact
     assert np.array_equal(H(out)[pois].astype(np.float64), ro[pois])
     rest = ~pois
     assert_close(H(out)[rest], ro[rest], _mixed_scale(tag[rest], p0[rest], p1[rest], ro[rest], cond[rest]),
@@ -352,6 +352,69 @@ def test_poisson_invalid_lambda():
     ro, rw, rpos, _ = O.poisson(2, 1, lam)
     g = H(out).astype(np.float64)
     assert np.isnan(g[1:6]).all() and np.array_equal(g[[0, 6]], ro[[0, 6]])
+    assert np.array_equal(h.positions(), rpos)
+
+
+def test_binomial_parity():
+    seed, S, n = 42, 1000, 200011
+    trials, prob = inputs.binomial_params(n, seed=4)
+    h = handle(seed, S)
+    out, w = _run_bulk("binomial", h, [trials, prob], n)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    ro, rw, rpos, _ = O.binomial(seed, S, trials, prob)
+    assert np.array_equal(H(out).astype(np.float64), ro)
+    assert np.array_equal(words_np(w), rw)
+    assert np.array_equal(h.positions(), rpos)
+    print("binomial rechecks", cnt["n_recheck"])
+
+
+def test_binomial_near_cdf_steps_redraw_in_fp64():
+    """Probabilities chosen so that each draw's uniform sits next to a step
+    of the Binomial CDF: those draws are redone in FP64; every count still
+    equals the oracle's."""
+    from scipy import stats
+    seed, S, per = 78, 32, 8
+    n = S * per
+    rng = np.random.default_rng(2)
+    trials = rng.integers(1, 120, n).astype(np.float32)
+    prob = np.full(n, 0.25, np.float32)
+    for i in range(n):
+        s_, m = i % S, i // S
+        u = float(O.elements(seed, O.DOM_U, s_, m, 1)[0][0])
+        t = int(trials[i])
+        k = int(rng.integers(0, min(t, 20) + 1))
+        lo, hi = 0.0, 0.5  # F(k; t, q) falls as q grows
+        if not (stats.binom.cdf(k, t, hi) < u < stats.binom.cdf(k, t, lo)):
+            continue
+        for _ in range(80):
+            mid = 0.5 * (lo + hi)
+            if stats.binom.cdf(k, t, mid) > u:
+                lo = mid
+            else:
+                hi = mid
+        if t * lo <= 64.0:
+            prob[i] = np.float32(lo)
+    h = handle(seed, S)
+    out, w = _run_bulk("binomial", h, [trials, prob], n)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    ro, rw, rpos, _ = O.binomial(seed, S, trials, prob)
+    assert np.array_equal(H(out).astype(np.float64), ro)
+    assert np.array_equal(words_np(w), rw)
+    assert cnt["n_recheck"] > n // 4, cnt  # the FP64 path ran
+
+
+def test_binomial_invalid_parameters():
+    trials = np.array([10, 2.5, -1, np.nan, 10, 10, 10, 100000, 10], np.float32)
+    prob = np.array([0.5, 0.5, 0.5, 0.5, -0.1, 1.5, np.nan, 0.5, 0.25], np.float32)
+    h = handle(2, 1)
+    out, w = _run_bulk("binomial", h, [trials, prob], trials.size)
+    code, cnt = h.counters()
+    assert code == B.BRNG_EDOMAIN and cnt["n_domain"] == 7
+    ro, rw, rpos, _ = O.binomial(2, 1, trials, prob)
+    g = H(out).astype(np.float64)
+    assert np.isnan(g[1:8]).all() and np.array_equal(g[[0, 8]], ro[[0, 8]])
     assert np.array_equal(h.positions(), rpos)
 
 
