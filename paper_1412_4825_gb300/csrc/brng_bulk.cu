@@ -57,15 +57,51 @@ __device__ __forceinline__ bool param_ok(int tag, float p0, float p1) {
 // (U: 2 = attempt + boost; N: 1; E: 1), and every read is a peek, so each
 // domain's generator code appears once in the kernel.  The next draw's tag
 // and parameters are loaded one step ahead.
-// Poisson(lambda) from one U element u (a multiple of 2^-24): the smallest k
-// with u < F(k), searched in FP32 with p_0 = e^-lambda (library expf, within
-// 2 ulp) and p_k = (p_{k-1} lambda) / k (IEEE), F summed left to right.  The
-// FP32 F(k) is within (4 + 3k) 2^-24 of the exact CDF (2^-24 the unit
-// roundoff: 4 for the exp, one per multiply and divide, one per sum), so the
-// two comparisons that fix k -- u < F(k) and u >= F(k-1) -- are taken in FP32
-// when u lies farther than (16 + 8k) 2^-24 from the bound; otherwise (and if
-// the FP32 search ran out) the draw is redone in FP64 in the reference
-// operation order (poisson_inv64), whose decisions are the reference's.
+// ---- discrete draws by inversion (Poisson, Binomial) ------------------------
+// Both search the CDF in FP32 and take the two comparisons that fix k (u <
+// F(k), u >= F(k-1)) only when u lies beyond twice the error bound of F from
+// the step; otherwise the draw is redone in FP64 in the reference operation
+// order, so every count equals the reference's.  u = 2^-24 below is the unit
+// roundoff.  The Binomial search runs in double-single FP32 (a value = hi +
+// lo, each operation's rounding error carried in lo via FMA), which adds only
+// O(k u^2), leaving the first term's relative error as the bound.
+struct DS {
+  float hi, lo;
+};
+__device__ __forceinline__ DS ds_norm(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return DS{s, b - (s - a)};
+}
+__device__ __forceinline__ DS ds_mul(DS x, float b) {  // (x.hi + x.lo) b
+  const float p = x.hi * b;
+  const float e = fmaf(x.hi, b, -p);  // exact product error
+  return ds_norm(p, fmaf(x.lo, b, e));
+}
+__device__ __forceinline__ DS ds_mul(DS x, DS y) {
+  const float p = x.hi * y.hi;
+  const float e = fmaf(x.hi, y.hi, -p);
+  return ds_norm(p, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e)));
+}
+__device__ __forceinline__ DS ds_div(DS x, float k) {  // (x.hi + x.lo) / k, k > 0
+  const float q1 = __fdividef(x.hi, k);
+  const float r = fmaf(-q1, k, x.hi) + x.lo;  // remainder (first part exact)
+  return ds_norm(q1, __fdividef(r, k));
+}
+__device__ __forceinline__ DS ds_add(DS x, DS y) {  // both >= 0
+  const float s = x.hi + y.hi;
+  const float bb = s - x.hi;
+  const float e = (x.hi - (s - bb)) + (y.hi - bb);  // exact sum error
+  return ds_norm(s, e + x.lo + y.lo);
+}
+// (u - F) as one float, F = hi + lo
+__device__ __forceinline__ float ds_gap(float u, DS F) { return (u - F.hi) - F.lo; }
+
+// Poisson(lambda) from one U element u: the smallest k with u < F(k).  Plain
+// FP32 here (the warp runs the search to its lanes' largest k, so each step's
+// cost counts more than the rare redraws): p_0 = e^-lambda (expf, within
+// 4 u), p_k = (p_{k-1} lambda) / k (IEEE), F summed left to right, so F(k) is
+// within (4 + 3k) u of the reference (one u per multiply, divide and sum);
+// the comparisons are taken beyond (16 + 8k) u, else the draw is redone in FP64.
 static __device__ __noinline__ float poisson_recheck(float lambda, float u) {
   return static_cast<float>(poisson_inv64(static_cast<double>(lambda), static_cast<double>(u),
                                           kPoissonMaxK));
@@ -97,15 +133,10 @@ __device__ __forceinline__ float poisson_draw(float lambda, float u, bool* reche
   return sure ? kf : poisson_recheck(lambda, u);
 }
 
-// Binomial(n, p) from one U element u, by inversion on q = min(p, 1 - p)
-// (then n - k when p > 1/2), searched in FP32: p_0 = exp(a), a = n log1p(-q)
-// (library log1pf and expf, within 1 and 2 ulp), r = q / (1 - q),
-// p_k = (p_{k-1} ((n - k + 1) r)) / k.  With u the unit roundoff 2^-24:
-// p_0 is within (5|a| + 4) u relative, each p_k adds 5 u (r, the product with
-// (n - k + 1), the multiply and the divide), each sum u, so F(k) is within
-// (5|a| + 4 + 6k) u of the reference; the two comparisons that fix k are
-// taken in FP32 beyond twice that, and otherwise the draw is redone in FP64
-// in the reference operation order (binomial_inv64).
+// Binomial(n, p) from one U element u, on q = min(p, 1 - p) (n - k when
+// p > 1/2): p_0 = exp(a), a = n log1p(-q) (library log1pf and expf: within
+// (3|a| + 4) u relative), r = q / (1 - q) and p_k = p_{k-1} ((n - k + 1) r) / k
+// in double-single.
 static __device__ __noinline__ float binomial_recheck(float n, float p, float u) {
   return static_cast<float>(binomial_inv64(static_cast<double>(n), static_cast<double>(p),
                                            static_cast<double>(u)));
@@ -115,28 +146,30 @@ __device__ __forceinline__ float binomial_draw(float n, float p, float u, bool* 
   const bool flip = p > 0.5f;
   const float q = flip ? 1.0f - p : p;  // exact for p in (1/2, 1]
   const float a = n * log1pf(-q);
-  const float r = q / (1.0f - q);
-  float pk = expf(a);
-  float F = pk, Fprev = 0.0f;
+  const float omq_hi = 1.0f - q;
+  const DS omq{omq_hi, (1.0f - omq_hi) - q};  // 1 - q exactly
+  const float r1 = __fdividef(q, omq.hi);
+  const DS r = ds_norm(r1, __fdividef(fmaf(-r1, omq.hi, q) - r1 * omq.lo, omq.hi));
+  DS pk{expf(a), 0.0f};
+  DS F = pk, Fprev{0.0f, 0.0f};
   float k = 0.0f;
   bool ran_out = false;
-  while (!(u < F)) {
+  while (!(ds_gap(u, F) < 0.0f)) {
     if (k >= n) {
       ran_out = true;
       break;
     }
     k += 1.0f;
-    pk = (pk * (((n - k) + 1.0f) * r)) / k;
+    pk = ds_div(ds_mul(pk, ds_mul(r, (n - k) + 1.0f)), k);
     Fprev = F;
-    if (pk == 0.0f) {
+    if (pk.hi == 0.0f) {
       ran_out = true;
       break;
     }
-    F = F + pk;
+    F = ds_add(F, pk);
   }
-  const float base = 10.0f * fabsf(a) + 8.0f;
-  const bool sure = !ran_out && (F - u > (base + 12.0f * k) * 0x1p-24f) &&
-                    (k == 0.0f || u - Fprev > (base + 12.0f * (k - 1.0f)) * 0x1p-24f);
+  const float tol = (6.0f * fabsf(a) + 8.0f) * 0x1p-24f + 0x1p-30f;
+  const bool sure = !ran_out && -ds_gap(u, F) > tol && (k == 0.0f || ds_gap(u, Fprev) > tol);
   *rechecked = !sure;
   if (!sure) return binomial_recheck(n, p, u);
   return flip ? n - k : k;
@@ -244,27 +277,17 @@ __global__ void __maxnreg__(128) bulk_kernel(const BulkArgs a) {
         done = true;
       }
     }
-    if constexpr (D::kU && (TAG < 0 || TAG == BRNG_TAG_POISSON)) {
-      if (__any_sync(kFull, isP)) {  // (a warp without Poisson tags skips this)
+    if constexpr (D::kU && (TAG < 0 || TAG == BRNG_TAG_POISSON || TAG == BRNG_TAG_BINOMIAL)) {
+      if (__builtin_expect(__any_sync(kFull, isP || isB), TAG >= 0)) {  // one vote for both
         bool rc = false;
-        if (isP) {
+        if (isP || isB) {
           const float u = RU.peek(0);
           if (WORDS) word = RU.peek_word(0);
           RU.advance(1);
-          out = poisson_draw(p0, u, &rc);
-          done = true;
-        }
-        count_warp(&a.cnt->n_recheck, rc);
-      }
-    }
-    if constexpr (D::kU && (TAG < 0 || TAG == BRNG_TAG_BINOMIAL)) {
-      if (__any_sync(kFull, isB)) {  // (a warp without Binomial tags skips this)
-        bool rc = false;
-        if (isB) {
-          const float u = RU.peek(0);
-          if (WORDS) word = RU.peek_word(0);
-          RU.advance(1);
-          out = binomial_draw(p0, p1, u, &rc);
+          if constexpr (TAG < 0 || TAG == BRNG_TAG_POISSON)
+            if (isP) out = poisson_draw(p0, u, &rc);
+          if constexpr (TAG < 0 || TAG == BRNG_TAG_BINOMIAL)
+            if (isB) out = binomial_draw(p0, p1, u, &rc);
           done = true;
         }
         count_warp(&a.cnt->n_recheck, rc);
