@@ -222,8 +222,15 @@ def extras(dev, stream, peaks, args):
     run_p = lambda: B.brng_poisson(hp.h, lam, o, w, stream)  # noqa: E731
     tune, _, table = AT.autotune(hp, run_p, AT.SPACES["mixed"], stream, "poisson-2^26-2^20", reps=2)
     t = _time_s(run_p, stream)
+
+    def rechecks_per_call(fn, h):  # FP64 redraws of one call (the counters accumulate)
+        before = h.counters()[1]["n_recheck"]
+        fn()
+        torch.cuda.synchronize()
+        return h.counters()[1]["n_recheck"] - before
+
     out["poisson_2^26"] = {"deviates_per_s": n / t, "ms": t * 1e3, "lambda": "log-uniform [0.05, 64]",
-                           "tuning": tune, "rechecks": hp.counters()[1]["n_recheck"]}
+                           "tuning": tune, "fp64_redraws_per_call": rechecks_per_call(run_p, hp)}
     # -- Binomial draws: trials log-uniform integers in [1, 1000], p uniform, mean <= 64
     tr = torch.floor(torch.exp(np.log(1001.0) * torch.rand(n, generator=g, device=dev)))
     pr = torch.rand(n, generator=g, device=dev)
@@ -235,7 +242,7 @@ def extras(dev, stream, peaks, args):
     t = _time_s(run_b, stream)
     out["binomial_2^26"] = {"deviates_per_s": n / t, "ms": t * 1e3,
                             "params": "n log-uniform integers [1, 1000], p uniform, n min(p, 1-p) <= 64",
-                            "tuning": hp.tuning, "rechecks": hp.counters()[1]["n_recheck"]}
+                            "tuning": hp.tuning, "fp64_redraws_per_call": rechecks_per_call(run_b, hp)}
     hp.close()
     del lam, o, w, tr, pr
     torch.cuda.empty_cache()
