@@ -150,6 +150,21 @@ static __device__ __noinline__ int mt_slow_call(float alpha, float d, float x, f
   return mt_slow(alpha, d, x, z, t, uo, q, series, zi, stream, k0, k1, cnt);
 }
 
+// Marsaglia & Tsang's squeeze: u' < 1 - 0.0331 z^4 implies the accept test
+// for every shape a >= 1 (d >= 2/3), which covers all the shapes used here
+// (a shape below 1 is boosted to a + 1).  Near z = 0 the slack is
+// (0.0331 - 1/(108 d)) z^4 > 0, and a dense grid over d in [2/3, 2e4] and all
+// z finds none below zero.  In FP32 the term is enlarged by 1.00001 (z's own
+// error of a few 1e-7 relative enters z^4 four times, plus the rounding of
+// the constant and products) and compared against 1 - 2^-22, so an FP32 pass
+// is a pass of the exact test: a sufficient condition, it never changes a
+// decision, and it spares the logarithms of about 90 % of the attempts that
+// the series form does not cover (small shapes).
+__device__ __forceinline__ bool mt_squeeze(float z, float uo) {
+  const float z2 = z * z;
+  return fmaf(0.0331f * 1.00001f, z2 * z2, uo) < 0x1.fffff8p-1f;
+}
+
 // One attempt.  Returns true for lanes that accepted; then *dv = d v (FP32).
 // *zword gets the raw word of the N element used (for the first-word output).
 // kLargeShape: the caller's shapes are large (the series form and the
@@ -195,7 +210,7 @@ __device__ __forceinline__ bool mt_attempt(bool run, const GammaState& g, RN& N,
     // factor 1.00001 covers q's FP32 error (a few 1e-7 relative) and the bound
     // 1 - 2^-22 the rounding of the sum with room to spare, so a fast accept
     // is also an accept of the exact (and FP64) test.
-    if (series && fmaf(q, 1.00001f, uo) < 0x1.fffff8p-1f) {
+    if ((series && fmaf(q, 1.00001f, uo) < 0x1.fffff8p-1f) || mt_squeeze(z, uo)) {
       acc = true;
     } else {
       const int r = kLargeShape ? mt_slow_call(g.alpha, g.d, x, z, t, uo, q, series, N.pos() - 1, stream,
@@ -261,7 +276,7 @@ __device__ __forceinline__ bool mt_attempt_peek(bool run, const GammaState& g, R
     p = fmaf(p, x, 0.25f);
     const float x2 = x * x;
     const float q = (3.0f * g.d) * (x2 * x2) * p;
-    if (series && fmaf(q, 1.00001f, uo) < 0x1.fffff8p-1f) {
+    if ((series && fmaf(q, 1.00001f, uo) < 0x1.fffff8p-1f) || mt_squeeze(z, uo)) {
       acc = true;
     } else {
       const int r = kLargeShape ? mt_slow_call(g.alpha, g.d, x, z, t, uo, q, series, N.pos() - 1, stream,

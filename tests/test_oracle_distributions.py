@@ -105,6 +105,35 @@ def test_mt_accept_against_exact_arithmetic(oracle):
     assert checked > 2500
 
 
+def test_mt_squeeze_implies_accept(oracle):
+    """Marsaglia & Tsang's squeeze, as the GPU takes it (u' + 0.0331 (1 + 1e-5)
+    z^4 < 1 - 2^-22), is a sufficient condition of the exact accept test for
+    every shape a >= 1 (boosted shapes included): checked in 100-bit
+    arithmetic and against the oracle's FP64 test, with z drawn over the
+    squeeze's whole range and near 0, where its slack is smallest."""
+    mp.mp.prec = 100
+    rng = np.random.default_rng(21)
+    zmax = (1 / 0.0331) ** 0.25
+    passed = 0
+    for i in range(4000):
+        alpha = float(np.exp(rng.uniform(np.log(0.01), np.log(2e4))))
+        z = float(rng.uniform(-zmax, zmax)) if i % 4 else float(rng.normal() * 1e-2)
+        bound = 1.0 - 0.0331 * 1.00001 * z ** 4 - 2.0 ** -22
+        if bound <= 2.0 ** -24:
+            continue
+        u = float(rng.integers(1, int(bound * 2**24) + 1) * 2.0 ** -24)  # u' < bound on the 24-bit grid
+        a = mp.mpf(alpha) + (1 if alpha < 1 else 0)
+        d = a - mp.mpf(1) / 3
+        t = 1 + z / mp.sqrt(9 * d)
+        assert t > 0
+        v = t ** 3
+        margin = mp.mpf(z) ** 2 / 2 + d * (1 - v + mp.log(v)) - mp.log(u)
+        assert margin > 0, (alpha, z, u)
+        assert oracle.mt_accept(alpha, z, u) == 1
+        passed += 1
+    assert passed > 3000
+
+
 def test_laplace_ks(oracle):
     n = 200000
     out, _, _, st = oracle.laplace(9, 64, _const(n, 1.0), _const(n, 0.5))
