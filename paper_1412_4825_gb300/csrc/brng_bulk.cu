@@ -3,11 +3,12 @@
 // every output is written) and the raw core-engine fill.
 //
 // One lane per stream: warp w serves streams 32w .. 32w+31, and draw i of the
-// call belongs to stream i mod S.  The warp walks its streams' draws m = 0, 1,
-// ... in lockstep, so each parameter load and output store of a warp is one
-// contiguous 128-byte access (i = s + m S for consecutive s).  Base deviates
-// come from the warp-shared rings (brng_ring.cuh); a Gamma draw loops over
-// Marsaglia-Tsang attempts until every lane of the warp has accepted.
+// call belongs to stream i mod S.  Each lane takes its stream's draws m = 0,
+// 1, ... in order, one step per iteration (a draw, or one Marsaglia-Tsang
+// attempt of a Gamma draw); the lanes stay within a few draws of each other,
+// so a warp's parameter loads and output stores (i = s + m S for consecutive
+// s) touch few 128-byte rows.  Base deviates come from the warp-shared
+// top-up rings (brng_ring.cuh), read by peek/advance.
 #include <cuda_runtime.h>
 
 #include <cmath>

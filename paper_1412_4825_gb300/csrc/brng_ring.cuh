@@ -7,7 +7,11 @@
 // column-minor, val[slot * NC + col], so a warp reading one element per
 // column hits NC distinct banks whatever each column's read pointer is.
 //
-// Refill-on-empty (Sec. 2.2), done by the whole warp: every get() is called
+// Two forms: Ring (below; the triangle sampler's U64 rings, NC columns) and
+// CRing (further down; 32 columns, circular, top-up refills and lookahead,
+// used by every other kernel).
+//
+// Ring: refill-on-empty (Sec. 2.2), done by the whole warp: every get() is called
 // by all 32 lanes at the same program point with a per-lane `want`; lanes
 // whose ring is exhausted vote (ballot), the warp lists them, and all 32 lanes
 // generate the needed Philox blocks round-robin over the needy columns (item
