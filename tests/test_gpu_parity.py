@@ -549,11 +549,11 @@ def test_triangle_resume_and_shard():
     assert torch.equal(torch.cat([a, b]), whole) and torch.equal(torch.cat([ma, mb]), mw)
 
 
-def _ng_gpu(nobs, xbar, sc, n_sweeps, offset=0, state=None, mom=None, **tune):
+def _ng_gpu(nobs, xbar, sc, n_sweeps, offset=0, state=None, mom=None, prior=(2.0, 1.0, 0.0, 0.01), **tune):
     n = nobs.size
     h = handle(42, 1, **tune)
     t = [T(nobs), T(xbar), T(sc)]
-    params = B.brng_normal_gamma_params_t(2.0, 1.0, 0.0, 0.01, *[x.data_ptr() for x in t])
+    params = B.brng_normal_gamma_params_t(*prior, *[x.data_ptr() for x in t])
     st = B.normal_gamma_state(n, device=DEV) if state is None else state
     m = torch.zeros((n, 4), dtype=torch.float64, device=DEV) if mom is None else mom
     B.brng_gibbs_run(h.h, B.MODEL_NORMAL_GAMMA, offset, n, n_sweeps, params, st, m)
@@ -647,6 +647,27 @@ def test_normal_gamma_producers_full_size_sampled():
         ref = O.gibbs_normal_gamma(42, n_sweeps, nobs[c0:c1], xbar[c0:c1], sc[c0:c1], chain_offset=c0,
                                    nthreads=NT)
         _ng_check(st[c0:c1], m[c0:c1], ref, n_sweeps, "normal-gamma producers chains %d..%d" % (c0, c1))
+
+
+@pytest.mark.parametrize("buf_len", [32, 8, 4])
+def test_normal_gamma_small_shapes_boosted(buf_len):
+    """Prior shape a0 = 0.4 and chains without observations: shapes below 1
+    take the boosted exact path (an extra U after each accept) in every round
+    structure (speculative width 8, 2, and the plain loop)."""
+    nobs, xbar, sc = inputs.normal_gamma_data(400, seed=12)
+    nobs = nobs.copy()
+    nobs[::3] = 0.0  # shape 0.4
+    nobs[1::3] = 1.0  # shape 0.9
+    prior = (0.4, 1.0, 0.0, 0.01)
+    st, m, cnt = _ng_gpu(nobs, xbar, sc, 120, prior=prior, buf_len=buf_len)
+    ref = O.gibbs_normal_gamma(42, 120, nobs, xbar, sc, prior=prior, nthreads=NT)
+    mu, tau, pn, pu = B.normal_gamma_unpack(st)
+    assert np.array_equal(pn, ref["pos"][:, 0]) and np.array_equal(pu, ref["pos"][:, 1])
+    rmu, rtau = ref["state"][:, 0], ref["state"][:, 1]
+    sd = 1.0 / np.sqrt(0.01 + np.maximum(nobs, 0) * rtau)
+    # boosted tau = G u_b^(1/a) / rate: FP32 at the scale |tau| (1 + |ln u_b / a|)
+    assert_close(tau, rtau, np.abs(rtau) * 40.0, rtol=1e-5, what="boosted tau")
+    assert_close(mu, rmu, np.abs(rmu) + 4 * sd, rtol=1e-4, what="boosted mu")
 
 
 def _lda_gpu(alpha, n_sweeps, offset=0, **tune):
