@@ -405,6 +405,34 @@ def test_binomial_near_cdf_steps_redraw_in_fp64():
     assert cnt["n_recheck"] > n // 4, cnt  # the FP64 path ran
 
 
+def test_discrete_extremes():
+    """Largest allowed means and trials, tiny means, p at 0 and 1."""
+    S = 64
+    lam = np.array([64.0, 1e-30, 63.999, 32.0] * 256, np.float32)
+    h = handle(5, S)
+    out, w = _run_bulk("poisson", h, [lam], lam.size)
+    ro, rw, rpos, st = O.poisson(5, S, lam)
+    assert st == O.OK and np.array_equal(H(out).astype(np.float64), ro)
+    assert np.all(ro[1::4] == 0)
+    trials = np.array([16777216, 16777216, 1000, 128, 7, 0] * 200, np.float32)
+    prob = np.array([3.8e-6, 1 - 3.8e-6, 0.0639, 0.5, 1.0, 0.3] * 200, np.float32)
+    h = handle(6, S)
+    out, w = _run_bulk("binomial", h, [trials, prob], trials.size)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    ro, rw, rpos, st = O.binomial(6, S, trials, prob)
+    assert st == O.OK and np.array_equal(H(out).astype(np.float64), ro)
+    assert np.array_equal(words_np(w), rw) and np.array_equal(h.positions(), rpos)
+    assert np.all(ro[4::6] == 7) and np.all(ro[5::6] == 0)
+
+
+def test_normal_gamma_zero_sweeps():
+    nobs, xbar, sc = inputs.normal_gamma_data(70, seed=2)
+    st, m, _ = _ng_gpu(nobs, xbar, sc, 0)
+    mu, tau, pn, pu = B.normal_gamma_unpack(st)
+    assert np.all(pn == 0) and np.all(pu == 0) and np.all(H(m) == 0)
+
+
 def test_binomial_invalid_parameters():
     trials = np.array([10, 2.5, -1, np.nan, 10, 10, 10, 100000, 10], np.float32)
     prob = np.array([0.5, 0.5, 0.5, 0.5, -0.1, 1.5, np.nan, 0.5, 0.25], np.float32)
