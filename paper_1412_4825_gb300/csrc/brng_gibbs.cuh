@@ -113,12 +113,38 @@ __host__ __device__ inline uint32_t normal_gamma_warp_bytes(uint32_t B) {
   return 128u + 2u * B * 32u * 4u;
 }
 
+// Compensated (Kahan) FP32 running sum: the sweep moments stay accurate to a
+// few FP32 ulp of the total over any number of sweeps with no FP64 arithmetic
+// in the loop, and the result does not depend on how the sweeps are grouped.
+struct Kahan {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const {
+    return static_cast<double>(s) - static_cast<double>(c);
+  }
+};
+
 // Chain state of one lane, read from and written back to global memory.
 struct NgChain {
   float n, xb, S, mu, tau;
   uint64_t pn, pu;
-  double d0, d1, d2, d3;
+  double d0, d1, d2, d3;  // FP64 moments (sum mu, tau, mu^2, tau^2)
+  Kahan k[4];             // this run's compensated partial sums, not yet in d
 };
+
+// Adds the run's compensated partial sums into the FP64 moments.
+__device__ __forceinline__ void ng_fold_moments(NgChain& s) {
+  s.d0 += s.k[0].value();
+  s.d1 += s.k[1].value();
+  s.d2 += s.k[2].value();
+  s.d3 += s.k[3].value();
+  s.k[0] = s.k[1] = s.k[2] = s.k[3] = Kahan{};
+}
 
 __device__ __forceinline__ NgChain ng_load(const NormalGammaArgs& a, uint64_t c, bool active) {
   NgChain s{};
@@ -153,22 +179,6 @@ __device__ __forceinline__ void ng_store(const NormalGammaArgs& a, uint64_t c, b
 
 template <class R>
 __device__ __forceinline__ bool ring_failed(const R&) { return false; }
-
-// Compensated (Kahan) FP32 running sum: the sweep moments stay accurate to a
-// few FP32 ulp of the total over any number of sweeps with no FP64 arithmetic
-// in the loop, and the result does not depend on how the sweeps are grouped.
-struct Kahan {
-  float s = 0.0f, c = 0.0f;
-  __device__ __forceinline__ void add(float v) {
-    const float y = v - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-  __device__ __forceinline__ double value() const {
-    return static_cast<double>(s) - static_cast<double>(c);
-  }
-};
 
 // mu | tau after tau = G / (b0 + SS/2): the sweep's state update (FP32)
 __device__ __forceinline__ void ng_update(const NormalGammaArgs& a, float n, float xb, float S,
@@ -206,21 +216,24 @@ __device__ __forceinline__ void ng_update(const NormalGammaArgs& a, float n, flo
 // in exact mode from the start needs at most 2 of each (boosted lanes never
 // speculate).
 template <int W, class RNT, class RUT>
-__device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t stream, bool active,
-                                          NgChain& s, RNT& RN, RUT& RU) {
+__device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t n_sweeps, uint32_t stream,
+                                          bool active, NgChain& s, RNT& RN, RUT& RU) {
   static_assert(W >= 2, "the speculative form needs W >= 2");
   const GammaState g = gamma_setup(a.a0 + 0.5f * s.n);
   const float prior_num = a.prec0 * a.mu0;
   const float nxb = s.n * s.xb;
   const float n = s.n, xb = s.xb, S = s.S;
   float mu = s.mu, tau = s.tau;
-  Kahan k0, k1, k2, k3;
+  Kahan& k0 = s.k[0];
+  Kahan& k1 = s.k[1];
+  Kahan& k2 = s.k[2];
+  Kahan& k3 = s.k[3];
   bool exact = g.boost;  // per lane: the next attempt is taken the exact way
   int att = 0;
   uint32_t sweep = 0;
   bool rejected = false;
   while (true) {
-    const bool run = active && sweep < a.n_sweeps && !ring_failed(RN) && !ring_failed(RU);
+    const bool run = active && sweep < n_sweeps && !ring_failed(RN) && !ring_failed(RU);
     if (!__any_sync(kFull, run)) break;
     RN.ensure(run, 2 * W, run, stream, a.rk);
     RU.ensure(run, W, run, stream, a.rk);
@@ -256,7 +269,7 @@ __device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t str
       if (!spec) fast = 0;
       uint32_t k = static_cast<uint32_t>(__ffs(~fast)) - 1u;  // leading accepted attempts
       k = min(k, static_cast<uint32_t>(W));
-      k = min(k, a.n_sweeps - min(sweep, a.n_sweeps));
+      k = min(k, n_sweeps - min(sweep, n_sweeps));
 #pragma unroll
       for (int i = 0; i < W; ++i) {
         if (static_cast<uint32_t>(i) < k) {
@@ -271,10 +284,10 @@ __device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t str
         RN.advance(2 * k);
         RU.advance(k);
         sweep += k;
-        if (k < W && sweep < a.n_sweeps) exact = true;
+        if (k < W && sweep < n_sweeps) exact = true;
       }
     }
-    const bool ex = run && exact && sweep < a.n_sweeps;
+    const bool ex = run && exact && sweep < n_sweeps;
     if (__any_sync(kFull, ex)) {
       float G = 0.0f;
       const bool acc = mt_attempt_peek<true, false>(ex, g, RN, RU, stream, a.rk, a.cnt, &G, nullptr);
@@ -307,10 +320,6 @@ __device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t str
   if (ring_failed(RN) || ring_failed(RU)) mu = tau = __int_as_float(0x7fc00000);
   s.mu = mu;
   s.tau = tau;
-  s.d0 += k0.value();
-  s.d1 += k1.value();
-  s.d2 += k2.value();
-  s.d3 += k3.value();
   s.pn = RN.pos();
   s.pu = RU.pos();
 }
@@ -318,19 +327,22 @@ __device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t str
 // Ring length 4 (one block): no room to look ahead, one exact attempt per
 // iteration with refill-on-demand reads.
 template <class RNT, class RUT>
-__device__ __forceinline__ void ng_sweeps_plain(const NormalGammaArgs& a, uint32_t stream, bool active,
-                                                NgChain& s, RNT& RN, RUT& RU) {
+__device__ __forceinline__ void ng_sweeps_plain(const NormalGammaArgs& a, uint32_t n_sweeps, uint32_t stream,
+                                                bool active, NgChain& s, RNT& RN, RUT& RU) {
   const GammaState g = gamma_setup(a.a0 + 0.5f * s.n);
   const float prior_num = a.prec0 * a.mu0;
   const float nxb = s.n * s.xb;
   const float n = s.n, xb = s.xb, S = s.S;
   float mu = s.mu, tau = s.tau;
-  Kahan k0, k1, k2, k3;
+  Kahan& k0 = s.k[0];
+  Kahan& k1 = s.k[1];
+  Kahan& k2 = s.k[2];
+  Kahan& k3 = s.k[3];
   uint32_t sweep = 0;
   int att = 0;
   bool rejected = false;
   while (true) {
-    const bool run = active && sweep < a.n_sweeps && !ring_failed(RN) && !ring_failed(RU);
+    const bool run = active && sweep < n_sweeps && !ring_failed(RN) && !ring_failed(RU);
     if (!__any_sync(kFull, run)) break;
     float dv = 0.0f;
     uint32_t zw;
@@ -366,10 +378,6 @@ __device__ __forceinline__ void ng_sweeps_plain(const NormalGammaArgs& a, uint32
   if (ring_failed(RN) || ring_failed(RU)) mu = tau = __int_as_float(0x7fc00000);
   s.mu = mu;
   s.tau = tau;
-  s.d0 += k0.value();
-  s.d1 += k1.value();
-  s.d2 += k2.value();
-  s.d3 += k3.value();
   s.pn = RN.pos();
   s.pu = RU.pos();
 }
@@ -378,14 +386,15 @@ __device__ __forceinline__ void ng_sweeps_plain(const NormalGammaArgs& a, uint32
 // N ring must hold 2W elements past the read point (B >= 4W).
 __host__ __device__ constexpr int ng_width(uint32_t B) { return B >= 32 ? 8 : B >= 16 ? 4 : B >= 8 ? 2 : 0; }
 
+// Runs n_sweeps sweeps of the lane's chain (all lanes call).
 template <class RNT, class RUT>
-__device__ __forceinline__ void ng_sweeps_any(const NormalGammaArgs& a, uint32_t stream, bool active,
-                                              NgChain& s, RNT& RN, RUT& RU) {
+__device__ __forceinline__ void ng_sweeps_any(const NormalGammaArgs& a, uint32_t n_sweeps, uint32_t stream,
+                                              bool active, NgChain& s, RNT& RN, RUT& RU) {
   switch (ng_width(a.B)) {  // warp-uniform
-    case 8: ng_sweeps<8>(a, stream, active, s, RN, RU); break;
-    case 4: ng_sweeps<4>(a, stream, active, s, RN, RU); break;
-    case 2: ng_sweeps<2>(a, stream, active, s, RN, RU); break;
-    default: ng_sweeps_plain(a, stream, active, s, RN, RU); break;
+    case 8: ng_sweeps<8>(a, n_sweeps, stream, active, s, RN, RU); break;
+    case 4: ng_sweeps<4>(a, n_sweeps, stream, active, s, RN, RU); break;
+    case 2: ng_sweeps<2>(a, n_sweeps, stream, active, s, RN, RU); break;
+    default: ng_sweeps_plain(a, n_sweeps, stream, active, s, RN, RU); break;
   }
 }
 
@@ -407,7 +416,8 @@ __device__ __forceinline__ void normal_gamma_unit(const NormalGammaArgs& a, uint
   CRing<GenU> RU;
   RN.init(ringN, nullptr, a.B, s.pn);
   RU.init(ringU, nullptr, a.B, s.pu);
-  ng_sweeps_any(a, stream, active, s, RN, RU);
+  ng_sweeps_any(a, a.n_sweeps, stream, active, s, RN, RU);
+  ng_fold_moments(s);
   ng_store(a, c, active, s);
   __syncwarp();  // the rings are reused by the warp's next unit
 }

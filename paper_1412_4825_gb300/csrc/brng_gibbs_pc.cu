@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(512) normal_gamma_pc_kernel(const NormalGammaA
     if (lane == 0) ctl[warp].done = has ? 0u : 1u;
     __syncthreads();  // counters and flags set; producers have read positions
     if (has) {
-      ng_sweeps_any(a, stream, active, s, RN, RU);
+      ng_sweeps_any(a, a.n_sweeps, stream, active, s, RN, RU);
+      ng_fold_moments(s);
       RN.flush();
       RU.flush();
       ng_store(a, c, active, s);
