@@ -403,7 +403,6 @@ __device__ __forceinline__ void ng_sweeps_any(const NormalGammaArgs& a, uint32_t
 __device__ __forceinline__ void normal_gamma_unit(const NormalGammaArgs& a, uint64_t unit,
                                                   unsigned char* base) {
   const unsigned lane = lane_id();
-  uint32_t* list = reinterpret_cast<uint32_t*>(base);
   float* ringN = reinterpret_cast<float*>(base + 128);
   float* ringU = ringN + a.B * 32u;
   if (unit * 32 >= a.n_chains) return;  // whole warp
@@ -411,7 +410,6 @@ __device__ __forceinline__ void normal_gamma_unit(const NormalGammaArgs& a, uint
   const bool active = c < a.n_chains;
   const uint32_t stream = static_cast<uint32_t>(a.chain_offset + c);
   NgChain s = ng_load(a, c, active);
-  (void)list;
   CRing<GenN> RN;
   CRing<GenU> RU;
   RN.init(ringN, nullptr, a.B, s.pn);
