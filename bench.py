@@ -44,7 +44,7 @@ PHILOX_MULS_PER_BLOCK = 20
 # launch at this workload, from a full ncu capture of the current kernel
 # (profiles/normal_gamma_kernel_65536x2000.md); the data, state and moment
 # arrays only -- the rings live in shared memory
-NG_DRAM_BYTES_PER_LAUNCH = 4566016
+NG_DRAM_BYTES_PER_LAUNCH = 4566784
 
 
 def _clock_sampler(uuid):
