@@ -296,6 +296,23 @@ def extras(dev, stream, peaks, args):
         jobs = fresh_jobs()
         bjobs = [B.make_job(m, c, sw, sd, prm, sarg, mm)[0] for m, c, sw, sd, prm, sarg, mm in jobs]
         t_batch = _time_s(lambda: B.brng_gibbs_batch(hb.h, bjobs, stream), stream, reps=2, warm=1)
+        # the same batch planned once and captured in a CUDA graph; each replay
+        # continues every job's chains by its sweeps
+        jobs = fresh_jobs()
+        plan = B.brng_batch_create(hb.h, [B.make_job(m, c, sw, sd, prm, sarg, mm)[0]
+                                          for m, c, sw, sd, prm, sarg, mm in jobs])
+        graph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=stream):
+            B.brng_batch_launch(plan, stream)
+
+        def replay():
+            with torch.cuda.stream(stream):
+                graph.replay()
+
+        t_graph = _time_s(replay, stream, reps=2, warm=1)
+        del graph
+        B.brng_batch_destroy(plan)
         for hh in handles.values():
             hh.close()
         hb.close()
@@ -304,7 +321,9 @@ def extras(dev, stream, peaks, args):
         return {"jobs": len(specs), "chains": "log-uniform [1, %d]" % max_chains,
                 "sweeps": "uniform [%d, %d]" % sweeps, "updates": upd,
                 "plain_updates_per_s": upd / t_plain, "batched_updates_per_s": upd / t_batch,
-                "batched_over_plain": t_plain / t_batch, "plain_ms": t_plain * 1e3, "batched_ms": t_batch * 1e3}
+                "batched_over_plain": t_plain / t_batch, "plain_ms": t_plain * 1e3, "batched_ms": t_batch * 1e3,
+                "graph_updates_per_s": upd / t_graph, "graph_over_plain": t_plain / t_graph,
+                "graph_ms": t_graph * 1e3}
 
     out["ensemble_48_jobs"] = ensemble(48, 65536, (100, 10000), SEED)
     out["ensemble_256_small_jobs"] = ensemble(256, 2048, (100, 1000), SEED + 1000)
