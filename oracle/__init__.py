@@ -53,6 +53,8 @@ def lib():
         for name in ("or_uniform", "or_normal", "or_laplace"):
             getattr(L, name).argtypes = [u64, u32, vp, u64, vp, vp, vp, vp, u32]
             getattr(L, name).restype = i32
+        L.or_uniform_f64.argtypes = [u64, u32, vp, u64, vp, vp, vp, vp, u32]
+        L.or_uniform_f64.restype = i32
         L.or_weibull.argtypes = [u64, u32, vp, u64, vp, vp, vp, vp, vp, u32]
         L.or_weibull.restype = i32
         L.or_exponential.argtypes = [u64, u32, vp, u64, vp, vp, vp, u32]
@@ -169,6 +171,19 @@ def _bulk(name, seed, S, pos, n, params, buf_len, with_cond=False):
 
 def uniform(seed, S, a, b, pos=None, buf_len=64):
     return _bulk("or_uniform", seed, S, pos, len(a), [a, b], buf_len)
+
+
+def uniform_f64(seed, S, a, b, pos64=None, buf_len=64):
+    """U[a, b) in FP64 from the 53-bit U64 domain; pos64 holds one U64
+    position per stream (separate from the U, N, E positions)."""
+    pos = np.array(pos64 if pos64 is not None else np.zeros(S, dtype=np.uint64), dtype=np.uint64, copy=True)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = len(a)
+    out = np.empty(n, dtype=np.float64)
+    words = np.zeros(n, dtype=np.uint32)
+    st = lib().or_uniform_f64(seed, S, _p(pos), n, _p(a), _p(b), _p(out), _p(words), buf_len)
+    return out, words, pos, st
 
 
 def normal(seed, S, mu, sigma, pos=None, buf_len=64):

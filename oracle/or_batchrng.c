@@ -306,6 +306,36 @@ int or_uniform(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float
                const float *b, double *out, uint32_t *words, uint32_t buf_len) {
   return single(0, seed, S, pos, n, a, b, out, words, NULL, buf_len);
 }
+/* U[a, b) in FP64 from the 53-bit U64 domain: Sec. 2.2's GetUniform at
+ * double precision, a + (b - a) U64 with one U64 element per valid draw.
+ * pos64[s] is stream s's U64 position (separate from its U, N, E positions).
+ * Needs finite a <= b; otherwise NaN, word 0, nothing consumed. */
+int or_uniform_f64(uint64_t seed, uint32_t S, uint64_t *pos64, uint64_t n, const double *a,
+                   const double *b, double *out, uint32_t *words, uint32_t buf_len) {
+  int n_domain = 0;
+  for (uint32_t s = 0; s < S && (uint64_t)s < n; ++s) {
+    or_batchrng g;
+    uint64_t start[OR_NDOM] = {0, 0, 0, 0, pos64[s]};
+    uint32_t len[OR_NDOM] = {0, 0, 0, 0, buf_len};
+    or_batchrng_init(&g, seed, s, start, len);
+    for (uint64_t i = s; i < n; i += S) {
+      uint32_t w = 0;
+      double v = NAN;
+      if (isfinite(a[i]) && isfinite(b[i]) && a[i] <= b[i]) {
+        const double u = or_get(&g, OR_DOM_U64, &w);
+        v = a[i] + (b[i] - a[i]) * u;
+      } else {
+        ++n_domain;
+      }
+      out[i] = v;
+      if (words) words[i] = w;
+    }
+    uint64_t end[OR_NDOM];
+    or_batchrng_free(&g, end);
+    pos64[s] = end[OR_DOM_U64];
+  }
+  return status_of(n_domain, 0);
+}
 int or_normal(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *mu,
               const float *sigma, double *out, uint32_t *words, uint32_t buf_len) {
   return single(1, seed, S, pos, n, mu, sigma, out, words, NULL, buf_len);

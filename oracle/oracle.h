@@ -77,6 +77,9 @@ void or_elem_values(uint64_t seed, uint32_t domain, uint32_t stream, uint64_t j0
  *      pos[3*s + {0,1,2}] = next U, N, E element of stream s (in/out).   */
 int or_uniform(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *a,
                const float *b, double *out, uint32_t *words, uint32_t buf_len);
+/* U[a, b) in FP64 from the U64 domain; pos64: one U64 position per stream */
+int or_uniform_f64(uint64_t seed, uint32_t S, uint64_t *pos64, uint64_t n, const double *a,
+                   const double *b, double *out, uint32_t *words, uint32_t buf_len);
 int or_normal(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *mu,
               const float *sigma, double *out, uint32_t *words, uint32_t buf_len);
 int or_exponential(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *lambda,
