@@ -246,6 +246,23 @@ def extras(dev, stream, peaks, args):
     hp.close()
     del lam, o, w, tr, pr
     torch.cuda.empty_cache()
+    # -- FP64 uniform from the U64 domain: 2^27 draws over 2^20 streams, an
+    # HBM-bound stream (a, b read, value and word written: 28 B/draw)
+    n64 = 1 << 27
+    h64 = B.Handle(SEED, 1 << 20)
+    a64 = torch.rand(n64, generator=g, device=dev, dtype=torch.float64)
+    b64 = a64 + torch.rand(n64, generator=g, device=dev, dtype=torch.float64)
+    o64 = torch.empty(n64, dtype=torch.float64, device=dev)
+    w64 = torch.empty(n64, dtype=torch.int32, device=dev)
+    t = _time_s(lambda: B.brng_uniform_f64(h64.h, a64, b64, o64, w64, stream), stream)
+    gbs = 28.0 * n64 / t / 1e9
+    out["uniform_f64_2^27"] = {"deviates_per_s": n64 / t, "ms": t * 1e3, "hbm_achieved_gbs": gbs,
+                               "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                               "hbm_frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                               "bytes_per_draw": 28}
+    h64.close()
+    del a64, b64, o64, w64
+    torch.cuda.empty_cache()
     # -- uneven ensembles: batched (one persistent launch) vs one kernel per job
     pool = serve.InputPool(65536, 64, SEED)
     d_nobs, d_xbar, d_sc = (torch.from_numpy(x).to(dev) for x in (pool.nobs, pool.xbar, pool.sc))

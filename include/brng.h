@@ -120,6 +120,10 @@ uint64_t brng_seed(const brng_t *h);
  * uint64, laid out [stream][U, N, E].  Synchronous (device-wide sync). */
 int brng_get_positions(brng_t *h, uint64_t *host_pos);
 int brng_set_positions(brng_t *h, const uint64_t *host_pos);
+/* The same for the streams' U64-domain positions (brng_uniform_f64): host
+ * array of n_streams uint64.  Synchronous (device-wide sync). */
+int brng_get_positions_u64(brng_t *h, uint64_t *host_pos);
+int brng_set_positions_u64(brng_t *h, const uint64_t *host_pos);
 
 /* Reads (and if `reset`, zeroes) the device counters after synchronising
  * `stream`.  Returns BRNG_EDOMAIN if n_domain > 0, else BRNG_EREJECT if
@@ -171,6 +175,16 @@ int brng_fp64_eval(uint32_t fn, size_t n, const double *in, double *out, brng_st
 /* U[a, b):  a + (b - a) U.  Needs finite a <= b. */
 int brng_uniform(brng_t *h, size_t n, const float *a, const float *b, float *out,
                  uint32_t *words, brng_stream_t stream);
+/* U[a, b) in FP64 (Sec. 2.2 GetUniform at double precision): a + (b - a) U64
+ * with the 53-bit uniform U64 = ((w0 >> 5) 2^26 + (w1 >> 6)) 2^-53 of domain 4,
+ * element j of a stream in Philox block j/2, words (w0, w1) = (2(j%2),
+ * 2(j%2)+1).  Each stream has its own U64 position (brng_get_positions_u64),
+ * apart from its U, N, E positions; draw i -> stream i mod n_streams as above.
+ * a, b, out: device, n float64 each; words: the pair's first word.  FP64
+ * arithmetic in that order without contraction: bit-exact with the oracle.
+ * Needs finite a <= b. */
+int brng_uniform_f64(brng_t *h, size_t n, const double *a, const double *b, double *out,
+                     uint32_t *words, brng_stream_t stream);
 /* N(mu, sigma): mu + sigma z.  Needs finite mu, finite sigma > 0. */
 int brng_normal(brng_t *h, size_t n, const float *mu, const float *sigma, float *out,
                 uint32_t *words, brng_stream_t stream);

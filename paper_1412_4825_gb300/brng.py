@@ -106,12 +106,15 @@ def _load():
         "brng_seed": ([vp], u64),
         "brng_get_positions": ([vp, vp], i32),
         "brng_set_positions": ([vp, vp], i32),
+        "brng_get_positions_u64": ([vp, vp], i32),
+        "brng_set_positions_u64": ([vp, vp], i32),
         "brng_read_counters": ([vp, vp, C.POINTER(brng_counters_t), i32], i32),
         "brng_philox_words": ([vp, u32, u32, u64, sz, vp, vp], i32),
         "brng_fp64_eval": ([u32, sz, vp, vp, vp], i32),
         "brng_fp32_eval": ([u32, sz, vp, vp, vp], i32),
         "brng_philox_peak": ([u64, u32, u32, vp, vp], i32),
         "brng_uniform": ([vp, sz, vp, vp, vp, vp, vp], i32),
+        "brng_uniform_f64": ([vp, sz, vp, vp, vp, vp, vp], i32),
         "brng_normal": ([vp, sz, vp, vp, vp, vp, vp], i32),
         "brng_exponential": ([vp, sz, vp, vp, vp, vp], i32),
         "brng_gamma": ([vp, sz, vp, vp, vp, vp], i32),
@@ -212,6 +215,17 @@ def brng_get_positions(h):
     return out
 
 
+def brng_get_positions_u64(h):
+    out = np.zeros(lib.brng_n_streams(h), dtype=np.uint64)
+    _check("brng_get_positions_u64", lib.brng_get_positions_u64(h, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def brng_set_positions_u64(h, pos):
+    pos = np.ascontiguousarray(pos, dtype=np.uint64)
+    return _check("brng_set_positions_u64", lib.brng_set_positions_u64(h, pos.ctypes.data_as(C.c_void_p)))
+
+
 def brng_set_positions(h, pos):
     pos = np.ascontiguousarray(pos, dtype=np.uint64)
     return _check("brng_set_positions", lib.brng_set_positions(h, pos.ctypes.data_as(C.c_void_p)))
@@ -252,6 +266,13 @@ def brng_uniform(h, a, b, out, words=None, stream=None):
     return _check("brng_uniform", lib.brng_uniform(
         h, out.numel(), _ptr(a, _f32(), "a"), _ptr(b, _f32(), "b"), _ptr(out, _f32(), "out"),
         _ptr(words, torch.int32, "words"), _stream(stream)))
+
+
+def brng_uniform_f64(h, a, b, out, words=None, stream=None):
+    import torch
+    return _check("brng_uniform_f64", lib.brng_uniform_f64(
+        h, out.numel(), _ptr(a, torch.float64, "a"), _ptr(b, torch.float64, "b"),
+        _ptr(out, torch.float64, "out"), _ptr(words, torch.int32, "words"), _stream(stream)))
 
 
 def brng_normal(h, mu, sigma, out, words=None, stream=None):
@@ -493,6 +514,12 @@ class Handle:
 
     def set_positions(self, pos):
         brng_set_positions(self.h, pos)
+
+    def positions_u64(self):
+        return brng_get_positions_u64(self.h)
+
+    def set_positions_u64(self, pos):
+        brng_set_positions_u64(self.h, pos)
 
     def counters(self, stream=None, reset=False):
         return brng_read_counters(self.h, stream, reset)

@@ -19,6 +19,7 @@ struct brng_handle {
   brng_tuning_t tune;
   brng::RoundKeys rk;
   uint64_t* d_pos;            // SoA [3][S]: U, N, E positions of every stream
+  uint64_t* d_pos64;          // [S]: U64-domain positions (brng_uniform_f64)
   brng::DevCounters* d_cnt;   // device counters
   int device;
   brng::BatchJob* d_batch_jobs = nullptr;        // brng_gibbs_batch job table
@@ -98,13 +99,19 @@ int brng_create(uint64_t seed, uint32_t n_streams, uint32_t buf_len, brng_t** ou
   h->rk = brng::make_round_keys(seed);
   cudaGetDevice(&h->device);
   const size_t pos_bytes = sizeof(uint64_t) * 3ull * n_streams;
+  h->d_pos = nullptr;
+  h->d_pos64 = nullptr;
+  h->d_cnt = nullptr;
   cudaError_t e = cudaMalloc(&h->d_pos, pos_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_pos64, sizeof(uint64_t) * static_cast<size_t>(n_streams));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_cnt, sizeof(brng::DevCounters));
   if (e == cudaSuccess) e = cudaMemset(h->d_pos, 0, pos_bytes);
+  if (e == cudaSuccess) e = cudaMemset(h->d_pos64, 0, sizeof(uint64_t) * static_cast<size_t>(n_streams));
   if (e == cudaSuccess) e = cudaMemset(h->d_cnt, 0, sizeof(brng::DevCounters));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     cudaFree(h->d_pos);
+    cudaFree(h->d_pos64);
     cudaFree(h->d_cnt);
     delete h;
     return cuda_status(e);
@@ -117,6 +124,7 @@ int brng_destroy(brng_t* h) {
   if (!h) return BRNG_OK;
   cudaFree(h->d_batch_jobs);
   cudaFree(h->d_batch_counter);
+  cudaFree(h->d_pos64);
   cudaError_t e1 = cudaFree(h->d_pos);
   cudaError_t e2 = cudaFree(h->d_cnt);
   delete h;
@@ -173,6 +181,22 @@ int brng_set_positions(brng_t* h, const uint64_t* host_pos) {
   return cuda_status(e);
 }
 
+int brng_get_positions_u64(brng_t* h, uint64_t* host_pos) {
+  if (!h || !host_pos) return BRNG_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(host_pos, h->d_pos64, sizeof(uint64_t) * static_cast<size_t>(h->S), cudaMemcpyDeviceToHost);
+  return cuda_status(e);
+}
+
+int brng_set_positions_u64(brng_t* h, const uint64_t* host_pos) {
+  if (!h || !host_pos) return BRNG_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->d_pos64, host_pos, sizeof(uint64_t) * static_cast<size_t>(h->S), cudaMemcpyHostToDevice);
+  return cuda_status(e);
+}
+
 int brng_read_counters(brng_t* h, brng_stream_t stream, brng_counters_t* out, int reset) {
   if (!h) return BRNG_EINVAL;
   static_assert(sizeof(brng_counters_t) == sizeof(brng::DevCounters), "counter layout");
@@ -221,6 +245,23 @@ int brng_fp64_eval(uint32_t fn, size_t n, const double* in, double* out, brng_st
 int brng_uniform(brng_t* h, size_t n, const float* a, const float* b, float* out, uint32_t* words,
                  brng_stream_t stream) {
   return bulk(h, BRNG_TAG_UNIFORM, n, nullptr, a, b, out, words, reinterpret_cast<cudaStream_t>(stream));
+}
+int brng_uniform_f64(brng_t* h, size_t n, const double* a, const double* b, double* out,
+                     uint32_t* words, brng_stream_t stream) {
+  if (!h) return BRNG_EINVAL;
+  if (n == 0) return BRNG_OK;
+  if (!a || !b || !out) return BRNG_EINVAL;
+  brng::Uniform64Args u;
+  u.rk = h->rk;
+  u.n = n;
+  u.S = h->S;
+  u.a = a;
+  u.b = b;
+  u.out = out;
+  u.words = words;
+  u.pos64 = h->d_pos64;
+  u.cnt = h->d_cnt;
+  return cuda_status(brng::launch_uniform64(u, reinterpret_cast<cudaStream_t>(stream)));
 }
 int brng_normal(brng_t* h, size_t n, const float* mu, const float* sigma, float* out,
                 uint32_t* words, brng_stream_t stream) {

@@ -445,6 +445,81 @@ cudaError_t launch_fp32_eval(uint32_t fn, size_t n, const float* in, float* out,
   return cudaGetLastError();
 }
 
+// ---- FP64 uniform from the U64 domain (brng_uniform_f64) -------------------
+// finite a <= b, decided on the bit patterns with integer operations: GB300's
+// FP64 pipe is narrow, and the three FP64 operations of the value are all a
+// draw should spend there.  Finite: exponent field below 0x7ff.  Order of
+// finite doubles: the sign-magnitude pattern mapped to a two's-complement key
+// (-0 and +0 both to 0), which orders like the values.
+__device__ __forceinline__ int64_t f64_order_key(uint64_t bits) {
+  const int64_t mag = static_cast<int64_t>(bits & 0x7fffffffffffffffull);
+  return (bits >> 63) ? -mag : mag;
+}
+__device__ __forceinline__ bool f64_interval_ok(double lo, double hi) {
+  const uint64_t a = static_cast<uint64_t>(__double_as_longlong(lo));
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(hi));
+  const bool finite = ((a >> 52) & 0x7ffu) != 0x7ffu && ((b >> 52) & 0x7ffu) != 0x7ffu;
+  return finite && f64_order_key(a) <= f64_order_key(b);
+}
+
+// One thread per stream walks that stream's draws i = s, s + S, ... in order
+// (reads and writes of a warp's 32 streams are consecutive, so coalesced).  A
+// draw takes the stream's next U64 element, two per Philox block; the block is
+// kept in registers between its two elements, so there is no ring.
+__global__ void __launch_bounds__(256) uniform64_kernel(const Uniform64Args a) {
+  constexpr int kU = 4;  // draws whose loads are in flight together
+  const uint64_t s = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (s >= a.S || s >= a.n) return;
+  const uint32_t stream = static_cast<uint32_t>(s);
+  const uint64_t S = a.S;
+  uint64_t j = a.pos64[s];
+  uint64_t have = ~0ull;  // Philox block held in w
+  uint4 w = make_uint4(0, 0, 0, 0);
+  uint32_t bad = 0;
+  for (uint64_t i0 = s; i0 < a.n; i0 += kU * S) {
+    double lo[kU], hi[kU];
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {  // streaming loads: every input is read once
+      const uint64_t i = i0 + k * S;
+      lo[k] = i < a.n ? __ldcs(a.a + i) : 0.0;
+      hi[k] = i < a.n ? __ldcs(a.b + i) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < kU; ++k) {
+      const uint64_t i = i0 + k * S;
+      if (i >= a.n) break;
+      double v = __longlong_as_double(0x7ff8000000000000ll);
+      uint32_t first = 0;
+      if (f64_interval_ok(lo[k], hi[k])) {
+        const uint64_t blk = j >> 1;
+        if (blk != have) {
+          w = philox_block(blk, kDomU64, stream, a.rk);
+          have = blk;
+        }
+        const bool second = (j & 1) != 0;
+        first = second ? w.z : w.x;
+        const double u = u53(first, second ? w.w : w.y);
+        v = __dadd_rn(lo[k], __dmul_rn(__dadd_rn(hi[k], -lo[k]), u));
+        ++j;
+      } else {
+        ++bad;
+      }
+      __stcs(a.out + i, v);
+      if (a.words) __stcs(a.words + i, first);
+    }
+  }
+  a.pos64[s] = j;
+  if (bad) atomicAdd(&a.cnt->n_domain, static_cast<unsigned long long>(bad));
+}
+
+cudaError_t launch_uniform64(const Uniform64Args& a, cudaStream_t st) {
+  const uint64_t threads = a.n < a.S ? a.n : a.S;
+  if (threads == 0) return cudaSuccess;
+  const uint64_t blocks = (threads + 255) / 256;
+  uniform64_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 // ---- the FP64 recheck functions, one element per thread -------------------
 __global__ void fp64_eval_kernel(uint32_t fn, uint64_t n, const double* in, double* out) {
   for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;

@@ -78,6 +78,19 @@ struct DirichletArgs {
 };
 cudaError_t launch_dirichlet(const DirichletArgs& a, const Geometry& g, bool lda, cudaStream_t st);
 
+// FP64 uniform from the U64 domain, one thread per stream (brng_bulk.cu)
+struct Uniform64Args {
+  RoundKeys rk;
+  uint64_t n;
+  uint32_t S;
+  const double *a, *b;
+  double* out;
+  uint32_t* words;
+  uint64_t* pos64;  // [S]
+  DevCounters* cnt;
+};
+cudaError_t launch_uniform64(const Uniform64Args& a, cudaStream_t st);
+
 // ---- Gibbs models (brng_gibbs.cu) ----
 struct TriangleArgs {
   RoundKeys rk;

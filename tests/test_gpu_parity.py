@@ -204,6 +204,87 @@ def test_bulk_parity(fn):
     assert_close(g, ro, scale, what=fn)
 
 
+def _uniform_f64_gpu(h, a, b):
+    n = len(a)
+    out = torch.empty(n, dtype=torch.float64, device=DEV)
+    w = torch.empty(n, dtype=torch.int32, device=DEV)
+    B.brng_uniform_f64(h.h, T(a), T(b), out, w)
+    return out, w
+
+
+@pytest.mark.parametrize("S,n", [(1000, 20011), (1, 77), (4099, 4099), (64, 1 << 16)])
+def test_uniform_f64_bit_exact(S, n):
+    """FP64 uniform from the U64 domain: values, words and U64 positions equal
+    the oracle's bit for bit (ragged draws per stream, odd start positions
+    through the checkpoint call, invalid parameters), and the U, N, E
+    positions stay untouched."""
+    rng = np.random.default_rng(S + n)
+    a = rng.uniform(-1e3, 1e3, n)
+    b = a + rng.exponential(10.0, n)
+    a[::97] = b[::97]          # a == b
+    b[5::211] = a[5::211] - 1  # b < a: invalid
+    a[7::307] = np.nan
+    h = handle(42, S)
+    start = rng.integers(0, 1 << 40, S).astype(np.uint64)
+    h.set_positions_u64(start)
+    out, w = _uniform_f64_gpu(h, a, b)
+    ro, rw, rpos, st = O.uniform_f64(42, S, a, b, start)
+    code, cnt = h.counters()
+    assert code == (B.BRNG_EDOMAIN if st == O.EDOMAIN else B.BRNG_OK)
+    g = H(out)
+    assert np.array_equal(np.isnan(g), np.isnan(ro))
+    assert np.array_equal(g[~np.isnan(g)].view(np.uint64), ro[~np.isnan(ro)].view(np.uint64))
+    assert np.array_equal(words_np(w), rw)
+    assert np.array_equal(h.positions_u64(), rpos)
+    assert not h.positions().any()
+
+
+def test_uniform_f64_special_parameters():
+    """The validity rule (finite a <= b, taken on the bit patterns on the
+    GPU) agrees with the oracle on signed zeros, subnormals, infinities, NaN
+    and the largest finite values, in every pairing."""
+    sp = np.array([0.0, -0.0, 5e-324, -5e-324, 2.2e-308, -2.2e-308, 1.0, -1.0, 1e308, -1e308,
+                   np.inf, -np.inf, np.nan])
+    a, b = np.repeat(sp, sp.size), np.tile(sp, sp.size)
+    h = handle(3, 7)
+    out, w = _uniform_f64_gpu(h, a, b)
+    ro, rw, rpos, st = O.uniform_f64(3, 7, a, b)
+    g = H(out)
+    assert np.array_equal(np.isnan(g), np.isnan(ro))
+    assert np.array_equal(g[~np.isnan(g)].view(np.uint64), ro[~np.isnan(ro)].view(np.uint64))
+    assert np.array_equal(words_np(w), rw) and np.array_equal(h.positions_u64(), rpos)
+    code, cnt = h.counters()
+    assert cnt["n_domain"] == int(np.isnan(ro).sum())
+
+
+def test_uniform_f64_call_splitting_and_full_size_sampled():
+    """Two calls continue every stream; at 2^26 draws over 2^20 streams a
+    sample of whole streams equals the oracle."""
+    S = 333
+    rng = np.random.default_rng(5)
+    a = rng.uniform(0, 1, 3 * S + 17)
+    b = a + 1.0
+    h = handle(9, S)
+    o1, w1 = _uniform_f64_gpu(h, a[: 2 * S], b[: 2 * S])
+    o2, w2 = _uniform_f64_gpu(h, a[2 * S:], b[2 * S:])
+    r1 = O.uniform_f64(9, S, a[: 2 * S], b[: 2 * S])
+    r2 = O.uniform_f64(9, S, a[2 * S:], b[2 * S:], r1[2])
+    assert np.array_equal(H(o1), r1[0]) and np.array_equal(H(o2), r2[0])
+    assert np.array_equal(words_np(w2), r2[1]) and np.array_equal(h.positions_u64(), r2[2])
+    S, n = 1 << 20, 1 << 26
+    a = torch.zeros(n, dtype=torch.float64, device=DEV)
+    b = torch.ones(n, dtype=torch.float64, device=DEV)
+    out = torch.empty(n, dtype=torch.float64, device=DEV)
+    h = handle(42, S)
+    B.brng_uniform_f64(h.h, a, b, out)
+    torch.cuda.synchronize()
+    pos = h.positions_u64()
+    assert np.all(pos == n // S)
+    for s in [0, 1, 12345, S - 1]:
+        vals, _ = O.elements(42, O.DOM_U64, s, 0, n // S)
+        assert np.array_equal(H(out[s::S]), vals)
+
+
 def test_gamma_decisions_many():
     """4M Gamma draws over alpha in [0.05, 500] and near 1: every attempt
     count (hence every accept decision) equals the oracle's."""
