@@ -126,8 +126,9 @@ int brng_get_positions_u64(brng_t *h, uint64_t *host_pos);
 int brng_set_positions_u64(brng_t *h, const uint64_t *host_pos);
 
 /* Reads (and if `reset`, zeroes) the device counters after synchronising
- * `stream`.  Returns BRNG_EDOMAIN if n_domain > 0, else BRNG_EREJECT if
- * n_reject > 0, else BRNG_OK (or a CUDA error).  `out` (host) may be NULL. */
+ * `stream`.  Returns BRNG_ETIMEOUT if n_timeout > 0 (a bounded device wait ran
+ * out), else BRNG_EDOMAIN if n_domain > 0, else BRNG_EREJECT if n_reject > 0,
+ * else BRNG_OK (or a CUDA error).  `out` (host) may be NULL. */
 int brng_read_counters(brng_t *h, brng_stream_t stream, brng_counters_t *out, int reset);
 
 /* ---- core engine (Sec. 2.2 "vectorized RNG for uniform distribution") ----
@@ -408,6 +409,7 @@ typedef struct {
 
 typedef struct {
   uint64_t submitted, admitted, completed, refused, batches, queued, device_bytes_in_use;
+  uint64_t cancelled;  /* by brng_serve_cancel, or still queued at close */
 } brng_serve_stats_t;
 
 int brng_serve_open(uint64_t mem_budget, uint32_t max_inflight, const brng_tuning_t *tuning,
@@ -422,9 +424,25 @@ int brng_serve_wait(brng_server_t *s, uint64_t job_id, double timeout_s);
 int brng_serve_result(brng_server_t *s, uint64_t job_id, void *host_state, double *host_moments,
                       brng_job_info_t *info);
 int brng_serve_stats(brng_server_t *s, brng_serve_stats_t *out);
+/* Withdraws a job that still waits for memory: it is forgotten (later calls
+ * on its id give BRNG_ENOTFOUND) and counted as cancelled.  BRNG_EAGAIN once
+ * it has been admitted (it then runs to the end), BRNG_ENOTFOUND for an
+ * unknown id. */
+int brng_serve_cancel(brng_server_t *s, uint64_t job_id);
 /* cancels jobs still waiting for memory, finishes the admitted ones, frees
  * everything; uncollected results are lost */
 int brng_serve_close(brng_server_t *s);
+
+/* ---- test hook: failure detection without a GPU fault ----------------------
+ * Runs brng_gibbs_run's normal-gamma sampler (chain_offset 0) in the
+ * producer/consumer form (the handle's producer_warps, 1 if none) with
+ * producer warps that write nothing, so that every consumer wait for ring
+ * elements runs out after its bound (1 s of the global timer): the chains end
+ * with NaN state, n_timeout counts the expired waits and brng_read_counters
+ * returns BRNG_ETIMEOUT.  Nothing hangs; the context stays usable.
+ * Asynchronous on `stream`; arguments as brng_gibbs_run. */
+int brng_test_pc_stall(brng_t *h, uint32_t n_chains, uint32_t n_sweeps, const void *params, void *state,
+                       double *moments, brng_stream_t stream);
 
 #ifdef __cplusplus
 }

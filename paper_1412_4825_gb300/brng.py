@@ -89,7 +89,7 @@ class brng_job_info_t(C.Structure):
 class brng_serve_stats_t(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
                 ("refused", C.c_uint64), ("batches", C.c_uint64), ("queued", C.c_uint64),
-                ("device_bytes_in_use", C.c_uint64)]
+                ("device_bytes_in_use", C.c_uint64), ("cancelled", C.c_uint64)]
 
 
 def _load():
@@ -137,6 +137,8 @@ def _load():
         "brng_serve_result": ([vp, u64, vp, vp, C.POINTER(brng_job_info_t)], i32),
         "brng_serve_stats": ([vp, C.POINTER(brng_serve_stats_t)], i32),
         "brng_serve_close": ([vp], i32),
+        "brng_serve_cancel": ([vp, u64], i32),
+        "brng_test_pc_stall": ([vp, u32, u32, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -234,7 +236,7 @@ def brng_set_positions(h, pos):
 def brng_read_counters(h, stream=None, reset=False):
     c = brng_counters_t()
     code = lib.brng_read_counters(h, _stream(stream), C.byref(c), int(bool(reset)))
-    _check("brng_read_counters", code, ok=(BRNG_OK, BRNG_EDOMAIN, BRNG_EREJECT))
+    _check("brng_read_counters", code, ok=(BRNG_OK, BRNG_EDOMAIN, BRNG_EREJECT, BRNG_ETIMEOUT))
     return code, c.as_dict()
 
 
@@ -446,6 +448,19 @@ def brng_serve_stats(s):
 
 def brng_serve_close(s):
     return _check("brng_serve_close", lib.brng_serve_close(s))
+
+
+def brng_serve_cancel(s, job_id):
+    """BRNG_OK (withdrawn), BRNG_EAGAIN (already admitted) or BRNG_ENOTFOUND."""
+    return lib.brng_serve_cancel(s, int(job_id))
+
+
+def brng_test_pc_stall(h, n_chains, n_sweeps, params, state, moments, stream=None):
+    """Failure-path test hook: the producer/consumer sampler with producers
+    that write nothing (every consumer wait runs out after its bound)."""
+    return _check("brng_test_pc_stall", lib.brng_test_pc_stall(
+        h, int(n_chains), int(n_sweeps), C.cast(C.byref(params), C.c_void_p) if params is not None else None,
+        _ptr(state, None, "state"), _ptr(moments, None, "moments"), _stream(stream)))
 
 
 # ---- state layouts (marshalling of the C structs held in device tensors) ------

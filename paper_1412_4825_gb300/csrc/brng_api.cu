@@ -207,6 +207,7 @@ int brng_read_counters(brng_t* h, brng_stream_t stream, brng_counters_t* out, in
   if (e == cudaSuccess && reset) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_status(e);
   if (out) *out = c;
+  if (c.n_timeout) return BRNG_ETIMEOUT;
   if (c.n_domain) return BRNG_EDOMAIN;
   if (c.n_reject) return BRNG_EREJECT;
   return BRNG_OK;
@@ -509,6 +510,20 @@ int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_
       return cuda_status(brng::launch_dirichlet(j.lda, g, true, st));
     }
   }
+}
+
+int brng_test_pc_stall(brng_t* h, uint32_t n_chains, uint32_t n_sweeps, const void* params, void* state,
+                       double* moments, brng_stream_t stream) {
+  if (!h) return BRNG_EINVAL;
+  if (n_chains == 0) return BRNG_OK;
+  brng::BatchJob j;
+  const int rc = make_job(h, BRNG_MODEL_NORMAL_GAMMA, h->rk, 0, n_chains, n_sweeps, params, state, moments, &j);
+  if (rc != BRNG_OK) return rc;
+  const uint32_t Wp = h->tune.producer_warps == BRNG_PRODUCERS_NONE ? 1u : h->tune.producer_warps;
+  const brng::Geometry g = geometry(h, brng::normal_gamma_pc_bytes_per_warp(h->tune.buf_len));
+  const uint32_t Wc = std::min({g.warps_per_block, 16u - Wp, 8u * Wp});
+  if (Wc == 0) return BRNG_EINVAL;
+  return cuda_status(brng::launch_normal_gamma_pc(j.ng, Wc, Wp, reinterpret_cast<cudaStream_t>(stream), true));
 }
 
 int brng_batch_create(brng_t* h, const brng_job_t* jobs, uint32_t n_jobs, brng_batch_t** out) {

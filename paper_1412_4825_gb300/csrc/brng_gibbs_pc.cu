@@ -17,7 +17,7 @@ __host__ __device__ inline uint32_t normal_gamma_pc_warp_bytes(uint32_t B) {
 // PER: consumer warps served by one producer warp (>= ceil(Wc / Wp)).
 template <int PER>
 __global__ void __launch_bounds__(512) normal_gamma_pc_kernel(const NormalGammaArgs a, uint32_t Wc,
-                                                              uint32_t Wp) {
+                                                              uint32_t Wp, uint32_t stall) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned lane = lane_id();
   const unsigned warp = threadIdx.x >> 5;
@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(512) normal_gamma_pc_kernel(const NormalGammaA
     fU[k] = PcFill{pu / 4u, 0ull, stream, on};
   }
   __syncthreads();
+  if (stall) return;  // failure-path test: the consumers' waits must run out
   uint64_t t0 = 0;
   while (true) {
     bool progress = false, any = false;
@@ -110,25 +111,27 @@ __global__ void __launch_bounds__(512) normal_gamma_pc_kernel(const NormalGammaA
 
 template <int PER>
 static cudaError_t launch_pc_t(const NormalGammaArgs& a, uint32_t Wc, uint32_t Wp, size_t smem,
-                               uint64_t blocks, cudaStream_t st) {
+                               uint64_t blocks, cudaStream_t st, bool stall) {
   cudaError_t e = cudaFuncSetAttribute(normal_gamma_pc_kernel<PER>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  normal_gamma_pc_kernel<PER><<<static_cast<unsigned>(blocks), 32u * (Wc + Wp), smem, st>>>(a, Wc, Wp);
+  normal_gamma_pc_kernel<PER><<<static_cast<unsigned>(blocks), 32u * (Wc + Wp), smem, st>>>(a, Wc, Wp,
+                                                                                          stall ? 1u : 0u);
   return cudaGetLastError();
 }
 
-cudaError_t launch_normal_gamma_pc(const NormalGammaArgs& a, uint32_t Wc, uint32_t Wp, cudaStream_t st) {
+cudaError_t launch_normal_gamma_pc(const NormalGammaArgs& a, uint32_t Wc, uint32_t Wp, cudaStream_t st,
+                                   bool stall) {
   const uint64_t units = (static_cast<uint64_t>(a.n_chains) + 31) / 32;
   if (units == 0) return cudaSuccess;
   if (Wc < 1 || Wp < 1 || Wc + Wp > 16 || a.B < 4 || (a.B & (a.B - 1)) != 0) return cudaErrorInvalidValue;
   const size_t smem = static_cast<size_t>(Wc) * normal_gamma_pc_warp_bytes(a.B);
   const uint64_t blocks = (units + Wc - 1) / Wc;
   const uint32_t per = (Wc + Wp - 1) / Wp;
-  if (per <= 1) return launch_pc_t<1>(a, Wc, Wp, smem, blocks, st);
-  if (per <= 2) return launch_pc_t<2>(a, Wc, Wp, smem, blocks, st);
-  if (per <= 4) return launch_pc_t<4>(a, Wc, Wp, smem, blocks, st);
-  if (per <= 8) return launch_pc_t<8>(a, Wc, Wp, smem, blocks, st);
+  if (per <= 1) return launch_pc_t<1>(a, Wc, Wp, smem, blocks, st, stall);
+  if (per <= 2) return launch_pc_t<2>(a, Wc, Wp, smem, blocks, st, stall);
+  if (per <= 4) return launch_pc_t<4>(a, Wc, Wp, smem, blocks, st, stall);
+  if (per <= 8) return launch_pc_t<8>(a, Wc, Wp, smem, blocks, st, stall);
   return cudaErrorInvalidValue;  // a producer warp serves at most 8 consumer warps
 }
 

@@ -114,7 +114,10 @@ struct NormalGammaArgs {
 };
 cudaError_t launch_normal_gamma(const NormalGammaArgs& a, const Geometry& g, cudaStream_t st);
 // With Wc consumer and Wp producer warps per block (brng_gibbs_pc.cu).
-cudaError_t launch_normal_gamma_pc(const NormalGammaArgs& a, uint32_t Wc, uint32_t Wp, cudaStream_t st);
+// `stall` (failure-path tests only): the producers write nothing, so every
+// consumer wait runs out after its bound.
+cudaError_t launch_normal_gamma_pc(const NormalGammaArgs& a, uint32_t Wc, uint32_t Wp, cudaStream_t st,
+                                   bool stall = false);
 size_t normal_gamma_pc_bytes_per_warp(uint32_t B);  // shared memory per consumer warp
 
 // ---- batched persistent kernel (brng_batch.cu) ----

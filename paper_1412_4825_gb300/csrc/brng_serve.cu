@@ -232,6 +232,7 @@ void brng_server::run() {
           j->stage = kFailed;
           j->status = BRNG_EAGAIN;
           j->t_done = t;
+          st.cancelled++;
         }
         queue.clear();
       }
@@ -524,6 +525,22 @@ int brng_serve_stats(brng_server_t* s, brng_serve_stats_t* out) {
   out->queued = s->queue.size();
   out->device_bytes_in_use = s->used;
   return s->fatal;
+}
+
+int brng_serve_cancel(brng_server_t* s, uint64_t id) {
+  if (!s) return BRNG_EINVAL;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->jobs.find(id);
+    if (it == s->jobs.end()) return BRNG_ENOTFOUND;
+    if (it->second->stage != kQueued) return BRNG_EAGAIN;  // admitted: it runs to the end
+    auto q = std::find(s->queue.begin(), s->queue.end(), id);
+    if (q != s->queue.end()) s->queue.erase(q);
+    s->jobs.erase(it);
+    s->st.cancelled++;
+  }
+  s->cv.notify_all();  // a waiter on the id sees BRNG_ENOTFOUND
+  return BRNG_OK;
 }
 
 int brng_serve_close(brng_server_t* s) {
