@@ -51,8 +51,15 @@ brng::Geometry geometry(const brng_t* h, size_t per_warp) {
   return brng::Geometry{w, h->tune.buf_len};
 }
 
+const char* bulk_name(int tag) {
+  static const char* const names[] = {"brng_uniform", "brng_normal", "brng_exponential", "brng_gamma",
+                                      "brng_laplace", "brng_weibull", "brng_poisson", "brng_binomial"};
+  return (tag >= 0 && tag < 8) ? names[tag] : "brng_mixed";
+}
+
 int bulk(brng_t* h, int tag, size_t n, const uint8_t* tagv, const float* p0, const float* p1,
          float* out, uint32_t* words, cudaStream_t st) {
+  const brng::TraceRange trace(bulk_name(tag));
   if (!h) return BRNG_EINVAL;
   if (n == 0) return BRNG_OK;
   if (!p0 || !out || (tag == brng::kTagMixed && !tagv)) return BRNG_EINVAL;
@@ -84,6 +91,7 @@ int bulk(brng_t* h, int tag, size_t n, const uint8_t* tagv, const float* p0, con
 extern "C" {
 
 int brng_create(uint64_t seed, uint32_t n_streams, uint32_t buf_len, brng_t** out) {
+  const brng::TraceRange trace("brng_create");
   if (!out || n_streams == 0) return BRNG_EINVAL;
   if (buf_len == 0) buf_len = brng::kDefaultBufLen;
   if (!pow2_in(buf_len, 4, brng::kMaxBufLen)) return BRNG_EINVAL;
@@ -249,6 +257,7 @@ int brng_uniform(brng_t* h, size_t n, const float* a, const float* b, float* out
 }
 int brng_uniform_f64(brng_t* h, size_t n, const double* a, const double* b, double* out,
                      uint32_t* words, brng_stream_t stream) {
+  const brng::TraceRange trace("brng_uniform_f64");
   if (!h) return BRNG_EINVAL;
   if (n == 0) return BRNG_OK;
   if (!a || !b || !out) return BRNG_EINVAL;
@@ -303,6 +312,7 @@ int brng_mixed(brng_t* h, size_t n, const uint8_t* tag, const float* p0, const f
 
 int brng_dirichlet(brng_t* h, size_t n_rows, uint32_t K, const float* alpha, float* out,
                    brng_stream_t stream) {
+  const brng::TraceRange trace("brng_dirichlet");
   if (!h || K == 0 || K > 128 || h->S % K != 0) return BRNG_EINVAL;
   if (n_rows == 0) return BRNG_OK;
   if (!alpha || !out) return BRNG_EINVAL;
@@ -477,6 +487,7 @@ extern "C" {
 int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_t n_chains,
                    uint32_t n_sweeps, const void* params, void* state, double* moments,
                    brng_stream_t stream) {
+  const brng::TraceRange trace("brng_gibbs_run");
   if (!h) return BRNG_EINVAL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (n_chains == 0) return BRNG_OK;
@@ -514,6 +525,7 @@ int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_
 
 int brng_test_pc_stall(brng_t* h, uint32_t n_chains, uint32_t n_sweeps, const void* params, void* state,
                        double* moments, brng_stream_t stream) {
+  const brng::TraceRange trace("brng_test_pc_stall");
   if (!h) return BRNG_EINVAL;
   if (n_chains == 0) return BRNG_OK;
   brng::BatchJob j;
@@ -527,6 +539,7 @@ int brng_test_pc_stall(brng_t* h, uint32_t n_chains, uint32_t n_sweeps, const vo
 }
 
 int brng_batch_create(brng_t* h, const brng_job_t* jobs, uint32_t n_jobs, brng_batch_t** out) {
+  const brng::TraceRange trace("brng_batch_create");
   if (!out) return BRNG_EINVAL;
   std::vector<brng::BatchJob> table;
   uint32_t P = 1, wpb = 1, wbytes = 128;
@@ -562,6 +575,7 @@ int brng_batch_create(brng_t* h, const brng_job_t* jobs, uint32_t n_jobs, brng_b
 }
 
 int brng_batch_launch(brng_batch_t* b, brng_stream_t stream) {
+  const brng::TraceRange trace("brng_batch_launch");
   if (!b) return BRNG_EINVAL;
   if (b->args.total_units == 0) return BRNG_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -579,6 +593,7 @@ int brng_batch_destroy(brng_batch_t* b) {
 }
 
 int brng_gibbs_batch(brng_t* h, const brng_job_t* jobs, uint32_t n_jobs, brng_stream_t stream) {
+  const brng::TraceRange trace("brng_gibbs_batch");
   if (!h) return BRNG_EINVAL;
   return brng::batch_launch_into(h, jobs, n_jobs, &h->d_batch_jobs, &h->batch_cap,
                                  &h->d_batch_counter, reinterpret_cast<cudaStream_t>(stream));

@@ -7,9 +7,21 @@
 #include <cstdint>
 
 #include "brng.h"
+#include <nvtx3/nvToolsExt.h>
 #include "brng_engine.cuh"
 
 namespace brng {
+
+// An NVTX range over a host-side call or phase: Nsight tools show the
+// library's calls by name (and ncu --nvtx can filter on them); without a tool
+// attached a push/pop costs a few nanoseconds.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+
 
 struct DevCounters;
 

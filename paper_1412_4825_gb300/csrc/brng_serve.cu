@@ -297,11 +297,15 @@ void brng_server::run() {
     }
     // admissions
     std::vector<int> admit_rc(admit.size());
-    for (size_t i = 0; i < admit.size(); ++i) admit_rc[i] = upload_job(admit[i], admit_stream);
+    if (!admit.empty()) {
+      const brng::TraceRange trace("brng_serve admit");
+      for (size_t i = 0; i < admit.size(); ++i) admit_rc[i] = upload_job(admit[i], admit_stream);
+    }
     if (!admit.empty()) cudaEventRecord(admit_event, admit_stream);
     // launch
     int launch_rc = BRNG_OK;
     if (launch_slot) {
+      const brng::TraceRange trace("brng_serve launch batch");
       std::vector<brng_job_t> batch;
       batch.reserve(launch_jobs.size());
       for (ServeJob* j : launch_jobs) batch.push_back(batch_entry(j));
