@@ -307,7 +307,9 @@ int or_uniform(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float
   return single(0, seed, S, pos, n, a, b, out, words, NULL, buf_len);
 }
 /* U[a, b) in FP64 from the 53-bit U64 domain: Sec. 2.2's GetUniform at
- * double precision, a + (b - a) U64 with one U64 element per valid draw.
+ * double precision, a + (b - a) U64 with one U64 element per valid draw,
+ * rounded as fma(b - a, U64, a): the difference rounded once, then the
+ * product and sum rounded together (C99 fma, correctly rounded).
  * pos64[s] is stream s's U64 position (separate from its U, N, E positions).
  * Needs finite a <= b; otherwise NaN, word 0, nothing consumed. */
 int or_uniform_f64(uint64_t seed, uint32_t S, uint64_t *pos64, uint64_t n, const double *a,
@@ -323,7 +325,7 @@ int or_uniform_f64(uint64_t seed, uint32_t S, uint64_t *pos64, uint64_t n, const
       double v = NAN;
       if (isfinite(a[i]) && isfinite(b[i]) && a[i] <= b[i]) {
         const double u = or_get(&g, OR_DOM_U64, &w);
-        v = a[i] + (b[i] - a[i]) * u;
+        v = fma(b[i] - a[i], u, a[i]);
       } else {
         ++n_domain;
       }

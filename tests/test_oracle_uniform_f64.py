@@ -1,17 +1,20 @@
 """Pins of the oracle's FP64 uniform (Sec. 2.2 GetUniform at double precision,
 from the 53-bit U64 domain).
 
-* brute force: every output equals a + (b - a) u53 with u53 built in Python
-  integers from Philox words computed by a Python-int Philox (the Salmon et al.
-  round function restated here, independent of the oracle's C), element j of
-  stream s in block j/2, words 2(j%2) and 2(j%2)+1; the word output is the
-  pair's first word;
+* brute force: every output equals fma(b - a, u53, a) -- the difference
+  rounded to double, then the product and sum rounded once, computed here in
+  exact rational arithmetic -- with u53 built in Python integers from Philox
+  words of a Python-int Philox (the Salmon et al. round function restated
+  here, independent of the oracle's C), element j of stream s in block j/2,
+  words 2(j%2) and 2(j%2)+1; the word output is the pair's first word;
 * closed forms: mean (a+b)/2 and variance (b-a)^2/12, KS against U(0, 1);
   u53 values are multiples of 2^-53 in [0, 1);
 * consumption: invalid (a, b) give NaN, word 0 and consume nothing; positions
   advance by the valid draws per stream; a call split in two (positions
   carried) equals one call; values do not depend on the buffer length.
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 from scipy import stats
@@ -54,7 +57,9 @@ def test_brute_force_against_python_philox():
         j = int(pos0[s])
         for i in range(s, n, S):
             u, w0 = _u53_element(seed, s, j)
-            assert out[i] == a[i] + (b[i] - a[i]) * u  # numpy: two roundings, no FMA
+            d = float(b[i]) - float(a[i])  # rounded once
+            want = float(Fraction(d) * Fraction(u) + Fraction(float(a[i])))  # one more rounding
+            assert out[i] == want
             assert words[i] == w0
             j += 1
         assert pos[s] == j
