@@ -207,7 +207,36 @@ def extras(dev, stream, peaks, args):
     out["mixed_2^28"] = {"deviates_per_s": n / t, "ms": t * 1e3, "tuning": tune, "autotune_ms": table,
                          "hbm_achieved_gbs": gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"),
                          "hbm_frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None}
+    # -- buffer length (the paper's vectorisation-vs-waste trade-off, Sec. 2.4):
+    # the mixed stream and the normal-gamma sampler at every ring length whose
+    # rings fit in shared memory (values never depend on it)
+    sweep = {}
+    for bl in (4, 8, 16, 32, 64, 128, 256, 512):
+        try:
+            hm.tune(buf_len=bl, warps_per_block=2)
+            tb = _time_s(run_mixed, stream, reps=2)
+            sweep[str(bl)] = {"ms": tb * 1e3, "hbm_frac": 17.0 * n / tb / 1e9 / peaks["hbm_gbs"]
+                              if peaks.get("hbm_gbs") else None}
+        except B.BrngError:
+            sweep[str(bl)] = "rings do not fit in shared memory"
+    out["buffer_length_sweep_mixed_2^28"] = sweep
     hm.close()
+    ng = [torch.from_numpy(x).to(dev) for x in inputs.normal_gamma_data(65536, seed=SEED)]
+    ngp = B.brng_normal_gamma_params_t(2.0, 1.0, 0.0, 0.01, *[x.data_ptr() for x in ng])
+    ngs = B.normal_gamma_state(65536, device=dev)
+    ngm = torch.zeros((65536, 4), dtype=torch.float64, device=dev)
+    hn = B.Handle(SEED, 1)
+    run_ng = lambda: B.brng_gibbs_run(hn.h, B.MODEL_NORMAL_GAMMA, 0, 65536, 2000, ngp, ngs, ngm, stream)  # noqa: E731
+    sweep = {}
+    for bl in (4, 8, 16, 32, 64, 128, 256):
+        try:
+            hn.tune(buf_len=bl, warps_per_block=8)
+            sweep[str(bl)] = {"ms": _time_s(run_ng, stream, reps=2) * 1e3}
+        except B.BrngError:
+            sweep[str(bl)] = "rings do not fit in shared memory"
+    out["buffer_length_sweep_normal_gamma_65536x2000"] = sweep
+    hn.close()
+    del ng, ngs, ngm
     del tag, p0, p1, o, w
     torch.cuda.empty_cache()
     # -- Poisson draws (discrete, by inversion of one U), lambda log-uniform in [0.05, 64]
@@ -574,6 +603,17 @@ def run_case(args):
         mom = torch.zeros((1024, 5), dtype=torch.float64, device=dev)
         fn = lambda: B.brng_gibbs_run(h.h, B.MODEL_TRIANGLE, 0, 1024, args.sweeps, None, st, mom, stream)  # noqa: E731
         info.update(chains=1024, sweeps=args.sweeps)
+    elif args.case == "uniform64":
+        n, S = 1 << args.log2n, 1 << args.log2s
+        g = torch.Generator(device=dev)
+        g.manual_seed(SEED)
+        a = torch.rand(n, generator=g, device=dev, dtype=torch.float64)
+        b = a + torch.rand(n, generator=g, device=dev, dtype=torch.float64)
+        o = torch.empty(n, dtype=torch.float64, device=dev)
+        w = torch.empty(n, dtype=torch.int32, device=dev)
+        h = B.Handle(SEED, S)
+        fn = lambda: B.brng_uniform_f64(h.h, a, b, o, w, stream)  # noqa: E731
+        info.update(draws=n, streams=S, bytes_per_launch=28 * n)
     else:
         raise SystemExit("unknown case %r" % args.case)
     for _ in range(args.warmup):
@@ -604,10 +644,10 @@ def main():
                     help="skip the secondary workloads (triangle, LDA, mixed stream, batched vs plain, served mix)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="arrival window of the served mix at 2,000 jobs/s")
-    ap.add_argument("--case", choices=["mixed", "lda", "triangle"], default=None,
-                    help="time one secondary workload instead (profiling): mixed, lda or triangle")
-    ap.add_argument("--log2n", type=int, default=28, help="--case mixed: log2 of the draws")
-    ap.add_argument("--log2s", type=int, default=20, help="--case mixed: log2 of the streams")
+    ap.add_argument("--case", choices=["mixed", "lda", "triangle", "uniform64"], default=None,
+                    help="time one secondary workload instead (profiling): mixed, lda, triangle or uniform64")
+    ap.add_argument("--log2n", type=int, default=28, help="--case mixed / uniform64: log2 of the draws")
+    ap.add_argument("--log2s", type=int, default=20, help="--case mixed / uniform64: log2 of the streams")
     ap.add_argument("--docs", type=int, default=16384, help="--case lda: documents")
     ap.add_argument("--sweeps", type=int, default=500, help="--case lda/triangle: sweeps")
     args = ap.parse_args()

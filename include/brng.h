@@ -176,13 +176,14 @@ int brng_fp64_eval(uint32_t fn, size_t n, const double *in, double *out, brng_st
 /* U[a, b):  a + (b - a) U.  Needs finite a <= b. */
 int brng_uniform(brng_t *h, size_t n, const float *a, const float *b, float *out,
                  uint32_t *words, brng_stream_t stream);
-/* U[a, b) in FP64 (Sec. 2.2 GetUniform at double precision): a + (b - a) U64
+/* U[a, b) in FP64 (Sec. 2.2 GetUniform at double precision): a + (b - a) U64,
+ * rounded as fma(b - a, U64, a),
  * with the 53-bit uniform U64 = ((w0 >> 5) 2^26 + (w1 >> 6)) 2^-53 of domain 4,
  * element j of a stream in Philox block j/2, words (w0, w1) = (2(j%2),
  * 2(j%2)+1).  Each stream has its own U64 position (brng_get_positions_u64),
  * apart from its U, N, E positions; draw i -> stream i mod n_streams as above.
- * a, b, out: device, n float64 each; words: the pair's first word.  FP64
- * arithmetic in that order without contraction: bit-exact with the oracle.
+ * a, b, out: device, n float64 each; words: the pair's first word.  The same
+ * two FP64 roundings as the oracle: bit-exact with it.
  * Needs finite a <= b. */
 int brng_uniform_f64(brng_t *h, size_t n, const double *a, const double *b, double *out,
                      uint32_t *words, brng_stream_t stream);

@@ -447,8 +447,8 @@ cudaError_t launch_fp32_eval(uint32_t fn, size_t n, const float* in, float* out,
 
 // ---- FP64 uniform from the U64 domain (brng_uniform_f64) -------------------
 // finite a <= b, decided on the bit patterns with integer operations: GB300's
-// FP64 pipe is narrow, and the three FP64 operations of the value are all a
-// draw should spend there.  Finite: exponent field below 0x7ff.  Order of
+// FP64 pipe is narrow, and the two FP64 operations of the value (a difference
+// and a fused multiply-add) are all a draw should spend there.  Finite: exponent field below 0x7ff.  Order of
 // finite doubles: the sign-magnitude pattern mapped to a two's-complement key
 // (-0 and +0 both to 0), which orders like the values.
 __device__ __forceinline__ int64_t f64_order_key(uint64_t bits) {
@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(256) uniform64_kernel(const Uniform64Args a) {
         const bool second = (j & 1) != 0;
         first = second ? w.z : w.x;
         const double u = u53(first, second ? w.w : w.y);
-        v = __dadd_rn(lo[k], __dmul_rn(__dadd_rn(hi[k], -lo[k]), u));
+        v = __fma_rn(__dadd_rn(hi[k], -lo[k]), u, lo[k]);  // fma(b - a, U64, a), as the oracle
         ++j;
       } else {
         ++bad;
