@@ -445,6 +445,13 @@ int brng_serve_close(brng_server_t *s);
 int brng_test_pc_stall(brng_t *h, uint32_t n_chains, uint32_t n_sweeps, const void *params, void *state,
                        double *moments, brng_stream_t stream);
 
+/* Checked build (compiled with -DBRNG_DEBUG): the number of failed protocol
+ * checks -- a ring element read or consumed before it was generated, a refill
+ * over unread slots, a batch unit outside its job -- counted on the device
+ * since the last reset (nothing traps).  Synchronous.  BRNG_EINVAL in the
+ * normal build, which has no checks. */
+int brng_debug_violations(uint64_t *count, int reset);
+
 #ifdef __cplusplus
 }
 #endif

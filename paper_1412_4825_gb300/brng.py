@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libbrng.so")
+# BRNG_LIB selects another build of the same library (the checked build,
+# libbrng_debug.so); the default is the in-tree libbrng.so
+LIB_PATH = os.environ.get("BRNG_LIB") or os.path.join(_HERE, "libbrng.so")
 
 BRNG_OK, BRNG_EINVAL, BRNG_ENOMEM, BRNG_ECUDA, BRNG_EDOMAIN, BRNG_EREJECT, BRNG_ETIMEOUT, \
     BRNG_EAGAIN, BRNG_ENOTFOUND = range(9)
@@ -138,6 +140,7 @@ def _load():
         "brng_serve_stats": ([vp, C.POINTER(brng_serve_stats_t)], i32),
         "brng_serve_close": ([vp], i32),
         "brng_serve_cancel": ([vp, u64], i32),
+        "brng_debug_violations": ([C.POINTER(u64), i32], i32),
         "brng_test_pc_stall": ([vp, u32, u32, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
@@ -453,6 +456,14 @@ def brng_serve_close(s):
 def brng_serve_cancel(s, job_id):
     """BRNG_OK (withdrawn), BRNG_EAGAIN (already admitted) or BRNG_ENOTFOUND."""
     return lib.brng_serve_cancel(s, int(job_id))
+
+
+def brng_debug_violations(reset=False):
+    """Failed protocol checks of the checked build since the last reset, or
+    None for the normal build."""
+    n = C.c_uint64()
+    code = lib.brng_debug_violations(C.byref(n), int(bool(reset)))
+    return n.value if code == BRNG_OK else None
 
 
 def brng_test_pc_stall(h, n_chains, n_sweeps, params, state, moments, stream=None):

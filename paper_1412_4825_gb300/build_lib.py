@@ -39,21 +39,30 @@ def _deps():
     return out
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+# the checked build (-DBRNG_DEBUG): protocol checks counted on the device
+# (csrc/brng_debug.cuh), same results; built on demand by its test
+LIB_DEBUG = os.path.join(PKG, "libbrng_debug.so")
+
+
+def needs_build(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not (force or needs_build()):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), debug: bool = False) -> str:
+    lib_path = LIB_DEBUG if debug else LIB
+    if not (force or needs_build(lib_path)):
+        return lib_path
+    build_dir = BUILD + ("_debug" if debug else "")
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
+    if debug:
+        extra = (*extra, "-DBRNG_DEBUG")
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -65,13 +74,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if verbose:
         for _, log in results:
             sys.stdout.write(log)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib_path + ".tmp%d" % os.getpid()
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

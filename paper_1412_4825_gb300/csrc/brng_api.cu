@@ -13,6 +13,18 @@
 #include "brng_gamma.cuh"
 #include "brng_internal.h"
 
+#ifdef BRNG_DEBUG
+namespace brng {
+namespace {
+std::vector<unsigned long long (*)(bool)>& debug_readers() {
+  static std::vector<unsigned long long (*)(bool)> r;  // filled at library load
+  return r;
+}
+}  // namespace
+void register_debug_reader(unsigned long long (*read)(bool reset)) { debug_readers().push_back(read); }
+}  // namespace brng
+#endif
+
 struct brng_handle {
   uint64_t seed;
   uint32_t S;
@@ -521,6 +533,22 @@ int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_
       return cuda_status(brng::launch_dirichlet(j.lda, g, true, st));
     }
   }
+}
+
+int brng_debug_violations(uint64_t* count, int reset) {
+#ifdef BRNG_DEBUG
+  if (!count) return BRNG_EINVAL;
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e);
+  uint64_t total = 0;
+  for (auto read : brng::debug_readers()) total += read(reset != 0);
+  *count = total;
+  return BRNG_OK;
+#else
+  (void)count;
+  (void)reset;
+  return BRNG_EINVAL;
+#endif
 }
 
 int brng_test_pc_stall(brng_t* h, uint32_t n_chains, uint32_t n_sweeps, const void* params, void* state,

@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a) {
     }
     const BatchJob* J = a.jobs + lo;
     const uint64_t local = u - J->first_unit;
+    BRNG_CHECK(J->first_unit <= u && local < J->n_units);  // the unit belongs to the job found
     switch (J->model) {
       case BRNG_MODEL_TRIANGLE: {
         const TriangleArgs ta = J->tri;

@@ -101,6 +101,7 @@ struct PcRing {
   }
   // Commits n elements and hands their slots back to the producer.
   __device__ __forceinline__ void advance(uint32_t n) {
+    BRNG_CHECK(failed || static_cast<int32_t>(seen - static_cast<uint32_t>(p)) >= static_cast<int32_t>(n));
     p += n;
     st_release_cta(head_p, static_cast<uint32_t>(p));
   }
@@ -129,6 +130,7 @@ struct PcRing {
         break;
       }
     }
+    BRNG_CHECK(failed || !want || static_cast<int32_t>(seen - static_cast<uint32_t>(p)) >= static_cast<int32_t>(k));
   }
 
   // Next element for lanes with `want` (all 32 lanes call this).

@@ -28,6 +28,7 @@
 
 #include <cstdint>
 
+#include "brng_debug.cuh"
 #include "brng_engine.cuh"
 
 namespace brng {
@@ -159,6 +160,7 @@ struct Ring {
     if (__any_sync(kFull, need)) refill(need, gen, stream, rk);
     T v = T(0);
     if (want) {
+      BRNG_CHECK(rp < valid && valid <= B);  // the slot was filled by this refill
       const unsigned lane = lane_id();
       v = val[rp * NC + (lane % NC)];
       if (kWords && word) *word = wrd[rp * NC + (lane % NC)];
@@ -211,7 +213,10 @@ struct CRing {
   __device__ __forceinline__ uint32_t peek_word(uint32_t i) const {
     return wrd[((rp + i) & mask) * 32u + lane_id()];
   }
-  __device__ __forceinline__ void advance(uint32_t n) { rp += n; }
+  __device__ __forceinline__ void advance(uint32_t n) {
+    BRNG_CHECK(avail() >= static_cast<int32_t>(n));  // every consumed element was generated
+    rp += n;
+  }
 
   __device__ __forceinline__ void gen_own(uint64_t blk, uint32_t slot, uint32_t stream,
                                           const RoundKeys& rk) {
@@ -237,6 +242,7 @@ struct CRing {
     }
     const uint32_t nb = (rp + mask + 1u - filled) / kEPB;
     const uint64_t first = b0 + filled / kEPB;
+    BRNG_CHECK(static_cast<int32_t>(filled + nb * kEPB - rp) <= static_cast<int32_t>(mask + 1u));  // no unread slot overwritten
     // one block per iteration, not unrolled: the generator code (Philox and
     // Box-Muller) is long and the instruction cache small; measured on GB300,
     // two blocks in flight (more ILP, three copies of the code) were 5-18 %
@@ -251,6 +257,7 @@ struct CRing {
                                          const RoundKeys& rk) {
     const bool need = want && avail() < static_cast<int32_t>(k);
     if (__any_sync(kFull, need)) topup(live || need, stream, rk);
+    BRNG_CHECK(!want || avail() >= static_cast<int32_t>(k));  // one top-up meets k <= B - 3
   }
 
   // Next element for lanes with `want` (all 32 lanes call this); `live`: the
