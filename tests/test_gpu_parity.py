@@ -12,7 +12,7 @@ Bars:
     logarithm (the oracle reports the Gamma's 3|cz|/t and boost exponent
     |ln(u_b)/alpha|, the Weibull exponent |ln(E)/k|, the Dirichlet log-Gammas);
     results below FLT_MIN compare absolutely (2 FLT_MIN).
-Sizes span several warps and a ragged tail; the BASELINE-size workloads are
+Sizes span several warps and a ragged tail; the full-size workloads are
 checked on sampled streams/chains the oracle recomputes one by one.
 """
 import os
