@@ -239,6 +239,54 @@ def extras(dev, stream, peaks, args):
     del ng, ngs, ngm
     del tag, p0, p1, o, w
     torch.cuda.empty_cache()
+    # -- the paper's per-distribution table (Sec. 2.4) in GPU form: each of its six
+    # distributions over 2^26 draws (2^20 streams) with per-draw (varying)
+    # parameters -- the BatchRNG column -- and with one constant parameter set
+    # -- the batch column; SM-cycles per sample (time x SM clock x SMs / draws)
+    # beside the paper's cycles per sample; and one draw per call through the
+    # C ABI, the one-at-a-time column
+    n, S = 1 << 26, 1 << 20
+    gd = torch.Generator(device=dev)
+    gd.manual_seed(SEED + 7)
+
+    def logu(lo, hi):
+        return torch.exp(np.log(lo) + (np.log(hi) - np.log(lo)) * torch.rand(n, generator=gd, device=dev))
+
+    ones = torch.ones(n, device=dev)
+    zeros = torch.zeros(n, device=dev)
+    a_u = logu(1e-3, 1e3)
+    b_u = a_u + logu(1e-3, 1e3)
+    mu = logu(1e-3, 1e3) * torch.where(torch.rand(n, generator=gd, device=dev) < 0.5, -1.0, 1.0)
+    sig, lam, alpha, kw = logu(1e-2, 1e2), logu(1e-2, 1e2), logu(0.05, 50.0), logu(0.5, 5.0)
+    dists = {"uniform": (B.brng_uniform, [a_u, b_u], [zeros, ones]),
+             "normal": (B.brng_normal, [mu, sig], [zeros, ones]),
+             "exponential": (B.brng_exponential, [lam], [ones]),
+             "gamma": (B.brng_gamma, [alpha], [ones * 2.0]),
+             "laplace": (B.brng_laplace, [mu, sig], [zeros, ones]),
+             "weibull": (B.brng_weibull, [kw, lam], [ones * 1.5, ones])}
+    o = torch.empty(n, device=dev)
+    hd = B.Handle(SEED, S)
+    hd.tune(buf_len=8, warps_per_block=2)
+    sm_cycles_per_s = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 * torch.cuda.get_device_properties(dev).multi_processor_count
+    table = {}
+    for name, (fn, pv, pf) in dists.items():
+        tv = _time_s(lambda: fn(hd.h, *pv, o, None, stream), stream)
+        tf = _time_s(lambda: fn(hd.h, *pf, o, None, stream), stream)
+        nbytes = 4.0 * (len(pv) + 1) * n  # parameters read, value written
+        table[name] = {"varying_deviates_per_s": n / tv, "fixed_deviates_per_s": n / tf,
+                       "varying_sm_cycles_per_sample": tv * sm_cycles_per_s / n,
+                       "fixed_sm_cycles_per_sample": tf * sm_cycles_per_s / n,
+                       "varying_hbm_frac": nbytes / tv / 1e9 / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None}
+    h1 = B.Handle(SEED, 1)
+    a1, o1 = alpha[:1].clone(), torch.empty(1, device=dev)
+    calls = 2000
+    t1 = _time_s(lambda: [B.brng_gamma(h1.h, a1, o1, None, stream) for _ in range(calls)], stream, reps=2)
+    table["gamma_one_draw_per_call"] = {"deviates_per_s": calls / t1, "us_per_draw": t1 / calls * 1e6}
+    out["per_distribution_2^26"] = table
+    hd.close()
+    h1.close()
+    del ones, zeros, a_u, b_u, mu, sig, lam, alpha, kw, o, dists
+    torch.cuda.empty_cache()
     # -- Poisson draws (discrete, by inversion of one U), lambda log-uniform in [0.05, 64]
     n, S = 1 << 26, 1 << 20
     g = torch.Generator(device=dev)
