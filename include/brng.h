@@ -26,14 +26,17 @@
  * Memory: every array argument marked "device" is caller-owned device memory
  * (e.g. a torch CUDA tensor), read or written asynchronously on `stream`; the
  * call returns once the work is enqueued.  "host" arrays are read or written
- * before the call returns.  Parameter arrays are float32 and contiguous.
+ * before the call returns.  Parameter arrays are float32 and contiguous
+ * (float64 for brng_uniform_f64).
  *
  * Errors: every call returns a brng_status_t.  Argument errors are detected
  * on the host before any launch (BRNG_EINVAL); CUDA launch/alloc failures give
  * BRNG_ECUDA / BRNG_ENOMEM.  Invalid per-draw parameters are *not* an error
  * of the call: the draw's output is NaN, it consumes nothing, and the
  * handle's device counters record it; brng_read_counters() synchronises the
- * stream and reports BRNG_EDOMAIN / BRNG_EREJECT from those counters.
+ * stream and reports BRNG_ETIMEOUT / BRNG_EDOMAIN / BRNG_EREJECT from those
+ * counters.  Calls on one handle must be ordered on one stream (they share its
+ * stream positions and counters).
  */
 #ifndef BRNG_H
 #define BRNG_H
@@ -103,8 +106,9 @@ typedef struct {
 /* ---- handle (Sec. 2.2 constructor / destructor) ---------------------------
  * brng_create: a handle with `n_streams` streams (>= 1, < 2^32) keyed by
  * `seed`, buffer length `buf_len` (0 = default 32; power of two, 4..512),
- * on the current CUDA device.  It owns per-stream positions (3 x uint64 per
- * stream, all zero = every stream at its start) and the counters.  The
+ * on the current CUDA device.  It owns per-stream positions (4 x uint64 per
+ * stream: the U, N, E domains and the U64 domain of brng_uniform_f64; all
+ * zero = every stream at its start) and the counters.  The
  * paper's constructor fills the buffers at once; here rings are filled lazily
  * inside each kernel, which gives the same values.  *out is set only on
  * BRNG_OK.  brng_destroy frees it (NULL is a no-op); no call on the handle
