@@ -460,10 +460,19 @@ def run_gpu(args):
     fixed = bool(args.buf_len or args.warps_per_block)
     if fixed:
         h.tune(buf_len=args.buf_len, warps_per_block=args.warps_per_block)
-    d_nobs, d_xbar, d_sc = (torch.from_numpy(a).to(dev) for a in (nobs, xbar, sc))
+    # one device buffer [nobs | xbar | sc | state | moments] (4+4+4+24+32 B per
+    # chain): the end-to-end leg moves the inputs in one copy and the results
+    # in one copy
+    n4 = 4 * N_CHAINS
+    dbuf = torch.empty(17 * n4, dtype=torch.uint8, device=dev)
+    d_nobs, d_xbar, d_sc = (dbuf[i * n4:(i + 1) * n4].view(torch.float32) for i in range(3))
+    state = dbuf[3 * n4:9 * n4].view(torch.int64).view(N_CHAINS, 3)
+    mom = dbuf[9 * n4:17 * n4].view(torch.float64).view(N_CHAINS, 4)
+    for d, a in ((d_nobs, nobs), (d_xbar, xbar), (d_sc, sc)):
+        d.copy_(torch.from_numpy(np.ascontiguousarray(a)))
+    state.copy_(B.normal_gamma_state(N_CHAINS, mu0=PRIOR[2], device="cpu"))
+    mom.zero_()
     params = B.brng_normal_gamma_params_t(*PRIOR, d_nobs.data_ptr(), d_xbar.data_ptr(), d_sc.data_ptr())
-    state = B.normal_gamma_state(N_CHAINS, mu0=PRIOR[2], device=dev)
-    mom = torch.zeros((N_CHAINS, 4), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step():
@@ -520,28 +529,28 @@ def run_gpu(args):
         total_s = shard.max_over_ranks(pg, total_s, device=dev)
     value = world * UPDATES_PER_STEP * args.steps / total_s
 
-    # end to end through the public API: host inputs -> device -> run -> host results
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
-    h_nobs, h_xbar, h_sc = pin(nobs), pin(xbar), pin(sc)
-    h_state_in = B.normal_gamma_state(N_CHAINS, mu0=PRIOR[2], device="cpu").pin_memory()
-    h_state_out = torch.empty_like(h_state_in).pin_memory()
-    h_mom = torch.empty((N_CHAINS, 4), dtype=torch.float64).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in (h_nobs, h_xbar, h_sc, h_state_in))
-    d2h = sum(t.numel() * t.element_size() for t in (h_state_out, h_mom))
+    # end to end through the public API: host inputs -> device -> run -> host
+    # results, every step: the inputs (data and start state) in one copy from
+    # pinned memory, the results (state and moments) in one copy back
+    h_in = torch.empty(9 * n4, dtype=torch.uint8).pin_memory()
+    for i, a in enumerate((nobs, xbar, sc)):
+        h_in[i * n4:(i + 1) * n4].view(torch.float32).copy_(torch.from_numpy(np.ascontiguousarray(a)))
+    h_in[3 * n4:].view(torch.int64).view(N_CHAINS, 3).copy_(B.normal_gamma_state(N_CHAINS, mu0=PRIOR[2],
+                                                                                  device="cpu"))
+    h_out = torch.empty(14 * n4, dtype=torch.uint8).pin_memory()
+    d_in, d_out = dbuf[:9 * n4], dbuf[3 * n4:]
+    h2d = h_in.numel()
+    d2h = h_out.numel()
     e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     with torch.cuda.stream(stream):
         for k in range(args.steps):
             flush.fill_(k & 0xFF)
             e_ev[k][0].record(stream)
-            d_nobs.copy_(h_nobs, non_blocking=True)
-            d_xbar.copy_(h_xbar, non_blocking=True)
-            d_sc.copy_(h_sc, non_blocking=True)
-            state.copy_(h_state_in, non_blocking=True)
+            d_in.copy_(h_in, non_blocking=True)
             mom.zero_()
             step()
-            h_state_out.copy_(state, non_blocking=True)
-            h_mom.copy_(mom, non_blocking=True)
+            h_out.copy_(d_out, non_blocking=True)
             e_ev[k][1].record(stream)
     barrier()
     e_s = sum(a.elapsed_time(b) for a, b in e_ev) / 1e3
