@@ -167,6 +167,21 @@ def extras(dev, stream, peaks, args):
 
     out = {}
     from paper_1412_4825_gb300 import autotune as AT
+    # integer-pipe roofline of a workload: the Philox blocks one call consumed
+    # (from the stream positions before and after it) per second, against the
+    # same peak as the headline's
+    peak_blocks = (torch.cuda.get_device_properties(dev).multi_processor_count * (64.0 / 2.0 / PHILOX_MULS_PER_BLOCK)
+                   * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6)
+
+    def philox_roofline(run, positions, per_block, seconds):
+        before = positions()
+        with torch.cuda.stream(stream):
+            run()
+        torch.cuda.synchronize(dev)
+        blocks = float((positions() - before).astype(np.float64).sum()) / per_block
+        return {"philox_blocks_per_call": blocks, "philox_blocks_per_s": blocks / seconds,
+                "philox_frac": blocks / seconds / peak_blocks}
+
     # -- triangle (Eq. 1, Fig. 1): FP64, 1,024 chains; tuning chosen by the autotuner
     h = B.Handle(SEED, 1)
     st = B.triangle_state(1024, device=dev)
@@ -176,6 +191,8 @@ def extras(dev, stream, peaks, args):
     t = _time_s(run_tri, stream)
     out["triangle_1024x10000"] = {"updates_per_s": 2 * 1024 * 10000 / t, "ms": t * 1e3, "tuning": tune,
                                   "autotune_ms": table}
+    out["triangle_1024x10000"].update(philox_roofline(
+        run_tri, lambda: st.view(torch.int64)[:, 2].cpu().numpy().astype(np.uint64), 2.0, t))
     h.close()
     # -- LDA document-topic Dirichlet step
     alpha, _, _ = inputs.lda_alpha(16384, K=64, seed=SEED)
@@ -192,6 +209,7 @@ def extras(dev, stream, peaks, args):
     out["lda_16384x64x500"] = {"dirichlet_updates_per_s": 16384 * 500 / t,
                                "gamma_deviates_per_s": 16384 * 64 * 500 / t, "ms": t * 1e3,
                                "tuning": tune, "autotune_ms": table}
+    out["lda_16384x64x500"].update(philox_roofline(run_lda, lambda: pos.cpu().numpy().astype(np.uint64), 4.0, t))
     h.close()
     del a, theta, pos, mom
     # -- mixed varying-parameter stream, 17 B per draw through HBM
@@ -207,6 +225,7 @@ def extras(dev, stream, peaks, args):
     out["mixed_2^28"] = {"deviates_per_s": n / t, "ms": t * 1e3, "tuning": tune, "autotune_ms": table,
                          "hbm_achieved_gbs": gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"),
                          "hbm_frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None}
+    out["mixed_2^28"].update(philox_roofline(run_mixed, hm.positions, 4.0, t))
     # -- buffer length (the paper's vectorisation-vs-waste trade-off, Sec. 2.4):
     # the mixed stream and the normal-gamma sampler at every ring length whose
     # rings fit in shared memory (values never depend on it)
