@@ -373,18 +373,23 @@ def extras(dev, stream, peaks, args):
             specs.append((model, nch, int(rng.integers(sweeps[0], sweeps[1] + 1)), seed + 1 + i))
         keep = []
 
+        positions = []  # per job of the last fresh_jobs(): (its stream positions, elements per block)
+
         def fresh_jobs():
             jobs = []
+            positions.clear()
             for model, nch, sw, sd in specs:
                 if model == B.MODEL_TRIANGLE:
                     st = B.triangle_state(nch, device=dev)
                     mm, prm, sarg = torch.zeros((nch, 5), dtype=torch.float64, device=dev), None, st
+                    positions.append((st.view(torch.int64)[:, 2], 2.0))
                 elif model == B.MODEL_NORMAL_GAMMA:
                     st = B.normal_gamma_state(nch, device=dev)
                     mm = torch.zeros((nch, 4), dtype=torch.float64, device=dev)
                     prm = B.brng_normal_gamma_params_t(2.0, 1.0, 0.0, 0.01, d_nobs.data_ptr(), d_xbar.data_ptr(),
                                                        d_sc.data_ptr())
                     sarg = st
+                    positions.append((st[:, 1:3], 4.0))
                 else:
                     th = torch.zeros((nch, 64), dtype=torch.float32, device=dev)
                     ps = torch.zeros((nch, 64, 2), dtype=torch.int64, device=dev)
@@ -392,9 +397,13 @@ def extras(dev, stream, peaks, args):
                     prm = B.brng_lda_params_t(64, d_alpha.data_ptr())
                     sarg = B.brng_lda_state_t(th.data_ptr(), ps.data_ptr())
                     keep.append((th, ps))
+                    positions.append((ps, 4.0))
                 keep.append((sarg, mm, prm))
                 jobs.append((model, nch, sw, sd, prm, sarg, mm))
             return jobs
+
+        def consumed_blocks():
+            return sum(float(p.cpu().numpy().astype(np.float64).sum()) / k for p, k in positions)
 
         upd = sum((1 if m == B.MODEL_LDA else 2) * c * sw for m, c, sw, _ in specs)
         hb = B.Handle(SEED, 1)
@@ -409,6 +418,13 @@ def extras(dev, stream, peaks, args):
         jobs = fresh_jobs()
         bjobs = [B.make_job(m, c, sw, sd, prm, sarg, mm)[0] for m, c, sw, sd, prm, sarg, mm in jobs]
         t_batch = _time_s(lambda: B.brng_gibbs_batch(hb.h, bjobs, stream), stream, reps=2, warm=1)
+        # the persistent kernel's integer-pipe roofline: the Philox blocks one
+        # batched call consumed (every job's stream positions before and after)
+        b0 = consumed_blocks()
+        with torch.cuda.stream(stream):
+            B.brng_gibbs_batch(hb.h, bjobs, stream)
+        torch.cuda.synchronize(dev)
+        batch_blocks = consumed_blocks() - b0
         # the same batch planned once and captured in a CUDA graph; each replay
         # continues every job's chains by its sweeps
         jobs = fresh_jobs()
@@ -436,7 +452,8 @@ def extras(dev, stream, peaks, args):
                 "plain_updates_per_s": upd / t_plain, "batched_updates_per_s": upd / t_batch,
                 "batched_over_plain": t_plain / t_batch, "plain_ms": t_plain * 1e3, "batched_ms": t_batch * 1e3,
                 "graph_updates_per_s": upd / t_graph, "graph_over_plain": t_plain / t_graph,
-                "graph_ms": t_graph * 1e3}
+                "graph_ms": t_graph * 1e3, "batch_philox_blocks_per_s": batch_blocks / t_batch,
+                "batch_philox_frac": batch_blocks / t_batch / peak_blocks}
 
     out["ensemble_48_jobs"] = ensemble(48, 65536, (100, 10000), SEED)
     out["ensemble_256_small_jobs"] = ensemble(256, 2048, (100, 1000), SEED + 1000)
