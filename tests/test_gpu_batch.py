@@ -100,6 +100,26 @@ def test_batch_equals_solo_runs():
             assert torch.equal(x, y), (a.model, a.n, a.sweeps)
 
 
+def test_batch_with_large_k_equals_solo_runs():
+    """LDA jobs with K = 100 and 128 put the whole batch on the four-components-
+    per-lane kernel; every job (LDA, triangle, normal-gamma) still equals its
+    solo run."""
+    def jobs():
+        return [Job(B.MODEL_LDA, 37, 15, seed=31, K=100), Job(B.MODEL_LDA, 20, 12, seed=32, K=128),
+                Job(B.MODEL_LDA, 50, 10, seed=33, K=64), Job(B.MODEL_TRIANGLE, 700, 40, seed=34),
+                Job(B.MODEL_NORMAL_GAMMA, 900, 30, seed=35, offset=77)]
+    solo = jobs()
+    for j in solo:
+        j.solo()
+    batch = jobs()
+    h = B.Handle(1, 1)
+    B.brng_gibbs_batch(h.h, [j.job() for j in batch])
+    torch.cuda.synchronize()
+    for a, b in zip(solo, batch):
+        for x, y in zip(a.snapshot(), b.snapshot()):
+            assert torch.equal(x, y), (a.model, a.n, a.sweeps)
+
+
 def test_batch_tuning_and_plan_reuse():
     solo = _jobs(300)
     for j in solo:
