@@ -285,6 +285,49 @@ def test_uniform_f64_call_splitting_and_full_size_sampled():
         assert np.array_equal(H(out[s::S]), vals)
 
 
+@pytest.mark.parametrize("case", range(12))
+def test_bulk_random_configurations(case):
+    """Seeded random configurations of the bulk calls: distribution, seed,
+    stream count, draw count, ring length, warps per block and a split of the
+    draws into two calls (each call maps its draw i to stream i mod S and
+    continues the streams): words and positions bit-exact, values within the
+    tolerance of the module doc."""
+    rng = np.random.default_rng(1000 + case)
+    fn = BULK[case % len(BULK)]
+    S = int(rng.integers(1, 3000))
+    n = int(rng.integers(1, 40000))
+    seed = int(rng.integers(0, 2**63))
+    h = handle(seed, S, buf_len=int(rng.choice([4, 8, 16, 32, 64, 128])),
+               warps_per_block=int(rng.choice([1, 2, 4, 8, 16])))
+    params = _params(fn, n, case + 50)
+    cut = int(rng.integers(0, n + 1))
+    parts = [[p[:cut] for p in params], [p[cut:] for p in params]]
+    outs, ws = [], []
+    pos = None
+    refs = []
+    for part in parts:
+        m = len(part[0])
+        if m == 0:
+            continue
+        o, w = _run_bulk(fn, h, part, m)
+        outs.append(H(o).astype(np.float64))
+        ws.append(words_np(w))
+        kw = {"with_cond": True} if fn in ("gamma", "weibull") else {}
+        r = getattr(O, fn)(seed, S, *part, pos=pos, **kw)
+        pos = r[2]
+        refs.append(r)
+    assert np.array_equal(np.concatenate(ws), np.concatenate([r[1] for r in refs]))
+    assert np.array_equal(h.positions(), pos)
+    ro = np.concatenate([r[0] for r in refs])
+    cond = np.concatenate([r[4] for r in refs]) if fn in ("gamma", "weibull") else None
+    if fn in ("normal", "laplace"):
+        mu = params[0].astype(np.float64)
+        scale = np.abs(mu) + np.abs(ro - mu)
+    else:
+        scale = _scale(fn, ro, params, cond)
+    assert_close(np.concatenate(outs), ro, scale, what="%s random case %d" % (fn, case))
+
+
 def test_gamma_decisions_many():
     """4M Gamma draws over alpha in [0.05, 500] and near 1: every attempt
     count (hence every accept decision) equals the oracle's."""
