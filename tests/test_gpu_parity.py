@@ -862,6 +862,46 @@ def test_lda_full_size_sampled():
         _lda_check(theta[d0:d1], pos[d0:d1], mom[d0:d1], ref, "lda docs %d..%d" % (d0, d1))
 
 
+@pytest.mark.parametrize("case", range(9))
+def test_gibbs_random_configurations(case):
+    """Seeded random configurations of the three Gibbs models -- chain or
+    document counts, sweeps, chain offset, ring length, warps per block,
+    lanes per chain (triangle), K and lookahead (LDA), a run split in two
+    with other tunings (triangle) -- against the oracle: triangle bit-exact,
+    normal-gamma and LDA positions bit-exact and values within tolerance."""
+    rng = np.random.default_rng(2000 + case)
+    model = case % 3
+    pick = lambda xs: int(rng.choice(xs))  # noqa: E731
+    offset = int(rng.integers(0, 100000))
+    if model == 0:
+        n, sweeps = int(rng.integers(1, 700)), int(rng.integers(2, 400))
+        s1 = int(rng.integers(1, sweeps))
+        st, m = _triangle_gpu(n, s1, lanes=pick([1, 2, 4, 8, 16, 32]), buf_len=pick([4, 8, 64, 256, 512]),
+                              wpb=pick([1, 2, 4, 8, 16]), offset=offset)
+        st, m = _triangle_gpu(n, sweeps - s1, lanes=pick([1, 2, 4, 8, 16, 32]), buf_len=pick([4, 16, 128]),
+                              wpb=pick([1, 4, 16]), state=st, mom=m, offset=offset)
+        x, y, pos = B.triangle_unpack(st)
+        ref = O.gibbs_triangle(42, n, sweeps, chain_offset=offset, nthreads=NT)
+        assert np.array_equal(x.view(np.int64), ref["xy"][:, 0].view(np.int64))
+        assert np.array_equal(y.view(np.int64), ref["xy"][:, 1].view(np.int64))
+        assert np.array_equal(pos, ref["pos"])
+        assert np.array_equal(H(m).view(np.int64), ref["mom"].view(np.int64))
+    elif model == 1:
+        n, sweeps = int(rng.integers(1, 1500)), int(rng.integers(1, 200))
+        nobs, xbar, sc = inputs.normal_gamma_data(n, seed=case)
+        st, m, cnt = _ng_gpu(nobs, xbar, sc, sweeps, offset=offset, buf_len=pick([4, 8, 16, 32, 64]),
+                             warps_per_block=pick([1, 2, 4, 8, 16]))
+        ref = O.gibbs_normal_gamma(42, sweeps, nobs, xbar, sc, chain_offset=offset, nthreads=NT)
+        _ng_check(st, m, ref, sweeps, "normal-gamma random case %d" % case)
+    else:
+        docs, K, sweeps = int(rng.integers(1, 120)), pick([5, 17, 32, 64, 100]), int(rng.integers(1, 30))
+        alpha, _, _ = inputs.lda_alpha(docs, K=K, seed=case)
+        theta, pos, mom = _lda_gpu(alpha, sweeps, offset=offset, buf_len=pick([4, 8, 16, 32]),
+                                   lookahead=pick([1, 2, 4, 8, 16]), warps_per_block=pick([1, 2, 4]))
+        ref = O.gibbs_lda(42, sweeps, alpha, doc_offset=offset, nthreads=NT)
+        _lda_check(theta, pos, mom, ref, "lda random case %d" % case)
+
+
 @pytest.mark.parametrize("tune", [dict(lookahead=1), dict(lookahead=16, buf_len=4), dict(warps_per_block=1, buf_len=128)])
 def test_lda_tuning_invariance(tune):
     alpha, _, _ = inputs.lda_alpha(50, K=64, seed=8)
