@@ -73,3 +73,43 @@ def test_mixed_stream_equals_its_single_distribution_calls(seed, S, n, n_tags, L
     mixed = O.mixed(seed, S, np.full(n, 6, np.uint8), lam, np.zeros(n, np.float32), buf_len=L)
     for x, y in zip(single[:3], mixed[:3]):
         assert np.array_equal(x, y, equal_nan=x.dtype.kind == "f")
+
+
+@hyp.settings(max_examples=30, deadline=None)
+@hyp.given(model=st.sampled_from([0, 1, 2]), n=st.integers(1, 30), sweeps=st.integers(1, 50),
+           cut=st.floats(0.0, 1.0), shard=st.floats(0.0, 1.0), L=st.sampled_from([1, 3, 8, 64, 256]),
+           seed=st.integers(0, 2**64 - 1), offset=st.integers(0, 10**6))
+def test_gibbs_resume_shard_and_buffer_length(model, n, sweeps, cut, shard, L, seed, offset):
+    """Each Gibbs model: a run split in two with the state carried equals one
+    run, chain (document) ranges run separately equal one run over all of
+    them, and the buffer length changes nothing -- states, positions and
+    moments bit for bit."""
+    from paper_1412_4825_gb300 import inputs
+    s1, k = int(cut * sweeps), int(shard * n)
+
+    def run(lo, hi, nsw, start=None, L_=L):
+        if model == 0:
+            kw = {} if start is None else dict(xy=start["xy"].ravel(), pos=start["pos"], mom=start["mom"].ravel())
+            r = O.gibbs_triangle(seed, hi - lo, nsw, chain_offset=offset + lo, buf_len=L_, **kw)
+            return r, (r["xy"], r["pos"], r["mom"])
+        if model == 1:
+            nobs, xbar, sc = (a[lo:hi] for a in inputs.normal_gamma_data(n, seed=7))
+            kw = {} if start is None else dict(state=start["state"].ravel(), pos=start["pos"].ravel(),
+                                               mom=start["mom"].ravel())
+            r = O.gibbs_normal_gamma(seed, nsw, nobs, xbar, sc, chain_offset=offset + lo, buf_len=L_, **kw)
+            return r, (r["state"], r["pos"], r["mom"])
+        alpha = inputs.lda_alpha(n, K=12, seed=7)[0][lo:hi]
+        kw = {} if start is None else dict(pos=start["pos"].ravel(), mom=start["mom"])
+        r = O.gibbs_lda(seed, nsw, alpha, doc_offset=offset + lo, buf_len=L_, **kw)
+        return r, (r["theta"] if nsw else None, r["pos"], r["mom"])
+
+    whole, w = run(0, n, sweeps, L_=64)
+    first, _ = run(0, n, s1)
+    _, resumed = run(0, n, sweeps - s1, start=first)
+    for a, b in zip(w[1:], resumed[1:]):
+        assert np.array_equal(a, b)
+    if model != 2 or sweeps - s1 > 0:  # LDA's theta is the last sweep's
+        assert np.array_equal(w[0], resumed[0])
+    parts = [run(lo, hi, sweeps)[1] for lo, hi in ((0, k), (k, n)) if hi > lo]
+    for j in range(3):
+        assert np.array_equal(np.concatenate([p[j] for p in parts]), w[j])
