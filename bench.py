@@ -111,9 +111,14 @@ def _oracle_sample(n_chains, n_sweeps, nthreads, seed=SEED):
 def cpu_baseline(n_chains=8192, n_sweeps=N_SWEEPS):
     cores = os.cpu_count() or 1
     dt = _oracle_sample(n_chains, n_sweeps, cores)
+    # the same oracle on one core, on an eighth of the sample
+    n1 = max(1, n_chains // 8)
+    dt1 = _oracle_sample(n1, n_sweeps, 1)
     return {"value": 2.0 * n_chains * n_sweeps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d of the 65,536 chains x %d sweeps (FP64 C oracle, %d threads, %.1f s)"
-                      % (n_chains, n_sweeps, cores, dt)}
+                      % (n_chains, n_sweeps, cores, dt),
+            "single_core_value": 2.0 * n1 * n_sweeps / dt1,
+            "single_core_sample": "%d chains x %d sweeps, 1 thread, %.1f s" % (n1, n_sweeps, dt1)}
 
 
 def run_reference(args):
