@@ -69,9 +69,9 @@ def lib():
         L.or_mixed_mt.restype = i32
         L.or_gibbs_triangle_mt.argtypes = [u64, u64, u32, u32, vp, vp, vp, u32, i32]
         L.or_gibbs_triangle_mt.restype = i32
-        L.or_gibbs_normal_gamma_mt.argtypes = [u64, u64, u32, u32, vp, vp, vp, vp, vp, vp, vp, u32, i32]
+        L.or_gibbs_normal_gamma_mt.argtypes = [u64, u64, u32, u32, vp, vp, vp, vp, vp, vp, vp, vp, u32, i32]
         L.or_gibbs_normal_gamma_mt.restype = i32
-        L.or_gibbs_lda_mt.argtypes = [u64, u64, u32, u32, u32, vp, vp, vp, vp, vp, vp, u32, i32]
+        L.or_gibbs_lda_mt.argtypes = [u64, u64, u32, u32, u32, vp, vp, vp, vp, vp, vp, vp, u32, i32]
         L.or_gibbs_lda_mt.restype = i32
         L.or_mt_accept.argtypes = [dbl, dbl, dbl]
         L.or_mt_accept.restype = i32
@@ -266,21 +266,31 @@ def gibbs_triangle(seed, n_chains, n_sweeps, chain_offset=0, xy=None, pos=None, 
 
 
 def gibbs_normal_gamma(seed, n_sweeps, nobs, xbar, sc, prior=(2.0, 1.0, 0.0, 0.01),
-                       chain_offset=0, state=None, pos=None, mom=None, buf_len=64, nthreads=1):
+                       chain_offset=0, state=None, pos=None, mom=None, buf_len=64, nthreads=1,
+                       trace=False):
+    """trace=True adds "trace": [n_chains, n_sweeps, 5] = per sweep (G, the
+    Gamma draw's conditioning, the Gaussian z of mu's draw, tau, mu)."""
     nobs, xbar, sc = _f32(nobs), _f32(xbar), _f32(sc)
     n_chains = nobs.size
     prior = np.ascontiguousarray(prior, dtype=np.float32)
     state = np.zeros(2 * n_chains) if state is None else np.array(state, np.float64, copy=True)
     pos = np.zeros(2 * n_chains, np.uint64) if pos is None else np.array(pos, np.uint64, copy=True)
     mom = np.zeros(4 * n_chains) if mom is None else np.array(mom, np.float64, copy=True)
+    tr = np.zeros((n_chains, n_sweeps, 5)) if trace else None
     st = lib().or_gibbs_normal_gamma_mt(seed, chain_offset, n_chains, n_sweeps, _p(prior),
                                         _p(nobs), _p(xbar), _p(sc), _p(state), _p(pos), _p(mom),
-                                        buf_len, _threads(nthreads))
-    return dict(state=state.reshape(n_chains, 2), pos=pos.reshape(n_chains, 2),
-                mom=mom.reshape(n_chains, 4), status=st)
+                                        _p(tr), buf_len, _threads(nthreads))
+    out = dict(state=state.reshape(n_chains, 2), pos=pos.reshape(n_chains, 2),
+               mom=mom.reshape(n_chains, 4), status=st)
+    if trace:
+        out["trace"] = tr
+    return out
 
 
-def gibbs_lda(seed, n_sweeps, alpha, doc_offset=0, pos=None, mom=None, buf_len=64, nthreads=1):
+def gibbs_lda(seed, n_sweeps, alpha, doc_offset=0, pos=None, mom=None, buf_len=64, nthreads=1,
+              trace=False):
+    """trace=True adds "trace": [n_docs, n_sweeps, K, 2] = per sweep and
+    component (log-Gamma, its conditioning)."""
     alpha = _f32(alpha)
     n_docs, K = alpha.shape
     theta = np.zeros((n_docs, K))
@@ -288,7 +298,12 @@ def gibbs_lda(seed, n_sweeps, alpha, doc_offset=0, pos=None, mom=None, buf_len=6
     cond = np.zeros((n_docs, K))
     pos = np.zeros(2 * n_docs * K, np.uint64) if pos is None else np.array(pos, np.uint64, copy=True)
     mom = np.zeros((n_docs, K)) if mom is None else np.array(mom, np.float64, copy=True)
+    tr = np.zeros((n_docs, n_sweeps, K, 2)) if trace else None
     st = lib().or_gibbs_lda_mt(seed, doc_offset, n_docs, K, n_sweeps, _p(alpha), _p(theta),
-                               _p(logs), _p(cond), _p(pos), _p(mom), buf_len, _threads(nthreads))
-    return dict(theta=theta, logs=logs, cond=cond, pos=pos.reshape(n_docs, K, 2), mom=mom,
-                status=st)
+                               _p(logs), _p(cond), _p(pos), _p(mom), _p(tr), buf_len,
+                               _threads(nthreads))
+    out = dict(theta=theta, logs=logs, cond=cond, pos=pos.reshape(n_docs, K, 2), mom=mom,
+               status=st)
+    if trace:
+        out["trace"] = tr
+    return out

@@ -57,7 +57,7 @@ int or_gibbs_triangle(uint64_t seed, uint64_t chain_offset, uint32_t n_chains, u
 int or_gibbs_normal_gamma(uint64_t seed, uint64_t chain_offset, uint32_t n_chains,
                           uint32_t n_sweeps, const float *prior, const float *nobs,
                           const float *xbar, const float *sc, double *state, uint64_t *pos,
-                          double *mom, uint32_t buf_len) {
+                          double *mom, double *trace, uint32_t buf_len) {
   if (buf_len == 0 || chain_offset + n_chains > 0x100000000ull) return OR_EINVAL;
   const float a0 = prior[0];
   const double b0 = prior[1], mu0 = prior[2], prec0 = prior[3];
@@ -77,7 +77,8 @@ int or_gibbs_normal_gamma(uint64_t seed, uint64_t chain_offset, uint32_t n_chain
       double dm = xb - mu;
       double SS = S + n * dm * dm;
       int rej = 0;
-      double G = or_get_gamma(&g, shape, NULL, NULL, &rej, NULL);
+      double kappa = 0.0;
+      double G = or_get_gamma(&g, shape, NULL, NULL, &rej, &kappa);
       n_reject += rej;
       tau = G / (b0 + 0.5 * SS);
       double P = prec0 + n * tau;
@@ -88,6 +89,14 @@ int or_gibbs_normal_gamma(uint64_t seed, uint64_t chain_offset, uint32_t n_chain
       m[1] += tau;
       m[2] += mu * mu;
       m[3] += tau * tau;
+      if (trace) {
+        double *tr = trace + 5 * ((uint64_t)c * n_sweeps + it);
+        tr[0] = G;
+        tr[1] = kappa;
+        tr[2] = z;
+        tr[3] = tau;
+        tr[4] = mu;
+      }
     }
     state[2 * c] = mu;
     state[2 * c + 1] = tau;
@@ -101,7 +110,7 @@ int or_gibbs_normal_gamma(uint64_t seed, uint64_t chain_offset, uint32_t n_chain
 
 int or_gibbs_lda(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K,
                  uint32_t n_sweeps, const float *alpha, double *theta, double *logs,
-                 double *cond, uint64_t *pos, double *mom, uint32_t buf_len) {
+                 double *cond, uint64_t *pos, double *mom, double *trace, uint32_t buf_len) {
   if (buf_len == 0 || K == 0 || (doc_offset + n_docs) * (uint64_t)K > 0x100000000ull)
     return OR_EINVAL;
   int n_domain = 0, n_reject = 0;
@@ -119,9 +128,16 @@ int or_gibbs_lda(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K
     double *m = mom + (uint64_t)d * K;
     for (uint32_t k = 0; k < K; ++k) l[k] = NAN;
     for (uint32_t it = 0; it < n_sweeps; ++it) {
-      or_dirichlet_row(comp, K, a, th, l, cond ? cond + (uint64_t)d * K : NULL, &n_domain,
-                       &n_reject);
+      double *cd = cond ? cond + (uint64_t)d * K : NULL;
+      or_dirichlet_row(comp, K, a, th, l, cd, &n_domain, &n_reject);
       for (uint32_t k = 0; k < K; ++k) m[k] += th[k];
+      if (trace) {
+        double *tr = trace + 2 * ((uint64_t)d * n_sweeps + it) * K;
+        for (uint32_t k = 0; k < K; ++k) {
+          tr[2 * k] = l[k];
+          tr[2 * k + 1] = cd ? cd[k] : 0.0;
+        }
+      }
     }
     if (logs)
       for (uint32_t k = 0; k < K; ++k) logs[(uint64_t)d * K + k] = l[k];
@@ -147,7 +163,7 @@ typedef struct {
   uint32_t n, K, sweeps, buf_len;
   const float *prior, *nobs, *xbar, *sc, *alpha;
   double *a, *b; /* model outputs */
-  double *logs, *cond;
+  double *logs, *cond, *trace;
   uint64_t *pos;
   int status;
   /* mixed stream */
@@ -167,11 +183,11 @@ static void *or_run(void *arg) {
     break;
   case 1:
     j->status = or_gibbs_normal_gamma(j->seed, j->offset, j->n, j->sweeps, j->prior, j->nobs,
-                                      j->xbar, j->sc, j->a, j->pos, j->b, j->buf_len);
+                                      j->xbar, j->sc, j->a, j->pos, j->b, j->trace, j->buf_len);
     break;
   case 2:
     j->status = or_gibbs_lda(j->seed, j->offset, j->n, j->K, j->sweeps, j->alpha, j->a,
-                             j->logs, j->cond, j->pos, j->b, j->buf_len);
+                             j->logs, j->cond, j->pos, j->b, j->trace, j->buf_len);
     break;
   default:
     j->status = or_mixed_streams(j->seed, j->S, j->s0, j->s1, j->pos, j->n_draws, j->tag, j->p0,
@@ -218,7 +234,7 @@ int or_gibbs_triangle_mt(uint64_t seed, uint64_t chain_offset, uint32_t n_chains
 int or_gibbs_normal_gamma_mt(uint64_t seed, uint64_t chain_offset, uint32_t n_chains,
                              uint32_t n_sweeps, const float *prior, const float *nobs,
                              const float *xbar, const float *sc, double *state, uint64_t *pos,
-                             double *mom, uint32_t buf_len, int nthreads) {
+                             double *mom, double *trace, uint32_t buf_len, int nthreads) {
   if (nthreads < 1) nthreads = 1;
   or_job *jobs = (or_job *)calloc(nthreads, sizeof(or_job));
   for (int t = 0; t < nthreads; ++t) {
@@ -228,7 +244,8 @@ int or_gibbs_normal_gamma_mt(uint64_t seed, uint64_t chain_offset, uint32_t n_ch
                        .sweeps = n_sweeps, .buf_len = buf_len, .prior = prior,
                        .nobs = nobs + b, .xbar = xbar + b, .sc = sc + b,
                        .a = state + 2 * (uint64_t)b, .b = mom + 4 * (uint64_t)b,
-                       .pos = pos + 2 * (uint64_t)b};
+                       .pos = pos + 2 * (uint64_t)b,
+                       .trace = trace ? trace + 5 * (uint64_t)b * n_sweeps : NULL};
   }
   int st = or_spawn(jobs, nthreads);
   free(jobs);
@@ -237,7 +254,8 @@ int or_gibbs_normal_gamma_mt(uint64_t seed, uint64_t chain_offset, uint32_t n_ch
 
 int or_gibbs_lda_mt(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K,
                     uint32_t n_sweeps, const float *alpha, double *theta, double *logs,
-                    double *cond, uint64_t *pos, double *mom, uint32_t buf_len, int nthreads) {
+                    double *cond, uint64_t *pos, double *mom, double *trace, uint32_t buf_len,
+                    int nthreads) {
   if (nthreads < 1) nthreads = 1;
   or_job *jobs = (or_job *)calloc(nthreads, sizeof(or_job));
   for (int t = 0; t < nthreads; ++t) {
@@ -247,7 +265,8 @@ int or_gibbs_lda_mt(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_
     jobs[t] = (or_job){.model = 2, .seed = seed, .offset = doc_offset + b, .n = e - b, .K = K,
                        .sweeps = n_sweeps, .buf_len = buf_len, .alpha = alpha + o,
                        .a = theta + o, .b = mom + o, .pos = pos + 2 * o,
-                       .logs = logs ? logs + o : NULL, .cond = cond ? cond + o : NULL};
+                       .logs = logs ? logs + o : NULL, .cond = cond ? cond + o : NULL,
+                       .trace = trace ? trace + 2 * o * n_sweeps : NULL};
   }
   int st = or_spawn(jobs, nthreads);
   free(jobs);

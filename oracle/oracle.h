@@ -127,18 +127,22 @@ int or_gibbs_triangle(uint64_t seed, uint64_t chain_offset, uint32_t n_chains, u
 /* Normal model with unknown mean and precision, semi-conjugate priors
  * mu ~ N(mu0, 1/prec0), tau ~ Gamma(a0, rate b0).  prior = {a0, b0, mu0, prec0}.
  * state[2c] = mu, state[2c+1] = tau; pos[2c] = N, pos[2c+1] = U;
- * mom[4c..4c+3] += (mu, tau, mu^2, tau^2). */
+ * mom[4c..4c+3] += (mu, tau, mu^2, tau^2).
+ * trace (nullable): per chain c and sweep t, trace[5 (c n_sweeps + t) + i] =
+ * (G, its conditioning as or_gamma's cond, the Gaussian z of mu's draw, tau,
+ * mu) -- the trajectory that FP32 error bounds are propagated along. */
 int or_gibbs_normal_gamma(uint64_t seed, uint64_t chain_offset, uint32_t n_chains,
                           uint32_t n_sweeps, const float *prior, const float *nobs,
                           const float *xbar, const float *sc, double *state, uint64_t *pos,
-                          double *mom, uint32_t buf_len);
+                          double *mom, double *trace, uint32_t buf_len);
 /* LDA-style document-topic draws theta_d ~ Dir(alpha_d) every sweep; component
  * (d, k) is stream (doc_offset + d)*K + k; pos[2(dK+k)] = N, [..+1] = U;
  * theta = last draw, logs (nullable) = its log-Gammas; mom[dK+k] += theta_dk
- * per sweep. */
+ * per sweep.  trace (nullable): per document d, sweep t and component k,
+ * trace[2 ((d n_sweeps + t) K + k) + i] = (log-Gamma, its conditioning). */
 int or_gibbs_lda(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K,
                  uint32_t n_sweeps, const float *alpha, double *theta, double *logs,
-                 double *cond, uint64_t *pos, double *mom, uint32_t buf_len);
+                 double *cond, uint64_t *pos, double *mom, double *trace, uint32_t buf_len);
 
 /* the same on `nthreads` host threads over contiguous chain ranges */
 int or_gibbs_triangle_mt(uint64_t seed, uint64_t chain_offset, uint32_t n_chains,
@@ -147,10 +151,11 @@ int or_gibbs_triangle_mt(uint64_t seed, uint64_t chain_offset, uint32_t n_chains
 int or_gibbs_normal_gamma_mt(uint64_t seed, uint64_t chain_offset, uint32_t n_chains,
                              uint32_t n_sweeps, const float *prior, const float *nobs,
                              const float *xbar, const float *sc, double *state, uint64_t *pos,
-                             double *mom, uint32_t buf_len, int nthreads);
+                             double *mom, double *trace, uint32_t buf_len, int nthreads);
 int or_gibbs_lda_mt(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K,
                     uint32_t n_sweeps, const float *alpha, double *theta, double *logs,
-                    double *cond, uint64_t *pos, double *mom, uint32_t buf_len, int nthreads);
+                    double *cond, uint64_t *pos, double *mom, double *trace, uint32_t buf_len,
+                    int nthreads);
 int or_mixed_mt(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const uint8_t *tag,
                 const float *p0, const float *p1, double *out, uint32_t *words, double *cond,
                 uint32_t buf_len, int nthreads);

@@ -23,6 +23,8 @@ import pytest
 import oracle as O
 from paper_1412_4825_gb300 import inputs
 
+import gibbs_bounds
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -701,7 +703,23 @@ def test_triangle_resume_and_shard():
     assert torch.equal(torch.cat([a, b]), whole) and torch.equal(torch.cat([ma, mb]), mw)
 
 
-def _ng_gpu(nobs, xbar, sc, n_sweeps, offset=0, state=None, mom=None, prior=(2.0, 1.0, 0.0, 0.01), **tune):
+PRIOR_NG = (2.0, 1.0, 0.0, 0.01)
+
+
+def _ng_state(mu, tau, pos):
+    """brng_normal_gamma_state_t[n] from FP32 (mu, tau) and the oracle's
+    positions [n, 2] = (N, U)."""
+    n = len(mu)
+    s = torch.zeros((n, 3), dtype=torch.int64)
+    f = s.view(torch.float32).view(n, 6)
+    f[:, 0] = torch.from_numpy(np.asarray(mu, np.float32))
+    f[:, 1] = torch.from_numpy(np.asarray(tau, np.float32))
+    s[:, 1] = torch.from_numpy(np.asarray(pos[:, 0], np.uint64).view(np.int64))
+    s[:, 2] = torch.from_numpy(np.asarray(pos[:, 1], np.uint64).view(np.int64))
+    return s.to(DEV)
+
+
+def _ng_gpu(nobs, xbar, sc, n_sweeps, offset=0, state=None, mom=None, prior=PRIOR_NG, **tune):
     n = nobs.size
     h = handle(42, 1, **tune)
     t = [T(nobs), T(xbar), T(sc)]
@@ -714,28 +732,33 @@ def _ng_gpu(nobs, xbar, sc, n_sweeps, offset=0, state=None, mom=None, prior=(2.0
     return st, m, cnt
 
 
-def _ng_check(st, m, ref, n_sweeps, what):
+def assert_bound(got, want, bound, what):
+    """|got - want| <= bound element by element (NaN only where both are)."""
+    assert_close(got, want, np.asarray(bound, np.float64) / RTOL, what=what)
+
+
+def _ng_check(st, m, ref, nobs, xbar, sc, what, prior=PRIOR_NG, mu_start=0.0, mom_start=None):
+    """Positions bit-exact; final (mu, tau) and the sweep moments within the
+    FP32 bound propagated along the oracle's trajectory (gibbs_bounds: the
+    per-draw 2e-6 of each sweep carried through the sweep map)."""
     mu, tau, pn, pu = B.normal_gamma_unpack(st)
     assert np.array_equal(pn, ref["pos"][:, 0]) and np.array_equal(pu, ref["pos"][:, 1])
-    rmu, rtau = ref["state"][:, 0], ref["state"][:, 1]
-    # the last sweep's mu = mean + z / sqrt(P): FP32 at the scale |mean| + |z|/sqrt(P),
-    # tau = G / rate; the chain contracts, so earlier sweeps' FP32 errors do not grow
-    sd = 1.0 / np.sqrt(0.01 + 100.0 * rtau)
-    assert_close(mu, rmu, np.abs(rmu) + 4 * sd, rtol=1e-5, what=what + " mu")
-    assert_close(tau, rtau, np.abs(rtau), rtol=1e-5, what=what + " tau")
+    bnd = gibbs_bounds.ng_bounds(nobs, xbar, sc, prior, mu_start, ref["trace"], RTOL)
+    assert_bound(mu, ref["state"][:, 0], bnd["mu"], what + " mu")
+    assert_bound(tau, ref["state"][:, 1], bnd["tau"], what + " tau")
     g = H(m)
-    rm = ref["mom"]
-    assert_close(g[:, 0], rm[:, 0], np.abs(rm[:, 0]) + n_sweeps * 4 * sd.mean(), rtol=1e-5, what=what + " sum mu")
-    assert_close(g[:, 1], rm[:, 1], np.abs(rm[:, 1]), rtol=1e-5, what=what + " sum tau")
-    assert_close(g[:, 2], rm[:, 2], np.abs(rm[:, 2]), rtol=2e-5, what=what + " sum mu^2")
-    assert_close(g[:, 3], rm[:, 3], np.abs(rm[:, 3]), rtol=2e-5, what=what + " sum tau^2")
+    base = 0.0 if mom_start is None else mom_start
+    for j, name in enumerate(["sum mu", "sum tau", "sum mu^2", "sum tau^2"]):
+        assert_bound(g[:, j] - base[:, j] if mom_start is not None else g[:, j],
+                     ref["mom"][:, j] - (base[:, j] if mom_start is not None else 0.0),
+                     bnd["mom"][:, j], what + " " + name)
 
 
 def test_normal_gamma_parity_small():
     nobs, xbar, sc = inputs.normal_gamma_data(1000, seed=5)
     st, m, cnt = _ng_gpu(nobs, xbar, sc, 300)
-    ref = O.gibbs_normal_gamma(42, 300, nobs, xbar, sc, nthreads=NT)
-    _ng_check(st, m, ref, 300, "normal-gamma 1000x300")
+    ref = O.gibbs_normal_gamma(42, 300, nobs, xbar, sc, nthreads=NT, trace=True)
+    _ng_check(st, m, ref, nobs, xbar, sc, "normal-gamma 1000x300")
 
 
 def test_normal_gamma_full_size_sampled():
@@ -745,9 +768,45 @@ def test_normal_gamma_full_size_sampled():
     st, m, cnt = _ng_gpu(nobs, xbar, sc, n_sweeps)
     print("counters", cnt)
     for c0, c1 in [(0, 128), (n_chains - 128, n_chains)]:
-        ref = O.gibbs_normal_gamma(42, n_sweeps, nobs[c0:c1], xbar[c0:c1], sc[c0:c1], chain_offset=c0,
-                                   nthreads=NT)
-        _ng_check(st[c0:c1], m[c0:c1], ref, n_sweeps, "normal-gamma chains %d..%d" % (c0, c1))
+        sl = slice(c0, c1)
+        ref = O.gibbs_normal_gamma(42, n_sweeps, nobs[sl], xbar[sl], sc[sl], chain_offset=c0,
+                                   nthreads=NT, trace=True)
+        _ng_check(st[c0:c1], m[c0:c1], ref, nobs[sl], xbar[sl], sc[sl],
+                  "normal-gamma chains %d..%d" % (c0, c1))
+
+
+@pytest.mark.parametrize("case", ["shape52", "boosted", "mixed_prior"])
+@pytest.mark.parametrize("buf_len", [32, 8, 4])
+def test_normal_gamma_one_sweep_from_shared_state(case, buf_len):
+    """One sweep from the same FP32 state on both sides isolates the per-draw
+    FP32 error from its propagation: the oracle runs k sweeps, its state is
+    rounded to FP32 and handed, with the same stream positions, to the GPU
+    (one sweep) and back to the oracle (one sweep).  tau and mu must then be
+    within 2e-6 of the magnitude each draw's FP32 arithmetic works at
+    (|tau| (1 + kappa) for tau = G / rate, |mean| + |z| / sqrt(P) for mu),
+    mu also carrying tau's bound through d mu / d tau."""
+    n = 4096 + 77
+    nobs, xbar, sc = inputs.normal_gamma_data(n, seed=21)
+    prior = PRIOR_NG
+    if case == "boosted":
+        nobs = nobs.copy()
+        nobs[::3] = 0.0  # shape 0.4: boosted
+        nobs[1::3] = 1.0  # shape 0.9: boosted
+        prior = (0.4, 1.0, 0.0, 0.01)
+    elif case == "mixed_prior":
+        nobs = np.floor(np.random.default_rng(4).uniform(0, 400, n)).astype(np.float32)
+        prior = (3.0, 2.0, -1.0, 1.0)
+    k = 57
+    ref0 = O.gibbs_normal_gamma(42, k, nobs, xbar, sc, prior=prior, nthreads=NT)
+    mu32 = ref0["state"][:, 0].astype(np.float32)
+    tau32 = ref0["state"][:, 1].astype(np.float32)
+    st = _ng_state(mu32, tau32, ref0["pos"])
+    st, m, cnt = _ng_gpu(nobs, xbar, sc, 1, state=st, prior=prior, buf_len=buf_len)
+    start = np.stack([mu32, tau32], axis=1).astype(np.float64)
+    ref1 = O.gibbs_normal_gamma(42, 1, nobs, xbar, sc, prior=prior, state=start.ravel(),
+                                pos=ref0["pos"].ravel(), nthreads=NT, trace=True)
+    _ng_check(st, m, ref1, nobs, xbar, sc, "one sweep %s B=%d" % (case, buf_len), prior=prior,
+              mu_start=mu32.astype(np.float64))
 
 
 def test_normal_gamma_invariance_and_resume():
@@ -776,16 +835,18 @@ def test_normal_gamma_producers_equal_inline(wpb, wp, buf_len):
 
 def test_normal_gamma_producers_oracle_and_resume():
     nobs, xbar, sc = inputs.normal_gamma_data(333, seed=10)
-    ref = O.gibbs_normal_gamma(42, 120, nobs, xbar, sc, nthreads=NT)
+    ref = O.gibbs_normal_gamma(42, 120, nobs, xbar, sc, nthreads=NT, trace=True)
     st, m, _ = _ng_gpu(nobs, xbar, sc, 120, producer_warps=2)
-    _ng_check(st, m, ref, 120, "normal-gamma producers 333x120")
+    _ng_check(st, m, ref, nobs, xbar, sc, "normal-gamma producers 333x120")
     # resume from mid-block positions (the rings then start inside a block)
     c, mc, _ = _ng_gpu(nobs, xbar, sc, 41, producer_warps=1)
     c, mc, cnt = _ng_gpu(nobs, xbar, sc, 79, state=c, mom=mc, producer_warps=3, buf_len=8)
     assert cnt["n_timeout"] == 0
     assert torch.equal(st, c)
-    # the FP32 partial sums are flushed at other iterations when a run is split
-    torch.testing.assert_close(mc, m, rtol=1e-6, atol=0)
+    # the FP32 partial sums are flushed at other iterations when a run is split:
+    # each part's compensated sum is within SUM_ERR of its exact value
+    bnd = gibbs_bounds.ng_bounds(nobs, xbar, sc, PRIOR_NG, 0.0, ref["trace"], RTOL)["mom"]
+    assert_bound(H(mc), H(m), 2 * bnd, "split-run moments")
 
 
 def test_normal_gamma_producers_full_size_sampled():
@@ -796,9 +857,11 @@ def test_normal_gamma_producers_full_size_sampled():
     st, m, cnt = _ng_gpu(nobs, xbar, sc, n_sweeps, producer_warps=2)
     assert cnt["n_timeout"] == 0, cnt
     for c0, c1 in [(0, 128), (n_chains - 128, n_chains)]:
-        ref = O.gibbs_normal_gamma(42, n_sweeps, nobs[c0:c1], xbar[c0:c1], sc[c0:c1], chain_offset=c0,
-                                   nthreads=NT)
-        _ng_check(st[c0:c1], m[c0:c1], ref, n_sweeps, "normal-gamma producers chains %d..%d" % (c0, c1))
+        sl = slice(c0, c1)
+        ref = O.gibbs_normal_gamma(42, n_sweeps, nobs[sl], xbar[sl], sc[sl], chain_offset=c0,
+                                   nthreads=NT, trace=True)
+        _ng_check(st[c0:c1], m[c0:c1], ref, nobs[sl], xbar[sl], sc[sl],
+                  "normal-gamma producers chains %d..%d" % (c0, c1))
 
 
 @pytest.mark.parametrize("buf_len", [32, 8, 4])
@@ -812,22 +875,19 @@ def test_normal_gamma_small_shapes_boosted(buf_len):
     nobs[1::3] = 1.0  # shape 0.9
     prior = (0.4, 1.0, 0.0, 0.01)
     st, m, cnt = _ng_gpu(nobs, xbar, sc, 120, prior=prior, buf_len=buf_len)
-    ref = O.gibbs_normal_gamma(42, 120, nobs, xbar, sc, prior=prior, nthreads=NT)
-    mu, tau, pn, pu = B.normal_gamma_unpack(st)
-    assert np.array_equal(pn, ref["pos"][:, 0]) and np.array_equal(pu, ref["pos"][:, 1])
-    rmu, rtau = ref["state"][:, 0], ref["state"][:, 1]
-    sd = 1.0 / np.sqrt(0.01 + np.maximum(nobs, 0) * rtau)
-    # boosted tau = G u_b^(1/a) / rate: FP32 at the scale |tau| (1 + |ln u_b / a|)
-    assert_close(tau, rtau, np.abs(rtau) * 40.0, rtol=1e-5, what="boosted tau")
-    assert_close(mu, rmu, np.abs(rmu) + 4 * sd, rtol=1e-4, what="boosted mu")
+    ref = O.gibbs_normal_gamma(42, 120, nobs, xbar, sc, prior=prior, nthreads=NT, trace=True)
+    _ng_check(st, m, ref, nobs, xbar, sc, "boosted B=%d" % buf_len, prior=prior)
 
 
-def _lda_gpu(alpha, n_sweeps, offset=0, **tune):
+def _lda_gpu(alpha, n_sweeps, offset=0, pos0=None, **tune):
     n_docs, K = alpha.shape
     h = handle(42, 1, **tune)
     a = T(alpha)
     theta = torch.zeros((n_docs, K), dtype=torch.float32, device=DEV)
-    pos = torch.zeros((n_docs, K, 2), dtype=torch.int64, device=DEV)
+    if pos0 is None:
+        pos = torch.zeros((n_docs, K, 2), dtype=torch.int64, device=DEV)
+    else:
+        pos = T(np.asarray(pos0, np.uint64).view(np.int64).reshape(n_docs, K, 2))
     mom = torch.zeros((n_docs, K), dtype=torch.float64, device=DEV)
     params = B.brng_lda_params_t(K, a.data_ptr())
     state = B.brng_lda_state_t(theta.data_ptr(), pos.data_ptr())
@@ -838,19 +898,33 @@ def _lda_gpu(alpha, n_sweeps, offset=0, **tune):
 
 
 def _lda_check(theta, pos, mom, ref, what):
+    """Positions bit-exact; the last draw within the per-draw bound; the sweep
+    sums within the per-draw bounds of every sweep summed (the sweeps are
+    independent draws from fixed counts, so nothing propagates) plus the
+    compensated sum's own error."""
     assert np.array_equal(H(pos).view(np.uint64), ref["pos"])
     assert_close(H(theta), ref["theta"], _dir_scale(ref["theta"], ref["logs"], ref["cond"]),
                  what=what + " theta")
-    # accumulated theta: every sweep within the per-draw bound; log-Gammas of
-    # these documents stay below ~60 in magnitude
-    assert_close(H(mom), ref["mom"], np.abs(ref["mom"]) * 250.0, what=what + " sum theta")
+    assert_bound(H(mom), ref["mom"], gibbs_bounds.lda_mom_bound(ref["trace"], RTOL), what + " sum theta")
 
 
 def test_lda_parity_small():
     alpha, _, _ = inputs.lda_alpha(96, K=64, seed=7)
     theta, pos, mom = _lda_gpu(alpha, 40)
-    ref = O.gibbs_lda(42, 40, alpha, nthreads=NT)
+    ref = O.gibbs_lda(42, 40, alpha, nthreads=NT, trace=True)
     _lda_check(theta, pos, mom, ref, "lda 96x64x40")
+
+
+@pytest.mark.parametrize("buf_len", [64, 16, 4])
+def test_lda_one_sweep_from_shared_positions(buf_len):
+    """One LDA sweep from the positions the oracle reached after k sweeps
+    (resuming inside Philox blocks): theta and its sum within the per-draw
+    bound."""
+    alpha, _, _ = inputs.lda_alpha(300, K=64, seed=17)
+    ref0 = O.gibbs_lda(42, 13, alpha, nthreads=NT)
+    theta, pos, mom = _lda_gpu(alpha, 1, pos0=ref0["pos"], buf_len=buf_len)
+    ref1 = O.gibbs_lda(42, 1, alpha, pos=ref0["pos"].ravel(), nthreads=NT, trace=True)
+    _lda_check(theta, pos, mom, ref1, "lda one sweep B=%d" % buf_len)
 
 
 def test_lda_full_size_sampled():
@@ -858,7 +932,7 @@ def test_lda_full_size_sampled():
     alpha, _, _ = inputs.lda_alpha(16384, K=64, seed=42)
     theta, pos, mom = _lda_gpu(alpha, 500)
     for d0, d1 in [(0, 4), (16380, 16384)]:
-        ref = O.gibbs_lda(42, 500, alpha[d0:d1], doc_offset=d0, nthreads=NT)
+        ref = O.gibbs_lda(42, 500, alpha[d0:d1], doc_offset=d0, nthreads=NT, trace=True)
         _lda_check(theta[d0:d1], pos[d0:d1], mom[d0:d1], ref, "lda docs %d..%d" % (d0, d1))
 
 
@@ -891,14 +965,15 @@ def test_gibbs_random_configurations(case):
         nobs, xbar, sc = inputs.normal_gamma_data(n, seed=case)
         st, m, cnt = _ng_gpu(nobs, xbar, sc, sweeps, offset=offset, buf_len=pick([4, 8, 16, 32, 64]),
                              warps_per_block=pick([1, 2, 4, 8, 16]))
-        ref = O.gibbs_normal_gamma(42, sweeps, nobs, xbar, sc, chain_offset=offset, nthreads=NT)
-        _ng_check(st, m, ref, sweeps, "normal-gamma random case %d" % case)
+        ref = O.gibbs_normal_gamma(42, sweeps, nobs, xbar, sc, chain_offset=offset, nthreads=NT,
+                                   trace=True)
+        _ng_check(st, m, ref, nobs, xbar, sc, "normal-gamma random case %d" % case)
     else:
         docs, K, sweeps = int(rng.integers(1, 120)), pick([5, 17, 32, 64, 100]), int(rng.integers(1, 30))
         alpha, _, _ = inputs.lda_alpha(docs, K=K, seed=case)
         theta, pos, mom = _lda_gpu(alpha, sweeps, offset=offset, buf_len=pick([4, 8, 16, 32]),
                                    lookahead=pick([1, 2, 4, 8, 16]), warps_per_block=pick([1, 2, 4]))
-        ref = O.gibbs_lda(42, sweeps, alpha, doc_offset=offset, nthreads=NT)
+        ref = O.gibbs_lda(42, sweeps, alpha, doc_offset=offset, nthreads=NT, trace=True)
         _lda_check(theta, pos, mom, ref, "lda random case %d" % case)
 
 
