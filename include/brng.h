@@ -260,7 +260,9 @@ int brng_mixed(brng_t *h, size_t n, const uint8_t *tag, const float *p0, const f
  *     can be read back through this entry point);
  *   - the first call on a device looks up the array's device address (a
  *     one-time set-up per device); make that first call before any stream
- *     capture;
+ *     capture.  The address is kept for the life of the process: after a
+ *     cudaDeviceReset it no longer belongs to the device's context, so a
+ *     process that resets a device must not call this entry point again;
  *   - every call clears the array on `stream` before its kernel, and all calls
  *     share it: calls whose work overlaps on the GPU (other streams, other
  *     host threads) race and give wrong results.  Order them on one stream.

@@ -27,6 +27,7 @@ TAG_UNIFORM, TAG_NORMAL, TAG_EXPONENTIAL, TAG_GAMMA, TAG_LAPLACE, TAG_WEIBULL, T
 POISSON_MAX_LAMBDA = 64.0
 BINOMIAL_MAX_MEAN = 64.0
 MODEL_TRIANGLE, MODEL_NORMAL_GAMMA, MODEL_LDA = 0, 1, 2
+BRNG_STATIC_MAX_STREAMS = 65536
 
 
 class BrngError(RuntimeError):

@@ -64,6 +64,29 @@ __device__ __forceinline__ uint4 philox_block(uint64_t blk, uint32_t dom, uint32
   return philox(philox_ctr(blk, dom, stream), rk);
 }
 
+// Round 0 multiplies counter word 2 (the stream) by M1, so for a fixed
+// (domain, stream) its half of round 0's output, (hi(M1 s) ^ dom ^ k0, lo(M1 s)),
+// is the same for every block: computed once per stream it leaves one
+// multiply and one XOR per block.  philox_block_sh(blk, philox_stream_half(
+// dom, s, rk), rk) == philox_block(blk, dom, s, rk) bit for bit.
+__device__ __forceinline__ uint2 philox_stream_half(uint32_t dom, uint32_t stream, const RoundKeys& rk) {
+  return make_uint2(__umulhi(kPhiloxM1, stream) ^ dom ^ rk.k[0][0], kPhiloxM1 * stream);
+}
+
+__device__ __forceinline__ uint4 philox_block_sh(uint64_t blk, uint2 sh, const RoundKeys& rk) {
+  const uint32_t lo = static_cast<uint32_t>(blk), hi = static_cast<uint32_t>(blk >> 32);
+  uint4 c = make_uint4(sh.x, sh.y, __umulhi(kPhiloxM0, lo) ^ hi ^ rk.k[0][1], kPhiloxM0 * lo);
+#pragma unroll
+  for (int r = 1; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+    const uint32_t lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+    const uint32_t lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ rk.k[r][0], lo1, hi0 ^ c.w ^ rk.k[r][1], lo0);
+  }
+  return c;
+}
+
 // ---- FP32 base conversions (brng_fp32.cuh: no conversion instructions) ----
 // Box-Muller pair from (w0, w1): radius from U'(w0), angle 2 pi U(w1) =
 // pi (w1 >> 8) 2^-23

@@ -19,8 +19,10 @@
 //  fsincospi_k(k) sin and cos of pi k 2^-23 for a 24-bit integer k: the
 //                quadrant and the reduced argument r = k - n 2^22, |r| <= 2^21,
 //                come from integer arithmetic (exact); y = pi r 2^-23; Taylor
-//                series of sin to y^11 and cos to y^12 (|y| <= pi/4, truncation
-//                below 3e-9); quadrant swap and signs.  About 2 ulp.
+//                series of sin to y^9 and cos to y^10 (|y| <= pi/4: the first
+//                dropped terms are below 1.8e-9 and 1.2e-10, i.e. under 0.05
+//                ulp of sin y >= 0.9 y and of cos y >= 0.7); quadrant swap and
+//                signs.  About 2 ulp.
 #pragma once
 
 #include <cstdint>
@@ -65,14 +67,12 @@ __device__ __forceinline__ void fsincospi_k(uint32_t k, float* s_out, float* c_o
   const int r = static_cast<int>(k) - static_cast<int>(n << 22);
   const float y = small_int_to_float(r) * 0x1.921fb6p-22f;  // pi r 2^-23, |y| <= pi/4
   const float y2 = y * y;
-  float ps = -0x1.ae6456p-26f;             // -1/11!
-  ps = fmaf(ps, y2, 0x1.71de3ap-19f);      //  1/9!
+  float ps = 0x1.71de3ap-19f;              //  1/9!
   ps = fmaf(ps, y2, -0x1.a01a02p-13f);     // -1/7!
   ps = fmaf(ps, y2, 0x1.111112p-7f);       //  1/5!
   ps = fmaf(ps, y2, -0x1.555556p-3f);      // -1/3!
   const float sn = fmaf(y * y2, ps, y);
-  float pc = 0x1.1eed8ep-29f;              //  1/12!
-  pc = fmaf(pc, y2, -0x1.27e4fcp-22f);     // -1/10!
+  float pc = -0x1.27e4fcp-22f;             // -1/10!
   pc = fmaf(pc, y2, 0x1.a01a02p-16f);      //  1/8!
   pc = fmaf(pc, y2, -0x1.6c16c2p-10f);     // -1/6!
   pc = fmaf(pc, y2, 0x1.555556p-5f);       //  1/4!

@@ -113,9 +113,8 @@ __host__ __device__ inline uint32_t normal_gamma_warp_bytes(uint32_t B) {
   return 128u + 2u * B * 32u * 4u;
 }
 
-// Compensated (Kahan) FP32 running sum: the sweep moments stay accurate to a
-// few FP32 ulp of the total over any number of sweeps with no FP64 arithmetic
-// in the loop, and the result does not depend on how the sweeps are grouped.
+// Compensated (Kahan) FP32 running sum: accurate to a few FP32 ulp of the
+// total over any number of terms, with no FP64 arithmetic in the loop.
 struct Kahan {
   float s = 0.0f, c = 0.0f;
   __device__ __forceinline__ void add(float v) {
@@ -129,21 +128,51 @@ struct Kahan {
   }
 };
 
+// Sweep moments of one chain (sum mu, tau, mu^2, tau^2).  The sweeps of a run
+// are taken in groups of kMomGroup consecutive sweeps, counted from the run's
+// first: within a group plain FP32 sums (one add or FMA per moment and
+// sweep), and each finished group's sums go into compensated FP32 sums, which
+// go into the FP64 moments at the end of the run.  The error stays within
+// (kMomGroup + 2) FP32 ulp of the sum of magnitudes over any number of
+// sweeps, and since the grouping depends only on the sweep count, every ring
+// length, round width and producer layout gives the same bits.
+constexpr uint32_t kMomGroup = 8;
+struct SweepMoments {
+  float p0 = 0.0f, p1 = 0.0f, p2 = 0.0f, p3 = 0.0f;  // the open group's sums
+  Kahan k[4];
+  __device__ __forceinline__ void add(float mu, float tau) {
+    p0 += mu;
+    p1 += tau;
+    p2 = fmaf(mu, mu, p2);
+    p3 = fmaf(tau, tau, p3);
+  }
+  // close the open group
+  __device__ __forceinline__ void fold() {
+    k[0].add(p0);
+    k[1].add(p1);
+    k[2].add(p2);
+    k[3].add(p3);
+    p0 = p1 = p2 = p3 = 0.0f;
+  }
+};
+
 // Chain state of one lane, read from and written back to global memory.
 struct NgChain {
   float n, xb, S, mu, tau;
   uint64_t pn, pu;
   double d0, d1, d2, d3;  // FP64 moments (sum mu, tau, mu^2, tau^2)
-  Kahan k[4];             // this run's compensated partial sums, not yet in d
+  SweepMoments m;         // this run's sums, not yet in d
 };
 
-// Adds the run's compensated partial sums into the FP64 moments.
+// Adds the run's sums (the last, possibly partial, group included) into the
+// FP64 moments.
 __device__ __forceinline__ void ng_fold_moments(NgChain& s) {
-  s.d0 += s.k[0].value();
-  s.d1 += s.k[1].value();
-  s.d2 += s.k[2].value();
-  s.d3 += s.k[3].value();
-  s.k[0] = s.k[1] = s.k[2] = s.k[3] = Kahan{};
+  s.m.fold();
+  s.d0 += s.m.k[0].value();
+  s.d1 += s.m.k[1].value();
+  s.d2 += s.m.k[2].value();
+  s.d3 += s.m.k[3].value();
+  s.m = SweepMoments{};
 }
 
 __device__ __forceinline__ NgChain ng_load(const NormalGammaArgs& a, uint64_t c, bool active) {
@@ -224,10 +253,7 @@ __device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t n_s
   const float nxb = s.n * s.xb;
   const float n = s.n, xb = s.xb, S = s.S;
   float mu = s.mu, tau = s.tau;
-  Kahan& k0 = s.k[0];
-  Kahan& k1 = s.k[1];
-  Kahan& k2 = s.k[2];
-  Kahan& k3 = s.k[3];
+  SweepMoments& mom = s.m;
   bool exact = g.boost;  // per lane: the next attempt is taken the exact way
   int att = 0;
   uint32_t sweep = 0;
@@ -247,18 +273,17 @@ __device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t n_s
         zm[i] = RN.peek(2 * i + 1);
         const float uo = RU.peek(i) + 0x1p-24f;  // U' = U + 2^-24, exact
         const float x = g.c * z;
-        float p = -0x1.111112p-4f;  // the series of mt_attempt
-        p = fmaf(p, x, 0x1.24924ap-4f);
-        p = fmaf(p, x, -0x1.3b13b2p-4f);
-        p = fmaf(p, x, 0x1.555556p-4f);
-        p = fmaf(p, x, -0x1.745d18p-4f);
-        p = fmaf(p, x, 0x1.99999ap-4f);
-        p = fmaf(p, x, -0x1.c71c72p-4f);
-        p = fmaf(p, x, 0.125f);
-        p = fmaf(p, x, -0x1.24924ap-3f);
-        p = fmaf(p, x, 0x1.555556p-3f);
-        p = fmaf(p, x, -0x1.99999ap-3f);
-        p = fmaf(p, x, 0.25f);
+        // q_hi >= q = 3 d x^4 p(x), p(x) = sum_k (-x)^k / (k + 4) (the margin's
+        // series, mt_attempt): for x >= 0 the series alternates with
+        // decreasing terms, so it is below its partial sum 1/4 - x/5 + x^2/6;
+        // for x < 0 every term is positive and the terms from x^3 on sum to at
+        // most |x|^3 / (7 (1 - |x|)) <= 0.1905 |x|^3 for |x| <= 1/4.  So
+        // p_hi(x) = 1/4 - x/5 + x^2/6 + 0.1905 |x|^3 bounds p on the whole
+        // series range, and U' + q_hi < 1 is still a sufficient condition of
+        // the accept test: a fast accept stays an exact accept, and an attempt
+        // the bound does not settle goes to the exact path.  The bound exceeds
+        // q by ~3 d |x|^7 / 7, far below U's resolution at the |x| that occur.
+        const float p = fmaf(x, fmaf(x, fmaf(fabsf(x), 0.1905f, 0x1.555556p-3f), -0x1.99999ap-3f), 0.25f);
         const float x2 = x * x;
         const float q = (3.0f * g.d) * (x2 * x2) * p;
         const float t = 1.0f + x;
@@ -270,21 +295,22 @@ __device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t n_s
       uint32_t k = static_cast<uint32_t>(__ffs(~fast)) - 1u;  // leading accepted attempts
       k = min(k, static_cast<uint32_t>(W));
       k = min(k, n_sweeps - min(sweep, n_sweeps));
+      const uint32_t kspec = k;
+      k = min(k, kMomGroup - sweep % kMomGroup);  // a round ends at a moment-group boundary
 #pragma unroll
       for (int i = 0; i < W; ++i) {
         if (static_cast<uint32_t>(i) < k) {
           ng_update(a, n, xb, S, nxb, prior_num, G[i], zm[i], mu, tau);
-          k0.add(mu);
-          k1.add(tau);
-          k2.add(mu * mu);
-          k3.add(tau * tau);
+          mom.add(mu, tau);
         }
       }
       if (spec) {
         RN.advance(2 * k);
         RU.advance(k);
         sweep += k;
-        if (k < W && sweep < n_sweeps) exact = true;
+        if (k > 0 && sweep % kMomGroup == 0) mom.fold();
+        // the attempt after the k sweeps was not settled by the fast test
+        if (k == kspec && k < W && sweep < n_sweeps) exact = true;
       }
     }
     const bool ex = run && exact && sweep < n_sweeps;
@@ -306,11 +332,9 @@ __device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t n_s
         const float z = RN.peek(0);
         RN.advance(1);
         ng_update(a, n, xb, S, nxb, prior_num, G, z, mu, tau);
-        k0.add(mu);
-        k1.add(tau);
-        k2.add(mu * mu);
-        k3.add(tau * tau);
+        mom.add(mu, tau);
         ++sweep;
+        if (sweep % kMomGroup == 0) mom.fold();
         att = 0;
         exact = g.boost;
       }
@@ -334,10 +358,7 @@ __device__ __forceinline__ void ng_sweeps_plain(const NormalGammaArgs& a, uint32
   const float nxb = s.n * s.xb;
   const float n = s.n, xb = s.xb, S = s.S;
   float mu = s.mu, tau = s.tau;
-  Kahan& k0 = s.k[0];
-  Kahan& k1 = s.k[1];
-  Kahan& k2 = s.k[2];
-  Kahan& k3 = s.k[3];
+  SweepMoments& mom = s.m;
   uint32_t sweep = 0;
   int att = 0;
   bool rejected = false;
@@ -366,11 +387,9 @@ __device__ __forceinline__ void ng_sweeps_plain(const NormalGammaArgs& a, uint32
     const float z = RN.get(finish, stream, a.rk);
     if (finish) {
       ng_update(a, n, xb, S, nxb, prior_num, dv, z, mu, tau);
-      k0.add(mu);
-      k1.add(tau);
-      k2.add(mu * mu);
-      k3.add(tau * tau);
+      mom.add(mu, tau);
       ++sweep;
+      if (sweep % kMomGroup == 0) mom.fold();
       att = 0;
     }
   }

@@ -218,9 +218,8 @@ struct CRing {
     rp += n;
   }
 
-  __device__ __forceinline__ void gen_own(uint64_t blk, uint32_t slot, uint32_t stream,
-                                          const RoundKeys& rk) {
-    const uint4 w = philox_block(blk, Gen::kDom, stream, rk);
+  __device__ __forceinline__ void gen_own(uint64_t blk, uint32_t slot, uint2 sh, const RoundKeys& rk) {
+    const uint4 w = philox_block_sh(blk, sh, rk);
     T v[kEPB];
     Gen::gen(w, v);
 #pragma unroll
@@ -247,8 +246,9 @@ struct CRing {
     // Box-Muller) is long and the instruction cache small; measured on GB300,
     // two blocks in flight (more ILP, three copies of the code) were 5-18 %
     // slower in every kernel
+    const uint2 sh = philox_stream_half(Gen::kDom, stream, rk);
 #pragma unroll 1
-    for (uint32_t j = 0; j < nb; ++j) gen_own(first + j, (filled + j * kEPB) & mask, stream, rk);
+    for (uint32_t j = 0; j < nb; ++j) gen_own(first + j, (filled + j * kEPB) & mask, sh, rk);
     filled += nb * kEPB;
   }
 

@@ -35,7 +35,10 @@ std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_scratch on the current device, looked up once per
-// device (host code cannot use the symbol itself as a device pointer).
+// device (host code cannot use the symbol itself as a device pointer).  The
+// cached address belongs to the device's context at the time of the lookup:
+// after cudaDeviceReset it is stale, so this entry point does not support a
+// device reset during the life of the process.
 int scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return BRNG_ECUDA;
@@ -71,10 +74,13 @@ extern "C" int brng_gamma_static(uint64_t seed, uint32_t n_streams, size_t n, co
   if (e != cudaSuccess) return BRNG_ECUDA;
 
   int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const uint32_t B = brng::kDefaultBufLen;
-  const size_t per_warp = 128u + 2u * B * 128u * (words ? 2u : 1u);  // N and U rings
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return BRNG_ECUDA;
+  // the same ring-length rule as brng_gamma's launch (a bulk ring holds at
+  // least kBulkMinRing elements); N and U rings, words beside the values
+  const uint32_t B = brng::ring_len_min8(brng::kDefaultBufLen);
+  const size_t per_warp = 128u + 2u * static_cast<size_t>(B) * 128u * (words ? 2u : 1u);
   uint32_t warps = brng::kDefaultWarpsPerBlock;
   while (warps > 1 && per_warp * warps > static_cast<size_t>(optin)) --warps;
 

@@ -27,17 +27,20 @@ sides start from the same FP32 value).  When the chain contracts
 settles at the per-draw error / (1 - contraction); nothing grows with the
 number of sweeps.
 
-The sweep moments are FP32 compensated (Kahan) sums on the GPU: their error is
-the sum of the per-sweep state errors plus the summation's own error, at most
-(2u + O(N u^2)) sum |x_i| for the unit roundoff u = 2^-24 (Higham, Accuracy
-and Stability of Numerical Algorithms, 2nd ed., Sec. 4.3); 4u covers it with
-the final FP64 fold.  A square adds 2|x| E + E^2 plus the product's rounding
-u x^2.
+The sweep moments are FP32 sums on the GPU: plain sums over groups of at most
+8 consecutive sweeps, whose results go into compensated (Kahan) sums.  Their
+error is the sum of the per-sweep state errors plus the summation's own error:
+a plain sum of m terms errs by at most (m - 1) u sum |x_i| and a compensated
+one by (2u + O(N u^2)) sum |x_i| for the unit roundoff u = 2^-24 (Higham,
+Accuracy and Stability of Numerical Algorithms, 2nd ed., Secs. 4.2-4.3), so
+(7 + 2 + 1) u covers both levels and the final FP64 fold.  (The LDA sums are
+compensated per sweep, well inside the same bound.)  A square adds 2|x| E + E^2
+plus the product's rounding u x^2.
 """
 import numpy as np
 
 U32 = 2.0 ** -24  # FP32 unit roundoff
-SUM_ERR = 4.0 * U32  # compensated summation: (2u + O(N u^2)) sum |x|, with margin
+SUM_ERR = 10.0 * U32  # groups of 8 plain (7u), compensated across groups (2u), FP64 fold
 
 
 def ng_sweep_terms(nobs, xbar, sc, prior, mu_prev, G, z):

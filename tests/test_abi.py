@@ -62,3 +62,11 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     mod = importlib.util.module_from_spec(spec)
     with pytest.raises(ImportError):
         spec.loader.exec_module(mod)
+
+
+def test_binding_constants_match_header():
+    """The binding's copies of the header's limits agree with it."""
+    from paper_1412_4825_gb300 import brng as B
+    text = open(HEADER).read()
+    defs = dict(re.findall(r"^#define\s+(BRNG_\w+)\s+([0-9.]+)[uf]?\s*$", text, flags=re.M))
+    assert int(defs["BRNG_STATIC_MAX_STREAMS"]) == B.BRNG_STATIC_MAX_STREAMS
