@@ -521,7 +521,7 @@ int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_
         if (Wc == 0) return BRNG_EINVAL;
         return cuda_status(brng::launch_normal_gamma_pc(j.ng, Wc, Wp, st));
       }
-      const brng::Geometry g = geometry(h, 128u + 2u * static_cast<size_t>(h->tune.buf_len) * 128u);
+      const brng::Geometry g = geometry(h, brng::normal_gamma_bytes_per_warp(h->tune.buf_len));
       if (g.warps_per_block == 0) return BRNG_EINVAL;
       return cuda_status(brng::launch_normal_gamma(j.ng, g, st));
     }

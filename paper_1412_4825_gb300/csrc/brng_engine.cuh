@@ -42,13 +42,21 @@ inline RoundKeys make_round_keys(uint64_t seed) {
   return rk;
 }
 
+// One 32x32 -> 64-bit product, both halves: written as a widening multiply
+// so that it is a single wide multiply-add instruction rather than separate
+// high-half and low-half multiplies.
+__device__ __forceinline__ void mul_hilo(uint32_t m, uint32_t x, uint32_t& hi, uint32_t& lo) {
+  const uint64_t p = static_cast<uint64_t>(m) * x;
+  hi = static_cast<uint32_t>(p >> 32);
+  lo = static_cast<uint32_t>(p);
+}
+
 __device__ __forceinline__ uint4 philox(uint4 c, const RoundKeys& rk) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
-    const uint32_t lo0 = kPhiloxM0 * c.x;
-    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
-    const uint32_t lo1 = kPhiloxM1 * c.z;
+    uint32_t hi0, lo0, hi1, lo1;
+    mul_hilo(kPhiloxM0, c.x, hi0, lo0);
+    mul_hilo(kPhiloxM1, c.z, hi1, lo1);
     c = make_uint4(hi1 ^ c.y ^ rk.k[r][0], lo1, hi0 ^ c.w ^ rk.k[r][1], lo0);
   }
   return c;
@@ -70,18 +78,21 @@ __device__ __forceinline__ uint4 philox_block(uint64_t blk, uint32_t dom, uint32
 // multiply and one XOR per block.  philox_block_sh(blk, philox_stream_half(
 // dom, s, rk), rk) == philox_block(blk, dom, s, rk) bit for bit.
 __device__ __forceinline__ uint2 philox_stream_half(uint32_t dom, uint32_t stream, const RoundKeys& rk) {
-  return make_uint2(__umulhi(kPhiloxM1, stream) ^ dom ^ rk.k[0][0], kPhiloxM1 * stream);
+  uint32_t hi1, lo1;
+  mul_hilo(kPhiloxM1, stream, hi1, lo1);
+  return make_uint2(hi1 ^ dom ^ rk.k[0][0], lo1);
 }
 
 __device__ __forceinline__ uint4 philox_block_sh(uint64_t blk, uint2 sh, const RoundKeys& rk) {
   const uint32_t lo = static_cast<uint32_t>(blk), hi = static_cast<uint32_t>(blk >> 32);
-  uint4 c = make_uint4(sh.x, sh.y, __umulhi(kPhiloxM0, lo) ^ hi ^ rk.k[0][1], kPhiloxM0 * lo);
+  uint32_t h0, l0;
+  mul_hilo(kPhiloxM0, lo, h0, l0);
+  uint4 c = make_uint4(sh.x, sh.y, h0 ^ hi ^ rk.k[0][1], l0);
 #pragma unroll
   for (int r = 1; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
-    const uint32_t lo0 = kPhiloxM0 * c.x;
-    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
-    const uint32_t lo1 = kPhiloxM1 * c.z;
+    uint32_t hi0, lo0, hi1, lo1;
+    mul_hilo(kPhiloxM0, c.x, hi0, lo0);
+    mul_hilo(kPhiloxM1, c.z, hi1, lo1);
     c = make_uint4(hi1 ^ c.y ^ rk.k[r][0], lo1, hi0 ^ c.w ^ rk.k[r][1], lo0);
   }
   return c;
@@ -92,7 +103,9 @@ __device__ __forceinline__ uint4 philox_block_sh(uint64_t blk, uint2 sh, const R
 // pi (w1 >> 8) 2^-23
 __device__ __forceinline__ float2 box_muller(uint32_t w0, uint32_t w1) {
   const float q = -2.0f * flog(u01_open(w0));  // >= 0; 0 only for U' = 1
-  const float r = q > 0.0f ? q * rsqrtf(q) : 0.0f;
+  // sqrt(q) = q / sqrt(q); for U' < 1, q >= -2 ln(1 - 2^-24) > FLT_MIN, and
+  // q = 0 gives 0 * rsqrt(FLT_MIN) = 0
+  const float r = q * rsqrtf(fmaxf(q, 0x1p-126f));
   float s, c;
   fsincospi_k(w1 >> 8, &s, &c);
   return make_float2(r * c, r * s);

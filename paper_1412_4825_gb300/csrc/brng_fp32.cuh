@@ -1,15 +1,18 @@
-// brng_fp32.cuh -- FP32 base conversions and elementary functions written
-// without integer<->float conversion instructions.
+// brng_fp32.cuh -- FP32 base conversions and elementary functions for the
+// rings' generators, written for instruction count (the Gibbs kernels are
+// bound by instruction issue).
 //
-// Why: on GB300 the conversion instructions (I2F/F2I/F2F) share the small FP64
-// pipe (2 operations per clock per SM), and the base conversions of the
-// method run one or more of them per deviate (U from a word; inside a library
-// logf, log1pf or sincospif).  A profile of the Gibbs kernel showed that pipe
-// two-thirds busy.  Everything here uses integer/logical operations, FP32
-// FMA-pipe arithmetic and at most one MUFU reciprocal.
+// Integer-to-float conversions are used only where they replace several
+// bit-manipulation instructions (U, U'); measured on GB300 they issue on
+// neither the FP64 nor the MUFU pipe.  The log and sin/cos are series
+// evaluated with FP32 FMAs after exact integer argument reduction, with one
+// MUFU reciprocal in the log.
 //
-//  u01(w)        U = (w >> 8) 2^-24, exact: the top 23 bits become the mantissa
-//                of 1 + f (minus 1, exact), the 24th bit adds 2^-24 (exact).
+//  u01(w)        U = (w >> 8) 2^-24, exact: the 24-bit integer converts to FP32
+//                exactly, and the power-of-two scale is exact.
+//  u01_open(w)   U' = ((w >> 8) + 1) 2^-24 in (0, 1], exact: the integer
+//                M = (w >> 8) + 1 <= 2^24 converts exactly, and 24 is taken off
+//                its exponent field (M >= 1, so the result stays normal).
 //  flog(x)       x = m 2^e with m in [sqrt(1/2), sqrt(2)) by subtracting the bit
 //                pattern of sqrt(1/2); s = (m-1)/(m+1);
 //                ln m = 2s + 2s s^2 (1/3 + s^2/5 + s^4/7 + s^6/9)  (atanh series;
@@ -18,11 +21,14 @@
 //                through the 1.5*2^23 magic-number addition.  About 3 ulp.
 //  fsincospi_k(k) sin and cos of pi k 2^-23 for a 24-bit integer k: the
 //                quadrant and the reduced argument r = k - n 2^22, |r| <= 2^21,
-//                come from integer arithmetic (exact); y = pi r 2^-23; Taylor
-//                series of sin to y^9 and cos to y^10 (|y| <= pi/4: the first
-//                dropped terms are below 1.8e-9 and 1.2e-10, i.e. under 0.05
-//                ulp of sin y >= 0.9 y and of cos y >= 0.7); quadrant swap and
-//                signs.  About 2 ulp.
+//                come from integer arithmetic (exact); y = pi r 2^-23;
+//                sin y = y + y^3 P(y^2), cos y = 1 - y^2/2 + y^4 Q(y^2) with P
+//                of degree 2 and Q of degree 2, minimax for |y| <= pi/4 (fitted
+//                for this library by linear programming over 3,000
+//                Chebyshev-spaced points, weighted for relative error, then
+//                rounded to FP32: polynomial error below 6.1e-9 and 2.4e-9
+//                relative, about 0.1 and 0.04 ulp); quadrant swap and signs.
+//                About 2 ulp.
 #pragma once
 
 #include <cstdint>
@@ -35,13 +41,11 @@ __device__ __forceinline__ float small_int_to_float(int i) {
 }
 
 // U = (w >> 8) 2^-24 in [0, 1), exact
-__device__ __forceinline__ float u01(uint32_t w) {
-  const float hi = __uint_as_float(0x3F800000u | (w >> 9)) - 1.0f;    // (w >> 9) 2^-23
-  const float lo = __uint_as_float((w & 0x100u) ? 0x33800000u : 0u);  // bit 8 of w: 2^-24
-  return hi + lo;
-}
+__device__ __forceinline__ float u01(uint32_t w) { return __uint2float_rn(w >> 8) * 0x1p-24f; }
 // U' = U + 2^-24 in (0, 1], exact
-__device__ __forceinline__ float u01_open(uint32_t w) { return u01(w) + 0x1p-24f; }
+__device__ __forceinline__ float u01_open(uint32_t w) {
+  return __int_as_float(__float_as_int(__uint2float_rn((w >> 8) + 1u)) - (24 << 23));
+}
 
 // natural log for finite normal x > 0
 __device__ __forceinline__ float flog(float x) {
@@ -67,16 +71,14 @@ __device__ __forceinline__ void fsincospi_k(uint32_t k, float* s_out, float* c_o
   const int r = static_cast<int>(k) - static_cast<int>(n << 22);
   const float y = small_int_to_float(r) * 0x1.921fb6p-22f;  // pi r 2^-23, |y| <= pi/4
   const float y2 = y * y;
-  float ps = 0x1.71de3ap-19f;              //  1/9!
-  ps = fmaf(ps, y2, -0x1.a01a02p-13f);     // -1/7!
-  ps = fmaf(ps, y2, 0x1.111112p-7f);       //  1/5!
-  ps = fmaf(ps, y2, -0x1.555556p-3f);      // -1/3!
+  float ps = -0x1.994eb4p-13f;             // P: minimax, near -1/7!, 1/5!, -1/3!
+  ps = fmaf(ps, y2, 0x1.11076p-7f);
+  ps = fmaf(ps, y2, -0x1.555546p-3f);
   const float sn = fmaf(y * y2, ps, y);
-  float pc = -0x1.27e4fcp-22f;             // -1/10!
-  pc = fmaf(pc, y2, 0x1.a01a02p-16f);      //  1/8!
-  pc = fmaf(pc, y2, -0x1.6c16c2p-10f);     // -1/6!
-  pc = fmaf(pc, y2, 0x1.555556p-5f);       //  1/4!
-  pc = fmaf(pc, y2, -0.5f);                // -1/2!
+  float pc = 0x1.99343p-16f;               // Q: minimax, near 1/8!, -1/6!, 1/4!
+  pc = fmaf(pc, y2, -0x1.6c087ep-10f);
+  pc = fmaf(pc, y2, 0x1.55553ep-5f);
+  pc = fmaf(pc, y2, -0.5f);
   const float cs = fmaf(y2, pc, 1.0f);
   const uint32_t q = n & 3u;
   const float a = (q & 1u) ? cs : sn;  // sin(pi a) up to sign

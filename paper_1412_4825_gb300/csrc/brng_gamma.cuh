@@ -78,10 +78,9 @@ __device__ __forceinline__ uint4 philox_keyed(uint4 c, uint32_t k0, uint32_t k1)
       k0 += kPhiloxW0;
       k1 += kPhiloxW1;
     }
-    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
-    const uint32_t lo0 = kPhiloxM0 * c.x;
-    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
-    const uint32_t lo1 = kPhiloxM1 * c.z;
+    uint32_t hi0, lo0, hi1, lo1;
+    mul_hilo(kPhiloxM0, c.x, hi0, lo0);
+    mul_hilo(kPhiloxM1, c.z, hi1, lo1);
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
   }
   return c;

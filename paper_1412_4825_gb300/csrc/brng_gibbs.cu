@@ -52,6 +52,8 @@ __global__ void __maxnreg__(128) normal_gamma_kernel(const NormalGammaArgs a) {
   normal_gamma_unit(a, unit, smem + warp * normal_gamma_warp_bytes(a.B));
 }
 
+size_t normal_gamma_bytes_per_warp(uint32_t B) { return normal_gamma_warp_bytes(B); }
+
 cudaError_t launch_normal_gamma(const NormalGammaArgs& a, const Geometry& g, cudaStream_t st) {
   const uint64_t units = (static_cast<uint64_t>(a.n_chains) + 31) / 32;
   if (units == 0) return cudaSuccess;

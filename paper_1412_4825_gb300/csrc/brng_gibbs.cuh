@@ -109,8 +109,13 @@ __device__ __forceinline__ void triangle_unit(const TriangleArgs& a, uint64_t un
 // P = prec0 + n tau.  The sweeps run in speculative rounds (ng_sweeps below);
 // moments are compensated FP32 sums added into FP64 at the end.
 // ---------------------------------------------------------------------------
+// The warp's N and U rings: circular, with mirrored heads as deep as a round's
+// lookahead (2W N and W U elements, W <= 8), so every read is one load.
+using NgRingN = CRing<GenN, false, 16>;
+using NgRingU = CRing<GenU, false, 8>;
+
 __host__ __device__ inline uint32_t normal_gamma_warp_bytes(uint32_t B) {
-  return 128u + 2u * B * 32u * 4u;
+  return 128u + (NgRingN::ring_slots(B) + NgRingU::ring_slots(B)) * 32u * 4u;
 }
 
 // Compensated (Kahan) FP32 running sum: accurate to a few FP32 ulp of the
@@ -423,14 +428,14 @@ __device__ __forceinline__ void normal_gamma_unit(const NormalGammaArgs& a, uint
                                                   unsigned char* base) {
   const unsigned lane = lane_id();
   float* ringN = reinterpret_cast<float*>(base + 128);
-  float* ringU = ringN + a.B * 32u;
+  float* ringU = ringN + NgRingN::ring_slots(a.B) * 32u;
   if (unit * 32 >= a.n_chains) return;  // whole warp
   const uint64_t c = unit * 32 + lane;
   const bool active = c < a.n_chains;
   const uint32_t stream = static_cast<uint32_t>(a.chain_offset + c);
   NgChain s = ng_load(a, c, active);
-  CRing<GenN> RN;
-  CRing<GenU> RU;
+  NgRingN RN;
+  NgRingU RU;
   RN.init(ringN, nullptr, a.B, s.pn);
   RU.init(ringU, nullptr, a.B, s.pu);
   ng_sweeps_any(a, a.n_sweeps, stream, active, s, RN, RU);

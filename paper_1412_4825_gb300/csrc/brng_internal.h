@@ -130,6 +130,7 @@ cudaError_t launch_normal_gamma(const NormalGammaArgs& a, const Geometry& g, cud
 // consumer wait runs out after its bound.
 cudaError_t launch_normal_gamma_pc(const NormalGammaArgs& a, uint32_t Wc, uint32_t Wp, cudaStream_t st,
                                    bool stall = false);
+size_t normal_gamma_bytes_per_warp(uint32_t B);     // shared memory per warp (inline rings)
 size_t normal_gamma_pc_bytes_per_warp(uint32_t B);  // shared memory per consumer warp
 
 // ---- batched persistent kernel (brng_batch.cu) ----

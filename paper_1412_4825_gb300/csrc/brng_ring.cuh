@@ -188,19 +188,29 @@ struct Ring {
 // each refill does nearly a full ring of work per lane instead of a few
 // blocks for the few lanes that ran dry.  kWords: also keep each element's
 // raw Philox word.
-template <class Gen, bool kWords = false>
+//
+// kHead > 0: the first min(kHead, B) slots are mirrored after the ring (slot
+// s < kHead is also stored at s + B), so the next kHead elements lie in
+// consecutive slots from the read point on: a lookahead read is one
+// shared-memory load at a constant offset from the read point, with no wrap
+// arithmetic.  The ring then occupies B + min(kHead, B) slots (ring_slots).
+template <class Gen, bool kWords = false, uint32_t kHead = 0>
 struct CRing {
   using T = typename Gen::T;
   static constexpr uint32_t kEPB = Gen::kEPB;
   static_assert(kEPB == 4, "four elements per block");
-  T* val;          // shared: [B][32]
-  uint32_t* wrd;   // shared: [B][32] when kWords
+  static_assert(kHead % kEPB == 0, "whole blocks are mirrored");
+  T* val;          // shared: [ring_slots][32]
+  uint32_t* wrd;   // shared: [ring_slots][32] when kWords
   uint64_t b0;     // Philox block of relative element 0
   uint32_t rp;     // next relative element to consume
   uint32_t filled; // relative elements generated (multiple of 4)
   uint32_t mask;   // B - 1
   bool live = false;  // get(): also top up this lane when another runs dry
 
+  __host__ __device__ static constexpr uint32_t ring_slots(uint32_t len) {
+    return len + (kHead < len ? kHead : len);
+  }
   __device__ __forceinline__ void init(T* v, uint32_t* w, uint32_t len, uint64_t pos) {
     val = v; wrd = w; mask = len - 1;
     b0 = pos / kEPB;
@@ -209,10 +219,16 @@ struct CRing {
   }
   __device__ __forceinline__ uint64_t pos() const { return b0 * kEPB + rp; }
   __device__ __forceinline__ int32_t avail() const { return static_cast<int32_t>(filled - rp); }
-  __device__ __forceinline__ T peek(uint32_t i) const { return val[((rp + i) & mask) * 32u + lane_id()]; }
-  __device__ __forceinline__ uint32_t peek_word(uint32_t i) const {
-    return wrd[((rp + i) & mask) * 32u + lane_id()];
+  __device__ __forceinline__ uint32_t slot_of(uint32_t i) const {
+    if constexpr (kHead > 0) {
+      BRNG_CHECK(i < kHead || i <= mask);  // within the mirrored head
+      return (rp & mask) + i;
+    } else {
+      return (rp + i) & mask;
+    }
   }
+  __device__ __forceinline__ T peek(uint32_t i) const { return val[slot_of(i) * 32u + lane_id()]; }
+  __device__ __forceinline__ uint32_t peek_word(uint32_t i) const { return wrd[slot_of(i) * 32u + lane_id()]; }
   __device__ __forceinline__ void advance(uint32_t n) {
     BRNG_CHECK(avail() >= static_cast<int32_t>(n));  // every consumed element was generated
     rp += n;
@@ -226,6 +242,16 @@ struct CRing {
     for (uint32_t i = 0; i < kEPB; ++i) {
       val[(slot + i) * 32u + lane_id()] = v[i];
       if (kWords) wrd[(slot + i) * 32u + lane_id()] = word_of(w, i);
+    }
+    if constexpr (kHead > 0) {
+      if (slot < kHead) {  // the mirror copy (slot is a multiple of 4, as kHead is)
+        const uint32_t m = slot + mask + 1u;
+#pragma unroll
+        for (uint32_t i = 0; i < kEPB; ++i) {
+          val[(m + i) * 32u + lane_id()] = v[i];
+          if (kWords) wrd[(m + i) * 32u + lane_id()] = word_of(w, i);
+        }
+      }
     }
   }
 
