@@ -238,10 +238,12 @@ __device__ __forceinline__ void ng_update(const NormalGammaArgs& a, float n, flo
 // and U element i, and its sweep's mu | tau normal is N element 2i + 1.  The
 // first k attempts that the log-free test accepts are exactly the sweeps the
 // one-at-a-time loop would run (same elements, same FP32 operations); the
-// cheap state recursion then runs over them.  The attempt after them (a
-// rejection, or one the fast test does not settle: about 0.05 % at shape 52)
-// puts the lane in exact mode: one attempt the exact way per round, in the
-// same round and the following ones, until one accepts and its sweep ends.
+// cheap state recursion then runs over them.  The attempt after them is
+// usually a rejection, which a log-free reject test settles: its z and U'
+// are consumed and the next round speculates from there.  One that neither
+// test settles (a few per million at shape 52) puts the lane in exact mode:
+// one attempt the exact way per round, in the same round and the following
+// ones, until one accepts and its sweep ends.
 // Shapes below 1 (boosted) stay in exact mode.  Each ring is refilled at one
 // point of the round only (its refill code is large, and the instruction
 // cache small): the round's 2W N and W U elements cover both parts, since
@@ -313,9 +315,37 @@ __device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t n_s
         RN.advance(2 * k);
         RU.advance(k);
         sweep += k;
-        if (k > 0 && sweep % kMomGroup == 0) mom.fold();
-        // the attempt after the k sweeps was not settled by the fast test
-        if (k == kspec && k < W && sweep < n_sweeps) exact = true;
+        if (k > 0) {
+          att = 0;
+          if (sweep % kMomGroup == 0) mom.fold();
+        }
+        if (k == kspec && k < W && sweep < n_sweeps) {
+          // The attempt after the k sweeps was not settled by the fast accept;
+          // it now sits at the read points (N element 0, U element 0).  Fast
+          // reject: q_lo = 3 d x^4 (1/4 - x/5) <= q for |x| < 1 (the margin
+          // series alternates with decreasing terms for x >= 0 and has only
+          // positive terms for x < 0), and U' (1 + q) >= 1 gives
+          // ln U' >= -ln(1 + q) >= -q, a rejection.  In FP32 q_lo is shrunk by
+          // 1e-5 and the product compared with 1 + 2^-22, covering q_lo's and
+          // z's rounding as the fast accept's margins do; so a fast reject is
+          // an exact (and FP64) reject.  It consumes the attempt's z and U'
+          // and the sweep goes on speculatively from the next elements; an
+          // attempt settled by neither test goes to the exact path.
+          const float z = RN.peek(0);
+          const float uo = RU.peek(0) + 0x1p-24f;  // U' = U + 2^-24, exact
+          const float x = g.c * z;
+          const float x2 = x * x;
+          const float ql = ((3.0f * g.d) * (x2 * x2)) * fmaf(x, -0.2f, 0.25f);
+          const bool rej = fabsf(x) <= kSeriesMaxX && att + 1 < kGammaMaxAttempts &&
+                           fmaf(uo, ql * 0.99999f, uo) >= 0x1.000004p+0f;
+          if (rej) {
+            RN.advance(1);
+            RU.advance(1);
+            ++att;
+          } else {
+            exact = true;
+          }
+        }
       }
     }
     const bool ex = run && exact && sweep < n_sweeps;
