@@ -40,11 +40,36 @@ METRIC = "Gibbs updates/s (normal-gamma, varying-parameter Gamma+Normal draws)"
 UNIT = "updates/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 PHILOX_MULS_PER_BLOCK = 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one normal_gamma_kernel
-# launch at this workload, from a full ncu capture of the current kernel
-# (profiles/normal_gamma_kernel_65536x2000.md); the data, state and moment
-# arrays only -- the rings live in shared memory
-NG_DRAM_BYTES_PER_LAUNCH = 4566784
+# DRAM traffic of one headline launch, as an ncu capture recorded it, keyed by
+# a hash of the kernel sources it was taken on; reported only while the
+# sources still hash the same (a changed kernel reports null traffic)
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "normal_gamma_kernel_traffic.txt")
+
+
+def kernel_sources_hash():
+    """sha256 (16 hex digits) over the CUDA sources and the public header."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1412_4825_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "brng.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """(dram bytes per launch, note) from the capture record, or (None, why)."""
+    try:
+        rec = dict(line.strip().split("=", 1) for line in open(TRAFFIC_RECORD)
+                   if "=" in line and not line.startswith("#"))
+    except OSError:
+        return None, "no capture record"
+    if rec.get("sources_sha16") != kernel_sources_hash():
+        return None, "kernel sources changed since the capture"
+    return int(rec["dram_bytes_per_launch"]), "ncu dram__bytes_read.sum + dram__bytes_write.sum, " + \
+        rec.get("captured", "?")
 
 
 def _clock_sampler(uuid):
@@ -174,9 +199,8 @@ def extras(dev, stream, peaks, args):
     from paper_1412_4825_gb300 import autotune as AT
     # integer-pipe roofline of a workload: the Philox blocks one call consumed
     # (from the stream positions before and after it) per second, against the
-    # same peak as the headline's
-    peak_blocks = (torch.cuda.get_device_properties(dev).multi_processor_count * (64.0 / 2.0 / PHILOX_MULS_PER_BLOCK)
-                   * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6)
+    # measured Philox probe, as the headline's
+    peak_blocks = philox_probe(B, dev, stream)
 
     def philox_roofline(run, positions, per_block, seconds):
         before = positions()
@@ -473,6 +497,22 @@ def extras(dev, stream, peaks, args):
     return out
 
 
+def philox_probe(B, dev, stream):
+    """Measured integer-pipe peak: Philox4x32-10 blocks per second of a
+    register-only kernel (8 blocks of 256 threads per SM, 2,048 blocks per
+    thread), timed with CUDA events on `stream` after a warm-up launch."""
+    import torch
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(sm_count * 8 * 256, dtype=torch.int32, device=dev)
+    B.brng_philox_peak(64, sm_count * 8, 256, sink, stream)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    B.brng_philox_peak(2048, sm_count * 8, 256, sink, stream)
+    pe1.record(stream)
+    torch.cuda.synchronize(dev)
+    return 4.0 * 2048 * sm_count * 8 * 256 / (pe0.elapsed_time(pe1) / 1e3)
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -609,18 +649,11 @@ def run_gpu(args):
     except Exception:
         pass
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_blocks = sm_count * (64.0 / 2.0 / PHILOX_MULS_PER_BLOCK) * sm_max * 1e6
+    derived_blocks = sm_count * (64.0 / 2.0 / PHILOX_MULS_PER_BLOCK) * sm_max * 1e6
     kernel_s = total_s / args.steps  # one launch per step, events bracket it alone
     achieved = blocks_per_step / kernel_s
-    # measured Philox probe for context
-    sink = torch.empty(sm_count * 8 * 256, dtype=torch.int32, device=dev)
-    B.brng_philox_peak(64, sm_count * 8, 256, sink, stream)
-    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    pe0.record(stream)
-    B.brng_philox_peak(2048, sm_count * 8, 256, sink, stream)
-    pe1.record(stream)
-    torch.cuda.synchronize(dev)
-    probe_blocks_s = 4.0 * 2048 * sm_count * 8 * 256 / (pe0.elapsed_time(pe1) / 1e3)
+    probe_blocks_s = philox_probe(B, dev, stream)
+    traffic, traffic_note = recorded_traffic()
 
     if rank != 0:
         if pg is not None:
@@ -637,10 +670,11 @@ def run_gpu(args):
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_blocks / 1e9,
-                     "unit": "GPhilox-block/s", "frac": achieved / peak_blocks, "traffic": NG_DRAM_BYTES_PER_LAUNCH,
-                     "kernel": "normal_gamma_kernel",
-                     "probe_measured": probe_blocks_s / 1e9,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": probe_blocks_s / 1e9,
+                     "unit": "GPhilox-block/s", "frac": achieved / probe_blocks_s, "traffic": traffic,
+                     "traffic_source": traffic_note, "kernel": "normal_gamma_kernel",
+                     "peak_source": "measured: register-only Philox4x32-10 probe on this GPU, same launch",
+                     "derived_peak": derived_blocks / 1e9,
                      "note": "integer pipe: 20 32x32->64 multiplies per Philox4x32-10 block; blocks = "
                              "exact consumption of the step (N+U elements / 4)"},
         "wall_s_timed": wall,
@@ -694,6 +728,17 @@ def run_case(args):
         ls = B.brng_lda_state_t(theta.data_ptr(), pos.data_ptr())
         fn = lambda: B.brng_gibbs_run(h.h, B.MODEL_LDA, 0, args.docs, args.sweeps, lp, ls, mom, stream)  # noqa: E731
         info.update(docs=args.docs, sweeps=args.sweeps, K=64)
+    elif args.case == "ng":  # the headline model at a chosen size (profiling)
+        nobs, xbar, sc = (torch.from_numpy(a).to(dev) for a in
+                          inputs.normal_gamma_data(args.chains, n_obs=N_OBS, seed=SEED))
+        st = B.normal_gamma_state(args.chains, device=dev)
+        mom = torch.zeros((args.chains, 4), dtype=torch.float64, device=dev)
+        h = B.Handle(SEED, 1)
+        h.tune(buf_len=args.buf_len or 32, warps_per_block=args.warps_per_block or 8)
+        prm = B.brng_normal_gamma_params_t(*PRIOR, nobs.data_ptr(), xbar.data_ptr(), sc.data_ptr())
+        fn = lambda: B.brng_gibbs_run(h.h, B.MODEL_NORMAL_GAMMA, 0, args.chains, args.sweeps, prm, st, mom,  # noqa: E731
+                                      stream)
+        info.update(chains=args.chains, sweeps=args.sweeps)
     elif args.case == "triangle":
         h = B.Handle(SEED, 1)
         h.tune(buf_len=256, lanes_per_chain=16)
@@ -742,12 +787,14 @@ def main():
                     help="skip the secondary workloads (triangle, LDA, mixed stream, batched vs plain, served mix)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="arrival window of the served mix at 2,000 jobs/s")
-    ap.add_argument("--case", choices=["mixed", "lda", "triangle", "uniform64"], default=None,
-                    help="time one secondary workload instead (profiling): mixed, lda, triangle or uniform64")
+    ap.add_argument("--case", choices=["mixed", "lda", "triangle", "uniform64", "ng"], default=None,
+                    help="time one workload at a chosen size instead (profiling): mixed, lda, triangle, "
+                         "uniform64, or ng (the headline normal-gamma model)")
     ap.add_argument("--log2n", type=int, default=28, help="--case mixed / uniform64: log2 of the draws")
     ap.add_argument("--log2s", type=int, default=20, help="--case mixed / uniform64: log2 of the streams")
     ap.add_argument("--docs", type=int, default=16384, help="--case lda: documents")
-    ap.add_argument("--sweeps", type=int, default=500, help="--case lda/triangle: sweeps")
+    ap.add_argument("--chains", type=int, default=N_CHAINS, help="--case ng: chains")
+    ap.add_argument("--sweeps", type=int, default=500, help="--case lda/triangle/ng: sweeps")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
