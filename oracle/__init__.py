@@ -73,6 +73,15 @@ def lib():
         L.or_gibbs_normal_gamma_mt.restype = i32
         L.or_gibbs_lda_mt.argtypes = [u64, u64, u32, u32, u32, vp, vp, vp, vp, vp, vp, vp, u32, i32]
         L.or_gibbs_lda_mt.restype = i32
+        f32 = C.c_float
+        L.or_lda_weights.argtypes = [u32, f32, f32, f32, vp, vp, vp, u32, vp, vp]
+        L.or_lda_pick.argtypes = [u32, vp, u32]
+        L.or_lda_pick.restype = u32
+        L.or_lda_z_sweep_mt.argtypes = [u64, u64, u32, u32, u32, f32, f32, vp, vp, vp, vp, vp, vp, vp, vp,
+                                        vp, i32]
+        L.or_lda_z_sweep_mt.restype = i32
+        L.or_lda_z_run.argtypes = [u64, u32, u32, u32, u32, f32, f32, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.or_lda_z_run.restype = i32
         L.or_mt_accept.argtypes = [dbl, dbl, dbl]
         L.or_mt_accept.restype = i32
         _lib = L
@@ -307,3 +316,82 @@ def gibbs_lda(seed, n_sweeps, alpha, doc_offset=0, pos=None, mom=None, buf_len=6
     if trace:
         out["trace"] = tr
     return out
+
+
+# ---- full LDA step: topic draws per token, then theta ~ Dir(alpha + n_d) --
+
+DOM_Z = 5
+
+
+def lda_weights(K, alpha, beta, V, ndk, nkw_w, nk, z_old):
+    """FP32 weights and their integer form for one token (counts include the
+    token itself, whose topic is z_old); Vbeta = float32(V) * beta."""
+    ndk, nkw_w, nk = (np.ascontiguousarray(a, dtype=np.int32) for a in (ndk, nkw_w, nk))
+    w = np.empty(K, dtype=np.float32)
+    q = np.empty(K, dtype=np.uint32)
+    vbeta = float(np.float32(V) * np.float32(beta))
+    lib().or_lda_weights(K, alpha, beta, vbeta, _p(ndk), _p(nkw_w), _p(nk), z_old, _p(w), _p(q))
+    return w, q
+
+
+def lda_pick(q, r24):
+    q = np.ascontiguousarray(q, dtype=np.uint32)
+    return int(lib().or_lda_pick(q.size, _p(q), r24))
+
+
+def lda_z_sweep(seed, corpus, state, alpha, beta, doc_offset=0, nthreads=1):
+    """One sweep of topic draws over the corpus's documents (state updated in
+    place: z, ndk, zpos); returns (dnkw, dnk), the sweep's word-topic and topic
+    count changes, which the caller adds into nkw and nk (the sweep's
+    snapshot is state["nkw"], state["nk"], left untouched)."""
+    K, V = corpus["K"], corpus["V"]
+    n_docs = corpus["doc_ptr"].size - 1
+    dnkw = np.zeros((V, K), dtype=np.int32)
+    dnk = np.zeros(K, dtype=np.int32)
+    st = lib().or_lda_z_sweep_mt(seed, doc_offset, n_docs, K, V, alpha, beta, _p(corpus["doc_ptr"]),
+                                 _p(corpus["words"]), _p(state["z"]), _p(state["ndk"]), _p(state["nkw"]),
+                                 _p(state["nk"]), _p(dnkw), _p(dnk), _p(state["zpos"]), _threads(nthreads))
+    if st != OK:
+        raise ValueError("or_lda_z_sweep: status %d" % st)
+    return dnkw, dnk
+
+
+def lda_z_run(seed, n_sweeps, corpus, state, alpha=0.1, beta=0.01, zhist=False):
+    """n_sweeps topic sweeps without theta draws, all in C (documents from id
+    0); state updated in place; returns the per-token topic histogram
+    [n_tokens, K] over the sweeps when zhist."""
+    K, V = corpus["K"], corpus["V"]
+    n_docs = corpus["doc_ptr"].size - 1
+    h = np.zeros((corpus["words"].size, K), dtype=np.uint32) if zhist else None
+    st = lib().or_lda_z_run(seed, n_sweeps, n_docs, K, V, alpha, beta, _p(corpus["doc_ptr"]),
+                            _p(corpus["words"]), _p(state["z"]), _p(state["ndk"]), _p(state["nkw"]),
+                            _p(state["nk"]), _p(state["zpos"]), _p(h))
+    if st != OK:
+        raise ValueError("or_lda_z_run: status %d" % st)
+    return h
+
+
+def lda_full(seed, n_sweeps, corpus, state, alpha=0.1, beta=0.01, doc_offset=0, nthreads=1, buf_len=64,
+             theta_draws=True):
+    """The full LDA Gibbs step, n_sweeps times: topic draws for every token
+    (lda_z_sweep), the sweep's count changes added into nkw and nk, then per
+    document theta_d ~ Dirichlet(alpha + n_d) with alpha + n_dk formed in FP32
+    (the Dirichlet of Sec. 1's LDA paragraph, from Gammas per its footnote),
+    its components on streams (doc_offset + d) K + k as in gibbs_lda.
+    `state` (dict of numpy arrays: z, ndk, nkw, nk, zpos, pos [n_docs, K, 2],
+    mom [n_docs, K], theta) is updated in place and returned."""
+    K = corpus["K"]
+    a32 = np.float32(alpha)
+    for _ in range(n_sweeps):
+        dnkw, dnk = lda_z_sweep(seed, corpus, state, alpha, beta, doc_offset, nthreads)
+        state["nkw"] += dnkw
+        state["nk"] += dnk
+        if theta_draws:
+            dir_alpha = (a32 + state["ndk"].astype(np.float32)).astype(np.float32)
+            r = gibbs_lda(seed, 1, dir_alpha, doc_offset=doc_offset, pos=state["pos"].ravel(),
+                          mom=state["mom"], buf_len=buf_len, nthreads=nthreads)
+            state["pos"] = r["pos"]
+            state["mom"] = r["mom"]
+            state["theta"] = r["theta"]
+    assert K == state["ndk"].shape[1]
+    return state

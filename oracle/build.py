@@ -11,7 +11,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["or_philox.c", "or_math.c", "or_batchrng.c", "or_gibbs.c"]
+SOURCES = ["or_philox.c", "or_math.c", "or_batchrng.c", "or_gibbs.c", "or_lda.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-pthread",
           "-Wall", "-Wextra", "-Wno-unused-parameter"]

@@ -36,7 +36,8 @@ extern "C" {
 #define OR_DOM_E 2u    /* exponentials -ln U', one word per element        */
 #define OR_DOM_DATA 3u /* reserved for synthetic data / set-up draws       */
 #define OR_DOM_U64 4u  /* 53-bit uniforms, two words per element           */
-#define OR_NDOM 5
+#define OR_NDOM 5      /* domains a buffered stream object holds            */
+#define OR_DOM_Z 5u    /* LDA topic draws: one word per element (top 24 bits) */
 
 /* status bits returned by the bulk and Gibbs functions */
 #define OR_OK 0
@@ -143,6 +144,37 @@ int or_gibbs_normal_gamma(uint64_t seed, uint64_t chain_offset, uint32_t n_chain
 int or_gibbs_lda(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K,
                  uint32_t n_sweeps, const float *alpha, double *theta, double *logs,
                  double *cond, uint64_t *pos, double *mom, double *trace, uint32_t buf_len);
+
+/* ---- full LDA step (or_lda.c): topic assignments resampled per token ---- */
+/* The FP32 weights w_k of one token's collapsed conditional and their
+ * integer form q_k (see or_lda.c): ndk, nkw_w, nk are the counts including
+ * the token itself, whose current topic is z_old. */
+void or_lda_weights(uint32_t K, float alpha, float beta, float vbeta, const int32_t *ndk,
+                    const int32_t *nkw_w, const int32_t *nk, uint32_t z_old, float *w_out,
+                    uint32_t *q_out);
+/* the topic for a 24-bit uniform integer r24: smallest k with C_k > (r24 Q) >> 24 */
+uint32_t or_lda_pick(uint32_t K, const uint32_t *q, uint32_t r24);
+/* One sweep of topic draws over documents [0, n_docs) (global ids doc_offset +
+ * d): tokens doc_ptr[d] .. doc_ptr[d+1]-1 with words[t] < V and topics z[t]
+ * (in/out), document-topic counts ndk [n_docs][K] (in/out), word-topic and
+ * topic counts nkw [V][K], nk [K] of the start of the sweep (read only); the
+ * sweep's changes are added to dnkw [V][K] and dnk [K]; zpos[d] = the
+ * document's next Z-domain element (in/out).  K <= 255. */
+int or_lda_z_sweep(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K, uint32_t V,
+                   float alpha, float beta, const uint32_t *doc_ptr, const uint32_t *words,
+                   uint8_t *z, int32_t *ndk, const int32_t *nkw, const int32_t *nk,
+                   int32_t *dnkw, int32_t *dnk, uint64_t *zpos);
+int or_lda_z_sweep_mt(uint64_t seed, uint64_t doc_offset, uint32_t n_docs, uint32_t K, uint32_t V,
+                      float alpha, float beta, const uint32_t *doc_ptr, const uint32_t *words,
+                      uint8_t *z, int32_t *ndk, const int32_t *nkw, const int32_t *nk,
+                      int32_t *dnkw, int32_t *dnk, uint64_t *zpos, int nthreads);
+/* n_sweeps topic sweeps (document ids from 0), each followed by adding its
+ * changes into nkw and nk; zhist (nullable) [n_tokens][K] += 1 at the topic of
+ * each token after each sweep. */
+int or_lda_z_run(uint64_t seed, uint32_t n_sweeps, uint32_t n_docs, uint32_t K, uint32_t V,
+                 float alpha, float beta, const uint32_t *doc_ptr, const uint32_t *words,
+                 uint8_t *z, int32_t *ndk, int32_t *nkw, int32_t *nk, uint64_t *zpos,
+                 uint32_t *zhist);
 
 /* the same on `nthreads` host threads over contiguous chain ranges */
 int or_gibbs_triangle_mt(uint64_t seed, uint64_t chain_offset, uint32_t n_chains,

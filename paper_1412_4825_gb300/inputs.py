@@ -12,6 +12,11 @@ Workloads (arXiv 1412.4825):
   * LDA document-topic step (Sec. 1, LDA paragraph): per document a topic mix
     phi ~ Dir(prior * 1_K), a length L ~ U{len_lo..len_hi}, counts ~ Mult(L, phi),
     and the Dirichlet parameter alpha = prior + counts formed in FP32;
+  * full LDA step (topic draws per token): a synthetic corpus from LDA's own
+    generative model (topic-word distributions ~ Dir(word_prior), per
+    document a topic mix ~ Dir(doc_prior), a length ~ U{len_lo..len_hi}, per
+    token a topic from the mix and a word from that topic), a uniformly random
+    initial topic per token and the count tables of that assignment;
   * varying-parameter streams (Sec. 2.3, parameters read from memory per
     draw): log-uniform parameters, and for the mixed stream a tag per draw.
 """
@@ -52,6 +57,57 @@ def lda_alpha(n_docs: int, K: int = 64, len_lo: int = 50, len_hi: int = 500, pri
     counts = np.stack([rng.multinomial(int(L), p) for L, p in zip(lengths, phi)]).astype(np.uint32)
     alpha = (np.float32(prior) + counts.astype(np.float32)).astype(np.float32)
     return alpha, counts, lengths
+
+
+def lda_corpus(n_docs: int, K: int = 64, V: int = 4096, len_lo: int = 50, len_hi: int = 500,
+               doc_prior: float = 0.1, word_prior: float = 0.05, seed: int = 42):
+    """A corpus drawn from LDA's generative model: dict(K, V, doc_ptr uint32
+    [n_docs + 1] token offsets, words uint32 [n_tokens])."""
+    rng = np.random.default_rng(seed)
+    phi = rng.dirichlet(np.full(V, word_prior), size=K)          # topic-word
+    lengths = rng.integers(len_lo, len_hi + 1, size=n_docs)
+    doc_ptr = np.zeros(n_docs + 1, dtype=np.uint32)
+    np.cumsum(lengths, out=doc_ptr[1:])
+    n_tok = int(doc_ptr[-1])
+    mix = rng.dirichlet(np.full(K, doc_prior), size=n_docs)      # document-topic
+    # per token: topic by inversion of its document's mix, word by inversion
+    # of its topic's distribution
+    cmix = np.cumsum(mix, axis=1)
+    cmix[:, -1] = 1.0
+    doc_of = np.repeat(np.arange(n_docs), lengths)
+    u = rng.random(n_tok)
+    # row-wise inversion: rows shifted by their document index, one search
+    flat = (cmix + np.arange(n_docs)[:, None]).ravel()
+    topic = np.searchsorted(flat, u + doc_of, side="right") - doc_of * K
+    topic = np.clip(topic, 0, K - 1)
+    cphi = np.cumsum(phi, axis=1)
+    cphi[:, -1] = 1.0
+    words = np.empty(n_tok, dtype=np.uint32)
+    v = rng.random(n_tok)
+    for k in range(K):
+        idx = np.nonzero(topic == k)[0]
+        words[idx] = np.minimum(np.searchsorted(cphi[k], v[idx], side="right"), V - 1)
+    return dict(K=K, V=V, doc_ptr=doc_ptr, words=words)
+
+
+def lda_initial_state(corpus: dict, seed: int = 7):
+    """Uniformly random initial topics and the count tables they imply:
+    dict(z uint8 [n_tokens], ndk int32 [n_docs, K], nkw int32 [V, K],
+    nk int32 [K], zpos uint64 [n_docs] (next topic-draw element per
+    document), pos uint64 [n_docs, K, 2] (Dirichlet component positions),
+    mom float64 [n_docs, K], theta float64 [n_docs, K])."""
+    K, V = corpus["K"], corpus["V"]
+    doc_ptr, words = corpus["doc_ptr"], corpus["words"]
+    n_docs = doc_ptr.size - 1
+    rng = np.random.default_rng(seed)
+    z = rng.integers(0, K, size=words.size, dtype=np.uint8)
+    doc_of = np.repeat(np.arange(n_docs), np.diff(doc_ptr.astype(np.int64)))
+    ndk = np.bincount(doc_of * K + z, minlength=n_docs * K).reshape(n_docs, K).astype(np.int32)
+    nkw = np.bincount(words.astype(np.int64) * K + z, minlength=V * K).reshape(V, K).astype(np.int32)
+    nk = np.bincount(z, minlength=K).astype(np.int32)
+    return dict(z=z, ndk=ndk, nkw=nkw, nk=nk, zpos=np.zeros(n_docs, dtype=np.uint64),
+                pos=np.zeros((n_docs, K, 2), dtype=np.uint64), mom=np.zeros((n_docs, K)),
+                theta=np.zeros((n_docs, K)))
 
 
 def uniform_params(n: int, seed: int = 42, lo: float = 1e-3, hi: float = 1e3):
