@@ -63,9 +63,10 @@ typedef enum {
   BRNG_ENOTFOUND = 8 /* unknown job id                                            */
 } brng_status_t;
 
-/* domain tags (counter word 1) */
+/* domain tags (counter word 1); Z: the full LDA step's topic draws, one word
+ * (its top 24 bits) per draw, stream = global document id */
 enum { BRNG_DOMAIN_U = 0, BRNG_DOMAIN_N = 1, BRNG_DOMAIN_E = 2, BRNG_DOMAIN_DATA = 3,
-       BRNG_DOMAIN_U64 = 4 };
+       BRNG_DOMAIN_U64 = 4, BRNG_DOMAIN_Z = 5 };
 
 /* distribution tags of the mixed stream */
 enum { BRNG_TAG_UNIFORM = 0, BRNG_TAG_NORMAL = 1, BRNG_TAG_EXPONENTIAL = 2, BRNG_TAG_GAMMA = 3,
@@ -77,7 +78,8 @@ enum { BRNG_TAG_UNIFORM = 0, BRNG_TAG_NORMAL = 1, BRNG_TAG_EXPONENTIAL = 2, BRNG
 typedef enum {
   BRNG_MODEL_TRIANGLE = 0,     /* Sec. 1, Eq. 1 and Fig. 1                              */
   BRNG_MODEL_NORMAL_GAMMA = 1, /* mean/precision of a normal sample, Gamma + Normal steps */
-  BRNG_MODEL_LDA = 2           /* LDA document-topic Dirichlet step (Sec. 1, footnote)   */
+  BRNG_MODEL_LDA = 2,          /* LDA document-topic Dirichlet step (Sec. 1, footnote)   */
+  BRNG_MODEL_LDA_FULL = 3      /* full LDA step: topic draws per token, then the Dirichlet */
 } brng_model_t;
 
 /* Device-side counters of a handle (brng_read_counters). */
@@ -329,8 +331,71 @@ typedef struct {
   uint64_t *pos;  /* device [n][K][2]: next (N, U) element of each component      */
 } brng_lda_state_t;
 
+/* LDA_FULL (Sec. 1, the LDA paragraph: a Dirichlet "whose parameters are
+ *   updated during each iteration"): per sweep, for every document d (a
+ *   "chain"; global id chain_offset + d), (1) each token's topic is redrawn
+ *   from the collapsed conditional
+ *       p(z = k) proportional to (n_dk' + alpha)(n_kw' + beta)/(n_k' + V beta)
+ *   (' = without the token itself), with the word-topic counts n_kw, n_k of
+ *   the start of the sweep plus the document's own changes so far (the
+ *   distributed sampler of Newman et al., JMLR 2009, one document per worker;
+ *   exact sequential collapsed Gibbs for a one-document corpus); the weights
+ *   are FP32 in a fixed operation order, made integers (q_k = trunc(w_k
+ *   2^(31-e)), 2^e <= max w < 2^(e+1)) and the topic is the smallest k whose
+ *   cumulative q exceeds (r Q) >> 24, r the top 24 bits of the document's
+ *   next Z-domain word; (2) theta_d ~ Dirichlet(alpha + n_d) exactly as the
+ *   LDA model (alpha + n_dk formed in FP32; component k on stream
+ *   (chain_offset + d) K + k).  After the sweep the documents' count changes
+ *   are added into n_kw and n_k (exchange = 0).  params:
+ *   brng_lda_full_params_t (host struct).  state: brng_lda_full_state_t
+ *   (host struct of device pointers).  moments: double[n][K] += theta per
+ *   sweep.  z, the counts and every position are bit-exact integer results;
+ *   theta is FP32.  Not available in brng_gibbs_batch.  Errors: BRNG_EINVAL
+ *   for K outside 1..128, V = 0, alpha or beta not in [1e-6, 1e6], a NULL
+ *   array, or exchange = 1 with n_sweeps != 1. */
+#define BRNG_LDA_NONE 0xFFFFFFFFu
+typedef struct {
+  uint32_t K, V;            /* topics (1..128), vocabulary size (words < V)             */
+  float alpha, beta;        /* symmetric document-topic and topic-word priors           */
+  const uint32_t *doc_ptr;  /* device [n+1]: document d holds tokens doc_ptr[d] ..
+                               doc_ptr[d+1]-1 (offsets into words, prev and z)           */
+  const uint32_t *words;    /* device [tokens]: word of each token                      */
+  const uint32_t *prev;     /* device [tokens]: the document's previous token with the
+                               same word, or BRNG_LDA_NONE (brng_lda_index makes it)      */
+  uint32_t exchange;        /* 0: every sweep's count changes are added into nkw, nk
+                               before the next; 1 (n_sweeps = 1 only): they are left in
+                               dnkw for the caller to sum over devices, then
+                               brng_lda_apply adds them                                  */
+} brng_lda_full_params_t;
+
+typedef struct {
+  uint8_t *z;         /* device [tokens]: topic of each token (in/out)              */
+  uint8_t *z_start;   /* device [tokens]: workspace (each token's topic at the start
+                         of the sweep)                                               */
+  int32_t *ndk;       /* device [n][K]: document-topic counts (in/out)              */
+  int32_t *nkw;       /* device [V][K]: word-topic counts of the whole corpus        */
+  int32_t *nk;        /* device [K]: topic totals of the whole corpus                */
+  int32_t *dnkw;      /* device [V*K + K]: count changes (word-topic, then topic);
+                         zero on entry and, with exchange = 0, on return              */
+  float *dir_alpha;   /* device [n][K]: workspace (alpha + n_dk of the theta draw)   */
+  uint64_t *zpos;     /* device [n]: next Z-domain element of each document          */
+  float *theta;       /* device [n][K]: last theta draw (output)                     */
+  uint64_t *pos;      /* device [n][K][2]: next (N, U) element of each component     */
+} brng_lda_full_state_t;
+
 int brng_gibbs_run(brng_t *h, brng_model_t model, uint64_t chain_offset, uint32_t n_chains,
                    uint32_t n_sweeps, const void *params, void *state, double *moments,
+                   brng_stream_t stream);
+
+/* The LDA_FULL model's helpers (no counterpart in the paper: corpus indexing
+ * and the count exchange of the distributed sampler).  brng_lda_index fills
+ * prev[t] (above) for the tokens of n_docs documents (device doc_ptr [n+1],
+ * words); one pass, O(L^2) per document of L tokens.  brng_lda_apply adds the
+ * changes dnkw [V*K + K] into nkw [V][K] and nk [K] and zeroes dnkw.  Both are
+ * asynchronous on `stream`; BRNG_EINVAL for NULL arrays or K outside 1..128. */
+int brng_lda_index(uint32_t n_docs, const uint32_t *doc_ptr, const uint32_t *words, uint32_t *prev,
+                   brng_stream_t stream);
+int brng_lda_apply(uint32_t K, uint32_t V, int32_t *nkw, int32_t *nk, int32_t *dnkw,
                    brng_stream_t stream);
 
 /* ---- batched Gibbs jobs: uneven ensembles in one persistent kernel ---------

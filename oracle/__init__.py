@@ -372,14 +372,15 @@ def lda_z_run(seed, n_sweeps, corpus, state, alpha=0.1, beta=0.01, zhist=False):
 
 
 def lda_full(seed, n_sweeps, corpus, state, alpha=0.1, beta=0.01, doc_offset=0, nthreads=1, buf_len=64,
-             theta_draws=True):
+             theta_draws=True, trace=False):
     """The full LDA Gibbs step, n_sweeps times: topic draws for every token
     (lda_z_sweep), the sweep's count changes added into nkw and nk, then per
     document theta_d ~ Dirichlet(alpha + n_d) with alpha + n_dk formed in FP32
     (the Dirichlet of Sec. 1's LDA paragraph, from Gammas per its footnote),
     its components on streams (doc_offset + d) K + k as in gibbs_lda.
     `state` (dict of numpy arrays: z, ndk, nkw, nk, zpos, pos [n_docs, K, 2],
-    mom [n_docs, K], theta) is updated in place and returned."""
+    mom [n_docs, K], theta) is updated in place and returned; trace=True
+    appends every theta draw's log-Gammas and conditioning to state["trace"]."""
     K = corpus["K"]
     a32 = np.float32(alpha)
     for _ in range(n_sweeps):
@@ -389,9 +390,13 @@ def lda_full(seed, n_sweeps, corpus, state, alpha=0.1, beta=0.01, doc_offset=0, 
         if theta_draws:
             dir_alpha = (a32 + state["ndk"].astype(np.float32)).astype(np.float32)
             r = gibbs_lda(seed, 1, dir_alpha, doc_offset=doc_offset, pos=state["pos"].ravel(),
-                          mom=state["mom"], buf_len=buf_len, nthreads=nthreads)
+                          mom=state["mom"], buf_len=buf_len, nthreads=nthreads, trace=trace)
             state["pos"] = r["pos"]
             state["mom"] = r["mom"]
             state["theta"] = r["theta"]
+            state["logs"], state["cond"] = r["logs"], r["cond"]
+            if trace:  # [n_docs, sweeps, K, 2]: every theta draw's log-Gammas and conditioning
+                prev = state.get("trace")
+                state["trace"] = r["trace"] if prev is None else np.concatenate([prev, r["trace"]], axis=1)
     assert K == state["ndk"].shape[1]
     return state

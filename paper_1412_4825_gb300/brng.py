@@ -22,11 +22,12 @@ BRNG_OK, BRNG_EINVAL, BRNG_ENOMEM, BRNG_ECUDA, BRNG_EDOMAIN, BRNG_EREJECT, BRNG_
     BRNG_EAGAIN, BRNG_ENOTFOUND = range(9)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EDOMAIN", "EREJECT", "ETIMEOUT", "EAGAIN",
                 "ENOTFOUND"]
-DOMAIN_U, DOMAIN_N, DOMAIN_E, DOMAIN_DATA, DOMAIN_U64 = 0, 1, 2, 3, 4
+DOMAIN_U, DOMAIN_N, DOMAIN_E, DOMAIN_DATA, DOMAIN_U64, DOMAIN_Z = 0, 1, 2, 3, 4, 5
 TAG_UNIFORM, TAG_NORMAL, TAG_EXPONENTIAL, TAG_GAMMA, TAG_LAPLACE, TAG_WEIBULL, TAG_POISSON, TAG_BINOMIAL = range(8)
 POISSON_MAX_LAMBDA = 64.0
 BINOMIAL_MAX_MEAN = 64.0
-MODEL_TRIANGLE, MODEL_NORMAL_GAMMA, MODEL_LDA = 0, 1, 2
+MODEL_TRIANGLE, MODEL_NORMAL_GAMMA, MODEL_LDA, MODEL_LDA_FULL = 0, 1, 2, 3
+LDA_NONE = 0xFFFFFFFF
 BRNG_STATIC_MAX_STREAMS = 65536
 
 
@@ -64,6 +65,17 @@ class brng_lda_params_t(C.Structure):
 
 class brng_lda_state_t(C.Structure):
     _fields_ = [("theta", C.c_void_p), ("pos", C.c_void_p)]
+
+
+class brng_lda_full_params_t(C.Structure):
+    _fields_ = [("K", C.c_uint32), ("V", C.c_uint32), ("alpha", C.c_float), ("beta", C.c_float),
+                ("doc_ptr", C.c_void_p), ("words", C.c_void_p), ("prev", C.c_void_p), ("exchange", C.c_uint32)]
+
+
+class brng_lda_full_state_t(C.Structure):
+    _fields_ = [("z", C.c_void_p), ("z_start", C.c_void_p), ("ndk", C.c_void_p), ("nkw", C.c_void_p),
+                ("nk", C.c_void_p), ("dnkw", C.c_void_p), ("dir_alpha", C.c_void_p), ("zpos", C.c_void_p),
+                ("theta", C.c_void_p), ("pos", C.c_void_p)]
 
 
 class brng_job_t(C.Structure):
@@ -129,6 +141,8 @@ def _load():
         "brng_dirichlet": ([vp, sz, u32, vp, vp, vp], i32),
         "brng_gamma_static": ([u64, u32, sz, vp, vp, vp, vp], i32),
         "brng_gibbs_run": ([vp, i32, u64, u32, u32, vp, vp, vp, vp], i32),
+        "brng_lda_index": ([u32, vp, vp, vp, vp], i32),
+        "brng_lda_apply": ([u32, u32, vp, vp, vp, vp], i32),
         "brng_batch_create": ([vp, vp, u32, C.POINTER(vp)], i32),
         "brng_batch_launch": ([vp, vp], i32),
         "brng_batch_destroy": ([vp], i32),
@@ -351,6 +365,77 @@ def brng_dirichlet(h, alpha, out, stream=None):
     n_rows, K = alpha.shape
     return _check("brng_dirichlet", lib.brng_dirichlet(
         h, n_rows, K, _ptr(alpha, _f32(), "alpha"), _ptr(out, _f32(), "out"), _stream(stream)))
+
+
+def brng_lda_index(doc_ptr, words, prev, stream=None):
+    import torch
+    return _check("brng_lda_index", lib.brng_lda_index(
+        doc_ptr.numel() - 1, _ptr(doc_ptr, torch.int32, "doc_ptr"), _ptr(words, torch.int32, "words"),
+        _ptr(prev, torch.int32, "prev"), _stream(stream)))
+
+
+def brng_lda_apply(K, V, nkw, nk, dnkw, stream=None):
+    import torch
+    return _check("brng_lda_apply", lib.brng_lda_apply(
+        int(K), int(V), _ptr(nkw, torch.int32, "nkw"), _ptr(nk, torch.int32, "nk"),
+        _ptr(dnkw, torch.int32, "dnkw"), _stream(stream)))
+
+
+class LdaFull:
+    """Device arrays of the LDA_FULL model for one corpus (torch tensors; the
+    32-bit unsigned arrays are held as int32 and passed by pointer):
+    doc_ptr, words, prev, z, z_start, ndk, nkw, nk, dnkw, dir_alpha, zpos,
+    theta, pos, mom.  `corpus`/`state` are the numpy dicts of
+    inputs.lda_corpus / inputs.lda_initial_state; prev is built on the device
+    with brng_lda_index."""
+
+    def __init__(self, corpus, state, alpha=0.1, beta=0.01, device="cuda", stream=None):
+        import torch
+
+        def dev(a, dtype):
+            return torch.from_numpy(np.ascontiguousarray(a).view(dtype)).to(device)
+
+        self.K, self.V = int(corpus["K"]), int(corpus["V"])
+        self.alpha, self.beta = float(alpha), float(beta)
+        self.n_docs = corpus["doc_ptr"].size - 1
+        n_tok = corpus["words"].size
+        self.doc_ptr = dev(corpus["doc_ptr"].astype(np.uint32), np.int32)
+        self.words = dev(corpus["words"].astype(np.uint32), np.int32)
+        self.prev = torch.empty(n_tok, dtype=torch.int32, device=device)
+        self.z = dev(state["z"].astype(np.uint8), np.uint8)
+        self.z_start = torch.empty(n_tok, dtype=torch.uint8, device=device)
+        self.ndk = dev(state["ndk"].astype(np.int32), np.int32)
+        self.nkw = dev(state["nkw"].astype(np.int32), np.int32)
+        self.nk = dev(state["nk"].astype(np.int32), np.int32)
+        self.dnkw = torch.zeros(self.V * self.K + self.K, dtype=torch.int32, device=device)
+        self.dir_alpha = torch.empty((self.n_docs, self.K), dtype=torch.float32, device=device)
+        self.zpos = dev(state["zpos"].astype(np.uint64), np.int64)
+        self.theta = torch.zeros((self.n_docs, self.K), dtype=torch.float32, device=device)
+        self.pos = dev(state["pos"].astype(np.uint64), np.int64)
+        self.mom = dev(state["mom"].astype(np.float64), np.float64)
+        brng_lda_index(self.doc_ptr, self.words, self.prev, stream)
+
+    def params(self, exchange=0):
+        return brng_lda_full_params_t(self.K, self.V, self.alpha, self.beta, self.doc_ptr.data_ptr(),
+                                      self.words.data_ptr(), self.prev.data_ptr(), int(exchange))
+
+    def state(self):
+        return brng_lda_full_state_t(*[t.data_ptr() for t in (
+            self.z, self.z_start, self.ndk, self.nkw, self.nk, self.dnkw, self.dir_alpha, self.zpos,
+            self.theta, self.pos)])
+
+    def run(self, h, n_sweeps, doc_offset=0, stream=None, exchange=0):
+        """h: a Handle or a raw brng_t* (its seed keys the draws)."""
+        h = getattr(h, "h", h)
+        return brng_gibbs_run(h, MODEL_LDA_FULL, doc_offset, self.n_docs, n_sweeps, self.params(exchange),
+                              self.state(), self.mom, stream)
+
+    def host(self):
+        """The state as numpy arrays (the oracle's dict layout)."""
+        g = lambda t: t.detach().cpu().numpy()  # noqa: E731
+        return dict(z=g(self.z), ndk=g(self.ndk), nkw=g(self.nkw).reshape(self.V, self.K), nk=g(self.nk),
+                    zpos=g(self.zpos).view(np.uint64), pos=g(self.pos).view(np.uint64), mom=g(self.mom),
+                    theta=g(self.theta), dnkw=g(self.dnkw), prev=g(self.prev).view(np.uint32))
 
 
 def brng_gibbs_run(h, model, chain_offset, n_chains, n_sweeps, params, state, moments, stream=None):

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbrng.so")
 SOURCES = ["brng_api.cu", "brng_bulk.cu", "brng_dirichlet.cu", "brng_gibbs.cu", "brng_static.cu",
-           "brng_batch.cu", "brng_serve.cu", "brng_gibbs_pc.cu"]
+           "brng_batch.cu", "brng_serve.cu", "brng_gibbs_pc.cu", "brng_lda_full.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -488,13 +488,85 @@ int plan_batch(const brng_t* h, const brng_job_t* jobs, uint32_t n_jobs,
   return BRNG_OK;
 }
 
+// The full LDA step, n_sweeps times: topic draws (one warp per document),
+// the count changes added into the corpus counts (unless the caller exchanges
+// them across devices first), then theta ~ Dirichlet(alpha + n_d) through the
+// LDA model's own launch, on the same stream.
+int lda_full_run(brng_t* h, uint64_t doc_offset, uint32_t n_docs, uint32_t n_sweeps,
+                 const brng_lda_full_params_t* p, const brng_lda_full_state_t* s, double* moments,
+                 brng_stream_t stream);
+
 uint64_t total_units(const std::vector<brng::BatchJob>& t) {
   return t.empty() ? 0 : t.back().first_unit + t.back().n_units;
+}
+
+int lda_full_run(brng_t* h, uint64_t doc_offset, uint32_t n_docs, uint32_t n_sweeps,
+                 const brng_lda_full_params_t* p, const brng_lda_full_state_t* s, double* moments,
+                 brng_stream_t stream) {
+  if (!p || !s || !moments) return BRNG_EINVAL;
+  if (p->K == 0 || p->K > 128 || p->V == 0 || !p->doc_ptr || !p->words || !p->prev) return BRNG_EINVAL;
+  if (!(p->alpha >= 1e-6f && p->alpha <= 1e6f && p->beta >= 1e-6f && p->beta <= 1e6f)) return BRNG_EINVAL;
+  if (!s->z || !s->z_start || !s->ndk || !s->nkw || !s->nk || !s->dnkw || !s->dir_alpha || !s->zpos ||
+      !s->theta || !s->pos)
+    return BRNG_EINVAL;
+  if (p->exchange > 1 || (p->exchange == 1 && n_sweeps != 1)) return BRNG_EINVAL;
+  if ((doc_offset + n_docs) * static_cast<uint64_t>(p->K) > 0x100000000ull) return BRNG_EINVAL;
+  if (n_docs == 0 || n_sweeps == 0) return BRNG_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  brng::LdaZArgs a;
+  a.rk = h->rk;
+  a.doc_offset = doc_offset;
+  a.n_docs = n_docs;
+  a.K = p->K;
+  a.V = p->V;
+  a.alpha = p->alpha;
+  a.beta = p->beta;
+  a.vbeta = static_cast<float>(p->V) * p->beta;  // one FP32 rounding, as the oracle
+  a.doc_ptr = p->doc_ptr;
+  a.words = p->words;
+  a.prev = p->prev;
+  a.z = s->z;
+  a.z_start = s->z_start;
+  a.ndk = s->ndk;
+  a.nkw = s->nkw;
+  a.nk = s->nk;
+  a.dnkw = s->dnkw;
+  a.dir_alpha = s->dir_alpha;
+  a.zpos = s->zpos;
+  brng_lda_params_t lp;
+  lp.K = p->K;
+  lp.alpha = s->dir_alpha;
+  brng_lda_state_t ls;
+  ls.theta = s->theta;
+  ls.pos = s->pos;
+  for (uint32_t sweep = 0; sweep < n_sweeps; ++sweep) {
+    int rc = cuda_status(brng::launch_lda_z(a, st));
+    if (rc != BRNG_OK) return rc;
+    if (p->exchange == 0) {
+      rc = cuda_status(brng::launch_lda_apply(p->K, p->V, s->nkw, s->nk, s->dnkw, st));
+      if (rc != BRNG_OK) return rc;
+    }
+    rc = brng_gibbs_run(h, BRNG_MODEL_LDA, doc_offset, n_docs, 1, &lp, &ls, moments, stream);
+    if (rc != BRNG_OK) return rc;
+  }
+  return BRNG_OK;
 }
 
 }  // namespace
 
 extern "C" {
+
+int brng_lda_index(uint32_t n_docs, const uint32_t* doc_ptr, const uint32_t* words, uint32_t* prev,
+                   brng_stream_t stream) {
+  if (n_docs == 0) return BRNG_OK;
+  if (!doc_ptr || !words || !prev) return BRNG_EINVAL;
+  return cuda_status(brng::launch_lda_index(n_docs, doc_ptr, words, prev, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int brng_lda_apply(uint32_t K, uint32_t V, int32_t* nkw, int32_t* nk, int32_t* dnkw, brng_stream_t stream) {
+  if (K == 0 || K > 128 || V == 0 || !nkw || !nk || !dnkw) return BRNG_EINVAL;
+  return cuda_status(brng::launch_lda_apply(K, V, nkw, nk, dnkw, reinterpret_cast<cudaStream_t>(stream)));
+}
 
 int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_t n_chains,
                    uint32_t n_sweeps, const void* params, void* state, double* moments,
@@ -502,6 +574,9 @@ int brng_gibbs_run(brng_t* h, brng_model_t model, uint64_t chain_offset, uint32_
   const brng::TraceRange trace("brng_gibbs_run");
   if (!h) return BRNG_EINVAL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (model == BRNG_MODEL_LDA_FULL)
+    return lda_full_run(h, chain_offset, n_chains, n_sweeps, static_cast<const brng_lda_full_params_t*>(params),
+                        static_cast<const brng_lda_full_state_t*>(state), moments, stream);
   if (n_chains == 0) return BRNG_OK;
   brng::BatchJob j;
   const int rc = make_job(h, model, h->rk, chain_offset, n_chains, n_sweeps, params, state, moments, &j);

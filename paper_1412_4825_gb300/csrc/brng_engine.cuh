@@ -24,6 +24,7 @@ constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
 constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 
 constexpr uint32_t kDomU = 0, kDomN = 1, kDomE = 2, kDomData = 3, kDomU64 = 4;
+constexpr uint32_t kDomZ = 5;  // the full LDA step's topic draws
 
 // Round keys (k0 + r W0, k1 + r W1), r = 0..9.
 struct RoundKeys {

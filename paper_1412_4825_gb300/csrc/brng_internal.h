@@ -133,6 +133,29 @@ cudaError_t launch_normal_gamma_pc(const NormalGammaArgs& a, uint32_t Wc, uint32
 size_t normal_gamma_bytes_per_warp(uint32_t B);     // shared memory per warp (inline rings)
 size_t normal_gamma_pc_bytes_per_warp(uint32_t B);  // shared memory per consumer warp
 
+// ---- full LDA step: topic draws per token (brng_lda_full.cu) ----
+struct LdaZArgs {
+  RoundKeys rk;
+  uint64_t doc_offset;       // global id of document 0 (its Z stream id)
+  uint32_t n_docs, K, V;
+  float alpha, beta, vbeta;  // vbeta = float(V) * beta, rounded once on the host
+  const uint32_t* doc_ptr;   // [n_docs + 1]
+  const uint32_t* words;     // [tokens]
+  const uint32_t* prev;      // [tokens]
+  uint8_t* z;                // [tokens]
+  uint8_t* z_start;          // [tokens]
+  int32_t* ndk;              // [n_docs][K]
+  const int32_t* nkw;        // [V][K] snapshot
+  const int32_t* nk;         // [K] snapshot
+  int32_t* dnkw;             // [V*K + K] changes
+  float* dir_alpha;          // [n_docs][K]
+  uint64_t* zpos;            // [n_docs]
+};
+cudaError_t launch_lda_index(uint32_t n_docs, const uint32_t* doc_ptr, const uint32_t* words, uint32_t* prev,
+                             cudaStream_t st);
+cudaError_t launch_lda_z(const LdaZArgs& a, cudaStream_t st);
+cudaError_t launch_lda_apply(uint32_t K, uint32_t V, int32_t* nkw, int32_t* nk, int32_t* dnkw, cudaStream_t st);
+
 // ---- batched persistent kernel (brng_batch.cu) ----
 struct BatchJob {
   uint32_t model;       // brng_model_t

@@ -1,0 +1,264 @@
+// brng_lda_full.cu -- the full LDA Gibbs step's topic draws (Sec. 1, the LDA
+// paragraph: the Dirichlet parameters of the document-topic draw change every
+// iteration because the topic assignments do).  One warp per document.
+//
+// Per token t of document d (word w, current topic zo), in token order:
+//   weights   w_k = ((float(n_dk') + alpha) * (float(n_kw') + beta)) * inv_k,
+//             inv_k = 1 / (float(n_k') + V beta), ' = without token t;
+//             n_kw', n_k' = the sweep's snapshot plus the document's own
+//             changes so far (for n_kw of word w: the earlier tokens of the
+//             document with word w, reached through the prev links);
+//             every operation IEEE round-to-nearest FP32 (no contraction),
+//             so that the oracle, doing the same operations, gets the same
+//             bits;
+//   integers  q_k = trunc(w_k 2^(31 - e)), 2^e <= max w < 2^(e+1);
+//   draw      the smallest k with C_k > (r Q) >> 24, C the inclusive sums of
+//             q, Q = C_(K-1), r = top 24 bits of the document's next Z word:
+//             exact integer arithmetic, so the choice is the oracle's.
+// Lane l holds topics l, l + 32, ... (KP = ceil(K / 32) per lane): its
+// document-topic counts, its topic totals and their two reciprocals (with and
+// without the token itself) live in registers; a reciprocal is recomputed only
+// when its topic's total changes.  The word's snapshot row is loaded one token
+// ahead, so its latency overlaps the current draw.  The Z words come from
+// 32 Philox blocks at a time, one per lane, into the warp's 128-word buffer.
+// The document's count changes go to dnkw (word-topic, two atomic adds per
+// changed token) and, at the end, dnk; the snapshot is never written.
+#include <cuda_runtime.h>
+
+#include "brng_internal.h"
+#include "brng_ring.cuh"
+
+namespace brng {
+
+constexpr uint32_t kLdaNone = BRNG_LDA_NONE;
+constexpr uint32_t kLdaWarps = 4;  // warps (documents) per block
+
+__global__ void __launch_bounds__(32 * kLdaWarps) lda_index_kernel(uint32_t n_docs,
+                                                                   const uint32_t* __restrict__ doc_ptr,
+                                                                   const uint32_t* __restrict__ words,
+                                                                   uint32_t* __restrict__ prev) {
+  const uint32_t d = blockIdx.x * kLdaWarps + (threadIdx.x >> 5);
+  if (d >= n_docs) return;
+  const uint32_t t0 = doc_ptr[d], t1 = doc_ptr[d + 1];
+  for (uint32_t t = t0 + lane_id(); t < t1; t += 32) {
+    const uint32_t w = words[t];
+    uint32_t p = kLdaNone;
+    for (uint32_t j = t; j > t0; --j) {
+      if (words[j - 1] == w) {
+        p = j - 1;
+        break;
+      }
+    }
+    prev[t] = p;
+  }
+}
+
+__device__ __forceinline__ uint64_t shfl_up_u64(uint64_t v, unsigned off) {
+  const uint32_t lo = __shfl_up_sync(kFull, static_cast<uint32_t>(v), off);
+  const uint32_t hi = __shfl_up_sync(kFull, static_cast<uint32_t>(v >> 32), off);
+  return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+
+__device__ __forceinline__ float lda_inv(int32_t n, float vbeta) {
+  return __frcp_rn(__fadd_rn(__int2float_rn(n), vbeta));
+}
+
+template <int KP>
+__global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a) {
+  __shared__ uint32_t zbuf[kLdaWarps][128];
+  const uint32_t wid = threadIdx.x >> 5;
+  const uint32_t d = blockIdx.x * kLdaWarps + wid;
+  if (d >= a.n_docs) return;  // whole warp
+  uint32_t* zw = zbuf[wid];
+  const uint32_t lane = lane_id();
+  const uint32_t K = a.K;
+  const uint32_t t0 = __ldg(a.doc_ptr + d), t1 = __ldg(a.doc_ptr + d + 1);
+  const uint32_t stream = static_cast<uint32_t>(a.doc_offset + d);
+  const uint2 sh = philox_stream_half(kDomZ, stream, a.rk);
+
+  int32_t nd[KP], nks[KP], own[KP];
+  float inv_c[KP], inv_m[KP];
+#pragma unroll
+  for (int p = 0; p < KP; ++p) {
+    const uint32_t k = lane + 32u * p;
+    const bool on = k < K;
+    nd[p] = on ? a.ndk[static_cast<uint64_t>(d) * K + k] : 0;
+    nks[p] = on ? a.nk[k] : 0;
+    own[p] = 0;
+    inv_c[p] = lda_inv(nks[p], a.vbeta);
+    inv_m[p] = lda_inv(nks[p] - 1, a.vbeta);
+  }
+  const uint64_t zp0 = a.zpos[d];
+  uint64_t cb = 0;      // first Z element held by zw (a multiple of 4)
+  bool have = false;    // zw holds elements cb .. cb + 127
+
+  int32_t row[KP];
+#pragma unroll
+  for (int p = 0; p < KP; ++p) row[p] = 0;
+  uint32_t w = 0;
+  if (t0 < t1) {
+    w = __ldg(a.words + t0);
+#pragma unroll
+    for (int p = 0; p < KP; ++p) {
+      const uint32_t k = lane + 32u * p;
+      row[p] = k < K ? __ldg(a.nkw + static_cast<uint64_t>(w) * K + k) : 0;
+    }
+  }
+  for (uint32_t t = t0; t < t1; ++t) {
+    // the next token's word and snapshot row, independent of this draw
+    int32_t row_n[KP];
+#pragma unroll
+    for (int p = 0; p < KP; ++p) row_n[p] = 0;
+    uint32_t w_n = 0;
+    if (t + 1 < t1) {
+      w_n = __ldg(a.words + t + 1);
+#pragma unroll
+      for (int p = 0; p < KP; ++p) {
+        const uint32_t k = lane + 32u * p;
+        row_n[p] = k < K ? __ldg(a.nkw + static_cast<uint64_t>(w_n) * K + k) : 0;
+      }
+    }
+    const uint32_t zo = a.z[t];  // not yet redrawn in this sweep
+    // this draw's Z word (element zp0 + (t - t0) of the document's stream)
+    const uint64_t e = zp0 + (t - t0);
+    if (!have || e - cb >= 128u) {
+      cb = e & ~3ull;
+      have = true;
+      const uint4 v = philox_block_sh(cb / 4u + lane, sh, a.rk);
+      __syncwarp();
+      zw[4u * lane + 0u] = v.x;
+      zw[4u * lane + 1u] = v.y;
+      zw[4u * lane + 2u] = v.z;
+      zw[4u * lane + 3u] = v.w;
+      __syncwarp();
+    }
+    const uint32_t r24 = zw[static_cast<uint32_t>(e - cb)] >> 8;
+    // the document's own changes of this word's counts in this sweep
+    int32_t ow[KP];
+#pragma unroll
+    for (int p = 0; p < KP; ++p) ow[p] = 0;
+    for (uint32_t j = __ldg(a.prev + t); j != kLdaNone; j = __ldg(a.prev + j)) {
+      const uint32_t zs = __ldcg(a.z_start + j), zc = __ldcg(a.z + j);
+      if (zs != zc) {
+#pragma unroll
+        for (int p = 0; p < KP; ++p) {
+          const uint32_t k = lane + 32u * p;
+          ow[p] += (k == zc ? 1 : 0) - (k == zs ? 1 : 0);
+        }
+      }
+    }
+    // FP32 weights, their maximum, integer weights, inclusive sums
+    float wk[KP];
+    float m = 0.0f;
+#pragma unroll
+    for (int p = 0; p < KP; ++p) {
+      const uint32_t k = lane + 32u * p;
+      const int32_t self = k == zo ? 1 : 0;
+      const float x = __fadd_rn(__int2float_rn(nd[p] - self), a.alpha);
+      const float y = __fadd_rn(__int2float_rn(row[p] + ow[p] - self), a.beta);
+      wk[p] = k < K ? __fmul_rn(__fmul_rn(x, y), self ? inv_m[p] : inv_c[p]) : 0.0f;
+      m = fmaxf(m, wk[p]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, off));
+    const uint32_t ef = (__float_as_uint(m) >> 23) & 0xFFu;
+    const float scale = __uint_as_float((285u - ef) << 23);
+    uint64_t c[KP];
+    uint64_t base = 0;
+#pragma unroll
+    for (int p = 0; p < KP; ++p) {
+      uint64_t v = __float2uint_rz(__fmul_rn(wk[p], scale));
+#pragma unroll
+      for (unsigned off = 1; off < 32; off <<= 1) {
+        const uint64_t u = shfl_up_u64(v, off);
+        if (lane >= off) v += u;
+      }
+      c[p] = base + v;
+      base += shfl_u64(v, 31);
+    }
+    const uint64_t tt = (static_cast<uint64_t>(r24) * base) >> 24;
+    uint32_t zn = 0;
+#pragma unroll
+    for (int p = 0; p < KP; ++p) zn += __popc(__ballot_sync(kFull, lane + 32u * p < K && c[p] <= tt));
+    if (zn != zo) {
+#pragma unroll
+      for (int p = 0; p < KP; ++p) {
+        const uint32_t k = lane + 32u * p;
+        const int32_t dlt = (k == zn ? 1 : 0) - (k == zo ? 1 : 0);
+        if (dlt != 0) {
+          nd[p] += dlt;
+          own[p] += dlt;
+          inv_c[p] = lda_inv(nks[p] + own[p], a.vbeta);
+          inv_m[p] = lda_inv(nks[p] + own[p] - 1, a.vbeta);
+        }
+      }
+      if (lane == 0) {
+        atomicAdd(a.dnkw + static_cast<uint64_t>(w) * K + zo, -1);
+        atomicAdd(a.dnkw + static_cast<uint64_t>(w) * K + zn, 1);
+      }
+    }
+    if (lane == 0) {
+      a.z_start[t] = static_cast<uint8_t>(zo);
+      a.z[t] = static_cast<uint8_t>(zn);
+    }
+    __syncwarp();  // this token's z and z_start are visible to the next tokens' walks
+    w = w_n;
+#pragma unroll
+    for (int p = 0; p < KP; ++p) row[p] = row_n[p];
+  }
+  if (lane == 0) a.zpos[d] = zp0 + (t1 - t0);
+#pragma unroll
+  for (int p = 0; p < KP; ++p) {
+    const uint32_t k = lane + 32u * p;
+    if (k < K) {
+      a.ndk[static_cast<uint64_t>(d) * K + k] = nd[p];
+      a.dir_alpha[static_cast<uint64_t>(d) * K + k] = __fadd_rn(a.alpha, __int2float_rn(nd[p]));
+      if (own[p] != 0) atomicAdd(a.dnkw + static_cast<uint64_t>(a.V) * K + k, own[p]);
+    }
+  }
+}
+
+__global__ void lda_apply_kernel(uint64_t n_kw, uint32_t K, int32_t* __restrict__ nkw, int32_t* __restrict__ nk,
+                                 int32_t* __restrict__ dnkw) {
+  const uint64_t total = n_kw + K;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const int32_t v = dnkw[i];
+    if (v != 0) {
+      if (i < n_kw) nkw[i] += v;
+      else nk[i - n_kw] += v;
+      dnkw[i] = 0;
+    }
+  }
+}
+
+cudaError_t launch_lda_index(uint32_t n_docs, const uint32_t* doc_ptr, const uint32_t* words, uint32_t* prev,
+                             cudaStream_t st) {
+  if (n_docs == 0) return cudaSuccess;
+  lda_index_kernel<<<(n_docs + kLdaWarps - 1) / kLdaWarps, 32 * kLdaWarps, 0, st>>>(n_docs, doc_ptr, words, prev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lda_z(const LdaZArgs& a, cudaStream_t st) {
+  if (a.n_docs == 0) return cudaSuccess;
+  const uint32_t blocks = (a.n_docs + kLdaWarps - 1) / kLdaWarps;
+  if (a.K <= 32) lda_z_kernel<1><<<blocks, 32 * kLdaWarps, 0, st>>>(a);
+  else if (a.K <= 64) lda_z_kernel<2><<<blocks, 32 * kLdaWarps, 0, st>>>(a);
+  else if (a.K <= 128) lda_z_kernel<4><<<blocks, 32 * kLdaWarps, 0, st>>>(a);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lda_apply(uint32_t K, uint32_t V, int32_t* nkw, int32_t* nk, int32_t* dnkw, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t total = static_cast<uint64_t>(V) * K + K;
+  uint64_t blocks = (total + 255) / 256;
+  if (blocks > static_cast<uint64_t>(sms) * 8) blocks = static_cast<uint64_t>(sms) * 8;
+  lda_apply_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(static_cast<uint64_t>(V) * K, K, nkw, nk, dnkw);
+  return cudaGetLastError();
+}
+
+}  // namespace brng
