@@ -241,6 +241,9 @@ def extras(dev, stream, peaks, args):
     out["lda_16384x64x500"].update(philox_roofline(run_lda, lambda: pos.cpu().numpy().astype(np.uint64), 4.0, t))
     h.close()
     del a, theta, pos, mom
+    # -- full LDA step: topic draw per token (collapsed conditional), count
+    # exchange, theta ~ Dir(alpha + n_d); the same corpus size, 20 sweeps
+    out["lda_full_16384x64"] = lda_full_extra(B, inputs, dev, stream, sweeps=20)
     # -- mixed varying-parameter stream, 17 B per draw through HBM
     n, S = 1 << 28, 1 << 20
     tag, p0, p1 = inputs.mixed_stream_torch(n, seed=SEED, device=dev)
@@ -497,6 +500,32 @@ def extras(dev, stream, peaks, args):
     return out
 
 
+def lda_full_extra(B, inputs, dev, stream, sweeps=20, n_docs=16384):
+    """The full LDA step on the synthetic corpus (K = 64, V = 4,096, lengths
+    U{50..500}): token topic updates per second over `sweeps` sweeps in one
+    call (3 launches per sweep), and the z kernel's share."""
+    import torch
+    corpus = inputs.lda_corpus(n_docs, K=64, V=4096, seed=SEED)
+    st = inputs.lda_initial_state(corpus, seed=7)
+    m = B.LdaFull(corpus, st, alpha=0.1, beta=0.01, stream=stream)
+    h = B.Handle(SEED, 1)
+    n_tok = int(corpus["doc_ptr"][-1])
+    run = lambda: m.run(h, sweeps, stream=stream)  # noqa: E731
+    t = _time_s(run, stream, reps=2, warm=1)
+    # the topic draws alone, one sweep, with the changes left unapplied
+    lp = m.params(exchange=1)
+    ls = m.state()
+    zrun = lambda: B.brng_gibbs_run(h.h, B.MODEL_LDA_FULL, 0, n_docs, 1, lp, ls, m.mom, stream)  # noqa: E731
+    t1 = _time_s(zrun, stream, reps=3, warm=1)
+    B.brng_lda_apply(m.K, m.V, m.nkw, m.nk, m.dnkw, stream)
+    torch.cuda.synchronize()
+    h.close()
+    return {"token_updates_per_s": n_tok * sweeps / t, "dirichlet_updates_per_s": n_docs * sweeps / t,
+            "ms_per_sweep": t * 1e3 / sweeps, "tokens": n_tok, "sweeps": sweeps,
+            "ms_one_sweep_without_apply": t1 * 1e3,
+            "corpus": "%d docs, K=64, V=4096, lengths U{50..500}, LDA generative model" % n_docs}
+
+
 def philox_probe(B, dev, stream):
     """Measured integer-pipe peak: Philox4x32-10 blocks per second of a
     register-only kernel (8 blocks of 256 threads per SM, 2,048 blocks per
@@ -739,6 +768,12 @@ def run_case(args):
         fn = lambda: B.brng_gibbs_run(h.h, B.MODEL_NORMAL_GAMMA, 0, args.chains, args.sweeps, prm, st, mom,  # noqa: E731
                                       stream)
         info.update(chains=args.chains, sweeps=args.sweeps)
+    elif args.case == "lda_full":  # the full LDA step, one call of `sweeps` sweeps
+        corpus = inputs.lda_corpus(args.docs, K=64, V=4096, seed=SEED)
+        m = B.LdaFull(corpus, inputs.lda_initial_state(corpus, seed=7), stream=stream)
+        h = B.Handle(SEED, 1)
+        fn = lambda: m.run(h, args.sweeps, stream=stream)  # noqa: E731
+        info.update(docs=args.docs, sweeps=args.sweeps, tokens=int(corpus["doc_ptr"][-1]))
     elif args.case == "triangle":
         h = B.Handle(SEED, 1)
         h.tune(buf_len=256, lanes_per_chain=16)
@@ -787,14 +822,14 @@ def main():
                     help="skip the secondary workloads (triangle, LDA, mixed stream, batched vs plain, served mix)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="arrival window of the served mix at 2,000 jobs/s")
-    ap.add_argument("--case", choices=["mixed", "lda", "triangle", "uniform64", "ng"], default=None,
+    ap.add_argument("--case", choices=["mixed", "lda", "triangle", "uniform64", "ng", "lda_full"], default=None,
                     help="time one workload at a chosen size instead (profiling): mixed, lda, triangle, "
                          "uniform64, or ng (the headline normal-gamma model)")
     ap.add_argument("--log2n", type=int, default=28, help="--case mixed / uniform64: log2 of the draws")
     ap.add_argument("--log2s", type=int, default=20, help="--case mixed / uniform64: log2 of the streams")
-    ap.add_argument("--docs", type=int, default=16384, help="--case lda: documents")
+    ap.add_argument("--docs", type=int, default=16384, help="--case lda / lda_full: documents")
     ap.add_argument("--chains", type=int, default=N_CHAINS, help="--case ng: chains")
-    ap.add_argument("--sweeps", type=int, default=500, help="--case lda/triangle/ng: sweeps")
+    ap.add_argument("--sweeps", type=int, default=500, help="--case lda/triangle/ng/lda_full: sweeps")
     args = ap.parse_args()
     if args.case:
         return run_case(args)

@@ -341,7 +341,8 @@ typedef struct {
  *   distributed sampler of Newman et al., JMLR 2009, one document per worker;
  *   exact sequential collapsed Gibbs for a one-document corpus); the weights
  *   are FP32 in a fixed operation order, made integers (q_k = trunc(w_k
- *   2^(31-e)), 2^e <= max w < 2^(e+1)) and the topic is the smallest k whose
+ *   2^(b-1-e)), 2^e <= max w < 2^(e+1), b = 32 - ceil(log2 K)) and the topic
+ *   is the smallest k whose
  *   cumulative q exceeds (r Q) >> 24, r the top 24 bits of the document's
  *   next Z-domain word; (2) theta_d ~ Dirichlet(alpha + n_d) exactly as the
  *   LDA model (alpha + n_dk formed in FP32; component k on stream

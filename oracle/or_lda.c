@@ -26,9 +26,10 @@
  *     inv_k = 1 / (float(n_k') + Vbeta),  Vbeta = float(V) * beta,
  *     w_k = ((float(n_dk') + alpha) * (float(n_kw') + beta)) * inv_k,
  * each operation rounded to FP32 in this order; the weights are then made
- * integers q_k = trunc(w_k 2^(31 - e)), with 2^e <= max_k w_k < 2^(e+1) (so
- * q_k < 2^32), and the topic is the smallest k whose integer cumulative sum
- * C_k exceeds floor(r Q / 2^24), Q = C_(K-1), r = the top 24 bits of the
+ * integers q_k = trunc(w_k 2^(b - 1 - e)), with 2^e <= max_k w_k < 2^(e+1)
+ * and b = 32 - ceil(log2 K) bits per weight (so q_k < 2^b and the K weights
+ * sum below 2^32), and the topic is the smallest k whose integer cumulative
+ * sum C_k exceeds floor(r Q / 2^24), Q = C_(K-1), r = the top 24 bits of the
  * token's word from the document's Z-domain stream (domain 5, stream = global
  * document id, one element per token draw).  Everything after the weights is
  * exact integer arithmetic.
@@ -66,9 +67,13 @@ void or_lda_weights(uint32_t K, float alpha, float beta, float vbeta, const int3
     w_out[k] = w;
     if (w > m) m = w;
   }
-  /* 2^e <= m < 2^(e+1) with e = exponent field - 127; scale = 2^(31 - e) */
+  /* 2^e <= m < 2^(e+1) with e = exponent field - 127; b = 32 - ceil(log2 K);
+   * scale = 2^(b - 1 - e), exponent field 127 + b - 1 - e = 253 + b - field */
+  uint32_t lg = 0;
+  while ((1u << lg) < K) ++lg;
+  uint32_t b = 32u - lg;
   uint32_t ef = (bits_of_f32(m) >> 23) & 0xFFu;
-  float scale = f32_of_bits((285u - ef) << 23);
+  float scale = f32_of_bits((253u + b - ef) << 23);
   for (uint32_t k = 0; k < K; ++k) q_out[k] = (uint32_t)(w_out[k] * scale);
 }
 

@@ -522,6 +522,9 @@ int lda_full_run(brng_t* h, uint64_t doc_offset, uint32_t n_docs, uint32_t n_swe
   a.alpha = p->alpha;
   a.beta = p->beta;
   a.vbeta = static_cast<float>(p->V) * p->beta;  // one FP32 rounding, as the oracle
+  uint32_t lg = 0;
+  while ((1u << lg) < p->K) ++lg;
+  a.qbits = 32u - lg;
   a.doc_ptr = p->doc_ptr;
   a.words = p->words;
   a.prev = p->prev;

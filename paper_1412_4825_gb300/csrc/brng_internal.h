@@ -139,6 +139,7 @@ struct LdaZArgs {
   uint64_t doc_offset;       // global id of document 0 (its Z stream id)
   uint32_t n_docs, K, V;
   float alpha, beta, vbeta;  // vbeta = float(V) * beta, rounded once on the host
+  uint32_t qbits;            // bits per integer weight: 32 - ceil(log2 K)
   const uint32_t* doc_ptr;   // [n_docs + 1]
   const uint32_t* words;     // [tokens]
   const uint32_t* prev;      // [tokens]

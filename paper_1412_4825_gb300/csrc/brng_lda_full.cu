@@ -11,10 +11,12 @@
 //             every operation IEEE round-to-nearest FP32 (no contraction),
 //             so that the oracle, doing the same operations, gets the same
 //             bits;
-//   integers  q_k = trunc(w_k 2^(31 - e)), 2^e <= max w < 2^(e+1);
+//   integers  q_k = trunc(w_k 2^(b - 1 - e)), 2^e <= max w < 2^(e+1),
+//             b = 32 - ceil(log2 K), so that the K weights sum below 2^32;
 //   draw      the smallest k with C_k > (r Q) >> 24, C the inclusive sums of
-//             q, Q = C_(K-1), r = top 24 bits of the document's next Z word:
-//             exact integer arithmetic, so the choice is the oracle's.
+//             q (32-bit warp scan), Q = C_(K-1), r = top 24 bits of the
+//             document's next Z word: exact integer arithmetic, so the choice
+//             is the oracle's.
 // Lane l holds topics l, l + 32, ... (KP = ceil(K / 32) per lane): its
 // document-topic counts, its topic totals and their two reciprocals (with and
 // without the token itself) live in registers; a reciprocal is recomputed only
@@ -31,7 +33,7 @@
 namespace brng {
 
 constexpr uint32_t kLdaNone = BRNG_LDA_NONE;
-constexpr uint32_t kLdaWarps = 4;  // warps (documents) per block
+constexpr uint32_t kLdaWarps = 1;  // warps (documents) per block: one, so that a block retires with its document (lengths vary 10x)
 
 __global__ void __launch_bounds__(32 * kLdaWarps) lda_index_kernel(uint32_t n_docs,
                                                                    const uint32_t* __restrict__ doc_ptr,
@@ -51,12 +53,6 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_index_kernel(uint32_t n_do
     }
     prev[t] = p;
   }
-}
-
-__device__ __forceinline__ uint64_t shfl_up_u64(uint64_t v, unsigned off) {
-  const uint32_t lo = __shfl_up_sync(kFull, static_cast<uint32_t>(v), off);
-  const uint32_t hi = __shfl_up_sync(kFull, static_cast<uint32_t>(v >> 32), off);
-  return (static_cast<uint64_t>(hi) << 32) | lo;
 }
 
 __device__ __forceinline__ float lda_inv(int32_t n, float vbeta) {
@@ -162,21 +158,21 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, off));
     const uint32_t ef = (__float_as_uint(m) >> 23) & 0xFFu;
-    const float scale = __uint_as_float((285u - ef) << 23);
-    uint64_t c[KP];
-    uint64_t base = 0;
+    const float scale = __uint_as_float((253u + a.qbits - ef) << 23);
+    uint32_t c[KP];
+    uint32_t base = 0;
 #pragma unroll
     for (int p = 0; p < KP; ++p) {
-      uint64_t v = __float2uint_rz(__fmul_rn(wk[p], scale));
+      uint32_t v = __float2uint_rz(__fmul_rn(wk[p], scale));
 #pragma unroll
       for (unsigned off = 1; off < 32; off <<= 1) {
-        const uint64_t u = shfl_up_u64(v, off);
+        const uint32_t u = __shfl_up_sync(kFull, v, off);
         if (lane >= off) v += u;
       }
       c[p] = base + v;
-      base += shfl_u64(v, 31);
+      base += __shfl_sync(kFull, v, 31);
     }
-    const uint64_t tt = (static_cast<uint64_t>(r24) * base) >> 24;
+    const uint32_t tt = static_cast<uint32_t>((static_cast<uint64_t>(r24) * base) >> 24);
     uint32_t zn = 0;
 #pragma unroll
     for (int p = 0; p < KP; ++p) zn += __popc(__ballot_sync(kFull, lane + 32u * p < K && c[p] <= tt));

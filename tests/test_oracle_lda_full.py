@@ -67,7 +67,7 @@ def test_weights_equal_conditional_from_joint(oracle, case):
         wn = w.astype(np.float64) / w.astype(np.float64).sum()
         assert np.allclose(wn, p, rtol=1e-5, atol=0), (t, wn, p)
         qn = q.astype(np.float64) / q.astype(np.float64).sum()
-        assert np.allclose(qn, p, rtol=1e-5, atol=2.0 ** -28)
+        assert np.allclose(qn, p, rtol=1e-5, atol=2.0 ** -24)
 
 
 def test_pick_inverts_integer_cdf_exactly(oracle):
