@@ -20,9 +20,9 @@ from . import build as _build
 DOM_U, DOM_N, DOM_E, DOM_DATA, DOM_U64 = 0, 1, 2, 3, 4
 OK, EINVAL, EDOMAIN, EREJECT = 0, 1, 4, 5
 GAMMA_MAX_ATTEMPTS = 64
-POISSON_MAX_LAMBDA = 64.0
+POISSON_MAX_LAMBDA = 1e7
 POISSON_MAX_K = 1024
-BINOMIAL_MAX_MEAN = 64.0
+INVERSION_MAX_MEAN = 64.0  # Poisson / Binomial means above this: PTRS / BTRD
 
 _lib = None
 
@@ -46,6 +46,8 @@ def lib():
         L.or_poisson.restype = i32
         L.or_binomial_inv.argtypes = [dbl, dbl, dbl]
         L.or_binomial_inv.restype = dbl
+        L.or_lfact.argtypes = [dbl]
+        L.or_lfact.restype = dbl
         L.or_binomial.argtypes = [u64, u32, vp, u64, vp, vp, vp, vp, u32]
         L.or_binomial.restype = i32
         L.or_sincospi_many.argtypes = [u64, vp, vp, vp]
@@ -217,6 +219,10 @@ def weibull(seed, S, shape, scale, pos=None, buf_len=64, with_cond=False):
 
 def poisson(seed, S, lam, pos=None, buf_len=64):
     return _bulk("or_poisson", seed, S, pos, len(lam), [lam], buf_len)
+
+
+def lfact(k):
+    return lib().or_lfact(float(k))
 
 
 def binomial_inv(n, p, u):

@@ -198,17 +198,29 @@ static double draw_tagged(or_batchrng *g, unsigned tag, float p0, float p1, uint
       kappa = fabs(log(e) / (double)p0);
     } else ++*n_domain;
     break;
-  case 6: /* Poisson(lambda) by inversion of one U */
+  case 6: /* Poisson(lambda): inversion of one U for small means, else PTRS */
     if (finite_f(p0) && p0 > 0.0f && p0 <= OR_POISSON_MAX_LAMBDA) {
-      double u = or_get_uniform(g, &w);
-      out = or_poisson_inv((double)p0, u);
+      if (p0 <= OR_INVERSION_MAX_MEAN) {
+        double u = or_get_uniform(g, &w);
+        out = or_poisson_inv((double)p0, u);
+      } else {
+        int rej = 0;
+        out = or_poisson_ptrs(g, (double)p0, &w, &rej);
+        if (rej) ++*n_reject;
+      }
     } else ++*n_domain;
     break;
-  case 7: /* Binomial(n, p) by inversion of one U */
+  case 7: /* Binomial(n, p): inversion of one U for small means, else BTRD */
     if (finite_f(p0) && p0 >= 0.0f && p0 == floorf(p0) && p0 <= 16777216.0f && finite_f(p1) &&
-        p1 >= 0.0f && p1 <= 1.0f && (double)p0 * fmin((double)p1, 1.0 - (double)p1) <= OR_BINOMIAL_MAX_MEAN) {
-      double u = or_get_uniform(g, &w);
-      out = or_binomial_inv((double)p0, (double)p1, u);
+        p1 >= 0.0f && p1 <= 1.0f) {
+      if ((double)p0 * fmin((double)p1, 1.0 - (double)p1) <= OR_INVERSION_MAX_MEAN) {
+        double u = or_get_uniform(g, &w);
+        out = or_binomial_inv((double)p0, (double)p1, u);
+      } else {
+        int rej = 0;
+        out = or_binomial_btrd(g, (double)p0, (double)p1, &w, &rej);
+        if (rej) ++*n_reject;
+      }
     } else ++*n_domain;
     break;
   default:
@@ -217,6 +229,142 @@ static double draw_tagged(or_batchrng *g, unsigned tag, float p0, float p1, uint
   if (word) *word = w;
   if (cond) *cond = kappa;
   return out;
+}
+
+/* ---- large means: transformed rejection (Hormann 1993) ----------------- */
+/*
+ * Both samplers run in FP64 with the oracle's own log (or_log), IEEE sqrt,
+ * floor and division, every operation in the order written and without
+ * contraction; ln k! comes from or_lfact.  A sampler that runs out of
+ * attempts (64, as the Gamma sampler; never seen) gives NaN.
+ */
+
+#define OR_HALF_LOG_2PI 0x1.d67f1c864beb5p-1 /* ln(2 pi) / 2 */
+
+/* Stirling's series of ln Gamma(x), x >= 17, to the x^-7 term (the next term,
+ * 1/(1188 x^9), is below 1e-14): (x - 1/2) ln x - x + ln(2 pi)/2
+ * + 1/(12x) - 1/(360x^3) + 1/(1260x^5) - 1/(1680x^7). */
+static double or_stirling_tail(double x) {
+  const double inv = 1.0 / x;
+  const double inv2 = inv * inv;
+  return inv * (1.0 / 12.0 - inv2 * (1.0 / 360.0 - inv2 * (1.0 / 1260.0 - inv2 * (1.0 / 1680.0))));
+}
+
+/* ln k! for an integer k >= 0: the log of the exact product for k <= 15
+ * (15! < 2^53), Stirling's series of ln Gamma(k + 1) above */
+double or_lfact(double k) {
+  if (k <= 15.0) {
+    double f = 1.0;
+    for (double i = 2.0; i <= k; i += 1.0) f = f * i;
+    return or_log(f);
+  }
+  const double x = k + 1.0;
+  return ((x - 0.5) * or_log(x) - x) + (OR_HALF_LOG_2PI + or_stirling_tail(x));
+}
+
+/* f_c(k) = ln k! - (k + 1/2) ln(k + 1) + (k + 1) - ln(2 pi)/2, the correction
+ * term of Stirling's formula that BTRD uses */
+static double or_stirling_fc(double k) {
+  if (k <= 15.0) {
+    const double x = k + 1.0;
+    return ((or_lfact(k) - (k + 0.5) * or_log(x)) + x) - OR_HALF_LOG_2PI;
+  }
+  return or_stirling_tail(k + 1.0);
+}
+
+/* PTRS for Poisson(lam), lam >= 10 (here > 64): per attempt U from the U
+ * domain [0, 1) (shifted by -1/2) and V = U' in (0, 1]; an attempt with
+ * 1/2 - |U| = 0 is rejected (the transformation is unbounded there). */
+double or_poisson_ptrs(or_batchrng *g, double lam, uint32_t *word, int *rejected) {
+  const double slam = sqrt(lam);
+  const double loglam = or_log(lam);
+  const double b = 0.931 + 2.53 * slam;
+  const double a = -0.059 + 0.02483 * b;
+  const double inv_alpha = 1.1239 + 1.1328 / (b - 3.4);
+  const double vr = 0.9277 - 3.6224 / (b - 2.0);
+  for (int attempt = 0; attempt < OR_GAMMA_MAX_ATTEMPTS; ++attempt) {
+    uint32_t w0;
+    const double u = or_get_uniform(g, &w0) - 0.5;
+    const double v = or_get_uniform_open(g);
+    if (attempt == 0 && word) *word = w0;
+    const double us = 0.5 - fabs(u);
+    if (us == 0.0) continue;
+    const double k = floor(((2.0 * a) / us + b) * u + lam + 0.43);
+    if (us >= 0.07 && v <= vr) return k;
+    if (k < 0.0 || (us < 0.013 && v > us)) continue;
+    if ((or_log(v) + or_log(inv_alpha)) - or_log(a / (us * us) + b) <= ((-lam) + k * loglam) - or_lfact(k))
+      return k;
+  }
+  *rejected = 1;
+  return NAN;
+}
+
+/* BTRD for Binomial(n, p), n min(p, 1 - p) >= 10 (here > 64), on
+ * p' = min(p, 1 - p) (n - k when p > 1/2).  Per attempt V = U' in (0, 1];
+ * unless V <= 0.86 v_r, one more element: U from [0, 1) (shifted by -1/2)
+ * when V >= v_r, else V' = U' v_r. */
+double or_binomial_btrd(or_batchrng *g, double n, double p_in, uint32_t *word, int *rejected) {
+  const int flip = p_in > 0.5;
+  const double p = flip ? 1.0 - p_in : p_in;
+  const double q = 1.0 - p;
+  const double m = floor((n + 1.0) * p);
+  const double r = p / q;
+  const double nr = (n + 1.0) * r;
+  const double npq = (n * p) * q;
+  const double spq = sqrt(npq);
+  const double b = 1.15 + 2.53 * spq;
+  const double a = (-0.0873 + 0.0248 * b) + 0.01 * p;
+  const double c = n * p + 0.5;
+  const double alpha = (2.83 + 5.1 / b) * spq;
+  const double vr = 0.92 - 4.2 / b;
+  const double urvr = 0.86 * vr;
+  for (int attempt = 0; attempt < OR_GAMMA_MAX_ATTEMPTS; ++attempt) {
+    uint32_t w0;
+    double v = or_get_uniform(g, &w0) + 0x1p-24; /* U' */
+    if (attempt == 0 && word) *word = w0;
+    double u, k;
+    if (v <= urvr) {
+      u = v / vr - 0.43;
+      k = floor(((2.0 * a) / (0.5 - fabs(u)) + b) * u + c);
+      return flip ? n - k : k;
+    }
+    if (v >= vr) {
+      u = or_get_uniform(g, NULL) - 0.5;
+    } else {
+      u = v / vr - 0.93;
+      u = (u < 0.0 ? -0.5 : 0.5) - u;
+      v = or_get_uniform_open(g) * vr;
+    }
+    const double us = 0.5 - fabs(u);
+    if (us == 0.0) continue;
+    k = floor(((2.0 * a) / us + b) * u + c);
+    if (k < 0.0 || k > n) continue;
+    v = (v * alpha) / (a / (us * us) + b);
+    const double km = fabs(k - m);
+    if (km <= 15.0) { /* f(k)/f(m) by its recursion */
+      double f = 1.0;
+      if (m < k) {
+        for (double i = m + 1.0; i <= k; i += 1.0) f = f * (nr / i - r);
+      } else if (m > k) {
+        for (double i = k + 1.0; i <= m; i += 1.0) v = v * (nr / i - r);
+      }
+      if (v <= f) return flip ? n - k : k;
+      continue;
+    }
+    v = or_log(v); /* squeeze on the log scale */
+    const double rho = (km / npq) * (((km / 3.0 + 0.625) * km + 1.0 / 6.0) / npq + 0.5);
+    const double t = -(km * km) / (2.0 * npq);
+    if (v < t - rho) return flip ? n - k : k;
+    if (v > t + rho) continue;
+    const double nm = (n - m) + 1.0;
+    const double h = ((m + 0.5) * or_log((m + 1.0) / (r * nm)) + or_stirling_fc(m)) + or_stirling_fc(n - m);
+    const double nk = (n - k) + 1.0;
+    if (v <= (((h + (n + 1.0) * or_log(nm / nk)) + (k + 0.5) * or_log((nk * r) / (k + 1.0))) -
+              or_stirling_fc(k)) - or_stirling_fc(n - k))
+      return flip ? n - k : k;
+  }
+  *rejected = 1;
+  return NAN;
 }
 
 double or_poisson_inv(double lambda, double u) {

@@ -35,6 +35,8 @@ double or_get_exponential(or_batchrng *g, uint32_t *word);
 double or_get_u64(or_batchrng *g);
 double or_get_gamma(or_batchrng *g, float alpha, uint32_t *first_word, double *log_y,
                     int *rejected, double *cond);
+double or_poisson_ptrs(or_batchrng *g, double lam, uint32_t *word, int *rejected);
+double or_binomial_btrd(or_batchrng *g, double n, double p, uint32_t *word, int *rejected);
 void or_dirichlet_row(or_batchrng *comp, uint32_t K, const float *alpha, double *out,
                       double *l, double *cond, int *n_domain, int *n_reject);
 

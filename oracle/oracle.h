@@ -47,12 +47,13 @@ extern "C" {
 
 /* Marsaglia-Tsang attempts before a Gamma draw gives up (NaN + EREJECT) */
 #define OR_GAMMA_MAX_ATTEMPTS 64
-/* Poisson by inversion (sequential search, O(lambda) steps): 0 < lambda <= this */
-#define OR_POISSON_MAX_LAMBDA 64.0f
+/* Poisson: 0 < lambda <= this; inversion (sequential search, O(lambda) steps)
+ * up to OR_INVERSION_MAX_MEAN, transformed rejection (PTRS) above */
+#define OR_POISSON_MAX_LAMBDA 1e7f
+/* Poisson and Binomial means (n min(p, 1-p)) up to this: inversion of one U */
+#define OR_INVERSION_MAX_MEAN 64.0
 /* the search stops here at the latest (far beyond any 24-bit uniform's reach) */
 #define OR_POISSON_MAX_K 1024
-/* Binomial by inversion: integer 0 <= n <= 2^24, 0 <= p <= 1, n min(p, 1-p) <= this */
-#define OR_BINOMIAL_MAX_MEAN 64.0
 
 /* ---- core engine ------------------------------------------------------ */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -108,6 +109,8 @@ int or_poisson(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float
  * p_0 = exp(n log(1 - q)) (or_exp, or_log), p_k = (p_{k-1} ((n - k + 1) r)) / k,
  * r = q / (1 - q), all FP64; the draw is k, or n - k when p > 1/2 */
 double or_binomial_inv(double n, double p, double u);
+/* ln k! of an integer k >= 0 (exact product's log to 15!, Stirling above) */
+double or_lfact(double k);
 int or_binomial(uint64_t seed, uint32_t S, uint64_t *pos, uint64_t n, const float *trials,
                 const float *prob, double *out, uint32_t *words, uint32_t buf_len);
 /* tag 0 U(p0,p1), 1 N(p0,p1), 2 Exp(rate p0), 3 Gamma(p0), 4 Laplace(p0,p1),

@@ -470,7 +470,7 @@ def test_mixed_with_discrete_tags():
 
 
 def test_poisson_invalid_lambda():
-    lam = np.array([1.0, 0.0, -2.0, np.nan, np.inf, 64.5, 3.0], np.float32)
+    lam = np.array([1.0, 0.0, -2.0, np.nan, np.inf, 2.0e7, 3.0], np.float32)
     h = handle(2, 1)
     out, w = _run_bulk("poisson", h, [lam], lam.size)
     code, cnt = h.counters()
@@ -560,7 +560,7 @@ def test_normal_gamma_zero_sweeps():
 
 
 def test_binomial_invalid_parameters():
-    trials = np.array([10, 2.5, -1, np.nan, 10, 10, 10, 100000, 10], np.float32)
+    trials = np.array([10, 2.5, -1, np.nan, 10, 10, 10, 2.0e7, 10], np.float32)
     prob = np.array([0.5, 0.5, 0.5, 0.5, -0.1, 1.5, np.nan, 0.5, 0.25], np.float32)
     h = handle(2, 1)
     out, w = _run_bulk("binomial", h, [trials, prob], trials.size)

@@ -119,7 +119,7 @@ def test_special_cases_words_and_consumption():
 
 
 def test_invalid_parameters_consume_nothing():
-    n = np.array([10, 2.5, -1, np.nan, 10, 10, 10, 100000, 10], np.float32)
+    n = np.array([10, 2.5, -1, np.nan, 10, 10, 10, 2.0e7, 10], np.float32)
     p = np.array([0.5, 0.5, 0.5, 0.5, -0.1, 1.5, np.nan, 0.5, 0.25], np.float32)
     out, words, pos, st = O.binomial(2, 1, n, p)
     assert st == O.EDOMAIN
