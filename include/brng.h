@@ -71,8 +71,8 @@ enum { BRNG_DOMAIN_U = 0, BRNG_DOMAIN_N = 1, BRNG_DOMAIN_E = 2, BRNG_DOMAIN_DATA
 /* distribution tags of the mixed stream */
 enum { BRNG_TAG_UNIFORM = 0, BRNG_TAG_NORMAL = 1, BRNG_TAG_EXPONENTIAL = 2, BRNG_TAG_GAMMA = 3,
        BRNG_TAG_LAPLACE = 4, BRNG_TAG_WEIBULL = 5, BRNG_TAG_POISSON = 6, BRNG_TAG_BINOMIAL = 7 };
-#define BRNG_POISSON_MAX_LAMBDA 64.0f
-#define BRNG_BINOMIAL_MAX_MEAN 64.0f
+#define BRNG_POISSON_MAX_LAMBDA 1e7f      /* Poisson: 0 < lambda <= this                     */
+#define BRNG_INVERSION_MAX_MEAN 64.0f     /* discrete means up to this: inversion; above: rejection */
 
 /* Gibbs models */
 typedef enum {
@@ -222,9 +222,17 @@ int brng_weibull(brng_t *h, size_t n, const float *k, const float *lambda, float
  * p_0 = e^-lambda, p_k = p_{k-1} lambda / k (inversion by sequential search,
  * O(lambda) steps).  The search runs in FP32 and is redone in FP64 (own exp,
  * fixed operation order) when u lies within the FP32 error bound of a CDF
- * step, so every k equals the FP64 reference's.  out gets k as a float
- * (exact).  Needs finite 0 < lambda <= BRNG_POISSON_MAX_LAMBDA; FP64 redraws
- * count in n_recheck. */
+ * step, so every k equals the FP64 reference's.  That holds for
+ * lambda <= BRNG_INVERSION_MAX_MEAN; above it the draw is Hormann's transformed
+ * rejection PTRS (Insurance: Math. Econ. 12, 1993): per attempt U in [0, 1)
+ * and V = U' from the same buffer, k = floor((2a/u_s + b)(U - 1/2) + lambda +
+ * 0.43) with u_s = 1/2 - |U - 1/2|, a squeeze accept, and otherwise the test
+ * ln(V / alpha'(u_s)) <= k ln lambda - lambda - ln k!; computed in FP64 (own
+ * log, IEEE sqrt/division, Stirling's series for ln k!) so that every count
+ * equals the FP64 reference's.  out gets k as a float (exact).  Needs finite
+ * 0 < lambda <= BRNG_POISSON_MAX_LAMBDA; FP64 redraws of the inversion count in
+ * n_recheck; a rejection draw that runs out of attempts (64) is NaN and counts
+ * in n_reject. */
 int brng_poisson(brng_t *h, size_t n, const float *lambda, float *out, uint32_t *words,
                  brng_stream_t stream);
 /* Binomial(n, p), the second discrete distribution of the expanded library
@@ -233,9 +241,13 @@ int brng_poisson(brng_t *h, size_t n, const float *lambda, float *out, uint32_t 
  * from (1 - q)^n, p_k = p_{k-1} (n - k + 1) q / ((1 - q) k); the draw is k, or
  * n - k when p > 1/2.  FP32 search, redone in FP64 (own log and exp, fixed
  * operation order) near a CDF step, so every count equals the FP64
- * reference's.  trials: device float[n] holding integers 0 <= n <= 2^24;
- * prob: device float[n] in [0, 1]; needs n min(p, 1-p) <=
- * BRNG_BINOMIAL_MAX_MEAN (O(mean) search). */
+ * reference's.  Above n min(p, 1-p) = BRNG_INVERSION_MAX_MEAN the draw is
+ * Hormann's BTRD (J. Statist. Comput. Simul. 46, 1993) on min(p, 1-p): per
+ * attempt one U' (V), and unless V falls in the immediate-accept region one
+ * more element (U when V >= v_r, else V' = U' v_r), then the recursive
+ * evaluation of f(k)/f(m) for |k - m| <= 15 or a log-scale squeeze and the
+ * Stirling-corrected log test -- all in FP64 as the reference.  trials: device
+ * float[n] holding integers 0 <= n <= 2^24; prob: device float[n] in [0, 1]. */
 int brng_binomial(brng_t *h, size_t n, const float *trials, const float *prob, float *out,
                   uint32_t *words, brng_stream_t stream);
 /* Mixed stream: draw i is distribution tag[i] (BRNG_TAG_*) with parameters

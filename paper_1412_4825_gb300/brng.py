@@ -24,8 +24,8 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EDOMAIN", "EREJECT", "ETIMEO
                 "ENOTFOUND"]
 DOMAIN_U, DOMAIN_N, DOMAIN_E, DOMAIN_DATA, DOMAIN_U64, DOMAIN_Z = 0, 1, 2, 3, 4, 5
 TAG_UNIFORM, TAG_NORMAL, TAG_EXPONENTIAL, TAG_GAMMA, TAG_LAPLACE, TAG_WEIBULL, TAG_POISSON, TAG_BINOMIAL = range(8)
-POISSON_MAX_LAMBDA = 64.0
-BINOMIAL_MAX_MEAN = 64.0
+POISSON_MAX_LAMBDA = 1e7
+INVERSION_MAX_MEAN = 64.0
 MODEL_TRIANGLE, MODEL_NORMAL_GAMMA, MODEL_LDA, MODEL_LDA_FULL = 0, 1, 2, 3
 LDA_NONE = 0xFFFFFFFF
 BRNG_STATIC_MAX_STREAMS = 65536

@@ -44,11 +44,41 @@ __device__ __forceinline__ bool param_ok(int tag, float p0, float p1) {
     case BRNG_TAG_POISSON: return isfinite(p0) && p0 > 0.0f && p0 <= kPoissonMaxLambda;
     case BRNG_TAG_BINOMIAL:
       return isfinite(p0) && p0 >= 0.0f && p0 == floorf(p0) && p0 <= 16777216.0f && isfinite(p1) &&
-             p1 >= 0.0f && p1 <= 1.0f &&
-             static_cast<double>(p0) * fmin(static_cast<double>(p1), 1.0 - static_cast<double>(p1)) <=
-                 static_cast<double>(kBinomialMaxMean);
+             p1 >= 0.0f && p1 <= 1.0f;
     default: return false;
   }
+}
+
+// Means above kInversionMaxMean take transformed rejection (PTRS, BTRD) in
+// FP64 instead of the O(mean) inversion (the comparison in FP64, as the
+// reference takes it).
+__device__ __forceinline__ bool discrete_large(int tag, float p0, float p1) {
+  if (tag == BRNG_TAG_POISSON) return p0 > kInversionMaxMean;
+  return static_cast<double>(p0) * fmin(static_cast<double>(p1), 1.0 - static_cast<double>(p1)) >
+         static_cast<double>(kInversionMaxMean);
+}
+
+// One rejection attempt for a large-mean Poisson or Binomial draw from the
+// next U elements u0, u1 of the lane's ring (u1 is consumed only when the
+// attempt reads it).  Out of line: its FP64 code runs on GB300's narrow FP64
+// pipe and must not be issued, even predicated off, on other draws' steps.
+struct LargeAttempt {
+  float k;   // the count, or -1 for a rejection
+  int used;  // U elements consumed (1 or 2)
+};
+static __device__ __noinline__ LargeAttempt large_attempt(bool poisson, float p0, float p1, float u0, float u1) {
+  LargeAttempt r;
+  if (poisson) {
+    r.used = 2;
+    r.k = static_cast<float>(ptrs_attempt64(static_cast<double>(p0), static_cast<double>(u0),
+                                            static_cast<double>(u1) + 0x1p-24));
+  } else {
+    int used = 1;
+    r.k = static_cast<float>(btrd_attempt64(static_cast<double>(p0), static_cast<double>(p1),
+                                            static_cast<double>(u0) + 0x1p-24, static_cast<double>(u1), &used));
+    r.used = used;
+  }
+  return r;
 }
 
 // Per lane, one step per iteration: the lane's current draw, or for a Gamma
@@ -280,18 +310,33 @@ __global__ void __maxnreg__(128) bulk_kernel(const BulkArgs a) {
     }
     if constexpr (D::kU && (TAG < 0 || TAG == BRNG_TAG_POISSON || TAG == BRNG_TAG_BINOMIAL)) {
       if (__builtin_expect(__any_sync(kFull, isP || isB), TAG >= 0)) {  // one vote for both
-        bool rc = false;
+        bool rc = false, rej = false;
         if (isP || isB) {
-          const float u = RU.peek(0);
-          if (WORDS) word = RU.peek_word(0);
-          RU.advance(1);
-          if constexpr (TAG < 0 || TAG == BRNG_TAG_POISSON)
-            if (isP) out = poisson_draw(p0, u, &rc);
-          if constexpr (TAG < 0 || TAG == BRNG_TAG_BINOMIAL)
-            if (isB) out = binomial_draw(p0, p1, u, &rc);
-          done = true;
+          if (!discrete_large(tag, p0, p1)) {  // inversion of one U
+            const float u = RU.peek(0);
+            if (WORDS) word = RU.peek_word(0);
+            RU.advance(1);
+            if constexpr (TAG < 0 || TAG == BRNG_TAG_POISSON)
+              if (isP) out = poisson_draw(p0, u, &rc);
+            if constexpr (TAG < 0 || TAG == BRNG_TAG_BINOMIAL)
+              if (isB) out = binomial_draw(p0, p1, u, &rc);
+            done = true;
+          } else {  // one transformed-rejection attempt (1 or 2 U elements)
+            if (WORDS && attempts == 0) word = RU.peek_word(0);
+            const LargeAttempt r = large_attempt(isP, p0, p1, RU.peek(0), RU.peek(1));
+            RU.advance(static_cast<uint32_t>(r.used));
+            ++attempts;
+            if (r.k >= 0.0f) {
+              out = r.k;
+              done = true;
+            } else if (attempts >= kGammaMaxAttempts) {
+              done = true;  // NaN
+              rej = true;
+            }
+          }
         }
         count_warp(&a.cnt->n_recheck, rc);
+        count_warp(&a.cnt->n_reject, rej);
       }
     }
     if constexpr (D::kN && D::kU && (TAG < 0 || TAG == BRNG_TAG_GAMMA)) {

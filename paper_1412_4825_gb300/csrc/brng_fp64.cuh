@@ -197,4 +197,139 @@ __device__ __forceinline__ bool mt_accept64(double d, double z, double t, double
   return lhs < rhs;
 }
 
+
+// ---- large means: transformed rejection (Hormann 1993), all FP64 ----------
+// The same operations in the same order as the reference definition (IEEE
+// sqrt, division and floor, dlog, no contraction), so that every accept
+// decision and every count is the reference's.
+
+constexpr double kHalfLog2Pi = 0x1.d67f1c864beb5p-1;  // ln(2 pi) / 2
+
+// Stirling's series of ln Gamma(x) beyond its leading terms, to x^-7 (x >= 17)
+__device__ __forceinline__ double dstirling_tail(double x) {
+  const double inv = __ddiv_rn(1.0, x);
+  const double inv2 = __dmul_rn(inv, inv);
+  double t = __dmul_rn(inv2, 1.0 / 1680.0);
+  t = __dmul_rn(inv2, __dadd_rn(1.0 / 1260.0, -t));
+  t = __dmul_rn(inv2, __dadd_rn(1.0 / 360.0, -t));
+  return __dmul_rn(inv, __dadd_rn(1.0 / 12.0, -t));
+}
+
+// ln k! for an integer k >= 0: log of the exact product to 15!, Stirling above
+__device__ __forceinline__ double dlfact(double k) {
+  if (k <= 15.0) {
+    double f = 1.0;
+    for (double i = 2.0; i <= k; i += 1.0) f = __dmul_rn(f, i);
+    return dlog(f);
+  }
+  const double x = __dadd_rn(k, 1.0);
+  return __dadd_rn(__dadd_rn(__dmul_rn(__dadd_rn(x, -0.5), dlog(x)), -x),
+                   __dadd_rn(kHalfLog2Pi, dstirling_tail(x)));
+}
+
+// f_c(k) = ln k! - (k + 1/2) ln(k + 1) + (k + 1) - ln(2 pi)/2
+__device__ __forceinline__ double dstirling_fc(double k) {
+  if (k <= 15.0) {
+    const double x = __dadd_rn(k, 1.0);
+    return __dadd_rn(__dadd_rn(__dadd_rn(dlfact(k), -__dmul_rn(__dadd_rn(k, 0.5), dlog(x))), x), -kHalfLog2Pi);
+  }
+  return dstirling_tail(__dadd_rn(k, 1.0));
+}
+
+// One PTRS attempt for Poisson(lam): u0 = U in [0, 1), v = U' in (0, 1].
+// Returns the count, or -1 for a rejection.
+__device__ __forceinline__ double ptrs_attempt64(double lam, double u0, double v) {
+  const double slam = __dsqrt_rn(lam);
+  const double b = __dadd_rn(0.931, __dmul_rn(2.53, slam));
+  const double a = __dadd_rn(-0.059, __dmul_rn(0.02483, b));
+  const double vr = __dadd_rn(0.9277, -__ddiv_rn(3.6224, __dadd_rn(b, -2.0)));
+  const double u = __dadd_rn(u0, -0.5);
+  const double us = __dadd_rn(0.5, -fabs(u));
+  if (us == 0.0) return -1.0;
+  const double k = floor(__dadd_rn(__dadd_rn(__dmul_rn(__dadd_rn(__ddiv_rn(__dmul_rn(2.0, a), us), b), u), lam),
+                                   0.43));
+  if (us >= 0.07 && v <= vr) return k;
+  if (k < 0.0 || (us < 0.013 && v > us)) return -1.0;
+  const double inv_alpha = __dadd_rn(1.1239, __ddiv_rn(1.1328, __dadd_rn(b, -3.4)));
+  const double lhs = __dadd_rn(__dadd_rn(dlog(v), dlog(inv_alpha)),
+                               -dlog(__dadd_rn(__ddiv_rn(a, __dmul_rn(us, us)), b)));
+  const double rhs = __dadd_rn(__dadd_rn(-lam, __dmul_rn(k, dlog(lam))), -dlfact(k));
+  return lhs <= rhs ? k : -1.0;
+}
+
+// One BTRD attempt for Binomial(n, p_in): v0 = U' in (0, 1] (first element),
+// u1 = U in [0, 1) (second element, read only when the attempt needs it).
+// Returns the count (n - k for p_in > 1/2) or -1 for a rejection; *used gets
+// the elements the attempt consumed (1 or 2).
+__device__ __forceinline__ double btrd_attempt64(double n, double p_in, double v0, double u1, int* used) {
+  const bool flip = p_in > 0.5;
+  const double p = flip ? __dadd_rn(1.0, -p_in) : p_in;
+  const double q = __dadd_rn(1.0, -p);
+  const double spq = __dsqrt_rn(__dmul_rn(__dmul_rn(n, p), q));
+  const double b = __dadd_rn(1.15, __dmul_rn(2.53, spq));
+  const double a = __dadd_rn(__dadd_rn(-0.0873, __dmul_rn(0.0248, b)), __dmul_rn(0.01, p));
+  const double c = __dadd_rn(__dmul_rn(n, p), 0.5);
+  const double vr = __dadd_rn(0.92, -__ddiv_rn(4.2, b));
+  const double urvr = __dmul_rn(0.86, vr);
+  double v = v0, u;
+  *used = 1;
+  if (v <= urvr) {
+    u = __dadd_rn(__ddiv_rn(v, vr), -0.43);
+    const double k = floor(__dadd_rn(__dmul_rn(__dadd_rn(__ddiv_rn(__dmul_rn(2.0, a),
+                                                                     __dadd_rn(0.5, -fabs(u))), b), u), c));
+    return flip ? __dadd_rn(n, -k) : k;
+  }
+  *used = 2;
+  if (v >= vr) {
+    u = __dadd_rn(u1, -0.5);
+  } else {
+    u = __dadd_rn(__ddiv_rn(v, vr), -0.93);
+    u = __dadd_rn(u < 0.0 ? -0.5 : 0.5, -u);
+    v = __dmul_rn(__dadd_rn(u1, 0x1p-24), vr);
+  }
+  const double us = __dadd_rn(0.5, -fabs(u));
+  if (us == 0.0) return -1.0;
+  const double k = floor(__dadd_rn(__dmul_rn(__dadd_rn(__ddiv_rn(__dmul_rn(2.0, a), us), b), u), c));
+  if (k < 0.0 || k > n) return -1.0;
+  const double m = floor(__dmul_rn(__dadd_rn(n, 1.0), p));
+  const double r = __ddiv_rn(p, q);
+  const double nr = __dmul_rn(__dadd_rn(n, 1.0), r);
+  const double npq = __dmul_rn(__dmul_rn(n, p), q);
+  const double alpha = __dmul_rn(__dadd_rn(2.83, __ddiv_rn(5.1, b)), spq);
+  v = __ddiv_rn(__dmul_rn(v, alpha), __dadd_rn(__ddiv_rn(a, __dmul_rn(us, us)), b));
+  const double km = fabs(__dadd_rn(k, -m));
+  const double res = flip ? __dadd_rn(n, -k) : k;
+  if (km <= 15.0) {  // f(k)/f(m) by its recursion
+    double f = 1.0;
+    if (m < k) {
+      for (double i = __dadd_rn(m, 1.0); i <= k; i = __dadd_rn(i, 1.0))
+        f = __dmul_rn(f, __dadd_rn(__ddiv_rn(nr, i), -r));
+    } else if (m > k) {
+      for (double i = __dadd_rn(k, 1.0); i <= m; i = __dadd_rn(i, 1.0))
+        v = __dmul_rn(v, __dadd_rn(__ddiv_rn(nr, i), -r));
+    }
+    return v <= f ? res : -1.0;
+  }
+  v = dlog(v);  // squeeze on the log scale
+  const double rho = __dmul_rn(__ddiv_rn(km, npq),
+                               __dadd_rn(__ddiv_rn(__dadd_rn(__dmul_rn(__dadd_rn(__ddiv_rn(km, 3.0), 0.625), km),
+                                                             1.0 / 6.0),
+                                                   npq),
+                                         0.5));
+  const double t = __ddiv_rn(-__dmul_rn(km, km), __dmul_rn(2.0, npq));
+  if (v < __dadd_rn(t, -rho)) return res;
+  if (v > __dadd_rn(t, rho)) return -1.0;
+  const double nm = __dadd_rn(__dadd_rn(n, -m), 1.0);
+  const double h = __dadd_rn(__dadd_rn(__dmul_rn(__dadd_rn(m, 0.5), dlog(__ddiv_rn(__dadd_rn(m, 1.0), __dmul_rn(r, nm)))),
+                                       dstirling_fc(m)),
+                             dstirling_fc(__dadd_rn(n, -m)));
+  const double nk = __dadd_rn(__dadd_rn(n, -k), 1.0);
+  const double bound =
+      __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(h, __dmul_rn(__dadd_rn(n, 1.0), dlog(__ddiv_rn(nm, nk)))),
+                                    __dmul_rn(__dadd_rn(k, 0.5), dlog(__ddiv_rn(__dmul_rn(nk, r), __dadd_rn(k, 1.0))))),
+                          -dstirling_fc(k)),
+                -dstirling_fc(__dadd_rn(n, -k)));
+  return v <= bound ? res : -1.0;
+}
+
 }  // namespace brng

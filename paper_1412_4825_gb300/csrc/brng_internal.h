@@ -31,9 +31,9 @@ constexpr uint32_t kDefaultWarpsPerBlock = 4;
 constexpr uint32_t kDefaultLookahead = 8;
 constexpr uint32_t kDefaultProducerWarps = BRNG_PRODUCERS_NONE;
 constexpr int kTagMixed = -1;
-constexpr float kPoissonMaxLambda = 64.0f;  // Poisson by inversion: 0 < lambda <= this
+constexpr float kPoissonMaxLambda = 1e7f;   // Poisson: 0 < lambda <= this
+constexpr float kInversionMaxMean = 64.0f;  // Poisson / Binomial by inversion up to this mean, PTRS / BTRD above
 constexpr int kPoissonMaxK = 1024;          // the inversion's search stops here at the latest
-constexpr float kBinomialMaxMean = 64.0f;   // Binomial by inversion: n min(p, 1-p) <= this
 constexpr uint32_t kBulkMinRing = 8;  // bulk streams and Dirichlet rows use rings of at least this length
 // (a step may take 2 U elements from a top-up ring, which guarantees B - 3)
 inline uint32_t ring_len_min8(uint32_t B) { return B < kBulkMinRing ? kBulkMinRing : B; }

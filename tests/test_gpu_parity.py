@@ -469,6 +469,73 @@ def test_mixed_with_discrete_tags():
                  what="mixed with Poisson")
 
 
+@pytest.mark.parametrize("lo,hi,S", [(64.0, 1e6, 1000), (0.05, 1e7, 777), (60.0, 70.0, 64)])
+def test_poisson_large_means_bit_exact(lo, hi, S):
+    """Means above 64 take PTRS (FP64 transformed rejection, 2 U per attempt):
+    every count, first word and stream position equals the oracle's, across
+    the switch at 64 and up to lambda = 1e7."""
+    seed, n = 42, 100003
+    lam = inputs.poisson_params(n, seed=11, lo=lo, hi=hi)
+    h = handle(seed, S)
+    out, w = _run_bulk("poisson", h, [lam], n)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    ro, rw, rpos, _ = O.poisson(seed, S, lam)
+    assert np.array_equal(H(out).astype(np.float64), ro)
+    assert np.array_equal(words_np(w), rw)
+    assert np.array_equal(h.positions(), rpos)
+
+
+@pytest.mark.parametrize("max_trials,S", [(1 << 24, 1000), (3000, 513)])
+def test_binomial_large_means_bit_exact(max_trials, S):
+    """n min(p, 1-p) above 64 takes BTRD (1 or 2 U per attempt, recursion,
+    log squeeze and the Stirling test, FP64): counts, words and positions
+    bit-exact, reflected (p > 1/2) draws included."""
+    seed, n = 42, 100003
+    rng = np.random.default_rng(12)
+    trials = np.floor(np.exp(rng.uniform(0.0, np.log(max_trials), n))).astype(np.float32)
+    prob = rng.random(n).astype(np.float32)
+    prob[::5] = np.float32(0.5)
+    h = handle(seed, S)
+    out, w = _run_bulk("binomial", h, [trials, prob], n)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    ro, rw, rpos, _ = O.binomial(seed, S, trials, prob)
+    assert (trials.astype(np.float64) * np.minimum(prob, 1 - prob) > 64).mean() > 0.2  # both paths run
+    assert np.array_equal(H(out).astype(np.float64), ro)
+    assert np.array_equal(words_np(w), rw)
+    assert np.array_equal(h.positions(), rpos)
+
+
+def test_mixed_with_large_discrete_means():
+    """All eight tags, Poisson means log-uniform up to 1e6 and Binomial trials
+    up to 2^24: discrete counts exact, continuous values within tolerance."""
+    seed, S, n = 42, 2048, 100003
+    tag, p0, p1 = inputs.mixed_stream(n, seed=seed, n_tags=8)
+    rng = np.random.default_rng(13)
+    big = rng.random(n) < 0.5
+    p0 = p0.copy()
+    p1 = p1.copy()
+    sel = (tag == 6) & big
+    p0[sel] = inputs.log_uniform(rng, 64.0, 1e6, int(sel.sum()))
+    sel = (tag == 7) & big
+    p0[sel] = np.floor(inputs.log_uniform(rng, 130.0, 1.6e7, int(sel.sum())))
+    h = handle(seed, S)
+    out = torch.empty(n, dtype=torch.float32, device=DEV)
+    w = torch.empty(n, dtype=torch.int32, device=DEV)
+    B.brng_mixed(h.h, T(tag), T(p0), T(p1), out, w)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    ro, rw, rpos, _, cond = O.mixed(seed, S, tag, p0, p1, nthreads=NT, with_cond=True)
+    assert np.array_equal(words_np(w), rw)
+    assert np.array_equal(h.positions(), rpos)
+    disc = (tag == 6) | (tag == 7)
+    assert np.array_equal(H(out)[disc].astype(np.float64), ro[disc])
+    rest = ~disc
+    assert_close(H(out)[rest], ro[rest], _mixed_scale(tag[rest], p0[rest], p1[rest], ro[rest], cond[rest]),
+                 what="mixed with large discrete means")
+
+
 def test_poisson_invalid_lambda():
     lam = np.array([1.0, 0.0, -2.0, np.nan, np.inf, 2.0e7, 3.0], np.float32)
     h = handle(2, 1)
