@@ -490,12 +490,17 @@ def extras(dev, stream, peaks, args):
     out["ensemble_48_jobs"] = ensemble(48, 65536, (100, 10000), SEED)
     out["ensemble_256_small_jobs"] = ensemble(256, 2048, (100, 1000), SEED + 1000)
     torch.cuda.empty_cache()
-    # -- served Poisson mix: the 2,000 jobs/s rate for a bounded window, and a sub-capacity rate
-    full = serve.run_mix(serve.MixSpec(rate=2000.0, duration=args.serve_seconds, seed=SEED), pool=pool,
-                         drain_s=args.serve_seconds)
-    sub = serve.run_mix(serve.MixSpec(rate=10.0, duration=max(2.0, args.serve_seconds / 2), seed=SEED + 1),
-                        pool=pool, drain_s=60.0)
-    out["served_2000_per_s"] = full.summary()
+    # -- served Poisson mix under a 40e9-byte budget: 2,000 jobs/s for the
+    # configured 60 s (far over capacity), then 0.8 x the job rate it sustained
+    # (near capacity), then 10 jobs/s (idle); latency percentiles over every
+    # submitted job, unfinished ones at their age when the window closes
+    full = serve.run_mix(serve.MixSpec(rate=2000.0, duration=args.serve_seconds, seed=SEED), pool=pool)
+    fs = full.summary()
+    out["served_2000_per_s"] = fs
+    near_rate = max(1.0, 0.8 * fs["jobs_completed_per_s"])
+    near = serve.run_mix(serve.MixSpec(rate=near_rate, duration=args.serve_near_seconds, seed=SEED + 2), pool=pool)
+    out["served_near_capacity"] = dict(near.summary(), rate_jobs_per_s=near_rate)
+    sub = serve.run_mix(serve.MixSpec(rate=10.0, duration=10.0, seed=SEED + 1), pool=pool)
     out["served_10_per_s"] = sub.summary()
     return out
 
@@ -820,8 +825,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary workloads (triangle, LDA, mixed stream, batched vs plain, served mix)")
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="arrival window of the served mix at 2,000 jobs/s")
+    ap.add_argument("--serve-near-seconds", type=float, default=20.0,
+                    help="arrival window of the served mix near its measured capacity")
     ap.add_argument("--case", choices=["mixed", "lda", "triangle", "uniform64", "ng", "lda_full"], default=None,
                     help="time one workload at a chosen size instead (profiling): mixed, lda, triangle, "
                          "uniform64, or ng (the headline normal-gamma model)")

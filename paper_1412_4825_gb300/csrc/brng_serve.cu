@@ -505,8 +505,11 @@ int brng_serve_result(brng_server_t* s, uint64_t id, void* host_state, double* h
     // server's result stream and return the memory there (stream-ordered, no
     // device-wide synchronisation while other batches run)
     std::lock_guard<std::mutex> rl(s->result_mu);
-    cudaError_t e = cudaSuccess;
-    if (rc == BRNG_OK && host_state)
+    // the job's uploads ran on the admission stream: a job that failed before
+    // its batch event fired has no launch ordering them before this stream,
+    // so wait for the admission work recorded so far before reusing the block
+    cudaError_t e = cudaStreamWaitEvent(s->result_stream, s->admit_event, 0);
+    if (e == cudaSuccess && rc == BRNG_OK && host_state)
       e = cudaMemcpyAsync(host_state, j->dev + j->off_state, j->state_bytes, cudaMemcpyDeviceToHost,
                           s->result_stream);
     if (e == cudaSuccess && rc == BRNG_OK && host_moments)

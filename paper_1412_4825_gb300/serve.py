@@ -38,16 +38,30 @@ class MixResult:
     failed: int = 0
     cancelled: int = 0
     updates: float = 0.0
-    latencies: list = field(default_factory=list)
+    latencies: list = field(default_factory=list)      # completed jobs: completion - submission
+    censored_ages: list = field(default_factory=list)  # unfinished at the window's end: their age then
+    window: float = 0.0                                 # arrival window (s)
     wall: float = 0.0
     stats: dict = field(default_factory=dict)
 
     def summary(self):
-        lat = np.array(self.latencies) if self.latencies else np.array([np.nan])
+        """Latency percentiles over ALL submitted jobs: a job still unfinished
+        when the arrival window closes enters with its age at that moment (a
+        right-censored latency, a lower bound of its true latency), so the
+        percentiles are lower bounds whenever they fall among censored jobs,
+        and never survivor-biased.  The completed-only percentiles are kept
+        beside them, with the completed fraction."""
+        lat = np.array(self.latencies)
+        both = np.concatenate([lat, np.array(self.censored_ages)])
+        pct = (lambda a, q: float(np.percentile(a, q)) if a.size else float("nan"))
+        n_all = max(1, self.submitted)
         return {"submitted": self.submitted, "completed": self.completed, "failed": self.failed,
-                "cancelled": self.cancelled, "p50_s": float(np.percentile(lat, 50)),
-                "p99_s": float(np.percentile(lat, 99)), "updates_per_s": self.updates / self.wall,
-                "wall_s": self.wall, "server": self.stats}
+                "censored": len(self.censored_ages), "completed_fraction": self.completed / n_all,
+                "p50_s": pct(both, 50), "p99_s": pct(both, 99),
+                "p50_completed_s": pct(lat, 50), "p99_completed_s": pct(lat, 99),
+                "updates_per_s": self.updates / max(self.window, 1e-9),
+                "jobs_completed_per_s": self.completed / max(self.window, 1e-9),
+                "window_s": self.window, "wall_s": self.wall, "server": self.stats}
 
 
 class InputPool:
@@ -82,10 +96,13 @@ def make_request(pool, model, n, sweeps, seed, borrow=True):
     return r
 
 
-def run_mix(spec: MixSpec, mem_budget=40 << 30, max_inflight=4, pool=None, max_jobs=None, drain_s=5.0):
-    """Drive the server with Poisson arrivals for spec.duration seconds, then
-    close it (jobs still waiting for memory are cancelled).  Results are
-    collected (and their memory released) as jobs finish."""
+def run_mix(spec: MixSpec, mem_budget=40_000_000_000, max_inflight=4, pool=None, max_jobs=None):
+    """Drive the server with Poisson arrivals for spec.duration seconds.
+    Results are collected (and their memory released) as jobs finish; when
+    the window closes, every job not yet finished is recorded with its age
+    (censored), and the server is closed (admitted jobs finish, queued ones
+    are cancelled; neither enters the completed counts).  Throughput is the
+    updates of jobs completed within the window over the window."""
     rng = np.random.default_rng(spec.seed)
     pool = pool or InputPool(spec.chains[1], spec.K, spec.seed)
     srv = B.brng_serve_open(mem_budget, max_inflight)
@@ -95,28 +112,29 @@ def run_mix(spec: MixSpec, mem_budget=40 << 30, max_inflight=4, pool=None, max_j
     stop = threading.Event()
 
     def collect():
-        while not stop.is_set() or pending:
+        while not stop.is_set():
             with lock:
                 ids = list(pending.items())
             progressed = False
-            for jid, (model, n, sw) in ids:
+            for jid, (model, n, sw, _) in ids:
+                if stop.is_set():
+                    break
                 code, done = B.brng_serve_poll(srv, jid)
                 if not done:
                     continue
                 code, info = B.brng_serve_result(srv, jid)
                 with lock:
-                    counted = pending.pop(jid, None) is not None
-                progressed = True
-                if not counted:  # already given up on (counted as cancelled)
-                    continue
-                if code == B.BRNG_OK:
-                    res.completed += 1
-                    res.updates += updates_of(model, n, sw)
-                    res.latencies.append((info["completed_ns"] - info["submitted_ns"]) / 1e9)
-                elif code == B.BRNG_EAGAIN:
-                    res.cancelled += 1
-                else:
-                    res.failed += 1
+                    if stop.is_set() or pending.pop(jid, None) is None:
+                        continue  # the window closed first: counted as censored
+                    progressed = True
+                    if code == B.BRNG_OK:
+                        res.completed += 1
+                        res.updates += updates_of(model, n, sw)
+                        res.latencies.append((info["completed_ns"] - info["submitted_ns"]) / 1e9)
+                    elif code == B.BRNG_EAGAIN:
+                        res.cancelled += 1
+                    else:
+                        res.failed += 1
             if not progressed:
                 time.sleep(0.0005)
 
@@ -136,26 +154,24 @@ def run_mix(spec: MixSpec, mem_budget=40 << 30, max_inflight=4, pool=None, max_j
         n = max(spec.chains[0], min(n, spec.chains[1]))
         sw = int(rng.integers(spec.sweeps[0], spec.sweeps[1] + 1))
         req = make_request(pool, model, n, sw, seed=int(rng.integers(0, 2**63)))
+        t_sub = time.perf_counter()
         jid = B.brng_serve_submit(srv, req)
         with lock:
-            pending[jid] = (model, n, sw)
+            pending[jid] = (model, n, sw, t_sub)
         n_total += 1
-    res.submitted = n_total
-    t_arrivals = time.perf_counter()
-    # let the server drain for up to drain_s, then stop collecting and close
-    # (closing finishes admitted jobs and cancels those still waiting)
-    while time.perf_counter() - t_arrivals < drain_s:
-        with lock:
-            if not pending:
-                break
+    # the window ends at the last arrival slot (spec.duration, or the job cap)
+    while time.perf_counter() - t0 < spec.duration and (max_jobs is None or n_total < max_jobs):
         time.sleep(0.001)
-    stop.set()
+    t_end = time.perf_counter()
     with lock:
-        res.cancelled += len(pending)
+        stop.set()
+        res.censored_ages = [t_end - t_sub for (_, _, _, t_sub) in pending.values()]
         pending.clear()
     th.join()
-    res.wall = time.perf_counter() - t0
+    res.submitted = n_total
+    res.window = t_end - t0
     code, res.stats = B.brng_serve_stats(srv)
     B.brng_serve_close(srv)
-    res.stats["arrival_window_s"] = t_arrivals - t0
+    res.wall = time.perf_counter() - t0
+    res.stats["arrival_window_s"] = res.window
     return res

@@ -95,8 +95,10 @@ def test_serve_refuses_job_larger_than_budget():
 
 def test_poisson_mix_small():
     spec = serve.MixSpec(rate=200.0, duration=1.0, chains=(1, 2048), sweeps=(10, 200), seed=5)
-    res = serve.run_mix(spec, mem_budget=1 << 30, max_inflight=4, drain_s=30.0)
+    res = serve.run_mix(spec, mem_budget=1 << 30, max_inflight=4)
     s = res.summary()
     print("served mix", s)
-    assert res.submitted > 100 and res.completed == res.submitted and res.failed == 0
+    assert res.submitted > 100 and res.failed == 0
+    assert res.completed + s["censored"] + res.cancelled == res.submitted
+    assert s["completed_fraction"] > 0.8
     assert s["p99_s"] >= s["p50_s"] > 0
