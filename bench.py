@@ -447,6 +447,27 @@ def extras(dev, stream, peaks, args):
                 B.brng_gibbs_run(handles[sd].h, model, 0, nch, sw, prm, sarg, mm, stream)
 
         t_plain = _time_s(plain, stream, reps=2, warm=1)
+        # a measured bound on what batching can gain: each job timed alone
+        # (one launch), each model's best time per unit-sweep (a unit = 32
+        # chains or one document: the work of one warp) taken from its jobs
+        # that fill the GPU best, and the mix's ideal time = its unit-sweeps at
+        # those costs; plain time / ideal time bounds batched / plain
+        ev = []
+        with torch.cuda.stream(stream):
+            for model, nch, sw, sd, prm, sarg, mm in jobs:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                B.brng_gibbs_run(handles[sd].h, model, 0, nch, sw, prm, sarg, mm, stream)
+                e1.record(stream)
+                ev.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        unit_sweeps = [((nch + 31) // 32 if m != B.MODEL_LDA else nch) * sw for m, nch, sw, _ in specs]
+        t_job = [a.elapsed_time(b) / 1e3 for a, b in ev]
+        best = {}
+        for (m, _, _, _), us, tj in zip(specs, unit_sweeps, t_job):
+            best[m] = min(best.get(m, float("inf")), tj / us)
+        t_ideal = sum(best[m] * us for (m, _, _, _), us in zip(specs, unit_sweeps))
+        t_alone = sum(t_job)
         jobs = fresh_jobs()
         bjobs = [B.make_job(m, c, sw, sd, prm, sarg, mm)[0] for m, c, sw, sd, prm, sarg, mm in jobs]
         t_batch = _time_s(lambda: B.brng_gibbs_batch(hb.h, bjobs, stream), stream, reps=2, warm=1)
@@ -483,6 +504,9 @@ def extras(dev, stream, peaks, args):
                 "sweeps": "uniform [%d, %d]" % sweeps, "updates": upd,
                 "plain_updates_per_s": upd / t_plain, "batched_updates_per_s": upd / t_batch,
                 "batched_over_plain": t_plain / t_batch, "plain_ms": t_plain * 1e3, "batched_ms": t_batch * 1e3,
+                "bound_batched_over_plain": t_alone / t_ideal, "ideal_ms": t_ideal * 1e3,
+                "jobs_alone_ms": t_alone * 1e3,
+                "share_of_plain_in_largest_3_jobs": sum(sorted(t_job)[-3:]) / t_alone,
                 "graph_updates_per_s": upd / t_graph, "graph_over_plain": t_plain / t_graph,
                 "graph_ms": t_graph * 1e3, "batch_philox_blocks_per_s": batch_blocks / t_batch,
                 "batch_philox_frac": batch_blocks / t_batch / peak_blocks}
@@ -609,14 +633,23 @@ def run_gpu(args):
         for _ in range(args.warmup):
             step()
     barrier()
-    # consumption of one step (exact count of Philox blocks the method used)
+    # consumption of one step (exact count of Philox blocks the method used),
+    # and the ring elements generated but unused when it ended (Sec. 2.4's
+    # buffer waste, from the handle's counter)
     before = state.clone()
+    h.counters(stream, reset=True)
     with torch.cuda.stream(stream):
         step()
     torch.cuda.synchronize(dev)
+    _, waste_cnt = h.counters(stream, reset=True)
     _, _, pn0, pu0 = B.normal_gamma_unpack(before)
     _, _, pn1, pu1 = B.normal_gamma_unpack(state)
-    blocks_per_step = float((pn1 - pn0).astype(np.float64).sum() + (pu1 - pu0).astype(np.float64).sum()) / 4.0
+    consumed = float((pn1 - pn0).astype(np.float64).sum() + (pu1 - pu0).astype(np.float64).sum())
+    blocks_per_step = consumed / 4.0
+    buffer_waste = {"elements_per_step": int(waste_cnt["n_wasted"]),
+                    "per_chain": waste_cnt["n_wasted"] / N_CHAINS,
+                    "fraction_of_consumed": waste_cnt["n_wasted"] / consumed,
+                    "ring_len": h.tuning["buf_len"]}
 
     uuid = None
     try:
@@ -712,6 +745,7 @@ def run_gpu(args):
                      "note": "integer pipe: 20 32x32->64 multiplies per Philox4x32-10 block; blocks = "
                              "exact consumption of the step (N+U elements / 4)"},
         "wall_s_timed": wall,
+        "buffer_waste": buffer_waste,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

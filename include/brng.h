@@ -90,6 +90,8 @@ typedef struct {
   uint64_t n_flip;     /* ... of which the FP64 decision differed from the FP32 sign  */
   float max_flip_ratio;/* max |FP32 margin| / tolerance over the flips (must stay < 1) */
   uint32_t n_timeout;  /* bounded device waits that ran out (chains ended with NaN)  */
+  uint64_t n_wasted;   /* base deviates generated into buffers but unused when a call
+                          ended (Sec. 2.4's buffer waste; regenerated by the next call) */
 } brng_counters_t;
 
 /* Tuning knobs; zero fields mean "library default". */
@@ -144,7 +146,13 @@ int brng_read_counters(brng_t *h, brng_stream_t stream, brng_counters_t *out, in
 int brng_philox_words(brng_t *h, uint32_t domain, uint32_t stream_id, uint64_t first_block,
                       size_t n_blocks, uint32_t *out, brng_stream_t stream);
 
-/* ---- integer-pipe probe ------------------------------------------------------
+/* ===== TEST AND MEASUREMENT HOOKS =========================================
+ * brng_philox_peak, brng_fp32_eval, brng_fp64_eval (below), brng_test_pc_stall
+ * and brng_debug_violations (end of file) are not part of the sampling
+ * interface: they exist for the parity tests, the roofline probe and the
+ * failure-detection test, and a user of the library does not need them. */
+
+/* ---- integer-pipe probe (test/measurement hook) -------------------------------
  * Runs `blocks` x `threads` (<= 256) threads, each generating 4 x `iters`
  * Philox4x32-10 blocks in registers (4 independent counter chains) and
  * writing one checksum word to sink[thread] (device, blocks*threads uint32).
@@ -153,7 +161,7 @@ int brng_philox_words(brng_t *h, uint32_t domain, uint32_t stream_id, uint64_t f
 int brng_philox_peak(uint64_t iters, uint32_t blocks, uint32_t threads, uint32_t *sink,
                      brng_stream_t stream);
 
-/* ---- FP32 elementary functions of the base conversions ----------------------
+/* ---- FP32 elementary functions of the base conversions (test hook) -----------
  * out[i] = f(in[i]) on the device for fn = 0: natural log (the FP32 log of
  * the exponential and Box-Muller buffers and of the Gamma test), 1: sin and
  * 2: cos of pi k 2^-23 for the integer k = in[i] in [0, 2^24) (the Box-Muller
@@ -161,7 +169,7 @@ int brng_philox_peak(uint64_t iters, uint32_t blocks, uint32_t threads, uint32_t
  * their error can be bounded against a reference.  in, out: device float[n]. */
 int brng_fp32_eval(uint32_t fn, size_t n, const float *in, float *out, brng_stream_t stream);
 
-/* ---- FP64 elementary functions of the Gamma and Poisson rechecks ----------
+/* ---- FP64 elementary functions of the Gamma and Poisson rechecks (test hook) -
  * out[i] = f(in[i]) on the device for fn = 0: log, 1: sin(pi x), 2: cos(pi x),
  * 3: exp (Taylor through r^16 after reduction by ln 2),
  * the fixed-operation-order FP64 functions the Gamma sampler uses when it
@@ -169,6 +177,7 @@ int brng_fp32_eval(uint32_t fn, size_t n, const float *in, float *out, brng_stre
  * exact reduction and Taylor series).  Exposed so that their bits can be
  * checked against a reference.  in, out: device double[n]. */
 int brng_fp64_eval(uint32_t fn, size_t n, const double *in, double *out, brng_stream_t stream);
+/* ===== end of the first group of test hooks ================================ */
 
 /* ---- varying-parameter streams (Sec. 2.2 Get* functions; Sec. 2.3 method:
  * parameters read from memory per draw, every output written) -------------
@@ -529,7 +538,7 @@ int brng_serve_close(brng_server_t *s);
 int brng_test_pc_stall(brng_t *h, uint32_t n_chains, uint32_t n_sweeps, const void *params, void *state,
                        double *moments, brng_stream_t stream);
 
-/* Checked build (compiled with -DBRNG_DEBUG): the number of failed protocol
+/* Test hook.  Checked build (compiled with -DBRNG_DEBUG): the number of failed protocol
  * checks -- a ring element read or consumed before it was generated, a refill
  * over unread slots, a batch unit outside its job -- counted on the device
  * since the last reset (nothing traps).  Synchronous.  BRNG_EINVAL in the

@@ -48,7 +48,8 @@ PRODUCERS_NONE = 0xFFFFFFFF
 
 class brng_counters_t(C.Structure):
     _fields_ = [("n_domain", C.c_uint64), ("n_reject", C.c_uint64), ("n_recheck", C.c_uint64),
-                ("n_flip", C.c_uint64), ("max_flip_ratio", C.c_float), ("n_timeout", C.c_uint32)]
+                ("n_flip", C.c_uint64), ("max_flip_ratio", C.c_float), ("n_timeout", C.c_uint32),
+                ("n_wasted", C.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}

@@ -372,6 +372,7 @@ int make_job(const brng_t* h, brng_model_t model, const brng::RoundKeys& rk, uin
       a.B = h->tune.buf_len;
       a.state = static_cast<brng_triangle_state_t*>(state);
       a.moments = moments;
+      a.cnt = h->d_cnt;
       j->n_units = (static_cast<uint64_t>(n_chains) + 31) / 32;
       return BRNG_OK;
     }

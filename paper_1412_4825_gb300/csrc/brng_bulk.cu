@@ -382,6 +382,11 @@ __global__ void __maxnreg__(128) bulk_kernel(const BulkArgs a) {
       }
     }
   }
+  uint32_t left = 0;
+  if constexpr (D::kU) left += static_cast<uint32_t>(max(RU.avail(), 0));
+  if constexpr (D::kN) left += static_cast<uint32_t>(max(RN.avail(), 0));
+  if constexpr (D::kE) left += static_cast<uint32_t>(max(RE.avail(), 0));
+  count_waste(a.cnt, has_stream ? left : 0u);
   if (has_stream) {
     if constexpr (D::kU) a.pos[s] = RU.pos();
     if constexpr (D::kN) a.pos[static_cast<uint64_t>(a.S) + s] = RN.pos();

@@ -225,6 +225,11 @@ __device__ __forceinline__ void dirichlet_unit(const DirichletArgs& a, uint64_t 
     __syncwarp();
   }
 
+  uint32_t left = 0;
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+    if (kvalid[p]) left += static_cast<uint32_t>(max(RN[p].avail(), 0) + max(RU[p].avail(), 0));
+  count_waste(a.cnt, left);
 #pragma unroll
   for (int p = 0; p < P; ++p) {
     if (!kvalid[p]) continue;

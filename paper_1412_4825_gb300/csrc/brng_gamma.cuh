@@ -41,12 +41,23 @@ struct DevCounters {
   unsigned long long n_domain, n_reject, n_recheck, n_flip;
   unsigned int max_flip_ratio_bits;  // float bits (non-negative -> monotone as uint)
   unsigned int n_timeout;            // bounded waits that ran out
+  unsigned long long n_wasted;       // ring elements generated but unused at exit
 };
 
 // warp-aggregated counter increment for lanes with `pred`
 __device__ __forceinline__ void count_warp(unsigned long long* ctr, bool pred) {
   const unsigned m = __ballot_sync(kFull, pred);
   if (m && lane_id() == static_cast<unsigned>(__ffs(m) - 1)) atomicAdd(ctr, static_cast<unsigned long long>(__popc(m)));
+}
+
+// The paper's buffer waste (Sec. 2.4: a buffer refilled in bulk holds
+// deviates that are never used when the stream stops): the elements left in
+// this lane's rings when its unit ends, summed over the warp into n_wasted
+// (all 32 lanes call).  The next call restarts each stream at its position,
+// so these elements are generated again there, not lost to the sequence.
+__device__ __forceinline__ void count_waste(DevCounters* cnt, uint32_t n) {
+  const uint32_t sum = __reduce_add_sync(kFull, n);
+  if (sum && lane_id() == 0) atomicAdd(&cnt->n_wasted, static_cast<unsigned long long>(sum));
 }
 
 struct GammaState {

@@ -87,6 +87,7 @@ __device__ __forceinline__ void triangle_unit(const TriangleArgs& a, uint64_t un
       }
     }
   }
+  count_waste(a.cnt, owner && R.valid > R.rp ? R.valid - R.rp : 0u);
   if (owner) {
     brng_triangle_state_t s;
     s.x = x;
@@ -469,6 +470,7 @@ __device__ __forceinline__ void normal_gamma_unit(const NormalGammaArgs& a, uint
   RN.init(ringN, nullptr, a.B, s.pn);
   RU.init(ringU, nullptr, a.B, s.pu);
   ng_sweeps_any(a, a.n_sweeps, stream, active, s, RN, RU);
+  count_waste(a.cnt, active ? static_cast<uint32_t>(RN.avail() + RU.avail()) : 0u);
   ng_fold_moments(s);
   ng_store(a, c, active, s);
   __syncwarp();  // the rings are reused by the warp's next unit

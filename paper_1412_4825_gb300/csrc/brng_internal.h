@@ -110,6 +110,7 @@ struct TriangleArgs {
   uint32_t n_chains, n_sweeps, B;
   brng_triangle_state_t* state;
   double* moments;
+  DevCounters* cnt;
 };
 cudaError_t launch_triangle(const TriangleArgs& a, const Geometry& g, uint32_t lanes_per_chain,
                             cudaStream_t st);

@@ -7,6 +7,12 @@ exchange while sweeping; the only collective steps are a final gather of
 per-chain state and moments in rank order (deterministic concatenation, no
 floating-point reduction) and the maximum of the ranks' timings.
 
+The full LDA step is the exception with a real exchange: its documents are
+sharded the same way, but the word-topic and topic counts are shared by the
+whole corpus, so after every sweep each rank's count changes are summed over
+the ranks (`lda_exchange`, an integer all-reduce: exact and independent of the
+order of the additions) before they are added into every rank's copy.
+
 Two partitions:
   * `chain_range`: a fixed total split into contiguous, balanced ranges
     (strong scaling);
@@ -61,3 +67,10 @@ def max_over_ranks(dist, value: float, device="cpu") -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def lda_exchange(dist, dnkw):
+    """Sum the ranks' count changes of one sweep of the full LDA step in place
+    (int32 [V*K + K] on the ranks' devices or hosts: word-topic, then topic)."""
+    dist.all_reduce(dnkw, op=dist.ReduceOp.SUM)
+    return dnkw

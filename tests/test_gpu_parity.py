@@ -536,6 +536,28 @@ def test_mixed_with_large_discrete_means():
                  what="mixed with large discrete means")
 
 
+def test_buffer_waste_counter():
+    """n_wasted counts the ring elements generated but unused when a call ends
+    (Sec. 2.4's buffer-length trade-off): at most one ring per stream and
+    domain, more for longer rings, and none that the next call loses (it
+    restarts each stream at its position, bit-exact as the parity tests show)."""
+    S, n = 1000, 20011
+    a, b = inputs.uniform_params(n, seed=3)
+    waste = {}
+    for buf_len in (8, 64):
+        h = handle(7, S, buf_len=buf_len)
+        _run_bulk("uniform", h, [a, b], n)
+        code, cnt = h.counters()
+        assert code == B.BRNG_OK
+        waste[buf_len] = cnt["n_wasted"]
+        assert 0 < cnt["n_wasted"] <= S * buf_len
+    assert waste[64] > waste[8]
+    nobs, xbar, sc = inputs.normal_gamma_data(333, seed=2)
+    for buf_len in (8, 32):
+        st, m, cnt = _ng_gpu(nobs, xbar, sc, 50, buf_len=buf_len)
+        assert 0 < cnt["n_wasted"] <= 333 * 2 * buf_len
+
+
 def test_poisson_invalid_lambda():
     lam = np.array([1.0, 0.0, -2.0, np.nan, np.inf, 2.0e7, 3.0], np.float32)
     h = handle(2, 1)

@@ -95,3 +95,57 @@ def test_sharded_equals_whole_gloo(world):
     O.lib()  # build the oracle before the ranks start
     mp.start_processes(_rank_main, args=(world, _free_port(), 257, 301, 37, 40), nprocs=world,
                        join=True, start_method="spawn")
+
+
+def _lda_rank_main(rank, world, port, n_docs, sweeps, out_q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        corpus = inputs.lda_corpus(n_docs, K=16, V=200, len_lo=5, len_hi=80, seed=21)
+        full = inputs.lda_initial_state(corpus, seed=22)
+        off, cnt = shard.chain_range(n_docs, world, rank)
+        sub = dict(K=corpus["K"], V=corpus["V"], doc_ptr=corpus["doc_ptr"][off:off + cnt + 1], words=corpus["words"])
+        st = {k: v.copy() for k, v in full.items()}
+        st["ndk"] = np.ascontiguousarray(full["ndk"][off:off + cnt])
+        st["zpos"] = np.ascontiguousarray(full["zpos"][off:off + cnt])
+        K, V = corpus["K"], corpus["V"]
+        for _ in range(sweeps):
+            dnkw, dnk = O.lda_z_sweep(SEED, sub, st, 0.1, 0.01, doc_offset=off)
+            d = torch.from_numpy(np.concatenate([dnkw.ravel(), dnk]))
+            shard.lda_exchange(dist, d)
+            st["nkw"] += d[: V * K].numpy().reshape(V, K)
+            st["nk"] += d[V * K:].numpy()
+        t0, t1 = int(corpus["doc_ptr"][off]), int(corpus["doc_ptr"][off + cnt])
+        ndk = shard.gather_rows(dist, torch.from_numpy(st["ndk"]), n_docs, world, rank)
+        z = torch.from_numpy(st["z"][t0:t1].astype(np.int32))
+        sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+        dist.all_gather(sizes, torch.tensor([t1 - t0]))
+        width = int(max(x.item() for x in sizes))
+        pad = torch.zeros(width, dtype=torch.int32)
+        pad[: t1 - t0] = z
+        parts = [torch.empty_like(pad) for _ in range(world)]
+        dist.all_gather(parts, pad)
+        if rank == 0:
+            zall = torch.cat([p[: int(c.item())] for p, c in zip(parts, sizes)]).numpy()
+            out_q.put((ndk.numpy(), zall, st["nkw"], st["nk"]))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_lda_full_sharded_exchange_equals_one_run(world):
+    """The full LDA step on `world` gloo ranks -- documents split by
+    chain_range, each sweep's count changes summed over the ranks with
+    lda_exchange -- gives the single run's topics and counts exactly."""
+    n_docs, sweeps = 37, 4
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    mp.start_processes(_lda_rank_main, args=(world, port, n_docs, sweeps, q), nprocs=world, join=True,
+                       start_method="spawn")
+    ndk, z, nkw, nk = q.get(timeout=60)
+    corpus = inputs.lda_corpus(n_docs, K=16, V=200, len_lo=5, len_hi=80, seed=21)
+    ref = inputs.lda_initial_state(corpus, seed=22)
+    O.lda_full(SEED, sweeps, corpus, ref, alpha=0.1, beta=0.01, theta_draws=False)
+    assert np.array_equal(ndk, ref["ndk"]) and np.array_equal(z, ref["z"].astype(np.int32))
+    assert np.array_equal(nkw, ref["nkw"]) and np.array_equal(nk, ref["nk"])
