@@ -371,6 +371,17 @@ def extras(dev, stream, peaks, args):
     out["binomial_2^26"] = {"deviates_per_s": n / t, "ms": t * 1e3,
                             "params": "n log-uniform integers [1, 1000], p uniform, n min(p, 1-p) <= 64",
                             "tuning": hp.tuning, "fp64_redraws_per_call": rechecks_per_call(run_b, hp)}
+    # -- large means: Poisson by PTRS (lambda log-uniform [64, 1e6]) and
+    # Binomial by BTRD (n log-uniform integers up to 2^24, p uniform), FP64
+    lam = torch.exp(np.log(64.0) + np.log(1e6 / 64.0) * torch.rand(n, generator=g, device=dev)).contiguous()
+    t = _time_s(run_p, stream)
+    out["poisson_large_2^26"] = {"deviates_per_s": n / t, "ms": t * 1e3, "lambda": "log-uniform [64, 1e6]",
+                                 "method": "PTRS, FP64"}
+    tr = torch.floor(torch.exp(np.log(2.0 ** 24) * torch.rand(n, generator=g, device=dev))).contiguous()
+    pr = torch.rand(n, generator=g, device=dev).contiguous()
+    t = _time_s(run_b, stream)
+    out["binomial_large_2^26"] = {"deviates_per_s": n / t, "ms": t * 1e3,
+                                  "params": "n log-uniform integers [1, 2^24], p uniform (BTRD above mean 64)"}
     hp.close()
     del lam, o, w, tr, pr
     torch.cuda.empty_cache()

@@ -352,8 +352,8 @@ typedef struct {
   uint64_t *pos;  /* device [n][K][2]: next (N, U) element of each component      */
 } brng_lda_state_t;
 
-/* LDA_FULL (Sec. 1, the LDA paragraph: a Dirichlet "whose parameters are
- *   updated during each iteration"): per sweep, for every document d (a
+/* LDA_FULL (Sec. 1, the LDA paragraph: the Dirichlet's parameters change from
+ *   one Gibbs iteration to the next): per sweep, for every document d (a
  *   "chain"; global id chain_offset + d), (1) each token's topic is redrawn
  *   from the collapsed conditional
  *       p(z = k) proportional to (n_dk' + alpha)(n_kw' + beta)/(n_k' + V beta)
@@ -523,8 +523,8 @@ int brng_serve_stats(brng_server_t *s, brng_serve_stats_t *out);
  * it has been admitted (it then runs to the end), BRNG_ENOTFOUND for an
  * unknown id. */
 int brng_serve_cancel(brng_server_t *s, uint64_t job_id);
-/* cancels jobs still waiting for memory, finishes the admitted ones, frees
- * everything; uncollected results are lost */
+/* cancels the jobs still waiting for memory or for a launch, lets the batches
+ * already launched finish, frees everything; uncollected results are lost */
 int brng_serve_close(brng_server_t *s);
 
 /* ---- test hook: failure detection without a GPU fault ----------------------

@@ -1,8 +1,8 @@
 /*
  * or_lda.c -- the full LDA Gibbs step: topic assignments resampled per token,
  * so that the document-topic counts, and with them the Dirichlet parameters
- * of the next theta draw, change every sweep (Sec. 1, the LDA paragraph: a
- * Dirichlet "whose parameters are updated during each iteration", and its
+ * of the next theta draw, change every sweep (Sec. 1, the LDA paragraph: the
+ * Dirichlet's parameters change from one Gibbs iteration to the next; its
  * footnote: Dirichlet from normalised Gammas).
  * TEST INFRASTRUCTURE ONLY (see oracle.h).
  *

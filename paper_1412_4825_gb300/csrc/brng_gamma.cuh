@@ -126,15 +126,46 @@ static __device__ __noinline__ void record_flip(DevCounters* cnt, float ratio) {
   atomicMax(&cnt->max_flip_ratio_bits, __float_as_uint(ratio));
 }
 
+// q = 3 d x^4 (1/4 - x/5 + x^2/6 - ...), the margin's correction term for
+// |x| <= 1/4 (12 terms, truncation < 2e-8 relative)
+__device__ __forceinline__ float mt_series_q(float d, float x) {
+  float p = -0x1.111112p-4f;         // -1/15
+  p = fmaf(p, x, 0x1.24924ap-4f);    //  1/14
+  p = fmaf(p, x, -0x1.3b13b2p-4f);   // -1/13
+  p = fmaf(p, x, 0x1.555556p-4f);    //  1/12
+  p = fmaf(p, x, -0x1.745d18p-4f);   // -1/11
+  p = fmaf(p, x, 0x1.99999ap-4f);    //  1/10
+  p = fmaf(p, x, -0x1.c71c72p-4f);   // -1/9
+  p = fmaf(p, x, 0.125f);            //  1/8
+  p = fmaf(p, x, -0x1.24924ap-3f);   // -1/7
+  p = fmaf(p, x, 0x1.555556p-3f);    //  1/6
+  p = fmaf(p, x, -0x1.99999ap-3f);   // -1/5
+  p = fmaf(p, x, 0.25f);             //  1/4
+  const float x2 = x * x;
+  return (3.0f * d) * (x2 * x2) * p;
+}
+
+// An upper bound of mt_series_q for |x| <= 1/4: the series alternates with
+// decreasing terms for x >= 0 (so it is below its partial sum to x^2/6), and
+// for x < 0 its terms from x^3 on sum to at most |x|^3 / (7 (1 - |x|)) <=
+// 0.1905 |x|^3.  A log-free accept with it is still sufficient, at a quarter
+// of the series' cost; the full series is evaluated only on the slow path.
+__device__ __forceinline__ float mt_series_qhi(float d, float x) {
+  const float p = fmaf(x, fmaf(x, fmaf(fabsf(x), 0.1905f, 0x1.555556p-3f), -0x1.99999ap-3f), 0.25f);
+  const float x2 = x * x;
+  return (3.0f * d) * (x2 * x2) * p;
+}
+
 // The attempts the log-free accept did not settle: the FP32 margin with its
 // tolerance, and the FP64 re-decision when the margin is within it.  Returns
 // accept | (rechecked << 1).
 __device__ __forceinline__ int mt_slow(float alpha, float d, float x, float z, float t, float uo,
-                                       float q, bool series, uint64_t zi, uint32_t stream,
+                                       bool series, uint64_t zi, uint32_t stream,
                                        uint32_t k0, uint32_t k1, DevCounters* cnt) {
   const float lnu = flog(uo);
   float m, tol;
   if (series) {
+    const float q = mt_series_q(d, x);
     m = -lnu - q;
     tol = kTauM * (1.0f + fabsf(lnu) + q);
   } else {
@@ -154,10 +185,10 @@ __device__ __forceinline__ int mt_slow(float alpha, float d, float x, float z, f
 // The same, out of line: for large shapes (a few per cent of attempts get
 // here), so that none of it is issued, even predicated off, on the common path.
 static __device__ __noinline__ int mt_slow_call(float alpha, float d, float x, float z, float t,
-                                                float uo, float q, bool series, uint64_t zi,
+                                                float uo, bool series, uint64_t zi,
                                                 uint32_t stream, uint32_t k0, uint32_t k1,
                                                 DevCounters* cnt) {
-  return mt_slow(alpha, d, x, z, t, uo, q, series, zi, stream, k0, k1, cnt);
+  return mt_slow(alpha, d, x, z, t, uo, series, zi, stream, k0, k1, cnt);
 }
 
 // Marsaglia & Tsang's squeeze: u' < 1 - 0.0331 z^4 implies the accept test
@@ -201,31 +232,19 @@ __device__ __forceinline__ bool mt_attempt(bool run, const GammaState& g, RN& N,
   bool recheck = false;
   if (needu) {
     const float uo = u + 0x1p-24f;  // U' = U + 2^-24, exact
-    // q = 3 d x^4 (1/4 - x/5 + x^2/6 - ...) >= 0: the margin is -ln U' - q
-    float p = -0x1.111112p-4f;         // -1/15
-    p = fmaf(p, x, 0x1.24924ap-4f);    //  1/14
-    p = fmaf(p, x, -0x1.3b13b2p-4f);   // -1/13
-    p = fmaf(p, x, 0x1.555556p-4f);    //  1/12
-    p = fmaf(p, x, -0x1.745d18p-4f);   // -1/11
-    p = fmaf(p, x, 0x1.99999ap-4f);    //  1/10
-    p = fmaf(p, x, -0x1.c71c72p-4f);   // -1/9
-    p = fmaf(p, x, 0.125f);            //  1/8
-    p = fmaf(p, x, -0x1.24924ap-3f);   // -1/7
-    p = fmaf(p, x, 0x1.555556p-3f);    //  1/6
-    p = fmaf(p, x, -0x1.99999ap-3f);   // -1/5
-    p = fmaf(p, x, 0.25f);             //  1/4
-    const float x2 = x * x;
-    const float q = (3.0f * g.d) * (x2 * x2) * p;
-    // Log-free accept: e^-q >= 1 - q, so U' + q < 1 implies ln U' < -q.  The
-    // factor 1.00001 covers q's FP32 error (a few 1e-7 relative) and the bound
-    // 1 - 2^-22 the rounding of the sum with room to spare, so a fast accept
-    // is also an accept of the exact (and FP64) test.
-    if ((series && fmaf(q, 1.00001f, uo) < 0x1.fffff8p-1f) || mt_squeeze(z, uo)) {
+    // q = 3 d x^4 (1/4 - x/5 + ...) >= 0 and the margin is -ln U' - q.
+    // Log-free accept: e^-q >= 1 - q, so U' + q < 1 implies ln U' < -q; with
+    // the upper bound q_hi >= q this still holds.  The factor 1.00001 covers
+    // q_hi's FP32 error (a few 1e-7 relative) and the bound 1 - 2^-22 the
+    // rounding of the sum with room to spare, so a fast accept is also an
+    // accept of the exact (and FP64) test.
+    const float qh = mt_series_qhi(g.d, x);
+    if ((series && fmaf(qh, 1.00001f, uo) < 0x1.fffff8p-1f) || mt_squeeze(z, uo)) {
       acc = true;
     } else {
-      const int r = kLargeShape ? mt_slow_call(g.alpha, g.d, x, z, t, uo, q, series, N.pos() - 1, stream,
+      const int r = kLargeShape ? mt_slow_call(g.alpha, g.d, x, z, t, uo, series, N.pos() - 1, stream,
                                                rk.k[0][0], rk.k[0][1], cnt)
-                                : mt_slow(g.alpha, g.d, x, z, t, uo, q, series, N.pos() - 1, stream,
+                                : mt_slow(g.alpha, g.d, x, z, t, uo, series, N.pos() - 1, stream,
                                           rk.k[0][0], rk.k[0][1], cnt);
       acc = (r & 1) != 0;
       recheck = (r & 2) != 0;
@@ -272,26 +291,13 @@ __device__ __forceinline__ bool mt_attempt_peek(bool run, const GammaState& g, R
   if (needu) {
     const float uo = U.peek(0) + 0x1p-24f;  // U' = U + 2^-24, exact
     U.advance(1);
-    float p = -0x1.111112p-4f;  // the series of mt_attempt
-    p = fmaf(p, x, 0x1.24924ap-4f);
-    p = fmaf(p, x, -0x1.3b13b2p-4f);
-    p = fmaf(p, x, 0x1.555556p-4f);
-    p = fmaf(p, x, -0x1.745d18p-4f);
-    p = fmaf(p, x, 0x1.99999ap-4f);
-    p = fmaf(p, x, -0x1.c71c72p-4f);
-    p = fmaf(p, x, 0.125f);
-    p = fmaf(p, x, -0x1.24924ap-3f);
-    p = fmaf(p, x, 0x1.555556p-3f);
-    p = fmaf(p, x, -0x1.99999ap-3f);
-    p = fmaf(p, x, 0.25f);
-    const float x2 = x * x;
-    const float q = (3.0f * g.d) * (x2 * x2) * p;
-    if ((series && fmaf(q, 1.00001f, uo) < 0x1.fffff8p-1f) || mt_squeeze(z, uo)) {
+    const float qh = mt_series_qhi(g.d, x);  // the log-free accept of mt_attempt
+    if ((series && fmaf(qh, 1.00001f, uo) < 0x1.fffff8p-1f) || mt_squeeze(z, uo)) {
       acc = true;
     } else {
-      const int r = kLargeShape ? mt_slow_call(g.alpha, g.d, x, z, t, uo, q, series, N.pos() - 1, stream,
+      const int r = kLargeShape ? mt_slow_call(g.alpha, g.d, x, z, t, uo, series, N.pos() - 1, stream,
                                                rk.k[0][0], rk.k[0][1], cnt)
-                                : mt_slow(g.alpha, g.d, x, z, t, uo, q, series, N.pos() - 1, stream,
+                                : mt_slow(g.alpha, g.d, x, z, t, uo, series, N.pos() - 1, stream,
                                           rk.k[0][0], rk.k[0][1], cnt);
       acc = (r & 1) != 0;
       recheck = (r & 2) != 0;

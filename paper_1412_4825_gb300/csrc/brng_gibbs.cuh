@@ -281,19 +281,12 @@ __device__ __forceinline__ void ng_sweeps(const NormalGammaArgs& a, uint32_t n_s
         zm[i] = RN.peek(2 * i + 1);
         const float uo = RU.peek(i) + 0x1p-24f;  // U' = U + 2^-24, exact
         const float x = g.c * z;
-        // q_hi >= q = 3 d x^4 p(x), p(x) = sum_k (-x)^k / (k + 4) (the margin's
-        // series, mt_attempt): for x >= 0 the series alternates with
-        // decreasing terms, so it is below its partial sum 1/4 - x/5 + x^2/6;
-        // for x < 0 every term is positive and the terms from x^3 on sum to at
-        // most |x|^3 / (7 (1 - |x|)) <= 0.1905 |x|^3 for |x| <= 1/4.  So
-        // p_hi(x) = 1/4 - x/5 + x^2/6 + 0.1905 |x|^3 bounds p on the whole
-        // series range, and U' + q_hi < 1 is still a sufficient condition of
-        // the accept test: a fast accept stays an exact accept, and an attempt
-        // the bound does not settle goes to the exact path.  The bound exceeds
-        // q by ~3 d |x|^7 / 7, far below U's resolution at the |x| that occur.
-        const float p = fmaf(x, fmaf(x, fmaf(fabsf(x), 0.1905f, 0x1.555556p-3f), -0x1.99999ap-3f), 0.25f);
-        const float x2 = x * x;
-        const float q = (3.0f * g.d) * (x2 * x2) * p;
+        // q_hi >= q (mt_series_qhi): U' + q_hi < 1 is still a sufficient
+        // condition of the accept test, so a fast accept stays an exact
+        // accept, and an attempt it does not settle goes to the fast reject
+        // or the exact path.  q_hi exceeds q by ~3 d |x|^7 / 7, far below U's
+        // resolution at the |x| that occur.
+        const float q = mt_series_qhi(g.d, x);
         const float t = 1.0f + x;
         G[i] = g.d * (t * t * t);
         const bool ok = fabsf(x) <= kSeriesMaxX && fmaf(q, 1.00001f, uo) < 0x1.fffff8p-1f;

@@ -225,7 +225,7 @@ void brng_server::run() {
     std::vector<Slot*> busy;
     {
       std::unique_lock<std::mutex> lock(mu);
-      if (stop) {  // closing: jobs still waiting for memory are cancelled
+      if (stop) {  // closing: jobs waiting for memory or for a launch are cancelled
         const int64_t t = now_ns();
         for (uint64_t id : queue) {
           ServeJob* j = jobs[id].get();
@@ -235,6 +235,16 @@ void brng_server::run() {
           st.cancelled++;
         }
         queue.clear();
+        // admitted but not launched: their device blocks are freed with the
+        // other uncollected jobs' once the launched batches have finished
+        for (uint64_t id : ready) {
+          ServeJob* j = jobs[id].get();
+          j->stage = kFailed;
+          j->status = BRNG_EAGAIN;
+          j->t_done = t;
+          st.cancelled++;
+        }
+        ready.clear();
       }
       bool inflight = false;
       for (auto& s : slots)

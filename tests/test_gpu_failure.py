@@ -130,7 +130,7 @@ def test_serve_close_cancels_queue_and_returns():
     code, st = B.brng_serve_stats(srv)
     assert st["submitted"] == len(ids)
     t0 = time.monotonic()
-    B.brng_serve_close(srv)  # finishes the admitted jobs, cancels the queued ones
+    B.brng_serve_close(srv)  # finishes the launched batches, cancels the rest
     assert time.monotonic() - t0 < 60.0
 
 
