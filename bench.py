@@ -824,6 +824,17 @@ def run_case(args):
         h = B.Handle(SEED, 1)
         fn = lambda: m.run(h, args.sweeps, stream=stream)  # noqa: E731
         info.update(docs=args.docs, sweeps=args.sweeps, tokens=int(corpus["doc_ptr"][-1]))
+    elif args.case == "poisson_large":  # PTRS: lambda log-uniform [64, 1e6]
+        n, S = 1 << args.log2n, 1 << args.log2s
+        g = torch.Generator(device=dev)
+        g.manual_seed(SEED)
+        lam = torch.exp(np.log(64.0) + np.log(1e6 / 64.0) * torch.rand(n, generator=g, device=dev)).contiguous()
+        o = torch.empty(n, dtype=torch.float32, device=dev)
+        w = torch.empty(n, dtype=torch.int32, device=dev)
+        h = B.Handle(SEED, S)
+        h.tune(buf_len=args.buf_len or 8, warps_per_block=args.warps_per_block or 4)
+        fn = lambda: B.brng_poisson(h.h, lam, o, w, stream)  # noqa: E731
+        info.update(draws=n, streams=S)
     elif args.case == "triangle":
         h = B.Handle(SEED, 1)
         h.tune(buf_len=256, lanes_per_chain=16)
@@ -874,11 +885,12 @@ def main():
                     help="arrival window of the served mix at 2,000 jobs/s")
     ap.add_argument("--serve-near-seconds", type=float, default=20.0,
                     help="arrival window of the served mix near its measured capacity")
-    ap.add_argument("--case", choices=["mixed", "lda", "triangle", "uniform64", "ng", "lda_full"], default=None,
+    ap.add_argument("--case", choices=["mixed", "lda", "triangle", "uniform64", "ng", "lda_full", "poisson_large"],
+                    default=None,
                     help="time one workload at a chosen size instead (profiling): mixed, lda, triangle, "
                          "uniform64, or ng (the headline normal-gamma model)")
-    ap.add_argument("--log2n", type=int, default=28, help="--case mixed / uniform64: log2 of the draws")
-    ap.add_argument("--log2s", type=int, default=20, help="--case mixed / uniform64: log2 of the streams")
+    ap.add_argument("--log2n", type=int, default=28, help="--case mixed / uniform64 / poisson_large: log2 of the draws")
+    ap.add_argument("--log2s", type=int, default=20, help="--case mixed / uniform64 / poisson_large: log2 of the streams")
     ap.add_argument("--docs", type=int, default=16384, help="--case lda / lda_full: documents")
     ap.add_argument("--chains", type=int, default=N_CHAINS, help="--case ng: chains")
     ap.add_argument("--sweeps", type=int, default=500, help="--case lda/triangle/ng/lda_full: sweeps")
