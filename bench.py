@@ -788,7 +788,7 @@ def run_case(args):
     info = {"case": args.case}
     if args.case == "mixed":
         n, S = 1 << args.log2n, 1 << args.log2s
-        tag, p0, p1 = inputs.mixed_stream_torch(n, seed=SEED, device=dev)
+        tag, p0, p1 = inputs.mixed_stream_torch(n, seed=SEED, n_tags=args.tags, device=dev)
         o = torch.empty(n, dtype=torch.float32, device=dev)
         w = torch.empty(n, dtype=torch.int32, device=dev)
         h = B.Handle(SEED, S)
@@ -891,6 +891,8 @@ def main():
                          "uniform64, or ng (the headline normal-gamma model)")
     ap.add_argument("--log2n", type=int, default=28, help="--case mixed / uniform64 / poisson_large: log2 of the draws")
     ap.add_argument("--log2s", type=int, default=20, help="--case mixed / uniform64 / poisson_large: log2 of the streams")
+    ap.add_argument("--tags", type=int, default=4,
+                    help="--case mixed: the draws' tags are uniform over the first TAGS distributions")
     ap.add_argument("--docs", type=int, default=16384, help="--case lda / lda_full: documents")
     ap.add_argument("--chains", type=int, default=N_CHAINS, help="--case ng: chains")
     ap.add_argument("--sweeps", type=int, default=500, help="--case lda/triangle/ng/lda_full: sweeps")
