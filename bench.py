@@ -372,16 +372,20 @@ def extras(dev, stream, peaks, args):
                             "params": "n log-uniform integers [1, 1000], p uniform, n min(p, 1-p) <= 64",
                             "tuning": hp.tuning, "fp64_redraws_per_call": rechecks_per_call(run_b, hp)}
     # -- large means: Poisson by PTRS (lambda log-uniform [64, 1e6]) and
-    # Binomial by BTRD (n log-uniform integers up to 2^24, p uniform), FP64
+    # Binomial by BTRD (n log-uniform integers up to 2^24, p uniform); each
+    # attempt decided in FP32 / float-float, undecided attempts in FP64
     lam = torch.exp(np.log(64.0) + np.log(1e6 / 64.0) * torch.rand(n, generator=g, device=dev)).contiguous()
     t = _time_s(run_p, stream)
     out["poisson_large_2^26"] = {"deviates_per_s": n / t, "ms": t * 1e3, "lambda": "log-uniform [64, 1e6]",
-                                 "method": "PTRS, FP64"}
+                                 "method": "PTRS, certified FP32 attempts",
+                                 "fp64_attempts_per_call": rechecks_per_call(run_p, hp)}
     tr = torch.floor(torch.exp(np.log(2.0 ** 24) * torch.rand(n, generator=g, device=dev))).contiguous()
     pr = torch.rand(n, generator=g, device=dev).contiguous()
     t = _time_s(run_b, stream)
     out["binomial_large_2^26"] = {"deviates_per_s": n / t, "ms": t * 1e3,
-                                  "params": "n log-uniform integers [1, 2^24], p uniform (BTRD above mean 64)"}
+                                  "params": "n log-uniform integers [1, 2^24], p uniform (BTRD above mean 64)",
+                                  "method": "BTRD, certified FP32 attempts",
+                                  "fp64_attempts_per_call": rechecks_per_call(run_b, hp)}
     hp.close()
     del lam, o, w, tr, pr
     torch.cuda.empty_cache()
@@ -835,6 +839,18 @@ def run_case(args):
         h.tune(buf_len=args.buf_len or 8, warps_per_block=args.warps_per_block or 4)
         fn = lambda: B.brng_poisson(h.h, lam, o, w, stream)  # noqa: E731
         info.update(draws=n, streams=S)
+    elif args.case == "binomial_large":  # BTRD: n log-uniform integers [1, 2^24], p uniform
+        n, S = 1 << args.log2n, 1 << args.log2s
+        g = torch.Generator(device=dev)
+        g.manual_seed(SEED)
+        tr = torch.floor(torch.exp(np.log(2.0 ** 24) * torch.rand(n, generator=g, device=dev))).contiguous()
+        pr = torch.rand(n, generator=g, device=dev).contiguous()
+        o = torch.empty(n, dtype=torch.float32, device=dev)
+        w = torch.empty(n, dtype=torch.int32, device=dev)
+        h = B.Handle(SEED, S)
+        h.tune(buf_len=args.buf_len or 8, warps_per_block=args.warps_per_block or 4)
+        fn = lambda: B.brng_binomial(h.h, tr, pr, o, w, stream)  # noqa: E731
+        info.update(draws=n, streams=S)
     elif args.case == "triangle":
         h = B.Handle(SEED, 1)
         h.tune(buf_len=256, lanes_per_chain=16)
@@ -885,12 +901,13 @@ def main():
                     help="arrival window of the served mix at 2,000 jobs/s")
     ap.add_argument("--serve-near-seconds", type=float, default=20.0,
                     help="arrival window of the served mix near its measured capacity")
-    ap.add_argument("--case", choices=["mixed", "lda", "triangle", "uniform64", "ng", "lda_full", "poisson_large"],
+    ap.add_argument("--case", choices=["mixed", "lda", "triangle", "uniform64", "ng", "lda_full", "poisson_large",
+                                       "binomial_large"],
                     default=None,
                     help="time one workload at a chosen size instead (profiling): mixed, lda, triangle, "
                          "uniform64, or ng (the headline normal-gamma model)")
-    ap.add_argument("--log2n", type=int, default=28, help="--case mixed / uniform64 / poisson_large: log2 of the draws")
-    ap.add_argument("--log2s", type=int, default=20, help="--case mixed / uniform64 / poisson_large: log2 of the streams")
+    ap.add_argument("--log2n", type=int, default=28, help="--case mixed / uniform64 / poisson_large / binomial_large: log2 of the draws")
+    ap.add_argument("--log2s", type=int, default=20, help="--case mixed / uniform64 / poisson_large / binomial_large: log2 of the streams")
     ap.add_argument("--tags", type=int, default=4,
                     help="--case mixed: the draws' tags are uniform over the first TAGS distributions")
     ap.add_argument("--docs", type=int, default=16384, help="--case lda / lda_full: documents")

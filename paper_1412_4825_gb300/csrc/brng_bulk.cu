@@ -14,6 +14,7 @@
 #include <cmath>
 
 #include "brng_gamma.cuh"
+#include "brng_rejection32.cuh"
 #include "brng_internal.h"
 
 namespace brng {
@@ -49,25 +50,30 @@ __device__ __forceinline__ bool param_ok(int tag, float p0, float p1) {
   }
 }
 
-// Means above kInversionMaxMean take transformed rejection (PTRS, BTRD) in
-// FP64 instead of the O(mean) inversion (the comparison in FP64, as the
-// reference takes it).
+// Means above kInversionMaxMean take transformed rejection (PTRS, BTRD)
+// instead of the O(mean) inversion.  The Binomial mean n min(p, 1 - p) is
+// compared exactly: min(p, 1 - p) is a float (1 - p is exact for p > 1/2) and
+// the product is held as the exact sum hi + lo.
 __device__ __forceinline__ bool discrete_large(int tag, float p0, float p1) {
   if (tag == BRNG_TAG_POISSON) return p0 > kInversionMaxMean;
-  return static_cast<double>(p0) * fmin(static_cast<double>(p1), 1.0 - static_cast<double>(p1)) >
-         static_cast<double>(kInversionMaxMean);
+  const FF m = two_prod(p0, p1 > 0.5f ? __fadd_rn(1.0f, -p1) : p1);
+  return m.hi > kInversionMaxMean || (m.hi == kInversionMaxMean && m.lo > 0.0f);
 }
 
 // One rejection attempt for a large-mean Poisson or Binomial draw from the
 // next U elements u0, u1 of the lane's ring (u1 is consumed only when the
-// attempt reads it).  Out of line: its FP64 code runs on GB300's narrow FP64
-// pipe and must not be issued, even predicated off, on other draws' steps.
+// attempt reads it).  Decided in FP32 and float-float where that provably
+// gives the FP64 evaluation's result (brng_rejection32.cuh), else redone in
+// FP64.  Out of line: the FP64 code runs on GB300's narrow FP64 pipe and
+// must not be issued, even predicated off, on other draws' steps.
 struct LargeAttempt {
-  float k;   // the count, or -1 for a rejection
-  int used;  // U elements consumed (1 or 2)
+  float k;        // the count, or -1 for a rejection
+  int used;       // U elements consumed (1 or 2)
+  bool recheck;   // decided in FP64
 };
-static __device__ __noinline__ LargeAttempt large_attempt(bool poisson, float p0, float p1, float u0, float u1) {
+static __device__ __noinline__ LargeAttempt large_attempt64(bool poisson, float p0, float p1, float u0, float u1) {
   LargeAttempt r;
+  r.recheck = true;
   if (poisson) {
     r.used = 2;
     r.k = static_cast<float>(ptrs_attempt64(static_cast<double>(p0), static_cast<double>(u0),
@@ -79,6 +85,16 @@ static __device__ __noinline__ LargeAttempt large_attempt(bool poisson, float p0
     r.used = used;
   }
   return r;
+}
+static __device__ __noinline__ LargeAttempt large_attempt(bool poisson, float p0, float p1, float u0, float u1) {
+  const Attempt32 c =
+      poisson ? ptrs_attempt32(p0, u0, __fadd_rn(u1, 0x1p-24f)) : btrd_attempt32(p0, p1, u0, u1);
+  if (c.k == kUndecided) return large_attempt64(poisson, p0, p1, u0, u1);
+#ifdef BRNG_DEBUG
+  const LargeAttempt e = large_attempt64(poisson, p0, p1, u0, u1);
+  BRNG_CHECK(e.k == c.k && e.used == c.used);
+#endif
+  return LargeAttempt{c.k, c.used, false};
 }
 
 // Per lane, one step per iteration: the lane's current draw, or for a Gamma
@@ -329,6 +345,7 @@ __global__ void __maxnreg__(96) bulk_kernel(const BulkArgs a) {
             if (WORDS && attempts == 0) word = RU.peek_word(0);
             const LargeAttempt r = large_attempt(isP, p0, p1, RU.peek(0), RU.peek(1));
             RU.advance(static_cast<uint32_t>(r.used));
+            rc = r.recheck;
             ++attempts;
             if (r.k >= 0.0f) {
               out = r.k;

@@ -7,7 +7,8 @@ Small sizes, but every ring path: the normal-gamma sampler at every
 speculation width (ring 32, 16, 8) and the plain loop (ring 4), boosted
 shapes, producer warps, a run resumed from mid-block positions; the triangle
 sampler at 1, 4 and 16 lanes per chain; LDA at K = 64 and K = 100; the mixed
-stream with all eight tags; bulk Gamma, Dirichlet, Poisson, Binomial and FP64
+stream with all eight tags; bulk Gamma, Dirichlet, Poisson, Binomial (small
+and large means) and FP64
 uniforms; one batch of all three models.
 """
 import hashlib
@@ -107,6 +108,17 @@ def main():
     tr, pr = inputs.binomial_params(50000, seed=3)
     B.brng_binomial(h.h, T(tr), T(pr), o)
     out["binomial"] = digest(o)
+    # large means (PTRS / BTRD): the checked build redoes every attempt the
+    # FP32 path decided in FP64 and counts a differing result as a violation
+    rng = np.random.default_rng(4)
+    lam = T(inputs.log_uniform(rng, 64.0, 1e7, 50000))
+    B.brng_poisson(h.h, lam, o)
+    out["poisson_large"] = digest(o)
+    tr = np.floor(inputs.log_uniform(rng, 130.0, 16777216.0, 50000)).astype(np.float32)
+    pr = rng.random(50000).astype(np.float32)
+    pr[::3] = np.float32(0.5)
+    B.brng_binomial(h.h, T(tr), T(pr), o)
+    out["binomial_large"] = digest(o)
     da = T(np.random.default_rng(4).uniform(0.05, 3.0, (1000, 10)).astype(np.float32))
     do = torch.empty((1000, 10), dtype=torch.float32, device=DEV)
     B.brng_dirichlet(h.h, da, do)

@@ -1,0 +1,47 @@
+"""CPU check of the certified FP32 attempts of the large-mean discrete
+samplers (PTRS for Poisson, BTRD for Binomial): the kernel headers are built
+for the host (tests/rejection32_host.cpp maps each device intrinsic to the
+IEEE host operation with the same rounding) and every attempt the FP32 /
+float-float path decides must give the count and element use of the FP64
+attempt, on random parameters over the whole large-mean range and random
+elements on the 2^-24 grid.  The FP32 path must also decide almost every
+attempt, else the FP64 pipe would still set the speed.
+
+The host's logf and log1pf are not CUDA's (both within about one ulp), so
+this also checks that the bands do not depend on one implementation of the
+two functions; the checked GPU build repeats the comparison with CUDA's.
+"""
+import json
+import os
+import shutil
+import subprocess
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_1412_4825_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("rejection32")
+    (d / "fake").mkdir()
+    (d / "fake" / "cuda_runtime.h").write_text("")  # the headers need nothing from it on the host
+    exe = str(d / "rejection32_host")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-ffp-contract=off", "-I", str(d / "fake"), "-I", CSRC,
+                    os.path.join(HERE, "rejection32_host.cpp"), "-o", exe], check=True)
+    return exe
+
+
+@pytest.mark.parametrize("method,seed", [("ptrs", 1), ("ptrs", 2), ("btrd", 3), ("btrd", 4)])
+def test_certified_attempts_equal_fp64(harness, method, seed):
+    n = 3_000_000
+    r = subprocess.run([harness, method, str(n), str(seed)], capture_output=True, text=True, check=True)
+    res = json.loads(r.stdout)
+    assert res["mismatches"] == 0, r.stderr
+    assert res["attempts"] == n
+    assert res["undecided"] <= 3e-3 * n, res  # FP64 for a few attempts in a thousand at most
+    assert 0.8 * n < res["accepted"] < 0.95 * n, res  # both outcomes are exercised
