@@ -147,8 +147,9 @@ __device__ __forceinline__ float ds_gap(float u, DS F) { return (u - F.hi) - F.l
 // FP32 here (the warp runs the search to its lanes' largest k, so each step's
 // cost counts more than the rare redraws): p_0 = e^-lambda (expf, within
 // 4 u), p_k = (p_{k-1} lambda) / k (IEEE), F summed left to right, so F(k) is
-// within (4 + 3k) u of the reference (one u per multiply, divide and sum);
-// the comparisons are taken beyond (16 + 8k) u, else the draw is redone in FP64.
+// within (4 + 3k) u of the reference relative to F(k) (one u per multiply,
+// divide and sum, all terms positive); the comparisons are taken beyond
+// (16 + 8k) u F, else the draw is redone in FP64.
 static __device__ __noinline__ float poisson_recheck(float lambda, float u) {
   return static_cast<float>(poisson_inv64(static_cast<double>(lambda), static_cast<double>(u),
                                           kPoissonMaxK));
@@ -174,8 +175,8 @@ __device__ __forceinline__ float poisson_draw(float lambda, float u, bool* reche
     F = F + p;
   }
   const float kf = static_cast<float>(k);
-  const bool sure = !ran_out && (F - u > (16.0f + 8.0f * kf) * 0x1p-24f) &&
-                    (k == 0 || u - Fprev > (8.0f + 8.0f * kf) * 0x1p-24f);
+  const float rel = (16.0f + 8.0f * kf) * 0x1p-24f;  // every error is relative to F
+  const bool sure = !ran_out && (F - u > rel * F) && (k == 0 || u - Fprev > rel * Fprev);
   *rechecked = !sure;
   return sure ? kf : poisson_recheck(lambda, u);
 }
@@ -183,7 +184,8 @@ __device__ __forceinline__ float poisson_draw(float lambda, float u, bool* reche
 // Binomial(n, p) from one U element u, on q = min(p, 1 - p) (n - k when
 // p > 1/2): p_0 = exp(a), a = n log1p(-q) (library log1pf and expf: within
 // (3|a| + 4) u relative), r = q / (1 - q) and p_k = p_{k-1} ((n - k + 1) r) / k
-// in double-single.
+// in double-single, so F(k) is within (3|a| + 4) u of the reference relative
+// to F(k); the comparisons are taken beyond twice that.
 static __device__ __noinline__ float binomial_recheck(float n, float p, float u) {
   return static_cast<float>(binomial_inv64(static_cast<double>(n), static_cast<double>(p),
                                            static_cast<double>(u)));
@@ -215,8 +217,9 @@ __device__ __forceinline__ float binomial_draw(float n, float p, float u, bool* 
     }
     F = ds_add(F, pk);
   }
-  const float tol = (6.0f * fabsf(a) + 8.0f) * 0x1p-24f + 0x1p-30f;
-  const bool sure = !ran_out && -ds_gap(u, F) > tol && (k == 0.0f || ds_gap(u, Fprev) > tol);
+  // all terms carry p_0's relative error: the tolerance scales with F
+  const float rel = (6.0f * fabsf(a) + 8.0f) * 0x1p-24f + 0x1p-30f;
+  const bool sure = !ran_out && -ds_gap(u, F) > rel * F.hi && (k == 0.0f || ds_gap(u, Fprev) > rel * Fprev.hi);
   *rechecked = !sure;
   if (!sure) return binomial_recheck(n, p, u);
   return flip ? n - k : k;

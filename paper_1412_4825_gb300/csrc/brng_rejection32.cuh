@@ -21,8 +21,9 @@
 //  * the log-scale tests: FP32, with every logarithm taken in a form whose
 //    argument is known to a few rounding errors (log1p(t) for ratios near 1,
 //    the factorials through g(t) = (1+t) log1p(t) - t), CUDA's logf and
-//    log1pf (at most 1 ulp), and a band of 2^-18 (64 u) times the sum of the
-//    magnitudes of the terms, plus the FP64 evaluation's own rounding.
+//    log1pf (at most 1 ulp), and a band of 32u or 64u times the sum of the
+//    magnitudes of the terms (twice or more the worst-case FP32 error), plus
+//    the FP64 evaluation's own rounding.
 // The bands are several times the error bounds stated with each decision, so
 // an attempt is reported decided only when the FP64 evaluation cannot decide
 // it otherwise; the checked build recomputes every decided attempt in FP64
@@ -161,13 +162,34 @@ __device__ __forceinline__ Attempt32 ptrs_attempt32(float lam, float u0, float v
                     fabsf(rhs) + fabsf(diff) + 1.0f;
   // the FP64 evaluation sums -lam, k ln lam and ln k! (each up to ~2e8)
   const float e64 = 0x1p-47f * (lam + x * (2.0f * fabsf(lnlam) + fabsf(L1) + 2.0f));
-  const float band = __fmaf_rn(mag, 0x1p-18f, e64);
+  // Each term's FP32 error is at most 12u times its magnitude (logf, log1pf
+  // within 1 ulp = 2u relative; the largest factor, 11.5u, on x |L1| and |d|
+  // of the |t| >= 1/8 form), so 32u (2^-19) times the sum is twice the bound.
+  const float band = __fmaf_rn(mag, 0x1p-19f, e64);
   if (diff <= -band) {
     r.k = k;
   } else if (!(diff > band)) {
     r.k = kUndecided;
   }
   return r;
+}
+
+// g1(x) = x - log1p(x) >= 0 for x > -1/2: the series x^2 (1/2 - x/3 + ...)
+// through x^9 for |x| < 1/8 (remainder below 2^-26 relative), else the
+// difference (which loses at most a factor 16 to cancellation there).
+__device__ __forceinline__ float g1_32(float x) {
+  if (fabsf(x) < 0.125f) {
+    float s = -1.0f / 9.0f;
+    s = __fmaf_rn(s, x, 0.125f);
+    s = __fmaf_rn(s, x, -1.0f / 7.0f);
+    s = __fmaf_rn(s, x, 1.0f / 6.0f);
+    s = __fmaf_rn(s, x, -0.2f);
+    s = __fmaf_rn(s, x, 0.25f);
+    s = __fmaf_rn(s, x, -1.0f / 3.0f);
+    s = __fmaf_rn(s, x, 0.5f);
+    return __fmul_rn(__fmul_rn(x, x), s);
+  }
+  return __fadd_rn(x, -log1pf(x));
 }
 
 // ---- BTRD ---------------------------------------------------------------
@@ -180,6 +202,7 @@ struct BtrdExact {
   FF np;      // n p, exactly
   float m;    // floor((n + 1) p)
   float fr;   // (n + 1) p - m, rounded once
+  FF fr_ff;   // (n + 1) p - m, exactly
 };
 
 __device__ __forceinline__ FF ull_to_ff(unsigned long long v, float scale) {  // v < 2^49, scale 2^-j
@@ -203,7 +226,8 @@ __device__ __forceinline__ BtrdExact btrd_exact(float n, float p) {  // p in [2^
   e.cfr = ull_to_ff(C & mask, scale);
   e.np = ull_to_ff(P, scale);
   e.m = __ull2float_rn(R >> sh);
-  e.fr = __fmul_rn(__ull2float_rn(R & mask), scale);
+  e.fr_ff = ull_to_ff(R & mask, scale);
+  e.fr = e.fr_ff.hi;
   return e;
 }
 
@@ -258,7 +282,8 @@ __device__ __forceinline__ Attempt32 btrd_attempt32(float n, float p_in, float u
     return r;
   }
   FF u, V;
-  if (d2 > 0.0f) {  // v >= vr: u from the second element, exactly
+  const bool exact_u = d2 > 0.0f;
+  if (exact_u) {  // v >= vr: u from the second element, exactly
     u = ff_from(__fadd_rn(u1, -0.5f));
     V = ff_from(v0);
   } else {
@@ -278,7 +303,8 @@ __device__ __forceinline__ Attempt32 btrd_attempt32(float n, float p_in, float u
   const FF A2 = ff_div(a2, us);
   const FF T = ff_mul(ff_add(A2, b), u);
   const FF Y = ff_add(T, e.cfr);
-  const float rel_us = __fdiv_rn(0x1p-36f, us.hi);  // bound on |us_ff - us| / us
+  // bound on |us_ff - us| / us: us is exact when u is
+  const float rel_us = exact_u ? 0.0f : __fdiv_rn(0x1p-36f, us.hi);
   const float ek = __fmaf_rn(fabsf(T.hi) + b.hi + 1.0f + fabsf(A2.hi) * rel_us * 0x1p36f, 0x1p-36f,
                              __fmul_rn(e.ci + fabsf(T.hi), 0x1p-48f));
   // k = ci + floor(Y); k < 0 or k > n rejects, decided on floor(Y) against
@@ -332,7 +358,8 @@ __device__ __forceinline__ Attempt32 btrd_attempt32(float n, float p_in, float u
                                         0.5f));
   const float t = -__fdiv_rn(__fmul_rn(km, km), __fmul_rn(2.0f, npq32));
   const float lo = __fadd_rn(t, -rho), hi = __fadd_rn(t, rho);
-  const float es = __fmaf_rn(fabsf(t) + rho + fabsf(lv) + 1.0f, 0x1p-18f, rel_v);
+  // t within 4u, rho within 12u, lv within 2u |lv| + rel_v: 32u covers twice
+  const float es = __fmaf_rn(fabsf(t) + rho + fabsf(lv) + 1.0f, 0x1p-19f, rel_v);
   if (lv < lo - es) {
     r.k = res;
     return r;
@@ -348,31 +375,37 @@ __device__ __forceinline__ Attempt32 btrd_attempt32(float n, float p_in, float u
 
   // the exact bound: h + (n+1) ln(nm/nk) + (k+1/2) ln(nk r/(k+1)) - fc(k) - fc(n-k),
   // h = (m+1/2) ln((m+1)/(r nm)) + fc(m) + fc(n-m), each ratio near 1 through log1p:
-  //   (m+1)/(r nm) = 1 + (q - fr)/(p nm),  nm/nk = 1 + (k - m)/nk,
-  //   nk r/(k+1) = 1 + (fr + p + m - k - 1)/(q (k+1))
+  //   (m+1)/(r nm) = 1 + (q - fr)/(p nm),  nm/nk = 1 + x1, x1 = (k - m)/nk,
+  //   nk r/(k+1) = 1 + x2, x2 = (fr + p + m - k - 1)/(q (k+1)).
+  // The two middle terms are each about (k - m)/q and cancel to O(1), so they
+  // are split as Lin - Quad with g1(x) = x - log1p(x) >= 0:
+  //   Lin  = (n+1) x1 + (k+1/2) x2           in float-float (the cancellation),
+  //   Quad = (n+1) g1(x1) + (k+1/2) g1(x2)   in FP32 (two non-negative terms).
   const float q32 = q.hi;
   const float nm = __fadd_rn(__fadd_rn(n, -m), 1.0f);  // exact
   const float nk = __fadd_rn(__fadd_rn(n, -k), 1.0f);  // exact
+  const float k1 = __fadd_rn(k, 1.0f);
   const float La = log1pf(__fdiv_rn(__fadd_rn(q32, -e.fr), __fmul_rn(p, nm)));
   const float hA = __fmul_rn(__fadd_rn(m, 0.5f), La);
-  const float fcm = stirling_tail32(__fadd_rn(m, 1.0f));
-  const float fcnm = stirling_tail32(nm);
-  const float Lb = log1pf(__fdiv_rn(__fadd_rn(k, -m), nk));
-  const float B1 = __fmaf_rn(n, Lb, Lb);
-  const float k1 = __fadd_rn(k, 1.0f);
-  const float num = __fadd_rn(__fadd_rn(e.fr, p), __fadd_rn(__fadd_rn(m, -k), -1.0f));
-  const float den = __fmul_rn(q32, k1);
-  const float argc = __fdiv_rn(num, den);
-  // near 1 + argc = 0 the ratio itself is the better-conditioned argument
-  const float Lc = argc < -0.5f ? logf(__fdiv_rn(__fmul_rn(nk, p), den)) : log1pf(argc);
-  const float B2 = __fmul_rn(__fadd_rn(k, 0.5f), Lc);
-  const float fck = stirling_tail32(k1);
-  const float fcnk = stirling_tail32(nk);
-  const float h = __fadd_rn(__fadd_rn(hA, fcm), fcnm);
-  const float bound = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(h, B1), B2), -fck), -fcnk);
+  const float h = __fadd_rn(__fadd_rn(hA, stirling_tail32(__fadd_rn(m, 1.0f))), stirling_tail32(nm));
+  const FF x1 = ff_div_f(ff_from(__fadd_rn(k, -m)), nk);
+  const FF num = ff_add(ff_add_f(e.fr_ff, p), ff_from(__fadd_rn(__fadd_rn(m, -k), -1.0f)));
+  const FF qk1 = ff_mul_f(q, k1);
+  const FF x2 = ff_div(num, qk1);
+  const FF P1 = ff_add(ff_mul_f(x1, n), x1);                  // (n + 1) x1
+  const FF P2 = ff_add(ff_mul_f(x2, k), ff_mul_f(x2, 0.5f));  // (k + 1/2) x2
+  const float Lin = ff_add(P1, P2).hi;
+  // 1 + x2 near 0: the ratio nk p / (q (k+1)) is the better-conditioned argument
+  const float g2 = x2.hi < -0.5f ? __fadd_rn(x2.hi, -logf(__fdiv_rn(__fmul_rn(nk, p), qk1.hi))) : g1_32(x2.hi);
+  const float g1v = g1_32(x1.hi);
+  const float Quad = __fadd_rn(__fmaf_rn(n, g1v, g1v), __fmul_rn(__fadd_rn(k, 0.5f), g2));
+  const float bound = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(h, Lin), -Quad), -stirling_tail32(k1)),
+                                -stirling_tail32(nk));
   const float diff = __fadd_rn(lv, -bound);
-  const float S = fabsf(hA) + fabsf(B1) + fabsf(B2) + fabsf(h) + fabsf(bound) + fabsf(diff) + 4.0f;
-  const float band = __fmaf_rn(S, 0x1p-18f, 0x1p-26f) + __fmaf_rn(4.0f * fabsf(lv), 0x1p-24f, rel_v);
+  const float S = fabsf(hA) + fabsf(h) + fabsf(Lin) + Quad + fabsf(bound) + fabsf(diff) + 4.0f;
+  // the FP64 evaluation rounds the middle terms (each up to |A1|, |A2|) on their own
+  const float e64 = __fmaf_rn(fabsf(P1.hi) + fabsf(P2.hi), 0x1p-46f, 0x1p-26f);
+  const float band = __fmaf_rn(S, 0x1p-18f, e64) + __fmaf_rn(4.0f * fabsf(lv), 0x1p-24f, rel_v);
   r.k = diff <= -band ? res : (diff > band ? -1.0f : kUndecided);
   return r;
 }
