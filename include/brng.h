@@ -86,7 +86,8 @@ typedef enum {
 typedef struct {
   uint64_t n_domain;   /* draws with an invalid parameter (NaN output)               */
   uint64_t n_reject;   /* Gamma draws that hit the attempt cap (NaN output)           */
-  uint64_t n_recheck;  /* Gamma tests re-decided in FP64 (FP32 margin within tolerance) */
+  uint64_t n_recheck;  /* Gamma tests, discrete draws and rejection attempts re-decided
+                          in FP64 (the FP32 result within its error bound of a boundary) */
   uint64_t n_flip;     /* ... of which the FP64 decision differed from the FP32 sign  */
   float max_flip_ratio;/* max |FP32 margin| / tolerance over the flips (must stay < 1) */
   uint32_t n_timeout;  /* bounded device waits that ran out (chains ended with NaN)  */
@@ -236,12 +237,14 @@ int brng_weibull(brng_t *h, size_t n, const float *k, const float *lambda, float
  * rejection PTRS (Insurance: Math. Econ. 12, 1993): per attempt U in [0, 1)
  * and V = U' from the same buffer, k = floor((2a/u_s + b)(U - 1/2) + lambda +
  * 0.43) with u_s = 1/2 - |U - 1/2|, a squeeze accept, and otherwise the test
- * ln(V / alpha'(u_s)) <= k ln lambda - lambda - ln k!; computed in FP64 (own
- * log, IEEE sqrt/division, Stirling's series for ln k!) so that every count
- * equals the FP64 reference's.  out gets k as a float (exact).  Needs finite
- * 0 < lambda <= BRNG_POISSON_MAX_LAMBDA; FP64 redraws of the inversion count in
- * n_recheck; a rejection draw that runs out of attempts (64) is NaN and counts
- * in n_reject. */
+ * ln(V / alpha'(u_s)) <= k ln lambda - lambda - ln k!.  The reference is the
+ * FP64 evaluation (own log, IEEE sqrt/division, Stirling's series for ln k!);
+ * each attempt is decided in FP32 and float-float where that provably gives
+ * the same result, else in FP64, so every count equals the reference's.  out
+ * gets k as a float (exact).  Needs finite 0 < lambda <=
+ * BRNG_POISSON_MAX_LAMBDA; FP64 redraws of the inversion and attempts redone
+ * in FP64 count in n_recheck; a rejection draw that runs out of attempts (64)
+ * is NaN and counts in n_reject. */
 int brng_poisson(brng_t *h, size_t n, const float *lambda, float *out, uint32_t *words,
                  brng_stream_t stream);
 /* Binomial(n, p), the second discrete distribution of the expanded library
@@ -255,7 +258,9 @@ int brng_poisson(brng_t *h, size_t n, const float *lambda, float *out, uint32_t 
  * attempt one U' (V), and unless V falls in the immediate-accept region one
  * more element (U when V >= v_r, else V' = U' v_r), then the recursive
  * evaluation of f(k)/f(m) for |k - m| <= 15 or a log-scale squeeze and the
- * Stirling-corrected log test -- all in FP64 as the reference.  trials: device
+ * Stirling-corrected log test; the reference is their FP64 evaluation, and
+ * each attempt is decided in FP32 / float-float only where that provably
+ * gives its result (else in FP64; counted in n_recheck).  trials: device
  * float[n] holding integers 0 <= n <= 2^24; prob: device float[n] in [0, 1]. */
 int brng_binomial(brng_t *h, size_t n, const float *trials, const float *prob, float *out,
                   uint32_t *words, brng_stream_t stream);
