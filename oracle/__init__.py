@@ -249,7 +249,7 @@ def dirichlet(seed, S, alpha, pos=None, buf_len=64, with_logs=False):
 
 def mixed(seed, S, tag, p0, p1, pos=None, buf_len=64, streams=None, nthreads=1, with_cond=False):
     """Mixed-tag stream; `streams=(s0, s1)` restricts to those streams only
-    (the other outputs stay NaN / 0)."""
+    (the other outputs stay NaN / 0); a list of such pairs computes each range."""
     tag = np.ascontiguousarray(tag, dtype=np.uint8)
     p0, p1 = _f32(p0), _f32(p1)
     n = tag.size
@@ -261,8 +261,13 @@ def mixed(seed, S, tag, p0, p1, pos=None, buf_len=64, streams=None, nthreads=1, 
         st = lib().or_mixed_mt(seed, S, _p(pos), n, _p(tag), _p(p0), _p(p1), _p(out), _p(words),
                                _p(cond), buf_len, _threads(nthreads))
     else:
-        st = lib().or_mixed_streams(seed, S, streams[0], streams[1], _p(pos), n, _p(tag), _p(p0),
-                                    _p(p1), _p(out), _p(words), _p(cond), buf_len)
+        ranges = [streams] if np.isscalar(streams[0]) else list(streams)
+        st = 0
+        for s0, s1 in ranges:
+            st = lib().or_mixed_streams(seed, S, int(s0), int(s1), _p(pos), n, _p(tag), _p(p0),
+                                        _p(p1), _p(out), _p(words), _p(cond), buf_len)
+            if st:
+                break
     if with_cond:
         return out, words, pos, st, cond
     return out, words, pos, st

@@ -143,18 +143,83 @@ __device__ __forceinline__ DS ds_add(DS x, DS y) {  // both >= 0
 // (u - F) as one float, F = hi + lo
 __device__ __forceinline__ float ds_gap(float u, DS F) { return (u - F.hi) - F.lo; }
 
+// In the single-distribution kernels the inversion searches run at most
+// kInvSteps steps per iteration of the kernel's loop and resume on the next:
+// a lane with a long search (a mean near 64) then takes several iterations
+// while its neighbours move on to their next draws, instead of the whole warp
+// running every step to the largest k among its lanes (GB300, 2^26 draws:
+// Poisson means <= 64 3.54 -> 2.28 ms, Binomial 8.1 -> 5.85 ms; 8 and 32
+// steps were slower).  The U element is consumed when the search starts, so
+// positions and values do not depend on the bound.  The mixed stream, and a
+// warp with rejection attempts (whose steps are dear anyway), search to the
+// end in one step: the mixed kernel has no registers left for the state.
+constexpr int kInvSteps = 16;
+
+struct InvSearch {  // a search in progress (Poisson uses the hi words only)
+  float u, k;
+  DS pk, F, Fprev;
+};
+
 // Poisson(lambda) from one U element u: the smallest k with u < F(k).  Plain
-// FP32 here (the warp runs the search to its lanes' largest k, so each step's
-// cost counts more than the rare redraws): p_0 = e^-lambda (expf, within
-// 4 u), p_k = (p_{k-1} lambda) / k (IEEE), F summed left to right, so F(k) is
-// within (4 + 3k) u of the reference relative to F(k) (one u per multiply,
-// divide and sum, all terms positive); the comparisons are taken beyond
-// (16 + 8k) u F, else the draw is redone in FP64.
+// FP32 here (a warp runs each step for all its searching lanes, so each
+// step's cost counts more than the rare redraws): p_0 = e^-lambda (expf,
+// within 4 u), p_k = (p_{k-1} lambda) / k (IEEE), F summed left to right, so
+// F(k) is within (4 + 3k) u of the reference relative to F(k) (one u per
+// multiply, divide and sum, all terms positive); the comparisons are taken
+// beyond (16 + 8k) u F, else the draw is redone in FP64.
 static __device__ __noinline__ float poisson_recheck(float lambda, float u) {
   return static_cast<float>(poisson_inv64(static_cast<double>(lambda), static_cast<double>(u),
                                           kPoissonMaxK));
 }
 
+__device__ __forceinline__ void poisson_start(InvSearch& s, float lambda, float u) {
+  s.u = u;
+  s.k = 0.0f;
+  s.pk = DS{expf(-lambda), 0.0f};
+  s.F = s.pk;
+  s.Fprev = DS{0.0f, 0.0f};
+}
+
+// Up to kInvSteps steps: 1 when u < F(k) (found), -1 when the search ran out
+// (k at its cap, or p_k underflowed), 0 to resume later.
+__device__ __forceinline__ int poisson_steps(InvSearch& s, float lambda) {
+  float p = s.pk.hi, F = s.F.hi, Fprev = s.Fprev.hi, k = s.k;
+  int st = 0;
+  for (int j = 0; j < kInvSteps; ++j) {
+    if (s.u < F) {
+      st = 1;
+      break;
+    }
+    if (k >= static_cast<float>(kPoissonMaxK)) {
+      st = -1;
+      break;
+    }
+    k += 1.0f;
+    p = (p * lambda) / k;
+    Fprev = F;
+    if (p == 0.0f) {
+      st = -1;
+      break;
+    }
+    F = F + p;
+  }
+  if (st == 0 && s.u < F) st = 1;
+  s.pk.hi = p;
+  s.F.hi = F;
+  s.Fprev.hi = Fprev;
+  s.k = k;
+  return st;
+}
+
+__device__ __forceinline__ float poisson_finish(const InvSearch& s, float lambda, bool ran_out, bool* rechecked) {
+  const float rel = (16.0f + 8.0f * s.k) * 0x1p-24f;  // every error is relative to F
+  const bool sure = !ran_out && (s.F.hi - s.u > rel * s.F.hi) && (s.k == 0.0f || s.u - s.Fprev.hi > rel * s.Fprev.hi);
+  *rechecked = !sure;
+  return sure ? s.k : poisson_recheck(lambda, s.u);
+}
+
+// The whole search in one step (the mixed stream, and warps with rejection
+// attempts, whose steps are dear anyway).
 __device__ __forceinline__ float poisson_draw(float lambda, float u, bool* rechecked) {
   float p = expf(-lambda);
   float F = p, Fprev = 0.0f;
@@ -191,6 +256,63 @@ static __device__ __noinline__ float binomial_recheck(float n, float p, float u)
                                            static_cast<double>(u)));
 }
 
+__device__ __forceinline__ float binomial_q(float p) { return p > 0.5f ? 1.0f - p : p; }  // exact
+
+__device__ __forceinline__ void binomial_start(InvSearch& s, float n, float p, float u) {
+  s.u = u;
+  s.k = 0.0f;
+  s.pk = DS{expf(n * log1pf(-binomial_q(p))), 0.0f};
+  s.F = s.pk;
+  s.Fprev = DS{0.0f, 0.0f};
+}
+
+__device__ __forceinline__ int binomial_steps(InvSearch& s, float n, float p) {
+  const float q = binomial_q(p);
+  const float omq_hi = 1.0f - q;
+  const DS omq{omq_hi, (1.0f - omq_hi) - q};  // 1 - q exactly
+  const float r1 = __fdividef(q, omq.hi);
+  const DS r = ds_norm(r1, __fdividef(fmaf(-r1, omq.hi, q) - r1 * omq.lo, omq.hi));
+  DS pk = s.pk, F = s.F, Fprev = s.Fprev;
+  float k = s.k;
+  int st = 0;
+  for (int j = 0; j < kInvSteps; ++j) {
+    if (ds_gap(s.u, F) < 0.0f) {
+      st = 1;
+      break;
+    }
+    if (k >= n) {
+      st = -1;
+      break;
+    }
+    k += 1.0f;
+    pk = ds_div(ds_mul(pk, ds_mul(r, (n - k) + 1.0f)), k);
+    Fprev = F;
+    if (pk.hi == 0.0f) {
+      st = -1;
+      break;
+    }
+    F = ds_add(F, pk);
+  }
+  if (st == 0 && ds_gap(s.u, F) < 0.0f) st = 1;
+  s.pk = pk;
+  s.F = F;
+  s.Fprev = Fprev;
+  s.k = k;
+  return st;
+}
+
+__device__ __forceinline__ float binomial_finish(const InvSearch& s, float n, float p, bool ran_out,
+                                                 bool* rechecked) {
+  // all terms carry p_0's relative error: the tolerance scales with F
+  const float a = n * log1pf(-binomial_q(p));
+  const float rel = (6.0f * fabsf(a) + 8.0f) * 0x1p-24f + 0x1p-30f;
+  const bool sure = !ran_out && -ds_gap(s.u, s.F) > rel * s.F.hi &&
+                    (s.k == 0.0f || ds_gap(s.u, s.Fprev) > rel * s.Fprev.hi);
+  *rechecked = !sure;
+  if (!sure) return binomial_recheck(n, p, s.u);
+  return p > 0.5f ? n - s.k : s.k;
+}
+
 __device__ __forceinline__ float binomial_draw(float n, float p, float u, bool* rechecked) {
   const bool flip = p > 0.5f;
   const float q = flip ? 1.0f - p : p;  // exact for p in (1/2, 1]
@@ -225,12 +347,19 @@ __device__ __forceinline__ float binomial_draw(float n, float p, float u, bool* 
   return flip ? n - k : k;
 }
 
-// 96 registers: the out-of-line rejection attempt for large discrete means
-// raised the mixed-stream kernel from 89 to 100 registers, one occupancy step
-// lower (measured on GB300, 2^28 draws: 6.59 ms without the call, 7.85 ms at
-// 100 registers, 6.69 ms capped at 96, no spills).
+// Register caps (measured on GB300, 2^28 mixed draws / 2^26 discrete draws;
+// no spills at 96, a few words at 72): the mixed stream at 96 -- the
+// out-of-line rejection attempt had raised it from 89 to 100 registers, one
+// occupancy step lower (6.59 ms without the call, 7.85 ms at 100, 6.69 ms
+// capped at 96); every single-distribution kernel at 72, seven blocks of 4
+// warps per SM (Poisson means <= 64: 2.45 ms at 80 registers, 2.28 at 72,
+// 2.72 at 64; Binomial 6.02 / 5.85 / 5.97; the other distributions need
+// fewer).
+template <int TAG>
+constexpr int kBulkMaxRegs = TAG < 0 ? 96 : 72;
+
 template <int TAG, bool WORDS>
-__global__ void __maxnreg__(96) bulk_kernel(const BulkArgs a) {
+__global__ void __maxnreg__(kBulkMaxRegs<TAG>) bulk_kernel(const BulkArgs a) {
   using D = BulkDomains<TAG>;
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned warp = threadIdx.x >> 5;
@@ -275,7 +404,8 @@ __global__ void __maxnreg__(96) bulk_kernel(const BulkArgs a) {
   bool ok = has_stream && i < a.n && param_ok(tag, p0, p1);
   count_warp(&a.cnt->n_domain, has_stream && i < a.n && !ok);
   GammaState g = gamma_setup(ok && tag == BRNG_TAG_GAMMA ? p0 : 1.0f);
-  int attempts = 0;
+  int attempts = 0;  // of the current draw (an inversion search: 1 once started)
+  InvSearch inv;
   uint32_t word = 0;
 
   while (true) {
@@ -334,16 +464,37 @@ __global__ void __maxnreg__(96) bulk_kernel(const BulkArgs a) {
     if constexpr (D::kU && (TAG < 0 || TAG == BRNG_TAG_POISSON || TAG == BRNG_TAG_BINOMIAL)) {
       if (__builtin_expect(__any_sync(kFull, isP || isB), TAG >= 0)) {  // one vote for both
         bool rc = false, rej = false;
+        const bool large = (isP || isB) && discrete_large(tag, p0, p1);
+        const bool any_large = __any_sync(kFull, large);
         if (isP || isB) {
-          if (!discrete_large(tag, p0, p1)) {  // inversion of one U
-            const float u = RU.peek(0);
-            if (WORDS) word = RU.peek_word(0);
-            RU.advance(1);
-            if constexpr (TAG < 0 || TAG == BRNG_TAG_POISSON)
-              if (isP) out = poisson_draw(p0, u, &rc);
-            if constexpr (TAG < 0 || TAG == BRNG_TAG_BINOMIAL)
-              if (isB) out = binomial_draw(p0, p1, u, &rc);
-            done = true;
+          if (!large) {  // inversion of one U
+            if (TAG < 0 || (attempts == 0 && any_large)) {  // the whole search now
+              const float u = RU.peek(0);
+              if (WORDS) word = RU.peek_word(0);
+              RU.advance(1);
+              if constexpr (TAG < 0 || TAG == BRNG_TAG_POISSON)
+                if (isP) out = poisson_draw(p0, u, &rc);
+              if constexpr (TAG < 0 || TAG == BRNG_TAG_BINOMIAL)
+                if (isB) out = binomial_draw(p0, p1, u, &rc);
+              done = true;
+            } else if constexpr (TAG >= 0) {  // resumable: at most kInvSteps steps per iteration
+              if (attempts == 0) {  // the draw's first step: take its U element
+                const float u = RU.peek(0);
+                if (WORDS) word = RU.peek_word(0);
+                RU.advance(1);
+                attempts = 1;
+                if constexpr (TAG == BRNG_TAG_POISSON) poisson_start(inv, p0, u);
+                if constexpr (TAG == BRNG_TAG_BINOMIAL) binomial_start(inv, p0, p1, u);
+              }
+              int st = 0;
+              if constexpr (TAG == BRNG_TAG_POISSON) st = poisson_steps(inv, p0);
+              if constexpr (TAG == BRNG_TAG_BINOMIAL) st = binomial_steps(inv, p0, p1);
+              if (st != 0) {
+                if constexpr (TAG == BRNG_TAG_POISSON) out = poisson_finish(inv, p0, st < 0, &rc);
+                if constexpr (TAG == BRNG_TAG_BINOMIAL) out = binomial_finish(inv, p0, p1, st < 0, &rc);
+                done = true;
+              }
+            }
           } else {  // one transformed-rejection attempt (1 or 2 U elements)
             if (WORDS && attempts == 0) word = RU.peek_word(0);
             const LargeAttempt r = large_attempt(isP, p0, p1, RU.peek(0), RU.peek(1));

@@ -159,6 +159,14 @@ def mixed_stream_torch(n: int, seed: int = 42, n_tags: int = 4, device="cuda"):
     if n_tags > TAG_POISSON:
         p0 = torch.where(tag == TAG_POISSON, logu(0.05, 64.0), p0)
         p1 = torch.where(tag == TAG_POISSON, torch.zeros_like(p1), p1)
+    if n_tags > TAG_BINOMIAL:  # as binomial_params: trials log-U integers [1, 1000], mean <= 64
+        trials = torch.floor(logu(1.0, 1001.0))
+        prob = torch.rand(n, generator=g, device=device, dtype=torch.float32)
+        q = torch.minimum(prob, 1.0 - prob)
+        cap = 0.999 * 64.0 / torch.clamp(trials, min=1.0)
+        prob = torch.where(trials * q > 64.0, torch.where(prob <= 0.5, cap, 1.0 - cap), prob)
+        p0 = torch.where(tag == TAG_BINOMIAL, trials, p0)
+        p1 = torch.where(tag == TAG_BINOMIAL, prob, p1)
     return tag, p0.contiguous(), p1.contiguous()
 
 

@@ -507,6 +507,47 @@ def test_binomial_large_means_bit_exact(max_trials, S):
     assert np.array_equal(h.positions(), rpos)
 
 
+@pytest.mark.parametrize("which", ["poisson", "binomial"])
+def test_large_means_full_size_sampled(which):
+    """The bench's large-mean lines in their launch configuration: 2^26 draws
+    over 2^20 streams, ring 8, 4 warps per block (Poisson with lambda
+    log-uniform [64, 1e6]: PTRS; Binomial with n log-uniform integers to 2^24
+    and p uniform: BTRD above mean 64, inversion below); 128 whole streams
+    recomputed by the oracle: counts, first words and positions bit-exact."""
+    seed, S, n = 42, 1 << 20, 1 << 26
+    g = torch.Generator(device=DEV)
+    g.manual_seed(3)
+    if which == "poisson":
+        p0 = torch.exp(np.log(64.0) + np.log(1e6 / 64.0) * torch.rand(n, generator=g, device=DEV)).contiguous()
+        p1 = torch.zeros_like(p0)
+        tag = 6
+    else:
+        p0 = torch.floor(torch.exp(np.log(2.0 ** 24) * torch.rand(n, generator=g, device=DEV))).contiguous()
+        p1 = torch.rand(n, generator=g, device=DEV).contiguous()
+        tag = 7
+    h = handle(seed, S, 8, warps_per_block=4)
+    out = torch.empty(n, dtype=torch.float32, device=DEV)
+    w = torch.empty(n, dtype=torch.int32, device=DEV)
+    if which == "poisson":
+        B.brng_poisson(h.h, p0, out, w)
+    else:
+        B.brng_binomial(h.h, p0, p1, out, w)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK, cnt
+    p0_h, p1_h, out_h, w_h = H(p0), H(p1), H(out), words_np(w)
+    tags = np.full(n, tag, np.uint8)
+    pos_gpu = h.positions().reshape(S, 3)
+    starts = np.random.default_rng(10).choice(np.arange(1, S // 64 - 1), 62, replace=False) * 64
+    ranges = [(0, 64), (S - 64, S)] + [(int(s0), int(s0) + 64) for s0 in starts]
+    ro, rw, rpos, _ = O.mixed(seed, S, tags, p0_h, p1_h, streams=ranges)
+    sel = np.concatenate([np.arange(s0, s1) for s0, s1 in ranges])
+    idx = (np.arange(n // S)[:, None] * S + sel[None, :]).ravel()
+    assert np.array_equal(out_h[idx].astype(np.float64), ro[idx])
+    assert np.array_equal(w_h[idx], rw[idx])
+    assert np.array_equal(pos_gpu[sel], rpos.reshape(S, 3)[sel])
+    print("%s: %d attempts or draws redone in FP64 over %d draws" % (which, cnt["n_recheck"], n))
+
+
 def test_mixed_with_large_discrete_means():
     """All eight tags, Poisson means log-uniform up to 1e6 and Binomial trials
     up to 2^24: discrete counts exact, continuous values within tolerance."""
@@ -687,8 +728,9 @@ def test_mixed_parity():
 
 
 def test_mixed_full_size_sampled():
-    """2^28 draws over 2^20 streams (the mixed-stream workload); 128 whole
-    streams recomputed by the oracle."""
+    """2^28 draws over 2^20 streams (the mixed-stream workload); 4,096 whole
+    streams recomputed by the oracle: the first and last 64 and 62 blocks of
+    64 at seeded random offsets."""
     seed, S, n = 42, 1 << 20, 1 << 28
     tag, p0, p1 = inputs.mixed_stream_torch(n, seed=seed, device=DEV)
     h = handle(seed, S)
@@ -700,13 +742,15 @@ def test_mixed_full_size_sampled():
     tag_h, p0_h, p1_h = H(tag), H(p0), H(p1)
     out_h, w_h = H(out), words_np(w)
     pos_gpu = h.positions().reshape(S, 3)
-    for s0, s1 in [(0, 64), (S - 64, S)]:
-        ro, rw, rpos, _, cond = O.mixed(seed, S, tag_h, p0_h, p1_h, streams=(s0, s1), with_cond=True)
-        idx = np.concatenate([np.arange(s, n, S) for s in range(s0, s1)])
-        assert np.array_equal(w_h[idx], rw[idx])
-        assert np.array_equal(pos_gpu[s0:s1], rpos.reshape(S, 3)[s0:s1])
-        assert_close(out_h[idx], ro[idx], _mixed_scale(tag_h[idx], p0_h[idx], p1_h[idx], ro[idx], cond[idx]),
-                     what="mixed 2^28 streams %d..%d" % (s0, s1))
+    starts = np.random.default_rng(9).choice(np.arange(1, S // 64 - 1), 62, replace=False) * 64
+    ranges = [(0, 64), (S - 64, S)] + [(int(s0), int(s0) + 64) for s0 in starts]
+    ro, rw, rpos, _, cond = O.mixed(seed, S, tag_h, p0_h, p1_h, streams=ranges, with_cond=True)
+    sel = np.concatenate([np.arange(s0, s1) for s0, s1 in ranges])
+    idx = (np.arange(n // S)[:, None] * S + sel[None, :]).ravel()
+    assert np.array_equal(w_h[idx], rw[idx])
+    assert np.array_equal(pos_gpu[sel], rpos.reshape(S, 3)[sel])
+    assert_close(out_h[idx], ro[idx], _mixed_scale(tag_h[idx], p0_h[idx], p1_h[idx], ro[idx], cond[idx]),
+                 what="mixed 2^28, %d streams" % sel.size)
 
 
 # ---- Dirichlet --------------------------------------------------------------
