@@ -33,6 +33,7 @@ struct brng_handle {
   uint64_t* d_pos;            // SoA [3][S]: U, N, E positions of every stream
   uint64_t* d_pos64;          // [S]: U64-domain positions (brng_uniform_f64)
   brng::DevCounters* d_cnt;   // device counters
+  unsigned int* d_flag;       // the mixed stream's dispatch word (discrete tags present)
   int device;
   brng::BatchJob* d_batch_jobs = nullptr;        // brng_gibbs_batch job table
   size_t batch_cap = 0;
@@ -95,6 +96,7 @@ int bulk(brng_t* h, int tag, size_t n, const uint8_t* tagv, const float* p0, con
   a.words = words;
   a.pos = h->d_pos;
   a.cnt = h->d_cnt;
+  a.mixed_flag = h->d_flag;
   return cuda_status(brng::launch_bulk(tag, a, g, st));
 }
 
@@ -122,9 +124,11 @@ int brng_create(uint64_t seed, uint32_t n_streams, uint32_t buf_len, brng_t** ou
   h->d_pos = nullptr;
   h->d_pos64 = nullptr;
   h->d_cnt = nullptr;
+  h->d_flag = nullptr;
   cudaError_t e = cudaMalloc(&h->d_pos, pos_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_pos64, sizeof(uint64_t) * static_cast<size_t>(n_streams));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_cnt, sizeof(brng::DevCounters));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_flag, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(h->d_pos, 0, pos_bytes);
   if (e == cudaSuccess) e = cudaMemset(h->d_pos64, 0, sizeof(uint64_t) * static_cast<size_t>(n_streams));
   if (e == cudaSuccess) e = cudaMemset(h->d_cnt, 0, sizeof(brng::DevCounters));
@@ -133,6 +137,7 @@ int brng_create(uint64_t seed, uint32_t n_streams, uint32_t buf_len, brng_t** ou
     cudaFree(h->d_pos);
     cudaFree(h->d_pos64);
     cudaFree(h->d_cnt);
+    cudaFree(h->d_flag);
     delete h;
     return cuda_status(e);
   }
@@ -145,6 +150,7 @@ int brng_destroy(brng_t* h) {
   cudaFree(h->d_batch_jobs);
   cudaFree(h->d_batch_counter);
   cudaFree(h->d_pos64);
+  cudaFree(h->d_flag);
   cudaError_t e1 = cudaFree(h->d_pos);
   cudaError_t e2 = cudaFree(h->d_cnt);
   delete h;

@@ -19,6 +19,12 @@
 
 namespace brng {
 
+// TAG: a distribution tag (one distribution per call), kTagMixed (-1: the
+// mixed stream, any tag) or kTagMixedContinuous (-2: the mixed stream when no
+// Poisson / Binomial tag is present; the same code without the discrete
+// draws, so it fits fewer registers).
+constexpr int kTagMixedContinuous = -2;
+
 template <int TAG>
 struct BulkDomains {
   static constexpr bool kU = TAG < 0 || TAG == BRNG_TAG_UNIFORM || TAG == BRNG_TAG_GAMMA ||
@@ -34,7 +40,11 @@ __host__ __device__ inline uint32_t bulk_warp_bytes(int n_domains, uint32_t B, b
   return 128u + static_cast<uint32_t>(n_domains) * B * 32u * 4u * (words ? 2u : 1u);
 }
 
+template <int TAG = kTagMixed>
 __device__ __forceinline__ bool param_ok(int tag, float p0, float p1) {
+  // the continuous-only mixed kernel never runs a discrete draw: if one were
+  // dispatched to it, it would be a domain error, not a step that never ends
+  if (TAG == kTagMixedContinuous && (tag == BRNG_TAG_POISSON || tag == BRNG_TAG_BINOMIAL)) return false;
   switch (tag) {
     case BRNG_TAG_UNIFORM: return isfinite(p0) && isfinite(p1) && p0 <= p1;
     case BRNG_TAG_NORMAL:
@@ -356,11 +366,14 @@ __device__ __forceinline__ float binomial_draw(float n, float p, float u, bool* 
 // 2.72 at 64; Binomial 6.02 / 5.85 / 5.97; the other distributions need
 // fewer).
 template <int TAG>
-constexpr int kBulkMaxRegs = TAG < 0 ? 96 : 72;
+constexpr int kBulkMaxRegs = TAG == kTagMixed ? 96 : TAG == kTagMixedContinuous ? 80 : 72;
 
 template <int TAG, bool WORDS>
 __global__ void __maxnreg__(kBulkMaxRegs<TAG>) bulk_kernel(const BulkArgs a) {
   using D = BulkDomains<TAG>;
+  if constexpr (TAG < 0) {  // both mixed kernels are launched; the flag picks one
+    if (a.mixed_flag && (*a.mixed_flag != 0u) != (TAG == kTagMixed)) return;
+  }
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned warp = threadIdx.x >> 5;
   const uint32_t wbytes = bulk_warp_bytes(D::kCount, a.B, WORDS);
@@ -401,7 +414,7 @@ __global__ void __maxnreg__(kBulkMaxRegs<TAG>) bulk_kernel(const BulkArgs a) {
   };
   if (has_stream && i < a.n) load(i, tag, p0, p1);
   if (has_stream && i + a.S < a.n) load(i + a.S, tag_n, p0_n, p1_n);
-  bool ok = has_stream && i < a.n && param_ok(tag, p0, p1);
+  bool ok = has_stream && i < a.n && param_ok<TAG>(tag, p0, p1);
   count_warp(&a.cnt->n_domain, has_stream && i < a.n && !ok);
   GammaState g = gamma_setup(ok && tag == BRNG_TAG_GAMMA ? p0 : 1.0f);
   int attempts = 0;  // of the current draw (an inversion search: 1 once started)
@@ -461,7 +474,7 @@ __global__ void __maxnreg__(kBulkMaxRegs<TAG>) bulk_kernel(const BulkArgs a) {
         done = true;
       }
     }
-    if constexpr (D::kU && (TAG < 0 || TAG == BRNG_TAG_POISSON || TAG == BRNG_TAG_BINOMIAL)) {
+    if constexpr (D::kU && (TAG == kTagMixed || TAG == BRNG_TAG_POISSON || TAG == BRNG_TAG_BINOMIAL)) {
       if (__builtin_expect(__any_sync(kFull, isP || isB), TAG >= 0)) {  // one vote for both
         bool rc = false, rej = false;
         const bool large = (isP || isB) && discrete_large(tag, p0, p1);
@@ -548,7 +561,7 @@ __global__ void __maxnreg__(kBulkMaxRegs<TAG>) bulk_kernel(const BulkArgs a) {
     }
     const bool fresh = done && i < a.n;
     if (__any_sync(kFull, done)) {
-      const bool okn = fresh && param_ok(tag, p0, p1);
+      const bool okn = fresh && param_ok<TAG>(tag, p0, p1);
       count_warp(&a.cnt->n_domain, fresh && !okn);
       if (done) {
         ok = okn;
@@ -585,10 +598,46 @@ static cudaError_t launch_bulk_t(const BulkArgs& a, const Geometry& g, cudaStrea
   return cudaGetLastError();
 }
 
+// The mixed stream's dispatch: one pass over the tags (1 byte per draw, 16
+// per load) sets the flag when a Poisson or Binomial tag is present; both
+// mixed kernels are then launched and the flag lets one of them run (the
+// other's blocks exit at once), so the choice needs no host round trip and
+// the call stays asynchronous and capturable.
+__global__ void mixed_scan_kernel(const uint8_t* tag, uint64_t n, unsigned int* flag) {
+  const uint64_t tid = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  const uint64_t nv = (reinterpret_cast<uintptr_t>(tag) & 15u) == 0 ? n / 16 : 0;
+  unsigned hit = 0;
+  const uint4* t4 = reinterpret_cast<const uint4*>(tag);
+  for (uint64_t i = tid; i < nv; i += stride) {
+    const uint4 v = __ldcs(t4 + i);
+    // bytes 6 and 7 are exactly those with (b & 0xfe) == 6
+    hit |= __vcmpeq4(v.x & 0xfefefefeu, 0x06060606u) | __vcmpeq4(v.y & 0xfefefefeu, 0x06060606u) |
+           __vcmpeq4(v.z & 0xfefefefeu, 0x06060606u) | __vcmpeq4(v.w & 0xfefefefeu, 0x06060606u);
+  }
+  for (uint64_t i = nv * 16 + tid; i < n; i += stride) hit |= (tag[i] & 0xfeu) == 6u;
+  if (__any_sync(kFull, hit != 0) && lane_id() == 0) *flag = 1u;
+}
+
+static cudaError_t launch_mixed(const BulkArgs& a, const Geometry& g, cudaStream_t st, bool w) {
+  cudaError_t e = cudaMemsetAsync(a.mixed_flag, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  if (a.n > 0) {
+    mixed_scan_kernel<<<4u * 152u, 256u, 0, st>>>(a.tag, a.n, a.mixed_flag);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  e = w ? launch_bulk_t<kTagMixedContinuous, true>(a, g, st) : launch_bulk_t<kTagMixedContinuous, false>(a, g, st);
+  if (e != cudaSuccess) return e;
+  return w ? launch_bulk_t<kTagMixed, true>(a, g, st) : launch_bulk_t<kTagMixed, false>(a, g, st);
+}
+
 cudaError_t launch_bulk(int tag, const BulkArgs& a, const Geometry& g, cudaStream_t st) {
   const bool w = a.words != nullptr;
   switch (tag) {
-    case kTagMixed: return w ? launch_bulk_t<-1, true>(a, g, st) : launch_bulk_t<-1, false>(a, g, st);
+    case kTagMixed:
+      if (a.mixed_flag) return launch_mixed(a, g, st, w);
+      return w ? launch_bulk_t<-1, true>(a, g, st) : launch_bulk_t<-1, false>(a, g, st);
     case BRNG_TAG_UNIFORM: return w ? launch_bulk_t<0, true>(a, g, st) : launch_bulk_t<0, false>(a, g, st);
     case BRNG_TAG_NORMAL: return w ? launch_bulk_t<1, true>(a, g, st) : launch_bulk_t<1, false>(a, g, st);
     case BRNG_TAG_EXPONENTIAL: return w ? launch_bulk_t<2, true>(a, g, st) : launch_bulk_t<2, false>(a, g, st);

@@ -57,6 +57,7 @@ struct BulkArgs {
   uint32_t* words;
   uint64_t* pos;  // SoA: pos[d * S + s], d = U, N, E
   DevCounters* cnt;
+  unsigned int* mixed_flag = nullptr;  // mixed stream: device word, 1 if a Poisson/Binomial tag is present
 };
 cudaError_t launch_bulk(int tag, const BulkArgs& a, const Geometry& g, cudaStream_t st);
 cudaError_t launch_philox_words(const RoundKeys& rk, uint32_t dom, uint32_t stream,
