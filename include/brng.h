@@ -393,6 +393,10 @@ typedef struct {
                                before the next; 1 (n_sweeps = 1 only): they are left in
                                dnkw for the caller to sum over devices, then
                                brng_lda_apply adds them                                  */
+  const uint32_t *order;    /* device [n] or NULL: the order in which the documents'
+                               topic draws are started (a permutation of 0..n-1;
+                               longest first balances the uneven lengths).  Speed only:
+                               no value depends on it.  NULL: 0, 1, ..., n-1             */
 } brng_lda_full_params_t;
 
 typedef struct {

@@ -70,7 +70,8 @@ class brng_lda_state_t(C.Structure):
 
 class brng_lda_full_params_t(C.Structure):
     _fields_ = [("K", C.c_uint32), ("V", C.c_uint32), ("alpha", C.c_float), ("beta", C.c_float),
-                ("doc_ptr", C.c_void_p), ("words", C.c_void_p), ("prev", C.c_void_p), ("exchange", C.c_uint32)]
+                ("doc_ptr", C.c_void_p), ("words", C.c_void_p), ("prev", C.c_void_p), ("exchange", C.c_uint32),
+                ("order", C.c_void_p)]
 
 
 class brng_lda_full_state_t(C.Structure):
@@ -414,21 +415,25 @@ class LdaFull:
         self.theta = torch.zeros((self.n_docs, self.K), dtype=torch.float32, device=device)
         self.pos = dev(state["pos"].astype(np.uint64), np.int64)
         self.mom = dev(state["mom"].astype(np.float64), np.float64)
+        # documents start longest first (speed only: the draws do not depend on it)
+        lengths = np.diff(corpus["doc_ptr"].astype(np.int64))
+        self.order = dev(np.argsort(-lengths, kind="stable").astype(np.uint32), np.int32)
         brng_lda_index(self.doc_ptr, self.words, self.prev, stream)
 
-    def params(self, exchange=0):
+    def params(self, exchange=0, ordered=True):
         return brng_lda_full_params_t(self.K, self.V, self.alpha, self.beta, self.doc_ptr.data_ptr(),
-                                      self.words.data_ptr(), self.prev.data_ptr(), int(exchange))
+                                      self.words.data_ptr(), self.prev.data_ptr(), int(exchange),
+                                      self.order.data_ptr() if ordered else None)
 
     def state(self):
         return brng_lda_full_state_t(*[t.data_ptr() for t in (
             self.z, self.z_start, self.ndk, self.nkw, self.nk, self.dnkw, self.dir_alpha, self.zpos,
             self.theta, self.pos)])
 
-    def run(self, h, n_sweeps, doc_offset=0, stream=None, exchange=0):
+    def run(self, h, n_sweeps, doc_offset=0, stream=None, exchange=0, ordered=True):
         """h: a Handle or a raw brng_t* (its seed keys the draws)."""
         h = getattr(h, "h", h)
-        return brng_gibbs_run(h, MODEL_LDA_FULL, doc_offset, self.n_docs, n_sweeps, self.params(exchange),
+        return brng_gibbs_run(h, MODEL_LDA_FULL, doc_offset, self.n_docs, n_sweeps, self.params(exchange, ordered),
                               self.state(), self.mom, stream)
 
     def host(self):

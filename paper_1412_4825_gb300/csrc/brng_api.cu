@@ -533,6 +533,7 @@ int lda_full_run(brng_t* h, uint64_t doc_offset, uint32_t n_docs, uint32_t n_swe
   while ((1u << lg) < p->K) ++lg;
   a.qbits = 32u - lg;
   a.doc_ptr = p->doc_ptr;
+  a.order = p->order;
   a.words = p->words;
   a.prev = p->prev;
   a.z = s->z;

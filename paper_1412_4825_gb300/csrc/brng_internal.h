@@ -145,6 +145,7 @@ struct LdaZArgs {
   const uint32_t* doc_ptr;   // [n_docs + 1]
   const uint32_t* words;     // [tokens]
   const uint32_t* prev;      // [tokens]
+  const uint32_t* order;     // [n_docs] processing order, or null (identity)
   uint8_t* z;                // [tokens]
   uint8_t* z_start;          // [tokens]
   int32_t* ndk;              // [n_docs][K]

@@ -63,7 +63,8 @@ template <int KP>
 __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a) {
   __shared__ uint32_t zbuf[kLdaWarps][128];
   const uint32_t wid = threadIdx.x >> 5;
-  const uint32_t d = blockIdx.x * kLdaWarps + wid;
+  const uint32_t slot = blockIdx.x * kLdaWarps + wid;
+  const uint32_t d = a.order && slot < a.n_docs ? a.order[slot] : slot;
   if (d >= a.n_docs) return;  // whole warp
   uint32_t* zw = zbuf[wid];
   const uint32_t lane = lane_id();

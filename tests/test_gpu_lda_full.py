@@ -141,3 +141,25 @@ def test_lda_full_full_size_sampled():
     c = inputs.lda_corpus(16384, K=64, V=4096, seed=SEED)
     g, ref = _run_pair(c, 3)
     _check(g, ref, "16384 docs")
+
+
+def test_lda_full_document_order_changes_nothing():
+    """The documents' start order (longest first by default, the identity, a
+    random permutation) is speed only: every output is bit-identical."""
+    c = inputs.lda_corpus(300, K=16, V=200, len_lo=5, len_hi=400, seed=21)
+    st0 = inputs.lda_initial_state(c, seed=22)
+    outs = []
+    for mode in ("longest", "identity", "random"):
+        m = B.LdaFull(c, st0)
+        if mode == "random":
+            perm = np.random.default_rng(5).permutation(m.n_docs).astype(np.uint32)
+            m.order = torch.from_numpy(perm.view(np.int32)).to(m.order.device)
+        h = B.Handle(SEED, 1)
+        m.run(h, 3, ordered=(mode != "identity"))
+        code, cnt = h.counters()
+        assert code == B.BRNG_OK, cnt
+        outs.append(m.host())
+        h.close()
+    for other in outs[1:]:
+        for key in ("z", "ndk", "nkw", "nk", "zpos", "pos", "theta", "mom"):
+            assert np.array_equal(outs[0][key], other[key]), key
