@@ -17,7 +17,12 @@
 //             q (32-bit warp scan), Q = C_(K-1), r = top 24 bits of the
 //             document's next Z word: exact integer arithmetic, so the choice
 //             is the oracle's.
-// Lane l holds topics l, l + 32, ... (KP = ceil(K / 32) per lane): its
+// The maximum weight and the pick (the number of topics whose inclusive sum
+// is <= (r Q) >> 24) are one warp reduction each (redux on the weights' bits,
+// which order as unsigned since the weights are non-negative, and on the
+// lanes' counts); the inclusive sums are each lane's own topics in order plus
+// an exclusive scan of the lanes' totals.
+// Lane l holds topics l KP .. l KP + KP - 1 (KP = ceil(K / 32)): its
 // document-topic counts, its topic totals and their two reciprocals (with and
 // without the token itself) live in registers; a reciprocal is recomputed only
 // when its topic's total changes.  The word's snapshot row is loaded one token
@@ -59,15 +64,21 @@ __device__ __forceinline__ float lda_inv(int32_t n, float vbeta) {
   return __frcp_rn(__fadd_rn(__int2float_rn(n), vbeta));
 }
 
+// One warp per document, G = 32 lanes, KP = ceil(K / 32) topics per lane.
+// (Two documents per warp, 16 lanes each, was measured slower: the two
+// documents' control flow diverges, and the per-token reductions are single
+// instructions here already.)
 template <int KP>
 __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a) {
-  __shared__ uint32_t zbuf[kLdaWarps][128];
+  constexpr uint32_t G = 32;
+  constexpr unsigned gmask = kFull;
+  __shared__ uint32_t zbuf[kLdaWarps][4 * G];
   const uint32_t wid = threadIdx.x >> 5;
+  const uint32_t gl = lane_id();
   const uint32_t slot = blockIdx.x * kLdaWarps + wid;
   const uint32_t d = a.order && slot < a.n_docs ? a.order[slot] : slot;
   if (d >= a.n_docs) return;  // whole warp
   uint32_t* zw = zbuf[wid];
-  const uint32_t lane = lane_id();
   const uint32_t K = a.K;
   const uint32_t t0 = __ldg(a.doc_ptr + d), t1 = __ldg(a.doc_ptr + d + 1);
   const uint32_t stream = static_cast<uint32_t>(a.doc_offset + d);
@@ -77,7 +88,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
   float inv_c[KP], inv_m[KP];
 #pragma unroll
   for (int p = 0; p < KP; ++p) {
-    const uint32_t k = lane + 32u * p;
+    const uint32_t k = gl * KP + p;
     const bool on = k < K;
     nd[p] = on ? a.ndk[static_cast<uint64_t>(d) * K + k] : 0;
     nks[p] = on ? a.nk[k] : 0;
@@ -87,7 +98,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
   }
   const uint64_t zp0 = a.zpos[d];
   uint64_t cb = 0;      // first Z element held by zw (a multiple of 4)
-  bool have = false;    // zw holds elements cb .. cb + 127
+  bool have = false;    // zw holds elements cb .. cb + 4G - 1
 
   int32_t row[KP];
 #pragma unroll
@@ -97,7 +108,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
     w = __ldg(a.words + t0);
 #pragma unroll
     for (int p = 0; p < KP; ++p) {
-      const uint32_t k = lane + 32u * p;
+      const uint32_t k = gl * KP + p;
       row[p] = k < K ? __ldg(a.nkw + static_cast<uint64_t>(w) * K + k) : 0;
     }
   }
@@ -111,23 +122,23 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
       w_n = __ldg(a.words + t + 1);
 #pragma unroll
       for (int p = 0; p < KP; ++p) {
-        const uint32_t k = lane + 32u * p;
+        const uint32_t k = gl * KP + p;
         row_n[p] = k < K ? __ldg(a.nkw + static_cast<uint64_t>(w_n) * K + k) : 0;
       }
     }
     const uint32_t zo = a.z[t];  // not yet redrawn in this sweep
     // this draw's Z word (element zp0 + (t - t0) of the document's stream)
     const uint64_t e = zp0 + (t - t0);
-    if (!have || e - cb >= 128u) {
+    if (!have || e - cb >= 4u * G) {
       cb = e & ~3ull;
       have = true;
-      const uint4 v = philox_block_sh(cb / 4u + lane, sh, a.rk);
-      __syncwarp();
-      zw[4u * lane + 0u] = v.x;
-      zw[4u * lane + 1u] = v.y;
-      zw[4u * lane + 2u] = v.z;
-      zw[4u * lane + 3u] = v.w;
-      __syncwarp();
+      const uint4 v = philox_block_sh(cb / 4u + gl, sh, a.rk);
+      __syncwarp(gmask);
+      zw[4u * gl + 0u] = v.x;
+      zw[4u * gl + 1u] = v.y;
+      zw[4u * gl + 2u] = v.z;
+      zw[4u * gl + 3u] = v.w;
+      __syncwarp(gmask);
     }
     const uint32_t r24 = zw[static_cast<uint32_t>(e - cb)] >> 8;
     // the document's own changes of this word's counts in this sweep
@@ -139,7 +150,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
       if (zs != zc) {
 #pragma unroll
         for (int p = 0; p < KP; ++p) {
-          const uint32_t k = lane + 32u * p;
+          const uint32_t k = gl * KP + p;
           ow[p] += (k == zc ? 1 : 0) - (k == zs ? 1 : 0);
         }
       }
@@ -149,38 +160,43 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
     float m = 0.0f;
 #pragma unroll
     for (int p = 0; p < KP; ++p) {
-      const uint32_t k = lane + 32u * p;
+      const uint32_t k = gl * KP + p;
       const int32_t self = k == zo ? 1 : 0;
       const float x = __fadd_rn(__int2float_rn(nd[p] - self), a.alpha);
       const float y = __fadd_rn(__int2float_rn(row[p] + ow[p] - self), a.beta);
       wk[p] = k < K ? __fmul_rn(__fmul_rn(x, y), self ? inv_m[p] : inv_c[p]) : 0.0f;
       m = fmaxf(m, wk[p]);
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, off));
+    // the maximum (weights are non-negative, so their bits order as unsigned)
+    m = __uint_as_float(__reduce_max_sync(gmask, __float_as_uint(m)));
     const uint32_t ef = (__float_as_uint(m) >> 23) & 0xFFu;
     const float scale = __uint_as_float((253u + a.qbits - ef) << 23);
+    // inclusive sums in topic order: the lane's own topics, then an exclusive
+    // scan of the lanes' totals
     uint32_t c[KP];
-    uint32_t base = 0;
+    uint32_t run = 0;
 #pragma unroll
     for (int p = 0; p < KP; ++p) {
-      uint32_t v = __float2uint_rz(__fmul_rn(wk[p], scale));
-#pragma unroll
-      for (unsigned off = 1; off < 32; off <<= 1) {
-        const uint32_t u = __shfl_up_sync(kFull, v, off);
-        if (lane >= off) v += u;
-      }
-      c[p] = base + v;
-      base += __shfl_sync(kFull, v, 31);
+      run += __float2uint_rz(__fmul_rn(wk[p], scale));
+      c[p] = run;
     }
-    const uint32_t tt = static_cast<uint32_t>((static_cast<uint64_t>(r24) * base) >> 24);
-    uint32_t zn = 0;
+    uint32_t incl = run;
 #pragma unroll
-    for (int p = 0; p < KP; ++p) zn += __popc(__ballot_sync(kFull, lane + 32u * p < K && c[p] <= tt));
+    for (unsigned off = 1; off < G; off <<= 1) {
+      const uint32_t u = __shfl_up_sync(gmask, incl, off, G);
+      if (gl >= off) incl += u;
+    }
+    const uint32_t excl = incl - run;
+    const uint32_t base = __shfl_sync(gmask, incl, G - 1, G);
+    const uint32_t tt = static_cast<uint32_t>((static_cast<uint64_t>(r24) * base) >> 24);
+    uint32_t below = 0;  // this lane's topics whose inclusive sum is <= tt
+#pragma unroll
+    for (int p = 0; p < KP; ++p) below += (gl * KP + p < K && excl + c[p] <= tt) ? 1u : 0u;
+    const uint32_t zn = __reduce_add_sync(gmask, below);
     if (zn != zo) {
 #pragma unroll
       for (int p = 0; p < KP; ++p) {
-        const uint32_t k = lane + 32u * p;
+        const uint32_t k = gl * KP + p;
         const int32_t dlt = (k == zn ? 1 : 0) - (k == zo ? 1 : 0);
         if (dlt != 0) {
           nd[p] += dlt;
@@ -189,24 +205,24 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
           inv_m[p] = lda_inv(nks[p] + own[p] - 1, a.vbeta);
         }
       }
-      if (lane == 0) {
+      if (gl == 0) {
         atomicAdd(a.dnkw + static_cast<uint64_t>(w) * K + zo, -1);
         atomicAdd(a.dnkw + static_cast<uint64_t>(w) * K + zn, 1);
       }
     }
-    if (lane == 0) {
+    if (gl == 0) {
       a.z_start[t] = static_cast<uint8_t>(zo);
       a.z[t] = static_cast<uint8_t>(zn);
     }
-    __syncwarp();  // this token's z and z_start are visible to the next tokens' walks
+    __syncwarp(gmask);  // this token's z and z_start are visible to the next tokens' walks
     w = w_n;
 #pragma unroll
     for (int p = 0; p < KP; ++p) row[p] = row_n[p];
   }
-  if (lane == 0) a.zpos[d] = zp0 + (t1 - t0);
+  if (gl == 0) a.zpos[d] = zp0 + (t1 - t0);
 #pragma unroll
   for (int p = 0; p < KP; ++p) {
-    const uint32_t k = lane + 32u * p;
+    const uint32_t k = gl * KP + p;
     if (k < K) {
       a.ndk[static_cast<uint64_t>(d) * K + k] = nd[p];
       a.dir_alpha[static_cast<uint64_t>(d) * K + k] = __fadd_rn(a.alpha, __int2float_rn(nd[p]));
