@@ -507,25 +507,41 @@ def test_binomial_large_means_bit_exact(max_trials, S):
     assert np.array_equal(h.positions(), rpos)
 
 
-@pytest.mark.parametrize("which", ["poisson", "binomial"])
+@pytest.mark.parametrize("which", ["poisson", "binomial", "poisson_small", "binomial_small"])
 def test_large_means_full_size_sampled(which):
-    """The bench's large-mean lines in their launch configuration: 2^26 draws
-    over 2^20 streams, ring 8, 4 warps per block (Poisson with lambda
-    log-uniform [64, 1e6]: PTRS; Binomial with n log-uniform integers to 2^24
-    and p uniform: BTRD above mean 64, inversion below); 128 whole streams
-    recomputed by the oracle: counts, first words and positions bit-exact."""
+    """The bench's discrete lines in their launch configuration, 2^26 draws
+    over 2^20 streams: Poisson with lambda log-uniform [64, 1e6] (PTRS) and
+    Binomial with n log-uniform integers to 2^24 and p uniform (BTRD above
+    mean 64, inversion below), ring 8, 4 warps per block; Poisson with lambda
+    log-uniform [0.05, 64] and Binomial with n to 1,000, means capped below 64
+    (the resumable inversion searches), ring 8, 2 warps per block.  4,096
+    whole streams recomputed by the oracle: counts, first words and positions
+    bit-exact."""
     seed, S, n = 42, 1 << 20, 1 << 26
     g = torch.Generator(device=DEV)
     g.manual_seed(3)
+    wpb = 4
     if which == "poisson":
         p0 = torch.exp(np.log(64.0) + np.log(1e6 / 64.0) * torch.rand(n, generator=g, device=DEV)).contiguous()
         p1 = torch.zeros_like(p0)
-        tag = 6
-    else:
+    elif which == "poisson_small":
+        p0 = torch.exp(np.log(0.05) + np.log(64 / 0.05) * torch.rand(n, generator=g, device=DEV)).contiguous()
+        p1 = torch.zeros_like(p0)
+        wpb = 2
+    elif which == "binomial":
         p0 = torch.floor(torch.exp(np.log(2.0 ** 24) * torch.rand(n, generator=g, device=DEV))).contiguous()
         p1 = torch.rand(n, generator=g, device=DEV).contiguous()
-        tag = 7
-    h = handle(seed, S, 8, warps_per_block=4)
+    else:
+        p0 = torch.floor(torch.exp(np.log(1001.0) * torch.rand(n, generator=g, device=DEV)))
+        pr = torch.rand(n, generator=g, device=DEV)
+        q = torch.minimum(pr, 1.0 - pr)
+        cap = 0.999 * 64.0 / torch.clamp(p0, min=1.0)
+        p1 = torch.where(p0 * q > 64.0, torch.where(pr <= 0.5, cap, 1.0 - cap), pr).contiguous()
+        p0 = p0.contiguous()
+        wpb = 2
+    tag = 6 if which.startswith("poisson") else 7
+    which = which.split("_")[0]
+    h = handle(seed, S, 8, warps_per_block=wpb)
     out = torch.empty(n, dtype=torch.float32, device=DEV)
     w = torch.empty(n, dtype=torch.int32, device=DEV)
     if which == "poisson":
