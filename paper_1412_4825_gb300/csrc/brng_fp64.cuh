@@ -201,7 +201,9 @@ __device__ __forceinline__ bool mt_accept64(double d, double z, double t, double
 // ---- large means: transformed rejection (Hormann 1993), all FP64 ----------
 // The same operations in the same order as the reference definition (IEEE
 // sqrt, division and floor, dlog, no contraction), so that every accept
-// decision and every count is the reference's.
+// decision and every count is the reference's.  The kernels run these only
+// for the attempts that the FP32 / float-float path (brng_rejection32.cuh)
+// leaves undecided, and, in the checked build, to verify the ones it decides.
 
 constexpr double kHalfLog2Pi = 0x1.d67f1c864beb5p-1;  // ln(2 pi) / 2
 
