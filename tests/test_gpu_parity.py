@@ -743,6 +743,35 @@ def test_mixed_parity():
     assert_close(H(out), ro, _mixed_scale(tag, p0, p1, ro, cond), what="mixed")
 
 
+def test_mixed_dispatch_across_calls():
+    """A call's kernel is picked on the device from its tags (the 96-register
+    kernel when a Poisson or Binomial tag is present, the continuous-only one
+    otherwise): calls that alternate between the two, on one handle, continue
+    every stream exactly as one oracle run over the concatenated draws."""
+    seed, S = 7, 1000
+    parts = []
+    for n_tags, n, sd in [(8, 30011, 1), (6, 20011, 2), (4, 25013, 3), (8, 10007, 4)]:
+        tag, p0, p1 = inputs.mixed_stream(n, seed=sd, n_tags=n_tags)
+        parts.append((tag, p0, p1))
+    h = handle(seed, S)
+    pos = O.new_positions(S)
+    for tag, p0, p1 in parts:
+        n = tag.size
+        out = torch.empty(n, dtype=torch.float32, device=DEV)
+        w = torch.empty(n, dtype=torch.int32, device=DEV)
+        B.brng_mixed(h.h, T(tag), T(p0), T(p1), out, w)
+        code, cnt = h.counters(reset=True)
+        assert code == B.BRNG_OK, cnt
+        ro, rw, pos, _, cond = O.mixed(seed, S, tag, p0, p1, pos=pos, nthreads=NT, with_cond=True)
+        assert np.array_equal(words_np(w), rw)
+        assert np.array_equal(h.positions(), pos)
+        disc = (tag == 6) | (tag == 7)
+        assert np.array_equal(H(out)[disc].astype(np.float64), ro[disc])
+        rest = ~disc
+        assert_close(H(out)[rest], ro[rest], _mixed_scale(tag[rest], p0[rest], p1[rest], ro[rest], cond[rest]),
+                     what="mixed call with %d tags" % int(tag.max() + 1))
+
+
 def test_mixed_full_size_sampled():
     """2^28 draws over 2^20 streams (the mixed-stream workload); 4,096 whole
     streams recomputed by the oracle: the first and last 64 and 62 blocks of
