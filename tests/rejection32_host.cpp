@@ -9,13 +9,15 @@
 // about one ulp, like CUDA's, so the bands are exercised against a second,
 // independent implementation of the two functions.
 //
-// Usage: rejection32_host {ptrs|btrd} N seed
+// Usage: rejection32_host {ptrs|btrd|ptrs_edges|btrd_edges} N seed
 // Prints one JSON line: attempts, decided, undecided, accepted, mismatches.
+// The *_edges modes place attempts next to the decisions' boundaries.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 
 #define __device__
 #define __host__
@@ -69,8 +71,162 @@ static uint64_t next64() {  // splitmix64
 static double unif() { return static_cast<double>(next64() >> 11) * 0x1p-53; }
 static float grid_u() { return static_cast<float>(next64() >> 40) * 0x1p-24f; }  // [0, 1) on 2^-24
 
+struct Tally {
+  long long attempts = 0, decided = 0, undecided = 0, accepted = 0, mismatches = 0;
+  void check(float k32, int used32, float k64, int used64, float p0, float p1, float u0, float u1) {
+    ++attempts;
+    if (k32 == brng::kUndecided) {
+      ++undecided;
+      return;
+    }
+    ++decided;
+    if (k32 >= 0.0f) ++accepted;
+    if (k32 != k64 || used32 != used64) {
+      if (mismatches < 5)
+        std::fprintf(stderr, "mismatch p0=%a p1=%a u0=%a u1=%a k32=%.1f k64=%.1f used %d/%d\n", p0, p1, u0, u1,
+                     k32, k64, used32, used64);
+      ++mismatches;
+    }
+  }
+};
+
+static float ptrs64(float lam, float u0, float u1) {
+  return static_cast<float>(brng::ptrs_attempt64(lam, u0, static_cast<double>(u1) + 0x1p-24));
+}
+static float btrd64(float n, float p, float u0, float u1, int* used) {
+  return static_cast<float>(brng::btrd_attempt64(n, p, static_cast<double>(u0) + 0x1p-24, u1, used));
+}
+static float grid(uint32_t j) { return static_cast<float>(j) * 0x1p-24f; }
+
+// The smallest grid index j in [lo, hi] at which pred(j) turns true (pred is
+// monotone false -> true on the range), or hi + 1.
+template <class P>
+static uint32_t first_true(uint32_t lo, uint32_t hi, P pred) {
+  if (!pred(hi)) return hi + 1;
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (pred(mid)) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Attempts placed next to the decisions' boundaries, found on the FP64
+// attempt by bisection over the 2^-24 grid: where floor(X) steps to the next
+// integer, where the squeeze's threshold on v lies, and where the log test
+// turns from accept to reject.  Every decided attempt there must still equal
+// the FP64 attempt.
+static void edges(bool ptrs, long long N, Tally& t) {
+  for (long long i = 0; i < N; ++i) {
+    const int kind = static_cast<int>(next64() % 3);
+    if (ptrs) {
+      const float lam = static_cast<float>(64.0 * std::exp(unif() * std::log(1e7 / 64.0)));
+      uint32_t j0;
+      float u1;
+      if (kind == 0) {  // floor(X) steps: X increases with u0; take u0 in the squeeze region, v small
+        u1 = 0.0f;
+        const float ref = ptrs64(lam, grid(1u << 23), u1);  // k at u0 = 1/2
+        const float target = ref + static_cast<float>(static_cast<int>(next64() % 41) - 20);
+        j0 = first_true(1174406u, (1u << 24) - 1174406u, [&](uint32_t j) { return ptrs64(lam, grid(j), u1) >= target; });
+        for (int d = -3; d <= 3; ++d) {
+          const uint32_t j = j0 + d;
+          const brng::Attempt32 a = brng::ptrs_attempt32(lam, grid(j), u1 + 0x1p-24f);
+          t.check(a.k, a.used, ptrs64(lam, grid(j), u1), 2, lam, 0.0f, grid(j), u1);
+        }
+      } else if (kind == 1) {  // the squeeze's v <= v_r: accept turns to the log test as v grows
+        const float u0 = grid(static_cast<uint32_t>(1174406u + next64() % 6000000u));
+        const uint32_t m = first_true(0u, (1u << 24) - 1u, [&](uint32_t m) {
+          const brng::Attempt32 a = brng::ptrs_attempt32(lam, u0, grid(m) + 0x1p-24f);
+          return a.k == brng::kUndecided || ptrs64(lam, u0, grid(m)) < 0.0f;
+        });
+        for (int d = -4; d <= 4; ++d) {
+          const uint32_t mm = static_cast<uint32_t>(std::min<long long>(std::max<long long>(m + d, 0), (1 << 24) - 1));
+          const brng::Attempt32 a = brng::ptrs_attempt32(lam, u0, grid(mm) + 0x1p-24f);
+          t.check(a.k, a.used, ptrs64(lam, u0, grid(mm)), 2, lam, 0.0f, u0, grid(mm));
+        }
+      } else {  // the log test: us in [0.013, 0.07), accept for v below a threshold
+        const uint32_t ju = static_cast<uint32_t>(218104u + next64() % (1174406u - 218104u));
+        const float u0 = (next64() & 1) ? grid(ju) : grid((1u << 24) - ju);
+        const uint32_t m = first_true(0u, (1u << 24) - 1u, [&](uint32_t m) { return ptrs64(lam, u0, grid(m)) < 0.0f; });
+        for (int d = -4; d <= 4; ++d) {
+          const uint32_t mm = static_cast<uint32_t>(std::min<long long>(std::max<long long>(m + d, 0), (1 << 24) - 1));
+          const brng::Attempt32 a = brng::ptrs_attempt32(lam, u0, grid(mm) + 0x1p-24f);
+          t.check(a.k, a.used, ptrs64(lam, u0, grid(mm)), 2, lam, 0.0f, u0, grid(mm));
+        }
+      }
+    } else {
+      float n, p;
+      do {
+        n = std::floor(static_cast<float>(129.0 * std::exp(unif() * std::log(16777216.0 / 129.0))));
+        p = static_cast<float>(unif());
+      } while (!(static_cast<double>(n) * std::fmin(static_cast<double>(p), 1.0 - static_cast<double>(p)) > 64.0));
+      int used = 0;
+      if (kind == 0) {  // the immediate accept's floor(X) steps: X increases with v (u1 unused)
+        const float ref = btrd64(n, p, grid(1u << 22), 0.0f, &used);
+        if (ref < 0.0f || used != 1) continue;
+        const float base = p > 0.5f ? n - ref : ref;
+        const float target = base + static_cast<float>(static_cast<int>(next64() % 21) - 10);
+        const uint32_t m = first_true(0u, 1u << 23, [&](uint32_t m) {
+          int us = 0;
+          const float k = btrd64(n, p, grid(m), 0.0f, &us);
+          return us != 1 || (p > 0.5f ? n - k : k) >= target;
+        });
+        for (int d = -3; d <= 3; ++d) {
+          const uint32_t mm = static_cast<uint32_t>(std::max<long long>(m + d, 0));
+          int u64 = 0;
+          const float k64 = btrd64(n, p, grid(mm), 0.0f, &u64);
+          const brng::Attempt32 a = brng::btrd_attempt32(n, p, grid(mm), 0.0f);
+          t.check(a.k, a.used, k64, u64, n, p, grid(mm), 0.0f);
+        }
+      } else {  // the thresholds 0.86 v_r and v_r on v, and the accept test beyond v_r
+        const float u1 = grid(static_cast<uint32_t>(next64() >> 40));
+        const double pq = p > 0.5f ? 1.0 - static_cast<double>(p) : static_cast<double>(p);
+        const double b = 1.15 + 2.53 * std::sqrt(static_cast<double>(n) * pq * (1.0 - pq));
+        const double vr = 0.92 - 4.2 / b;
+        uint32_t m;
+        if (kind == 1) {
+          const int which = static_cast<int>(next64() % 2);
+          if (which == 0) {  // 0.86 v_r: one element below, two above
+            m = first_true(0u, (1u << 24) - 1u, [&](uint32_t mm) {
+              int us = 0;
+              btrd64(n, p, grid(mm), u1, &us);
+              return us == 2;
+            });
+          } else {  // v_r (v = u0 + 2^-24)
+            m = static_cast<uint32_t>(std::ceil(vr * 16777216.0)) - 1u;
+          }
+        } else {  // beyond v_r the element u1 fixes k; the test turns from accept to reject as v grows
+          const uint32_t lo = static_cast<uint32_t>(std::ceil(vr * 16777216.0)) + 1u;
+          int us = 0;
+          if (btrd64(n, p, grid(lo), u1, &us) < 0.0f) continue;  // k outside or rejected everywhere
+          m = first_true(lo, (1u << 24) - 1u, [&](uint32_t mm) {
+            int u2 = 0;
+            return btrd64(n, p, grid(mm), u1, &u2) < 0.0f;
+          });
+        }
+        for (int d = -4; d <= 4; ++d) {
+          const uint32_t mm = static_cast<uint32_t>(std::min<long long>(std::max<long long>(static_cast<long long>(m) + d, 0),
+                                                                       (1 << 24) - 1));
+          int u64 = 0;
+          const float k64 = btrd64(n, p, grid(mm), u1, &u64);
+          const brng::Attempt32 a = brng::btrd_attempt32(n, p, grid(mm), u1);
+          t.check(a.k, a.used, k64, u64, n, p, grid(mm), u1);
+        }
+      }
+    }
+  }
+}
+
 int main(int argc, char** argv) {
   if (argc != 4) return 2;
+  if (std::strcmp(argv[1], "ptrs_edges") == 0 || std::strcmp(argv[1], "btrd_edges") == 0) {
+    g_state = std::strtoull(argv[3], nullptr, 10);
+    Tally t;
+    edges(argv[1][0] == 'p', std::atoll(argv[2]), t);
+    std::printf("{\"attempts\": %lld, \"decided\": %lld, \"undecided\": %lld, \"accepted\": %lld, \"mismatches\": %lld}\n",
+                t.attempts, t.decided, t.undecided, t.accepted, t.mismatches);
+    return 0;
+  }
   const bool ptrs = std::strcmp(argv[1], "ptrs") == 0;
   const long long N = std::atoll(argv[2]);
   g_state = std::strtoull(argv[3], nullptr, 10);

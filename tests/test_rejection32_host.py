@@ -10,6 +10,8 @@ attempt, else the FP64 pipe would still set the speed.
 The host's logf and log1pf are not CUDA's (both within about one ulp), so
 this also checks that the bands do not depend on one implementation of the
 two functions; the checked GPU build repeats the comparison with CUDA's.
+Random attempts rarely fall near a boundary, so a second mode places them
+there on purpose.
 """
 import json
 import os
@@ -34,6 +36,21 @@ def harness(tmp_path_factory):
     subprocess.run([cxx, "-O2", "-std=c++17", "-ffp-contract=off", "-I", str(d / "fake"), "-I", CSRC,
                     os.path.join(HERE, "rejection32_host.cpp"), "-o", exe], check=True)
     return exe
+
+
+@pytest.mark.parametrize("method,seed", [("ptrs_edges", 5), ("btrd_edges", 6)])
+def test_certified_attempts_at_the_boundaries(harness, method, seed):
+    """Attempts placed next to each decision's boundary (found on the FP64
+    attempt by bisection over the 2^-24 grid: the steps of floor(X), the
+    thresholds on v, the turn from accept to reject of the log and product
+    tests): still no decided attempt differs from FP64, and the boundaries
+    are reached (many attempts there are left undecided, as the bands
+    intend)."""
+    r = subprocess.run([harness, method, "60000", str(seed)], capture_output=True, text=True, check=True)
+    res = json.loads(r.stdout)
+    assert res["mismatches"] == 0, r.stderr
+    assert res["undecided"] > 0.05 * res["attempts"], res
+    assert res["decided"] > 0.3 * res["attempts"], res
 
 
 @pytest.mark.parametrize("method,seed", [("ptrs", 1), ("ptrs", 2), ("btrd", 3), ("btrd", 4)])
