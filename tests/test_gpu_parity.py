@@ -772,6 +772,35 @@ def test_mixed_dispatch_across_calls():
                      what="mixed call with %d tags" % int(tag.max() + 1))
 
 
+@pytest.mark.parametrize("offset,where", [(0, "tail"), (1, "tail"), (3, "head"), (0, "middle")])
+def test_mixed_dispatch_finds_a_single_discrete_tag(offset, where):
+    """The tag scan reads 16 tags per load when the array is 16-byte aligned
+    and one at a time otherwise (and for the tail): a single Poisson tag
+    anywhere, with the tag array at any byte offset, still selects the kernel
+    with the discrete draws (the continuous-only one would report it as a
+    domain error)."""
+    seed, S, n = 11, 64, 4099
+    tag, p0, p1 = inputs.mixed_stream(n, seed=5, n_tags=6)
+    idx = {"tail": n - 1, "head": 0, "middle": n // 2}[where]
+    tag = tag.copy()
+    p0 = p0.copy()
+    p1 = p1.copy()
+    tag[idx], p0[idx], p1[idx] = 6, np.float32(3.5), np.float32(0.0)
+    buf = torch.zeros(n + 16, dtype=torch.uint8, device=DEV)
+    buf[offset:offset + n] = T(tag)
+    tview = buf[offset:offset + n]
+    assert (tview.data_ptr() % 16 == 0) == (offset == 0)
+    h = handle(seed, S)
+    out = torch.empty(n, dtype=torch.float32, device=DEV)
+    w = torch.empty(n, dtype=torch.int32, device=DEV)
+    B.brng_mixed(h.h, tview, T(p0), T(p1), out, w)
+    code, cnt = h.counters()
+    assert code == B.BRNG_OK and cnt["n_domain"] == 0, cnt
+    ro, rw, rpos, _ = O.mixed(seed, S, tag, p0, p1)
+    assert H(out)[idx] == ro[idx] and np.array_equal(words_np(w), rw)
+    assert np.array_equal(h.positions(), rpos)
+
+
 def test_mixed_full_size_sampled():
     """2^28 draws over 2^20 streams (the mixed-stream workload); 4,096 whole
     streams recomputed by the oracle: the first and last 64 and 62 blocks of
