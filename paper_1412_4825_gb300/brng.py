@@ -431,9 +431,11 @@ class LdaFull:
             self.theta, self.pos)])
 
     def run(self, h, n_sweeps, doc_offset=0, stream=None, exchange=0, ordered=True):
-        """h: a Handle or a raw brng_t* (its seed keys the draws)."""
-        h = getattr(h, "h", h)
-        return brng_gibbs_run(h, MODEL_LDA_FULL, doc_offset, self.n_docs, n_sweeps, self.params(exchange, ordered),
+        """h: a Handle or a raw brng_t* (its seed keys the draws).  `h` stays
+        referenced for the whole call, so a Handle made in the argument list
+        is not destroyed under it."""
+        raw = getattr(h, "h", h)
+        return brng_gibbs_run(raw, MODEL_LDA_FULL, doc_offset, self.n_docs, n_sweeps, self.params(exchange, ordered),
                               self.state(), self.mom, stream)
 
     def host(self):

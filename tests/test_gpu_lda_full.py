@@ -163,3 +163,17 @@ def test_lda_full_document_order_changes_nothing():
     for other in outs[1:]:
         for key in ("z", "ndk", "nkw", "nk", "zpos", "pos", "theta", "mom"):
             assert np.array_equal(outs[0][key], other[key]), key
+
+
+def test_lda_full_run_with_a_handle_made_in_the_call():
+    """A Handle created in the argument list stays alive for the whole call
+    (the binding must not drop its last reference before the library runs)."""
+    c = inputs.lda_corpus(50, K=8, V=64, len_lo=5, len_hi=40, seed=31)
+    st0 = inputs.lda_initial_state(c, seed=32)
+    m = B.LdaFull(c, st0)
+    m.run(B.Handle(SEED, 1), 2)
+    ref = {k: v.copy() for k, v in st0.items()}
+    O.lda_full(SEED, 2, c, ref, alpha=0.1, beta=0.01, nthreads=NT)
+    g = m.host()
+    for key in ("z", "ndk", "nkw", "nk", "zpos"):
+        assert np.array_equal(g[key].astype(np.int64), ref[key].astype(np.int64)), key
