@@ -18,3 +18,20 @@ def oracle():
     import oracle as O
     O.lib()
     return O
+
+
+@pytest.fixture(autouse=True)
+def _checked_build_guard(request):
+    """With BRNG_CHECKED_RUN=1 (and BRNG_LIB naming the checked build), every
+    GPU test also asserts that the checked build counted no failed check while
+    it ran: ring protocol, table lookups, and every large-mean Poisson/Binomial
+    attempt the FP32 path decided, redone in FP64."""
+    if os.environ.get("BRNG_CHECKED_RUN") != "1" or request.node.get_closest_marker("gpu") is None:
+        yield
+        return
+    from paper_1412_4825_gb300 import brng as B
+    if B.brng_debug_violations() is None:
+        pytest.fail("BRNG_CHECKED_RUN=1 needs the checked build (BRNG_LIB)")
+    B.brng_debug_violations(reset=True)
+    yield
+    assert B.brng_debug_violations() == 0, "the checked build counted failed checks"
