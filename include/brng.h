@@ -117,7 +117,9 @@ typedef struct {
  * paper's constructor fills the buffers at once; here rings are filled lazily
  * inside each kernel, which gives the same values.  *out is set only on
  * BRNG_OK.  brng_destroy frees it (NULL is a no-op); no call on the handle
- * may be in flight. */
+ * may be in flight.  Calls on one handle must be ordered on the device (one
+ * CUDA stream, or streams ordered by events): they read and advance the same
+ * stream positions (and brng_mixed its dispatch word). */
 int brng_create(uint64_t seed, uint32_t n_streams, uint32_t buf_len, brng_t **out);
 int brng_destroy(brng_t *h);
 int brng_set_tuning(brng_t *h, const brng_tuning_t *t); /* host struct */
