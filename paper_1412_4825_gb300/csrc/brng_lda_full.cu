@@ -64,6 +64,34 @@ __device__ __forceinline__ float lda_inv(int32_t n, float vbeta) {
   return __frcp_rn(__fadd_rn(__int2float_rn(n), vbeta));
 }
 
+// The lane's KP consecutive topics of a word-topic row (one 8- or 16-byte
+// load when every lane's topics are all inside the row).
+template <int KP>
+__device__ __forceinline__ void load_row(const int32_t* rowp, uint32_t gl, uint32_t K, bool vec, int32_t* out) {
+  if constexpr (KP == 2) {
+    if (vec) {
+      const int2 v = __ldg(reinterpret_cast<const int2*>(rowp) + gl);
+      out[0] = v.x;
+      out[1] = v.y;
+      return;
+    }
+  } else if constexpr (KP == 4) {
+    if (vec) {
+      const int4 v = __ldg(reinterpret_cast<const int4*>(rowp) + gl);
+      out[0] = v.x;
+      out[1] = v.y;
+      out[2] = v.z;
+      out[3] = v.w;
+      return;
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < KP; ++p) {
+    const uint32_t k = gl * KP + p;
+    out[p] = k < K ? __ldg(rowp + k) : 0;
+  }
+}
+
 // One warp per document, G = 32 lanes, KP = ceil(K / 32) topics per lane.
 // (Two documents per warp, 16 lanes each, was measured slower: the two
 // documents' control flow diverges, and the per-token reductions are single
@@ -86,6 +114,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
 
   int32_t nd[KP], nks[KP], own[KP];
   float inv_c[KP], inv_m[KP];
+  float xc[KP], xm[KP];  // float(n_dk) + alpha with and without the token itself
 #pragma unroll
   for (int p = 0; p < KP; ++p) {
     const uint32_t k = gl * KP + p;
@@ -95,7 +124,13 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
     own[p] = 0;
     inv_c[p] = lda_inv(nks[p], a.vbeta);
     inv_m[p] = lda_inv(nks[p] - 1, a.vbeta);
+    xc[p] = __fadd_rn(__int2float_rn(nd[p]), a.alpha);
+    xm[p] = __fadd_rn(__int2float_rn(nd[p] - 1), a.alpha);
   }
+  // a lane's topics are consecutive: with every lane full and the table
+  // aligned to the vector, one vector load per row
+  const bool vec = K == 32u * KP && (KP == 2 || KP == 4) &&
+                   (reinterpret_cast<uintptr_t>(a.nkw) % (4u * KP)) == 0;
   const uint64_t zp0 = a.zpos[d];
   uint64_t cb = 0;      // first Z element held by zw (a multiple of 4)
   bool have = false;    // zw holds elements cb .. cb + 4G - 1
@@ -106,11 +141,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
   uint32_t w = 0;
   if (t0 < t1) {
     w = __ldg(a.words + t0);
-#pragma unroll
-    for (int p = 0; p < KP; ++p) {
-      const uint32_t k = gl * KP + p;
-      row[p] = k < K ? __ldg(a.nkw + static_cast<uint64_t>(w) * K + k) : 0;
-    }
+    load_row<KP>(a.nkw + static_cast<uint64_t>(w) * K, gl, K, vec, row);
   }
   for (uint32_t t = t0; t < t1; ++t) {
     // the next token's word and snapshot row, independent of this draw
@@ -120,11 +151,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
     uint32_t w_n = 0;
     if (t + 1 < t1) {
       w_n = __ldg(a.words + t + 1);
-#pragma unroll
-      for (int p = 0; p < KP; ++p) {
-        const uint32_t k = gl * KP + p;
-        row_n[p] = k < K ? __ldg(a.nkw + static_cast<uint64_t>(w_n) * K + k) : 0;
-      }
+      load_row<KP>(a.nkw + static_cast<uint64_t>(w_n) * K, gl, K, vec, row_n);
     }
     const uint32_t zo = a.z[t];  // not yet redrawn in this sweep
     // this draw's Z word (element zp0 + (t - t0) of the document's stream)
@@ -162,7 +189,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
     for (int p = 0; p < KP; ++p) {
       const uint32_t k = gl * KP + p;
       const int32_t self = k == zo ? 1 : 0;
-      const float x = __fadd_rn(__int2float_rn(nd[p] - self), a.alpha);
+      const float x = self ? xm[p] : xc[p];
       const float y = __fadd_rn(__int2float_rn(row[p] + ow[p] - self), a.beta);
       wk[p] = k < K ? __fmul_rn(__fmul_rn(x, y), self ? inv_m[p] : inv_c[p]) : 0.0f;
       m = fmaxf(m, wk[p]);
@@ -203,6 +230,8 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
           own[p] += dlt;
           inv_c[p] = lda_inv(nks[p] + own[p], a.vbeta);
           inv_m[p] = lda_inv(nks[p] + own[p] - 1, a.vbeta);
+          xc[p] = __fadd_rn(__int2float_rn(nd[p]), a.alpha);
+          xm[p] = __fadd_rn(__int2float_rn(nd[p] - 1), a.alpha);
         }
       }
       if (gl == 0) {
