@@ -225,13 +225,20 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
       for (int p = 0; p < KP; ++p) {
         const uint32_t k = gl * KP + p;
         const int32_t dlt = (k == zn ? 1 : 0) - (k == zo ? 1 : 0);
+        // a count moving by one turns the "with" term into the "without" one
+        // (or back): one new reciprocal and one new n_dk term per change,
+        // taken without a branch so that the lanes of zo and zn share them
         if (dlt != 0) {
+          const bool up = dlt > 0;
           nd[p] += dlt;
           own[p] += dlt;
-          inv_c[p] = lda_inv(nks[p] + own[p], a.vbeta);
-          inv_m[p] = lda_inv(nks[p] + own[p] - 1, a.vbeta);
-          xc[p] = __fadd_rn(__int2float_rn(nd[p]), a.alpha);
-          xm[p] = __fadd_rn(__int2float_rn(nd[p] - 1), a.alpha);
+          const float r = lda_inv(nks[p] + own[p] - (up ? 0 : 1), a.vbeta);
+          const float xn = __fadd_rn(__int2float_rn(nd[p] - (up ? 0 : 1)), a.alpha);
+          const float ic = inv_c[p], im = inv_m[p], c = xc[p], m = xm[p];
+          inv_c[p] = up ? r : im;
+          inv_m[p] = up ? ic : r;
+          xc[p] = up ? xn : m;
+          xm[p] = up ? c : xn;
         }
       }
       if (gl == 0) {
