@@ -364,9 +364,11 @@ __device__ __forceinline__ float binomial_draw(float n, float p, float u, bool* 
 // capped at 96); every single-distribution kernel at 72, seven blocks of 4
 // warps per SM (Poisson means <= 64: 2.45 ms at 80 registers, 2.28 at 72,
 // 2.72 at 64; Binomial 6.02 / 5.85 / 5.97; the other distributions need
-// fewer).
+// fewer).  The mixed stream without discrete tags at 64 (a few spilled
+// words; 5.88 ms against 5.96 at 80 and 5.99 at 72, with the shared-memory
+// carveout at its maximum so that 32 warps fit).
 template <int TAG>
-constexpr int kBulkMaxRegs = TAG == kTagMixed ? 96 : TAG == kTagMixedContinuous ? 80 : 72;
+constexpr int kBulkMaxRegs = TAG == kTagMixed ? 96 : TAG == kTagMixedContinuous ? 64 : 72;
 
 template <int TAG, bool WORDS>
 __global__ void __maxnreg__(kBulkMaxRegs<TAG>) bulk_kernel(const BulkArgs a) {
@@ -593,6 +595,9 @@ static cudaError_t launch_bulk_t(const BulkArgs& a, const Geometry& g, cudaStrea
   const uint64_t blocks = (warps + g.warps_per_block - 1) / g.warps_per_block;
   cudaError_t e = cudaFuncSetAttribute(bulk_kernel<TAG, WORDS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  if constexpr (TAG < 0)  // room for every warp the register cap allows
+    e = cudaFuncSetAttribute(bulk_kernel<TAG, WORDS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   bulk_kernel<TAG, WORDS><<<static_cast<unsigned>(blocks), threads, smem, st>>>(b);
   return cudaGetLastError();

@@ -65,8 +65,8 @@ __device__ __forceinline__ float lda_inv(int32_t n, float vbeta) {
 }
 
 // The lane's KP consecutive topics of a word-topic row (one 8- or 16-byte
-// load when every lane's topics are all inside the row).
-template <int KP>
+// load when every lane's topics are all inside the row).  FULL: K = 32 KP.
+template <int KP, bool FULL>
 __device__ __forceinline__ void load_row(const int32_t* rowp, uint32_t gl, uint32_t K, bool vec, int32_t* out) {
   if constexpr (KP == 2) {
     if (vec) {
@@ -88,15 +88,16 @@ __device__ __forceinline__ void load_row(const int32_t* rowp, uint32_t gl, uint3
 #pragma unroll
   for (int p = 0; p < KP; ++p) {
     const uint32_t k = gl * KP + p;
-    out[p] = k < K ? __ldg(rowp + k) : 0;
+    out[p] = FULL || k < K ? __ldg(rowp + k) : 0;
   }
 }
 
-// One warp per document, G = 32 lanes, KP = ceil(K / 32) topics per lane.
+// One warp per document, G = 32 lanes, KP = ceil(K / 32) topics per lane;
+// FULL: K = 32 KP, every lane's topics exist (no bounds tests per token).
 // (Two documents per warp, 16 lanes each, was measured slower: the two
 // documents' control flow diverges, and the per-token reductions are single
 // instructions here already.)
-template <int KP>
+template <int KP, bool FULL>
 __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a) {
   constexpr uint32_t G = 32;
   constexpr unsigned gmask = kFull;
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
 #pragma unroll
   for (int p = 0; p < KP; ++p) {
     const uint32_t k = gl * KP + p;
-    const bool on = k < K;
+    const bool on = FULL || k < K;
     nd[p] = on ? a.ndk[static_cast<uint64_t>(d) * K + k] : 0;
     nks[p] = on ? a.nk[k] : 0;
     own[p] = 0;
@@ -129,11 +130,9 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
   }
   // a lane's topics are consecutive: with every lane full and the table
   // aligned to the vector, one vector load per row
-  const bool vec = K == 32u * KP && (KP == 2 || KP == 4) &&
-                   (reinterpret_cast<uintptr_t>(a.nkw) % (4u * KP)) == 0;
+  const bool vec = FULL && (KP == 2 || KP == 4) && (reinterpret_cast<uintptr_t>(a.nkw) % (4u * KP)) == 0;
   const uint64_t zp0 = a.zpos[d];
-  uint64_t cb = 0;      // first Z element held by zw (a multiple of 4)
-  bool have = false;    // zw holds elements cb .. cb + 4G - 1
+  uint32_t zoff = 4u * G;  // the next Z element's slot in zw (4G: refill first)
 
   int32_t row[KP];
 #pragma unroll
@@ -141,7 +140,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
   uint32_t w = 0;
   if (t0 < t1) {
     w = __ldg(a.words + t0);
-    load_row<KP>(a.nkw + static_cast<uint64_t>(w) * K, gl, K, vec, row);
+    load_row<KP, FULL>(a.nkw + static_cast<uint64_t>(w) * K, gl, K, vec, row);
   }
   for (uint32_t t = t0; t < t1; ++t) {
     // the next token's word and snapshot row, independent of this draw
@@ -151,15 +150,15 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
     uint32_t w_n = 0;
     if (t + 1 < t1) {
       w_n = __ldg(a.words + t + 1);
-      load_row<KP>(a.nkw + static_cast<uint64_t>(w_n) * K, gl, K, vec, row_n);
+      load_row<KP, FULL>(a.nkw + static_cast<uint64_t>(w_n) * K, gl, K, vec, row_n);
     }
     const uint32_t zo = a.z[t];  // not yet redrawn in this sweep
-    // this draw's Z word (element zp0 + (t - t0) of the document's stream)
-    const uint64_t e = zp0 + (t - t0);
-    if (!have || e - cb >= 4u * G) {
-      cb = e & ~3ull;
-      have = true;
-      const uint4 v = philox_block_sh(cb / 4u + gl, sh, a.rk);
+    // this draw's Z word (element zp0 + (t - t0) of the document's stream);
+    // zw holds the 4G elements from the block of the element that refilled it
+    if (zoff >= 4u * G) {
+      const uint64_t e = zp0 + (t - t0);
+      zoff = static_cast<uint32_t>(e & 3u);
+      const uint4 v = philox_block_sh(e / 4u + gl, sh, a.rk);
       __syncwarp(gmask);
       zw[4u * gl + 0u] = v.x;
       zw[4u * gl + 1u] = v.y;
@@ -167,7 +166,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
       zw[4u * gl + 3u] = v.w;
       __syncwarp(gmask);
     }
-    const uint32_t r24 = zw[static_cast<uint32_t>(e - cb)] >> 8;
+    const uint32_t r24 = zw[zoff++] >> 8;
     // the document's own changes of this word's counts in this sweep
     int32_t ow[KP];
 #pragma unroll
@@ -191,7 +190,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
       const int32_t self = k == zo ? 1 : 0;
       const float x = self ? xm[p] : xc[p];
       const float y = __fadd_rn(__int2float_rn(row[p] + ow[p] - self), a.beta);
-      wk[p] = k < K ? __fmul_rn(__fmul_rn(x, y), self ? inv_m[p] : inv_c[p]) : 0.0f;
+      wk[p] = FULL || k < K ? __fmul_rn(__fmul_rn(x, y), self ? inv_m[p] : inv_c[p]) : 0.0f;
       m = fmaxf(m, wk[p]);
     }
     // the maximum (weights are non-negative, so their bits order as unsigned)
@@ -218,7 +217,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
     const uint32_t tt = static_cast<uint32_t>((static_cast<uint64_t>(r24) * base) >> 24);
     uint32_t below = 0;  // this lane's topics whose inclusive sum is <= tt
 #pragma unroll
-    for (int p = 0; p < KP; ++p) below += (gl * KP + p < K && excl + c[p] <= tt) ? 1u : 0u;
+    for (int p = 0; p < KP; ++p) below += ((FULL || gl * KP + p < K) && excl + c[p] <= tt) ? 1u : 0u;
     const uint32_t zn = __reduce_add_sync(gmask, below);
     if (zn != zo) {
 #pragma unroll
@@ -291,9 +290,12 @@ cudaError_t launch_lda_index(uint32_t n_docs, const uint32_t* doc_ptr, const uin
 cudaError_t launch_lda_z(const LdaZArgs& a, cudaStream_t st) {
   if (a.n_docs == 0) return cudaSuccess;
   const uint32_t blocks = (a.n_docs + kLdaWarps - 1) / kLdaWarps;
-  if (a.K <= 32) lda_z_kernel<1><<<blocks, 32 * kLdaWarps, 0, st>>>(a);
-  else if (a.K <= 64) lda_z_kernel<2><<<blocks, 32 * kLdaWarps, 0, st>>>(a);
-  else if (a.K <= 128) lda_z_kernel<4><<<blocks, 32 * kLdaWarps, 0, st>>>(a);
+  if (a.K == 32) lda_z_kernel<1, true><<<blocks, 32 * kLdaWarps, 0, st>>>(a);
+  else if (a.K == 64) lda_z_kernel<2, true><<<blocks, 32 * kLdaWarps, 0, st>>>(a);
+  else if (a.K == 128) lda_z_kernel<4, true><<<blocks, 32 * kLdaWarps, 0, st>>>(a);
+  else if (a.K < 32) lda_z_kernel<1, false><<<blocks, 32 * kLdaWarps, 0, st>>>(a);
+  else if (a.K < 64) lda_z_kernel<2, false><<<blocks, 32 * kLdaWarps, 0, st>>>(a);
+  else if (a.K < 128) lda_z_kernel<4, false><<<blocks, 32 * kLdaWarps, 0, st>>>(a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
