@@ -171,15 +171,58 @@ struct InvSearch {  // a search in progress (Poisson uses the hi words only)
 };
 
 // Poisson(lambda) from one U element u: the smallest k with u < F(k).  Plain
-// FP32 here (a warp runs each step for all its searching lanes, so each
+// FP32 first (a warp runs each step for all its searching lanes, so each
 // step's cost counts more than the rare redraws): p_0 = e^-lambda (expf,
 // within 4 u), p_k = (p_{k-1} lambda) / k (IEEE), F summed left to right, so
-// F(k) is within (4 + 3k) u of the reference relative to F(k) (one u per
+// F(k) is within (4 + 3k) u of the exact CDF relative to F(k) (one u per
 // multiply, divide and sum, all terms positive); the comparisons are taken
-// beyond (16 + 8k) u F, else the draw is redone in FP64.
+// beyond (16 + 8k) u F.  An undecided draw takes the double-single search
+// (poisson_draw_ds), and only the draws it leaves open are redone in FP64.
 static __device__ __noinline__ float poisson_recheck(float lambda, float u) {
   return static_cast<float>(poisson_inv64(static_cast<double>(lambda), static_cast<double>(u),
                                           kPoissonMaxK));
+}
+
+// The double-single tier: p_0 = expf(-lambda) (4 u), the recurrence and the
+// sums in double-single (O(k u^2) more), so F(k) is within 4 u of the exact
+// CDF relative to F(k) plus a term far below 2^-30; the comparisons are
+// taken beyond 8 u F + 2^-30 F.  *rechecked: the draw was redone in FP64.
+static __device__ __noinline__ float poisson_draw_ds(float lambda, float u, bool* rechecked) {
+  DS pk{expf(-lambda), 0.0f};
+  DS F = pk, Fprev{0.0f, 0.0f};
+  float k = 0.0f;
+  bool ran_out = false;
+  while (!(ds_gap(u, F) < 0.0f)) {
+    if (k >= static_cast<float>(kPoissonMaxK)) {
+      ran_out = true;
+      break;
+    }
+    k += 1.0f;
+    pk = ds_div(ds_mul(pk, lambda), k);
+    Fprev = F;
+    if (pk.hi == 0.0f) {
+      ran_out = true;
+      break;
+    }
+    F = ds_add(F, pk);
+  }
+  const float rel = 8.0f * 0x1p-24f + 0x1p-30f;
+  const bool sure = !ran_out && -ds_gap(u, F) > rel * F.hi && (k == 0.0f || ds_gap(u, Fprev) > rel * Fprev.hi);
+  *rechecked = !sure;
+  return sure ? k : poisson_recheck(lambda, u);
+}
+
+// The FP32 tier's decision on a finished search.
+__device__ __forceinline__ float poisson_decide32(float lambda, float u, float k, float F, float Fprev,
+                                                  bool ran_out, bool* rechecked) {
+  const float rel = (16.0f + 8.0f * k) * 0x1p-24f;  // every error is relative to F
+  const bool sure = !ran_out && (F - u > rel * F) && (k == 0.0f || u - Fprev > rel * Fprev);
+  if (!sure) return poisson_draw_ds(lambda, u, rechecked);
+  *rechecked = false;
+#ifdef BRNG_DEBUG
+  BRNG_CHECK(k == poisson_recheck(lambda, u));  // a decided draw is the FP64 draw
+#endif
+  return k;
 }
 
 __device__ __forceinline__ void poisson_start(InvSearch& s, float lambda, float u) {
@@ -222,10 +265,7 @@ __device__ __forceinline__ int poisson_steps(InvSearch& s, float lambda) {
 }
 
 __device__ __forceinline__ float poisson_finish(const InvSearch& s, float lambda, bool ran_out, bool* rechecked) {
-  const float rel = (16.0f + 8.0f * s.k) * 0x1p-24f;  // every error is relative to F
-  const bool sure = !ran_out && (s.F.hi - s.u > rel * s.F.hi) && (s.k == 0.0f || s.u - s.Fprev.hi > rel * s.Fprev.hi);
-  *rechecked = !sure;
-  return sure ? s.k : poisson_recheck(lambda, s.u);
+  return poisson_decide32(lambda, s.u, s.k, s.F.hi, s.Fprev.hi, ran_out, rechecked);
 }
 
 // The whole search in one step (the mixed stream, and warps with rejection
@@ -249,18 +289,22 @@ __device__ __forceinline__ float poisson_draw(float lambda, float u, bool* reche
     }
     F = F + p;
   }
-  const float kf = static_cast<float>(k);
-  const float rel = (16.0f + 8.0f * kf) * 0x1p-24f;  // every error is relative to F
-  const bool sure = !ran_out && (F - u > rel * F) && (k == 0 || u - Fprev > rel * Fprev);
-  *rechecked = !sure;
-  return sure ? kf : poisson_recheck(lambda, u);
+  return poisson_decide32(lambda, u, static_cast<float>(k), F, Fprev, ran_out, rechecked);
 }
 
 // Binomial(n, p) from one U element u, on q = min(p, 1 - p) (n - k when
-// p > 1/2): p_0 = exp(a), a = n log1p(-q) (library log1pf and expf: within
-// (3|a| + 4) u relative), r = q / (1 - q) and p_k = p_{k-1} ((n - k + 1) r) / k
-// in double-single, so F(k) is within (3|a| + 4) u of the reference relative
-// to F(k); the comparisons are taken beyond twice that.
+// p > 1/2), in two tiers.  First plain FP32, one multiply, one product and
+// one IEEE quotient per step: p_0 = exp(a), a = n log1p(-q) (log1pf within
+// 1 ulp, the product, expf within 2 ulp: (3|a| + 4) u relative), r =
+// q / (1 - q) from the rounded 1 - q (2 u), p_k = (p_{k-1} ((n - k + 1) r)) / k
+// (3 more roundings a step, so p_j carries at most (3|a| + 4 + 5j) u) and F
+// summed left to right (all terms positive: j u more), so F(j) is within
+// (3|a| + 4 + 6j) u of the exact CDF, to first order; the comparisons are
+// taken beyond (6|a| + 16 + 14k) u F + 2^-30 F, more than twice that, and p_0
+// below 2^-125 (next to the subnormal range, where a rounding is no longer
+// relative) decides nothing.  Undecided draws take the double-single search
+// below, whose bound no longer grows with k, and only the draws it leaves
+// undecided are redone in FP64.
 static __device__ __noinline__ float binomial_recheck(float n, float p, float u) {
   return static_cast<float>(binomial_inv64(static_cast<double>(n), static_cast<double>(p),
                                            static_cast<double>(u)));
@@ -268,62 +312,11 @@ static __device__ __noinline__ float binomial_recheck(float n, float p, float u)
 
 __device__ __forceinline__ float binomial_q(float p) { return p > 0.5f ? 1.0f - p : p; }  // exact
 
-__device__ __forceinline__ void binomial_start(InvSearch& s, float n, float p, float u) {
-  s.u = u;
-  s.k = 0.0f;
-  s.pk = DS{expf(n * log1pf(-binomial_q(p))), 0.0f};
-  s.F = s.pk;
-  s.Fprev = DS{0.0f, 0.0f};
-}
-
-__device__ __forceinline__ int binomial_steps(InvSearch& s, float n, float p) {
-  const float q = binomial_q(p);
-  const float omq_hi = 1.0f - q;
-  const DS omq{omq_hi, (1.0f - omq_hi) - q};  // 1 - q exactly
-  const float r1 = __fdividef(q, omq.hi);
-  const DS r = ds_norm(r1, __fdividef(fmaf(-r1, omq.hi, q) - r1 * omq.lo, omq.hi));
-  DS pk = s.pk, F = s.F, Fprev = s.Fprev;
-  float k = s.k;
-  int st = 0;
-  for (int j = 0; j < kInvSteps; ++j) {
-    if (ds_gap(s.u, F) < 0.0f) {
-      st = 1;
-      break;
-    }
-    if (k >= n) {
-      st = -1;
-      break;
-    }
-    k += 1.0f;
-    pk = ds_div(ds_mul(pk, ds_mul(r, (n - k) + 1.0f)), k);
-    Fprev = F;
-    if (pk.hi == 0.0f) {
-      st = -1;
-      break;
-    }
-    F = ds_add(F, pk);
-  }
-  if (st == 0 && ds_gap(s.u, F) < 0.0f) st = 1;
-  s.pk = pk;
-  s.F = F;
-  s.Fprev = Fprev;
-  s.k = k;
-  return st;
-}
-
-__device__ __forceinline__ float binomial_finish(const InvSearch& s, float n, float p, bool ran_out,
-                                                 bool* rechecked) {
-  // all terms carry p_0's relative error: the tolerance scales with F
-  const float a = n * log1pf(-binomial_q(p));
-  const float rel = (6.0f * fabsf(a) + 8.0f) * 0x1p-24f + 0x1p-30f;
-  const bool sure = !ran_out && -ds_gap(s.u, s.F) > rel * s.F.hi &&
-                    (s.k == 0.0f || ds_gap(s.u, s.Fprev) > rel * s.Fprev.hi);
-  *rechecked = !sure;
-  if (!sure) return binomial_recheck(n, p, s.u);
-  return p > 0.5f ? n - s.k : s.k;
-}
-
-__device__ __forceinline__ float binomial_draw(float n, float p, float u, bool* rechecked) {
+// The double-single tier: p_0 = exp(a) as above, r = q / (1 - q) and the
+// recurrence in double-single, so F(k) is within (3|a| + 4) u of the exact
+// CDF relative to F(k) plus O(k u^2); the comparisons are taken beyond
+// twice that.  *rechecked: the draw was redone in FP64.
+static __device__ __noinline__ float binomial_draw_ds(float n, float p, float u, bool* rechecked) {
   const bool flip = p > 0.5f;
   const float q = flip ? 1.0f - p : p;  // exact for p in (1/2, 1]
   const float a = n * log1pf(-q);
@@ -355,6 +348,96 @@ __device__ __forceinline__ float binomial_draw(float n, float p, float u, bool* 
   *rechecked = !sure;
   if (!sure) return binomial_recheck(n, p, u);
   return flip ? n - k : k;
+}
+
+// The FP32 tier's decision on a finished search (k, F(k), F(k-1)); a draw
+// it leaves open goes to the double-single tier.
+__device__ __forceinline__ float binomial_decide32(float n, float p, float u, float k, float F, float Fprev,
+                                                   bool ran_out, bool* rechecked) {
+  const float a = n * log1pf(-binomial_q(p));
+  const float rel = (6.0f * fabsf(a) + 16.0f + 14.0f * k) * 0x1p-24f + 0x1p-30f;
+  const bool sure = !ran_out && (F - u > rel * F) && (k == 0.0f || u - Fprev > rel * Fprev);
+  if (!sure) return binomial_draw_ds(n, p, u, rechecked);
+  *rechecked = false;
+  const float res = p > 0.5f ? n - k : k;
+#ifdef BRNG_DEBUG
+  BRNG_CHECK(res == binomial_recheck(n, p, u));  // a decided draw is the FP64 draw
+#endif
+  return res;
+}
+
+__device__ __forceinline__ float binomial_ratio(float p) {
+  const float q = binomial_q(p);
+  return __fdiv_rn(q, 1.0f - q);
+}
+
+__device__ __forceinline__ void binomial_start(InvSearch& s, float n, float p, float u) {
+  s.u = u;
+  s.k = 0.0f;
+  s.pk.hi = expf(n * log1pf(-binomial_q(p)));
+  s.F.hi = s.pk.hi;
+  s.Fprev.hi = 0.0f;
+}
+
+// Up to kInvSteps FP32 steps (as poisson_steps)
+__device__ __forceinline__ int binomial_steps(InvSearch& s, float n, float p) {
+  float pk = s.pk.hi, F = s.F.hi, Fprev = s.Fprev.hi, k = s.k;
+  if (k == 0.0f && !(pk >= 0x1p-125f)) return -1;  // p_0 too small to decide in FP32
+  const float r = binomial_ratio(p);
+  int st = 0;
+  for (int j = 0; j < kInvSteps; ++j) {
+    if (s.u < F) {
+      st = 1;
+      break;
+    }
+    if (k >= n) {
+      st = -1;
+      break;
+    }
+    k += 1.0f;
+    pk = (pk * (((n - k) + 1.0f) * r)) / k;
+    Fprev = F;
+    if (pk == 0.0f) {
+      st = -1;
+      break;
+    }
+    F = F + pk;
+  }
+  if (st == 0 && s.u < F) st = 1;
+  s.pk.hi = pk;
+  s.F.hi = F;
+  s.Fprev.hi = Fprev;
+  s.k = k;
+  return st;
+}
+
+__device__ __forceinline__ float binomial_finish(const InvSearch& s, float n, float p, bool ran_out,
+                                                 bool* rechecked) {
+  return binomial_decide32(n, p, s.u, s.k, s.F.hi, s.Fprev.hi, ran_out, rechecked);
+}
+
+// The whole search in one step (the mixed stream, and warps with rejection
+// attempts).
+__device__ __forceinline__ float binomial_draw(float n, float p, float u, bool* rechecked) {
+  const float r = binomial_ratio(p);
+  float pk = expf(n * log1pf(-binomial_q(p)));
+  float F = pk, Fprev = 0.0f, k = 0.0f;
+  bool ran_out = !(pk >= 0x1p-125f);
+  while (!ran_out && !(u < F)) {
+    if (k >= n) {
+      ran_out = true;
+      break;
+    }
+    k += 1.0f;
+    pk = (pk * (((n - k) + 1.0f) * r)) / k;
+    Fprev = F;
+    if (pk == 0.0f) {
+      ran_out = true;
+      break;
+    }
+    F = F + pk;
+  }
+  return binomial_decide32(n, p, u, k, F, Fprev, ran_out, rechecked);
 }
 
 // Register caps (measured on GB300, 2^28 mixed draws / 2^26 discrete draws;
