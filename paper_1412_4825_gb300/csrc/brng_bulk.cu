@@ -209,7 +209,11 @@ static __device__ __noinline__ float poisson_draw_ds(float lambda, float u, bool
   const float rel = 8.0f * 0x1p-24f + 0x1p-30f;
   const bool sure = !ran_out && -ds_gap(u, F) > rel * F.hi && (k == 0.0f || ds_gap(u, Fprev) > rel * Fprev.hi);
   *rechecked = !sure;
-  return sure ? k : poisson_recheck(lambda, u);
+  if (!sure) return poisson_recheck(lambda, u);
+#ifdef BRNG_DEBUG
+  BRNG_CHECK(k == poisson_recheck(lambda, u));  // a decided draw is the FP64 draw
+#endif
+  return k;
 }
 
 // The FP32 tier's decision on a finished search.
@@ -347,6 +351,9 @@ static __device__ __noinline__ float binomial_draw_ds(float n, float p, float u,
   const bool sure = !ran_out && -ds_gap(u, F) > rel * F.hi && (k == 0.0f || ds_gap(u, Fprev) > rel * Fprev.hi);
   *rechecked = !sure;
   if (!sure) return binomial_recheck(n, p, u);
+#ifdef BRNG_DEBUG
+  BRNG_CHECK((flip ? n - k : k) == binomial_recheck(n, p, u));  // a decided draw is the FP64 draw
+#endif
   return flip ? n - k : k;
 }
 
