@@ -232,9 +232,10 @@ int brng_weibull(brng_t *h, size_t n, const float *k, const float *lambda, float
  * item 1), drawn from the same U buffer: one U element u per draw, the result
  * the smallest k with u < F(k), F the Poisson CDF summed left to right from
  * p_0 = e^-lambda, p_k = p_{k-1} lambda / k (inversion by sequential search,
- * O(lambda) steps).  The search runs in FP32 and is redone in FP64 (own exp,
- * fixed operation order) when u lies within the FP32 error bound of a CDF
- * step, so every k equals the FP64 reference's.  That holds for
+ * O(lambda) steps).  The search runs in FP32; when u lies within the FP32
+ * error bound of a CDF step it is repeated in double-single FP32, and when u
+ * lies within that bound too, in FP64 (own exp, fixed operation order), so
+ * every k equals the FP64 reference's.  That holds for
  * lambda <= BRNG_INVERSION_MAX_MEAN; above it the draw is Hormann's transformed
  * rejection PTRS (Insurance: Math. Econ. 12, 1993): per attempt U in [0, 1)
  * and V = U' from the same buffer, k = floor((2a/u_s + b)(U - 1/2) + lambda +
@@ -253,9 +254,10 @@ int brng_poisson(brng_t *h, size_t n, const float *lambda, float *out, uint32_t 
  * (Sec. 3 item 1): one U element u per draw; with q = min(p, 1 - p), the
  * smallest k with u < F(k), F the Binomial(n, q) CDF summed left to right
  * from (1 - q)^n, p_k = p_{k-1} (n - k + 1) q / ((1 - q) k); the draw is k, or
- * n - k when p > 1/2.  FP32 search, redone in FP64 (own log and exp, fixed
- * operation order) near a CDF step, so every count equals the FP64
- * reference's.  Above n min(p, 1-p) = BRNG_INVERSION_MAX_MEAN the draw is
+ * n - k when p > 1/2.  FP32 search, repeated in double-single FP32 near a
+ * CDF step and in FP64 (own log and exp, fixed operation order) nearer
+ * still, so every count equals the FP64 reference's (FP64 redraws count in
+ * n_recheck).  Above n min(p, 1-p) = BRNG_INVERSION_MAX_MEAN the draw is
  * Hormann's BTRD (J. Statist. Comput. Simul. 46, 1993) on min(p, 1-p): per
  * attempt one U' (V), and unless V falls in the immediate-accept region one
  * more element (U when V >= v_r, else V' = U' v_r), then the recursive
