@@ -11,6 +11,16 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: longer CPU test")
+    # Several CPU tests load the library (its exports, host-side argument
+    # checks, the autotuner's host logic), some at import: build it before
+    # collection when it is missing or older than its sources (nvcc
+    # cross-compiles without a GPU; a no-op when it is current).  Not with
+    # BRNG_LIB, which names a build made elsewhere (the checked build).
+    if not os.environ.get("BRNG_LIB"):
+        import shutil
+        if shutil.which("nvcc") or os.path.exists("/usr/local/cuda/bin/nvcc"):
+            from paper_1412_4825_gb300 import build_lib
+            build_lib.build()
 
 
 @pytest.fixture(scope="session")
