@@ -6,8 +6,15 @@
 
 namespace brng {
 
+// Register cap: up to two components per lane at 80 (a few spilled words at
+// P = 2; the K = 64 LDA step, 16,384 documents x 500 sweeps, measured on
+// GB300: 9.83 ms at its natural 107 registers, 9.12 at 96, 8.77 at 80 with
+// rings of 16 and lookahead 4, 8.87 at 72, 9.66 at 64), four at 128.
+template <int P>
+constexpr int kDirichletMaxRegs = P >= 4 ? 128 : 80;
+
 template <int P, bool LDA>
-__global__ void __maxnreg__(128) dirichlet_kernel(const DirichletArgs a) {
+__global__ void __maxnreg__(kDirichletMaxRegs<P>) dirichlet_kernel(const DirichletArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned warp = threadIdx.x >> 5;
   const uint64_t unit = static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + warp;
