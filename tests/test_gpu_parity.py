@@ -853,6 +853,27 @@ def test_dirichlet_parity(K, rows, R):
     assert np.max(np.abs(g.sum(axis=1) - 1.0)) < 1e-5
 
 
+@pytest.mark.parametrize("K", [5, 64])
+def test_dirichlet_tuning_invariance(K):
+    """Short rings and a short row queue (the register-capped kernel, chosen
+    when shared memory holds enough of its warps) give the same bits as the
+    default tuning (the natural register budget)."""
+    rng = np.random.default_rng(K + 1)
+    rows, R = 700, 350
+    alpha = np.exp(rng.uniform(np.log(0.05), np.log(20.0), (rows, K))).astype(np.float32)
+    outs, poss = [], []
+    for tune in [{}, dict(buf_len=8, lookahead=2), dict(buf_len=16, lookahead=4, warps_per_block=2)]:
+        h = handle(21, R * K, **tune)
+        out = torch.empty((rows, K), dtype=torch.float32, device=DEV)
+        B.brng_dirichlet(h.h, T(alpha), out)
+        code, cnt = h.counters()
+        assert code == B.BRNG_OK, cnt
+        outs.append(out)
+        poss.append(h.positions())
+    for o, p in zip(outs[1:], poss[1:]):
+        assert torch.equal(o, outs[0]) and np.array_equal(p, poss[0])
+
+
 def test_dirichlet_invalid_rows():
     seed, K, rows = 3, 40, 30
     alpha = np.full((rows, K), 0.7, dtype=np.float32)
