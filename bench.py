@@ -379,6 +379,13 @@ def extras(dev, stream, peaks, args):
     out["poisson_large_2^26"] = {"deviates_per_s": n / t, "ms": t * 1e3, "lambda": "log-uniform [64, 1e6]",
                                  "method": "PTRS, certified FP32 attempts",
                                  "fp64_attempts_per_call": rechecks_per_call(run_p, hp)}
+    # both methods in one call: lambda log-uniform [0.05, 1e6] (inversion below
+    # mean 64, PTRS above, in the same warps)
+    lam = torch.exp(np.log(0.05) + np.log(1e6 / 0.05) * torch.rand(n, generator=g, device=dev)).contiguous()
+    t = _time_s(run_p, stream)
+    out["poisson_wide_2^26"] = {"deviates_per_s": n / t, "ms": t * 1e3, "lambda": "log-uniform [0.05, 1e6]",
+                                "method": "inversion below mean 64, PTRS above",
+                                "fp64_redraws_per_call": rechecks_per_call(run_p, hp)}
     tr = torch.floor(torch.exp(np.log(2.0 ** 24) * torch.rand(n, generator=g, device=dev))).contiguous()
     pr = torch.rand(n, generator=g, device=dev).contiguous()
     t = _time_s(run_b, stream)

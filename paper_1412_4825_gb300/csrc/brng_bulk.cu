@@ -161,8 +161,12 @@ __device__ __forceinline__ float ds_gap(float u, DS F) { return (u - F.hi) - F.l
 // Poisson means <= 64 3.54 -> 2.28 ms, Binomial 8.1 -> 5.85 ms; 8 and 32
 // steps were slower).  The U element is consumed when the search starts, so
 // positions and values do not depend on the bound.  The mixed stream, and a
-// warp with rejection attempts (whose steps are dear anyway), search to the
-// end in one step: the mixed kernel has no registers left for the state.
+// Binomial warp with BTRD attempts, search to the end in one step: the mixed
+// kernel has no registers left for the state, and a warp paying a BTRD
+// attempt every iteration loses more to the extra iterations than it gains
+// (n log-uniform to 2^24: 11.2 ms one-shot, 13.4 ms resumable).  A Poisson
+// warp with PTRS attempts resumes too (lambda log-uniform [0.05, 1e6]:
+// 4.42 ms one-shot, 3.70 ms resumable).
 constexpr int kInvSteps = 16;
 
 struct InvSearch {  // a search in progress (Poisson uses the hi words only)
@@ -573,7 +577,7 @@ __global__ void __maxnreg__(kBulkMaxRegs<TAG>) bulk_kernel(const BulkArgs a) {
         const bool any_large = __any_sync(kFull, large);
         if (isP || isB) {
           if (!large) {  // inversion of one U
-            if (TAG < 0 || (attempts == 0 && any_large)) {  // the whole search now
+            if (TAG < 0 || (TAG == BRNG_TAG_BINOMIAL && attempts == 0 && any_large)) {  // the whole search now
               const float u = RU.peek(0);
               if (WORDS) word = RU.peek_word(0);
               RU.advance(1);
