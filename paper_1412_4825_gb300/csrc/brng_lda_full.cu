@@ -137,22 +137,26 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
   int32_t row[KP];
 #pragma unroll
   for (int p = 0; p < KP; ++p) row[p] = 0;
-  uint32_t w = 0;
+  uint32_t w = 0, zo = 0, pv = kLdaNone;  // the token's word, start topic and same-word link
   if (t0 < t1) {
     w = __ldg(a.words + t0);
+    zo = a.z[t0];
+    pv = __ldg(a.prev + t0);
     load_row<KP, FULL>(a.nkw + static_cast<uint64_t>(w) * K, gl, K, vec, row);
   }
   for (uint32_t t = t0; t < t1; ++t) {
-    // the next token's word and snapshot row, independent of this draw
+    // the next token's word, snapshot row, topic (not yet redrawn: only this
+    // warp writes it, at that token) and link, independent of this draw
     int32_t row_n[KP];
 #pragma unroll
     for (int p = 0; p < KP; ++p) row_n[p] = 0;
-    uint32_t w_n = 0;
+    uint32_t w_n = 0, zo_n = 0, pv_n = kLdaNone;
     if (t + 1 < t1) {
       w_n = __ldg(a.words + t + 1);
+      zo_n = a.z[t + 1];
+      pv_n = __ldg(a.prev + t + 1);
       load_row<KP, FULL>(a.nkw + static_cast<uint64_t>(w_n) * K, gl, K, vec, row_n);
     }
-    const uint32_t zo = a.z[t];  // not yet redrawn in this sweep
     // this draw's Z word (element zp0 + (t - t0) of the document's stream);
     // zw holds the 4G elements from the block of the element that refilled it
     if (zoff >= 4u * G) {
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
     int32_t ow[KP];
 #pragma unroll
     for (int p = 0; p < KP; ++p) ow[p] = 0;
-    for (uint32_t j = __ldg(a.prev + t); j != kLdaNone; j = __ldg(a.prev + j)) {
+    for (uint32_t j = pv; j != kLdaNone; j = __ldg(a.prev + j)) {
       const uint32_t zs = __ldcg(a.z_start + j), zc = __ldcg(a.z + j);
       if (zs != zc) {
 #pragma unroll
@@ -251,6 +255,8 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
     }
     __syncwarp(gmask);  // this token's z and z_start are visible to the next tokens' walks
     w = w_n;
+    zo = zo_n;
+    pv = pv_n;
 #pragma unroll
     for (int p = 0; p < KP; ++p) row[p] = row_n[p];
   }
