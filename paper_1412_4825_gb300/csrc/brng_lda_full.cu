@@ -64,6 +64,21 @@ __device__ __forceinline__ float lda_inv(int32_t n, float vbeta) {
   return __frcp_rn(__fadd_rn(__int2float_rn(n), vbeta));
 }
 
+// One step of an inclusive warp scan: v plus the value `off` lanes below,
+// where there is one.  The shuffle's own predicate (the source lane lies in
+// the warp) guards the add, so a step is two instructions.
+__device__ __forceinline__ uint32_t scan_step_up(uint32_t v, uint32_t off) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t.reg .u32 t;\n\t"
+      "mov.u32 %0, %1;\n\t"
+      "shfl.sync.up.b32 t|p, %1, %2, 0, 0xffffffff;\n\t"
+      "@p add.u32 %0, %0, t;\n\t}"
+      : "=r"(r)
+      : "r"(v), "r"(off));
+  return r;
+}
+
 // The lane's KP consecutive topics of a word-topic row (one 8- or 16-byte
 // load when every lane's topics are all inside the row).  FULL: K = 32 KP.
 template <int KP, bool FULL>
@@ -212,10 +227,7 @@ __global__ void __launch_bounds__(32 * kLdaWarps) lda_z_kernel(const LdaZArgs a)
     }
     uint32_t incl = run;
 #pragma unroll
-    for (unsigned off = 1; off < G; off <<= 1) {
-      const uint32_t u = __shfl_up_sync(gmask, incl, off, G);
-      if (gl >= off) incl += u;
-    }
+    for (unsigned off = 1; off < G; off <<= 1) incl = scan_step_up(incl, off);
     const uint32_t excl = incl - run;
     const uint32_t base = __shfl_sync(gmask, incl, G - 1, G);
     const uint32_t tt = static_cast<uint32_t>((static_cast<uint64_t>(r24) * base) >> 24);
