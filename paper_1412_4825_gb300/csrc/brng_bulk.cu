@@ -107,21 +107,15 @@ static __device__ __noinline__ LargeAttempt large_attempt(bool poisson, float p0
   return LargeAttempt{c.k, c.used, false};
 }
 
-// Per lane, one step per iteration: the lane's current draw, or for a Gamma
-// draw one Marsaglia-Tsang attempt (a rejected attempt leaves the lane on the
-// same draw for the next iteration, while its neighbours move on).  Each ring
-// is topped up at one point of the iteration, for the most a step can take
-// (U: 2 = attempt + boost; N: 1; E: 1), and every read is a peek, so each
-// domain's generator code appears once in the kernel.  The next draw's tag
-// and parameters are loaded one step ahead.
 // ---- discrete draws by inversion (Poisson, Binomial) ------------------------
-// Both search the CDF in FP32 and take the two comparisons that fix k (u <
-// F(k), u >= F(k-1)) only when u lies beyond twice the error bound of F from
-// the step; otherwise the draw is redone in FP64 in the reference operation
-// order, so every count equals the reference's.  u = 2^-24 below is the unit
-// roundoff.  The Binomial search runs in double-single FP32 (a value = hi +
-// lo, each operation's rounding error carried in lo via FMA), which adds only
-// O(k u^2), leaving the first term's relative error as the bound.
+// A draw is the smallest k with u < F(k).  Each of the three tiers below
+// takes the two comparisons that fix k (u < F(k), u >= F(k-1)) only when u
+// lies beyond a band of at least twice its bound on the error of F, relative
+// to F; what it leaves open goes to the next: a plain FP32 search (every
+// draw), a double-single search (hi + lo floats, each operation's rounding
+// error carried in lo through FMA, so the bound no longer grows with k), and
+// an FP64 redraw in the reference operation order, so every count equals the
+// reference's.  u = 2^-24 below is the FP32 unit roundoff.
 struct DS {
   float hi, lo;
 };
@@ -169,9 +163,8 @@ __device__ __forceinline__ float ds_gap(float u, DS F) { return (u - F.hi) - F.l
 // 4.42 ms one-shot, 3.70 ms resumable).
 constexpr int kInvSteps = 16;
 
-struct InvSearch {  // a search in progress (Poisson uses the hi words only)
-  float u, k;
-  DS pk, F, Fprev;
+struct InvSearch {  // an FP32-tier search in progress
+  float u, k, pk, F, Fprev;
 };
 
 // Poisson(lambda) from one U element u: the smallest k with u < F(k).  Plain
@@ -236,15 +229,15 @@ __device__ __forceinline__ float poisson_decide32(float lambda, float u, float k
 __device__ __forceinline__ void poisson_start(InvSearch& s, float lambda, float u) {
   s.u = u;
   s.k = 0.0f;
-  s.pk = DS{expf(-lambda), 0.0f};
+  s.pk = expf(-lambda);
   s.F = s.pk;
-  s.Fprev = DS{0.0f, 0.0f};
+  s.Fprev = 0.0f;
 }
 
 // Up to kInvSteps steps: 1 when u < F(k) (found), -1 when the search ran out
 // (k at its cap, or p_k underflowed), 0 to resume later.
 __device__ __forceinline__ int poisson_steps(InvSearch& s, float lambda) {
-  float p = s.pk.hi, F = s.F.hi, Fprev = s.Fprev.hi, k = s.k;
+  float p = s.pk, F = s.F, Fprev = s.Fprev, k = s.k;
   int st = 0;
   for (int j = 0; j < kInvSteps; ++j) {
     if (s.u < F) {
@@ -265,15 +258,15 @@ __device__ __forceinline__ int poisson_steps(InvSearch& s, float lambda) {
     F = F + p;
   }
   if (st == 0 && s.u < F) st = 1;
-  s.pk.hi = p;
-  s.F.hi = F;
-  s.Fprev.hi = Fprev;
+  s.pk = p;
+  s.F = F;
+  s.Fprev = Fprev;
   s.k = k;
   return st;
 }
 
 __device__ __forceinline__ float poisson_finish(const InvSearch& s, float lambda, bool ran_out, bool* rechecked) {
-  return poisson_decide32(lambda, s.u, s.k, s.F.hi, s.Fprev.hi, ran_out, rechecked);
+  return poisson_decide32(lambda, s.u, s.k, s.F, s.Fprev, ran_out, rechecked);
 }
 
 // The whole search in one step (the mixed stream, and warps with rejection
@@ -385,14 +378,14 @@ __device__ __forceinline__ float binomial_ratio(float p) {
 __device__ __forceinline__ void binomial_start(InvSearch& s, float n, float p, float u) {
   s.u = u;
   s.k = 0.0f;
-  s.pk.hi = expf(n * log1pf(-binomial_q(p)));
-  s.F.hi = s.pk.hi;
-  s.Fprev.hi = 0.0f;
+  s.pk = expf(n * log1pf(-binomial_q(p)));
+  s.F = s.pk;
+  s.Fprev = 0.0f;
 }
 
 // Up to kInvSteps FP32 steps (as poisson_steps)
 __device__ __forceinline__ int binomial_steps(InvSearch& s, float n, float p) {
-  float pk = s.pk.hi, F = s.F.hi, Fprev = s.Fprev.hi, k = s.k;
+  float pk = s.pk, F = s.F, Fprev = s.Fprev, k = s.k;
   if (k == 0.0f && !(pk >= 0x1p-125f)) return -1;  // p_0 too small to decide in FP32
   const float r = binomial_ratio(p);
   int st = 0;
@@ -415,16 +408,16 @@ __device__ __forceinline__ int binomial_steps(InvSearch& s, float n, float p) {
     F = F + pk;
   }
   if (st == 0 && s.u < F) st = 1;
-  s.pk.hi = pk;
-  s.F.hi = F;
-  s.Fprev.hi = Fprev;
+  s.pk = pk;
+  s.F = F;
+  s.Fprev = Fprev;
   s.k = k;
   return st;
 }
 
 __device__ __forceinline__ float binomial_finish(const InvSearch& s, float n, float p, bool ran_out,
                                                  bool* rechecked) {
-  return binomial_decide32(n, p, s.u, s.k, s.F.hi, s.Fprev.hi, ran_out, rechecked);
+  return binomial_decide32(n, p, s.u, s.k, s.F, s.Fprev, ran_out, rechecked);
 }
 
 // The whole search in one step (the mixed stream, and warps with rejection
@@ -464,6 +457,13 @@ __device__ __forceinline__ float binomial_draw(float n, float p, float u, bool* 
 template <int TAG>
 constexpr int kBulkMaxRegs = TAG == kTagMixed ? 96 : TAG == kTagMixedContinuous ? 64 : 72;
 
+// Per lane, one step per iteration: the lane's current draw, or for a Gamma
+// draw one Marsaglia-Tsang attempt (a rejected attempt leaves the lane on the
+// same draw for the next iteration, while its neighbours move on).  Each ring
+// is topped up at one point of the iteration, for the most a step can take
+// (U: 2 = attempt + boost; N: 1; E: 1), and every read is a peek, so each
+// domain's generator code appears once in the kernel.  The next draw's tag
+// and parameters are loaded one step ahead.
 template <int TAG, bool WORDS>
 __global__ void __maxnreg__(kBulkMaxRegs<TAG>) bulk_kernel(const BulkArgs a) {
   using D = BulkDomains<TAG>;
