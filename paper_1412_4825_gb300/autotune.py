@@ -22,7 +22,7 @@ _MEM: dict = {}
 
 # candidate spaces per workload kind (the library's defaults are among them)
 SPACES = {
-    "normal_gamma": {"buf_len": [16, 32], "warps_per_block": [1, 2, 4, 8],
+    "normal_gamma": {"buf_len": [16, 32], "warps_per_block": [1, 2, 4, 8, 16],
                      "producer_warps": [B.PRODUCERS_NONE, 4]},
     "triangle": {"buf_len": [64, 256], "lanes_per_chain": [4, 8, 16]},
     "lda": {"buf_len": [16, 32], "lookahead": [4, 8, 16], "warps_per_block": [2, 4]},
