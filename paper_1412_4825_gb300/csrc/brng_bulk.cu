@@ -14,6 +14,7 @@
 #include <cmath>
 
 #include "brng_gamma.cuh"
+#include "brng_inversion.cuh"
 #include "brng_rejection32.cuh"
 #include "brng_internal.h"
 
@@ -108,44 +109,56 @@ static __device__ __noinline__ LargeAttempt large_attempt(bool poisson, float p0
 }
 
 // ---- discrete draws by inversion (Poisson, Binomial) ------------------------
-// A draw is the smallest k with u < F(k).  Each of the three tiers below
-// takes the two comparisons that fix k (u < F(k), u >= F(k-1)) only when u
-// lies beyond a band of at least twice its bound on the error of F, relative
-// to F; what it leaves open goes to the next: a plain FP32 search (every
-// draw), a double-single search (hi + lo floats, each operation's rounding
-// error carried in lo through FMA, so the bound no longer grows with k), and
-// an FP64 redraw in the reference operation order, so every count equals the
-// reference's.  u = 2^-24 below is the FP32 unit roundoff.
-struct DS {
-  float hi, lo;
-};
-__device__ __forceinline__ DS ds_norm(float a, float b) {  // |a| >= |b|
-  const float s = a + b;
-  return DS{s, b - (s - a)};
+// The FP32 and double-single tiers of brng_inversion.cuh, then an FP64 redraw
+// in the reference operation order for the draws both leave undecided, so
+// every count equals the reference's.  The FP32 tier runs inline; the rest,
+// about one draw in a thousand, out of line.
+static __device__ __noinline__ float poisson_recheck(float lambda, float u) {
+  return static_cast<float>(poisson_inv64(static_cast<double>(lambda), static_cast<double>(u),
+                                          kPoissonMaxK));
 }
-__device__ __forceinline__ DS ds_mul(DS x, float b) {  // (x.hi + x.lo) b
-  const float p = x.hi * b;
-  const float e = fmaf(x.hi, b, -p);  // exact product error
-  return ds_norm(p, fmaf(x.lo, b, e));
+static __device__ __noinline__ float binomial_recheck(float n, float p, float u) {
+  return static_cast<float>(binomial_inv64(static_cast<double>(n), static_cast<double>(p),
+                                           static_cast<double>(u)));
 }
-__device__ __forceinline__ DS ds_mul(DS x, DS y) {
-  const float p = x.hi * y.hi;
-  const float e = fmaf(x.hi, y.hi, -p);
-  return ds_norm(p, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e)));
+
+// The double-single tier, then FP64.  *rechecked: the draw was redone in FP64.
+static __device__ __noinline__ float poisson_slow(float lambda, float u, bool* rechecked) {
+  const float k = poisson_inv_ds(lambda, u, kPoissonMaxK);
+  *rechecked = k == kUndecided;
+  if (*rechecked) return poisson_recheck(lambda, u);
+#ifdef BRNG_DEBUG
+  BRNG_CHECK(k == poisson_recheck(lambda, u));  // a decided draw is the FP64 draw
+#endif
+  return k;
 }
-__device__ __forceinline__ DS ds_div(DS x, float k) {  // (x.hi + x.lo) / k, k > 0
-  const float q1 = __fdividef(x.hi, k);
-  const float r = fmaf(-q1, k, x.hi) + x.lo;  // remainder (first part exact)
-  return ds_norm(q1, __fdividef(r, k));
+static __device__ __noinline__ float binomial_slow(float n, float p, float u, bool* rechecked) {
+  const float k = binomial_inv_ds(n, p, u);
+  *rechecked = k == kUndecided;
+  if (*rechecked) return binomial_recheck(n, p, u);
+#ifdef BRNG_DEBUG
+  BRNG_CHECK(k == binomial_recheck(n, p, u));
+#endif
+  return k;
 }
-__device__ __forceinline__ DS ds_add(DS x, DS y) {  // both >= 0
-  const float s = x.hi + y.hi;
-  const float bb = s - x.hi;
-  const float e = (x.hi - (s - bb)) + (y.hi - bb);  // exact sum error
-  return ds_norm(s, e + x.lo + y.lo);
+
+// The FP32 tier's result k32 (kUndecided: the slower tiers decide).
+__device__ __forceinline__ float poisson_take(float k32, float lambda, float u, bool* rechecked) {
+  if (k32 == kUndecided) return poisson_slow(lambda, u, rechecked);
+  *rechecked = false;
+#ifdef BRNG_DEBUG
+  BRNG_CHECK(k32 == poisson_recheck(lambda, u));
+#endif
+  return k32;
 }
-// (u - F) as one float, F = hi + lo
-__device__ __forceinline__ float ds_gap(float u, DS F) { return (u - F.hi) - F.lo; }
+__device__ __forceinline__ float binomial_take(float k32, float n, float p, float u, bool* rechecked) {
+  if (k32 == kUndecided) return binomial_slow(n, p, u, rechecked);
+  *rechecked = false;
+#ifdef BRNG_DEBUG
+  BRNG_CHECK(k32 == binomial_recheck(n, p, u));
+#endif
+  return k32;
+}
 
 // In the single-distribution kernels the inversion searches run at most
 // kInvSteps steps per iteration of the kernel's loop and resume on the next:
@@ -167,65 +180,6 @@ struct InvSearch {  // an FP32-tier search in progress
   float u, k, pk, F, Fprev;
 };
 
-// Poisson(lambda) from one U element u: the smallest k with u < F(k).  Plain
-// FP32 first (a warp runs each step for all its searching lanes, so each
-// step's cost counts more than the rare redraws): p_0 = e^-lambda (expf,
-// within 4 u), p_k = (p_{k-1} lambda) / k (IEEE), F summed left to right, so
-// F(k) is within (4 + 3k) u of the exact CDF relative to F(k) (one u per
-// multiply, divide and sum, all terms positive); the comparisons are taken
-// beyond (16 + 8k) u F.  An undecided draw takes the double-single search
-// (poisson_draw_ds), and only the draws it leaves open are redone in FP64.
-static __device__ __noinline__ float poisson_recheck(float lambda, float u) {
-  return static_cast<float>(poisson_inv64(static_cast<double>(lambda), static_cast<double>(u),
-                                          kPoissonMaxK));
-}
-
-// The double-single tier: p_0 = expf(-lambda) (4 u), the recurrence and the
-// sums in double-single (O(k u^2) more), so F(k) is within 4 u of the exact
-// CDF relative to F(k) plus a term far below 2^-30; the comparisons are
-// taken beyond 8 u F + 2^-30 F.  *rechecked: the draw was redone in FP64.
-static __device__ __noinline__ float poisson_draw_ds(float lambda, float u, bool* rechecked) {
-  DS pk{expf(-lambda), 0.0f};
-  DS F = pk, Fprev{0.0f, 0.0f};
-  float k = 0.0f;
-  bool ran_out = false;
-  while (!(ds_gap(u, F) < 0.0f)) {
-    if (k >= static_cast<float>(kPoissonMaxK)) {
-      ran_out = true;
-      break;
-    }
-    k += 1.0f;
-    pk = ds_div(ds_mul(pk, lambda), k);
-    Fprev = F;
-    if (pk.hi == 0.0f) {
-      ran_out = true;
-      break;
-    }
-    F = ds_add(F, pk);
-  }
-  const float rel = 8.0f * 0x1p-24f + 0x1p-30f;
-  const bool sure = !ran_out && -ds_gap(u, F) > rel * F.hi && (k == 0.0f || ds_gap(u, Fprev) > rel * Fprev.hi);
-  *rechecked = !sure;
-  if (!sure) return poisson_recheck(lambda, u);
-#ifdef BRNG_DEBUG
-  BRNG_CHECK(k == poisson_recheck(lambda, u));  // a decided draw is the FP64 draw
-#endif
-  return k;
-}
-
-// The FP32 tier's decision on a finished search.
-__device__ __forceinline__ float poisson_decide32(float lambda, float u, float k, float F, float Fprev,
-                                                  bool ran_out, bool* rechecked) {
-  const float rel = (16.0f + 8.0f * k) * 0x1p-24f;  // every error is relative to F
-  const bool sure = !ran_out && (F - u > rel * F) && (k == 0.0f || u - Fprev > rel * Fprev);
-  if (!sure) return poisson_draw_ds(lambda, u, rechecked);
-  *rechecked = false;
-#ifdef BRNG_DEBUG
-  BRNG_CHECK(k == poisson_recheck(lambda, u));  // a decided draw is the FP64 draw
-#endif
-  return k;
-}
-
 __device__ __forceinline__ void poisson_start(InvSearch& s, float lambda, float u) {
   s.u = u;
   s.k = 0.0f;
@@ -234,8 +188,8 @@ __device__ __forceinline__ void poisson_start(InvSearch& s, float lambda, float 
   s.Fprev = 0.0f;
 }
 
-// Up to kInvSteps steps: 1 when u < F(k) (found), -1 when the search ran out
-// (k at its cap, or p_k underflowed), 0 to resume later.
+// Up to kInvSteps FP32 steps: 1 when u < F(k) (found), -1 when the search ran
+// out (k at its cap, or p_k underflowed), 0 to resume later.
 __device__ __forceinline__ int poisson_steps(InvSearch& s, float lambda) {
   float p = s.pk, F = s.F, Fprev = s.Fprev, k = s.k;
   int st = 0;
@@ -266,119 +220,18 @@ __device__ __forceinline__ int poisson_steps(InvSearch& s, float lambda) {
 }
 
 __device__ __forceinline__ float poisson_finish(const InvSearch& s, float lambda, bool ran_out, bool* rechecked) {
-  return poisson_decide32(lambda, s.u, s.k, s.F, s.Fprev, ran_out, rechecked);
+  return poisson_take(poisson_decide32(s.u, s.k, s.F, s.Fprev, ran_out), lambda, s.u, rechecked);
 }
 
-// The whole search in one step (the mixed stream, and warps with rejection
-// attempts, whose steps are dear anyway).
+// The whole search in one step.
 __device__ __forceinline__ float poisson_draw(float lambda, float u, bool* rechecked) {
-  float p = expf(-lambda);
-  float F = p, Fprev = 0.0f;
-  int k = 0;
-  bool ran_out = false;
-  while (!(u < F)) {
-    if (k >= kPoissonMaxK) {
-      ran_out = true;
-      break;
-    }
-    ++k;
-    p = (p * lambda) / static_cast<float>(k);
-    Fprev = F;
-    if (p == 0.0f) {
-      ran_out = true;
-      break;
-    }
-    F = F + p;
-  }
-  return poisson_decide32(lambda, u, static_cast<float>(k), F, Fprev, ran_out, rechecked);
-}
-
-// Binomial(n, p) from one U element u, on q = min(p, 1 - p) (n - k when
-// p > 1/2), in two tiers.  First plain FP32, one multiply, one product and
-// one IEEE quotient per step: p_0 = exp(a), a = n log1p(-q) (log1pf within
-// 1 ulp, the product, expf within 2 ulp: (3|a| + 4) u relative), r =
-// q / (1 - q) from the rounded 1 - q (2 u), p_k = (p_{k-1} ((n - k + 1) r)) / k
-// (3 more roundings a step, so p_j carries at most (3|a| + 4 + 5j) u) and F
-// summed left to right (all terms positive: j u more), so F(j) is within
-// (3|a| + 4 + 6j) u of the exact CDF, to first order; the comparisons are
-// taken beyond (6|a| + 16 + 14k) u F + 2^-30 F, more than twice that, and p_0
-// below 2^-125 (next to the subnormal range, where a rounding is no longer
-// relative) decides nothing.  Undecided draws take the double-single search
-// below, whose bound no longer grows with k, and only the draws it leaves
-// undecided are redone in FP64.
-static __device__ __noinline__ float binomial_recheck(float n, float p, float u) {
-  return static_cast<float>(binomial_inv64(static_cast<double>(n), static_cast<double>(p),
-                                           static_cast<double>(u)));
-}
-
-__device__ __forceinline__ float binomial_q(float p) { return p > 0.5f ? 1.0f - p : p; }  // exact
-
-// The double-single tier: p_0 = exp(a) as above, r = q / (1 - q) and the
-// recurrence in double-single, so F(k) is within (3|a| + 4) u of the exact
-// CDF relative to F(k) plus O(k u^2); the comparisons are taken beyond
-// twice that.  *rechecked: the draw was redone in FP64.
-static __device__ __noinline__ float binomial_draw_ds(float n, float p, float u, bool* rechecked) {
-  const bool flip = p > 0.5f;
-  const float q = flip ? 1.0f - p : p;  // exact for p in (1/2, 1]
-  const float a = n * log1pf(-q);
-  const float omq_hi = 1.0f - q;
-  const DS omq{omq_hi, (1.0f - omq_hi) - q};  // 1 - q exactly
-  const float r1 = __fdividef(q, omq.hi);
-  const DS r = ds_norm(r1, __fdividef(fmaf(-r1, omq.hi, q) - r1 * omq.lo, omq.hi));
-  DS pk{expf(a), 0.0f};
-  DS F = pk, Fprev{0.0f, 0.0f};
-  float k = 0.0f;
-  bool ran_out = false;
-  while (!(ds_gap(u, F) < 0.0f)) {
-    if (k >= n) {
-      ran_out = true;
-      break;
-    }
-    k += 1.0f;
-    pk = ds_div(ds_mul(pk, ds_mul(r, (n - k) + 1.0f)), k);
-    Fprev = F;
-    if (pk.hi == 0.0f) {
-      ran_out = true;
-      break;
-    }
-    F = ds_add(F, pk);
-  }
-  // all terms carry p_0's relative error: the tolerance scales with F
-  const float rel = (6.0f * fabsf(a) + 8.0f) * 0x1p-24f + 0x1p-30f;
-  const bool sure = !ran_out && -ds_gap(u, F) > rel * F.hi && (k == 0.0f || ds_gap(u, Fprev) > rel * Fprev.hi);
-  *rechecked = !sure;
-  if (!sure) return binomial_recheck(n, p, u);
-#ifdef BRNG_DEBUG
-  BRNG_CHECK((flip ? n - k : k) == binomial_recheck(n, p, u));  // a decided draw is the FP64 draw
-#endif
-  return flip ? n - k : k;
-}
-
-// The FP32 tier's decision on a finished search (k, F(k), F(k-1)); a draw
-// it leaves open goes to the double-single tier.
-__device__ __forceinline__ float binomial_decide32(float n, float p, float u, float k, float F, float Fprev,
-                                                   bool ran_out, bool* rechecked) {
-  const float a = n * log1pf(-binomial_q(p));
-  const float rel = (6.0f * fabsf(a) + 16.0f + 14.0f * k) * 0x1p-24f + 0x1p-30f;
-  const bool sure = !ran_out && (F - u > rel * F) && (k == 0.0f || u - Fprev > rel * Fprev);
-  if (!sure) return binomial_draw_ds(n, p, u, rechecked);
-  *rechecked = false;
-  const float res = p > 0.5f ? n - k : k;
-#ifdef BRNG_DEBUG
-  BRNG_CHECK(res == binomial_recheck(n, p, u));  // a decided draw is the FP64 draw
-#endif
-  return res;
-}
-
-__device__ __forceinline__ float binomial_ratio(float p) {
-  const float q = binomial_q(p);
-  return __fdiv_rn(q, 1.0f - q);
+  return poisson_take(poisson_inv32(lambda, u, kPoissonMaxK), lambda, u, rechecked);
 }
 
 __device__ __forceinline__ void binomial_start(InvSearch& s, float n, float p, float u) {
   s.u = u;
   s.k = 0.0f;
-  s.pk = expf(n * log1pf(-binomial_q(p)));
+  s.pk = binomial_p0(n, p);
   s.F = s.pk;
   s.Fprev = 0.0f;
 }
@@ -417,31 +270,11 @@ __device__ __forceinline__ int binomial_steps(InvSearch& s, float n, float p) {
 
 __device__ __forceinline__ float binomial_finish(const InvSearch& s, float n, float p, bool ran_out,
                                                  bool* rechecked) {
-  return binomial_decide32(n, p, s.u, s.k, s.F, s.Fprev, ran_out, rechecked);
+  return binomial_take(binomial_decide32(n, p, s.u, s.k, s.F, s.Fprev, ran_out), n, p, s.u, rechecked);
 }
 
-// The whole search in one step (the mixed stream, and warps with rejection
-// attempts).
 __device__ __forceinline__ float binomial_draw(float n, float p, float u, bool* rechecked) {
-  const float r = binomial_ratio(p);
-  float pk = expf(n * log1pf(-binomial_q(p)));
-  float F = pk, Fprev = 0.0f, k = 0.0f;
-  bool ran_out = !(pk >= 0x1p-125f);
-  while (!ran_out && !(u < F)) {
-    if (k >= n) {
-      ran_out = true;
-      break;
-    }
-    k += 1.0f;
-    pk = (pk * (((n - k) + 1.0f) * r)) / k;
-    Fprev = F;
-    if (pk == 0.0f) {
-      ran_out = true;
-      break;
-    }
-    F = F + pk;
-  }
-  return binomial_decide32(n, p, u, k, F, Fprev, ran_out, rechecked);
+  return binomial_take(binomial_inv32(n, p, u), n, p, u, rechecked);
 }
 
 // Register caps (measured on GB300, 2^28 mixed draws / 2^26 discrete draws;

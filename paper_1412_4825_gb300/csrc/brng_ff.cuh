@@ -28,6 +28,10 @@
 
 namespace brng {
 
+// the result of a certified decision that its error bound did not allow
+// (the caller takes the next, more precise tier)
+constexpr float kUndecided = -2.0f;
+
 struct FF {
   float hi, lo;
 };

@@ -38,8 +38,6 @@
 
 namespace brng {
 
-constexpr float kUndecided = -2.0f;
-
 struct Attempt32 {
   float k;   // the count; -1 rejected; kUndecided: redo the attempt in FP64
   int used;  // U elements the attempt consumed (when decided)

@@ -12,6 +12,11 @@
 // Usage: rejection32_host {ptrs|btrd|ptrs_edges|btrd_edges} N seed
 // Prints one JSON line: attempts, decided, undecided, accepted, mismatches.
 // The *_edges modes place attempts next to the decisions' boundaries.
+//
+// The small-mean inversions (csrc/brng_inversion.cuh) the same way:
+//   rejection32_host {inv|inv_edges} N seed -- N Poisson and N Binomial
+//   draws through the FP32 tier, then the double-single tier, each decided
+//   draw against the FP64 inversion (inv_edges: u next to a CDF step).
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -26,6 +31,7 @@
 static inline float __fadd_rn(float a, float b) { return a + b; }
 static inline float __fmul_rn(float a, float b) { return a * b; }
 static inline float __fdiv_rn(float a, float b) { return a / b; }
+static inline float __fdividef(float a, float b) { return a / b; }  // the device one is within 2 ulp
 static inline float __fsqrt_rn(float a) { return std::sqrt(a); }
 static inline float __fmaf_rn(float a, float b, float c) { return std::fma(a, b, c); }
 static inline double __dadd_rn(double a, double b) { return a + b; }
@@ -60,6 +66,7 @@ using std::floor;
 
 #include "brng_fp64.cuh"
 #include "brng_rejection32.cuh"
+#include "brng_inversion.cuh"
 
 static uint64_t g_state;
 static uint64_t next64() {  // splitmix64
@@ -217,8 +224,88 @@ static void edges(bool ptrs, long long N, Tally& t) {
   }
 }
 
+// ---- the small-mean inversions -------------------------------------------------
+struct InvTally {
+  long long draws = 0, decided32 = 0, decided_ds = 0, undecided = 0, mismatches = 0;
+  // one draw through both tiers, checked against FP64
+  void run(bool poisson, float a, float b, float u) {
+    ++draws;
+    const float ref = poisson ? static_cast<float>(brng::poisson_inv64(a, u, 1024))
+                              : static_cast<float>(brng::binomial_inv64(a, b, u));
+    float k = poisson ? brng::poisson_inv32(a, u, 1024) : brng::binomial_inv32(a, b, u);
+    if (k != brng::kUndecided) {
+      ++decided32;
+    } else {
+      k = poisson ? brng::poisson_inv_ds(a, u, 1024) : brng::binomial_inv_ds(a, b, u);
+      if (k == brng::kUndecided) {
+        ++undecided;
+        return;
+      }
+      ++decided_ds;
+    }
+    if (k != ref) {
+      if (mismatches < 5)
+        std::fprintf(stderr, "inversion mismatch %s a=%a b=%a u=%a k=%.1f fp64=%.1f\n", poisson ? "poisson" : "binomial",
+                     a, b, u, k, ref);
+      ++mismatches;
+    }
+  }
+};
+
+// Poisson lambda log-uniform in [0.05, 64]; Binomial n log-uniform integers
+// in [1, 2^24] and p uniform with n min(p, 1 - p) <= 64 (a few at the ends)
+static float rand_lambda(long long i) {
+  if (i % 97 == 0) return 64.0f;
+  return static_cast<float>(0.05 * std::exp(unif() * std::log(64.0 / 0.05)));
+}
+static void rand_binomial(long long i, float* n, float* p) {
+  do {
+    *n = i % 101 == 0 ? 16777216.0f : std::floor(static_cast<float>(std::exp(unif() * std::log(16777216.0))));
+    *p = i % 7 == 0 && *n <= 128.0f ? 0.5f : static_cast<float>(unif());
+  } while (!(static_cast<double>(*n) * std::fmin(static_cast<double>(*p), 1.0 - static_cast<double>(*p)) <= 64.0));
+}
+
+static void inversions(bool at_steps, long long N, InvTally& t) {
+  for (long long i = 0; i < N; ++i) {
+    const float lam = rand_lambda(i);
+    float n, p;
+    rand_binomial(i, &n, &p);
+    if (!at_steps) {
+      t.run(true, lam, 0.0f, grid_u());
+      t.run(false, n, p, grid_u());
+      continue;
+    }
+    // u on the grid points next to a step of the CDF: the first one whose
+    // FP64 draw passes a count near the middle of the distribution, and its
+    // neighbours
+    const uint32_t mid = 1u << 23;
+    const float kp = static_cast<float>(brng::poisson_inv64(lam, grid(mid), 1024)) +
+                     static_cast<float>(static_cast<int>(next64() % 5) - 2);
+    uint32_t j = first_true(0u, (1u << 24) - 1u, [&](uint32_t m) { return brng::poisson_inv64(lam, grid(m), 1024) > kp; });
+    for (int d = -3; d <= 3; ++d)
+      if (static_cast<long long>(j) + d >= 0 && j + d < (1u << 24)) t.run(true, lam, 0.0f, grid(j + d));
+    const bool flip = p > 0.5f;  // the draw falls as u grows when p > 1/2
+    const float kb = static_cast<float>(brng::binomial_inv64(n, p, grid(mid))) +
+                     static_cast<float>(static_cast<int>(next64() % 5) - 2);
+    j = first_true(0u, (1u << 24) - 1u, [&](uint32_t m) {
+      const float k = static_cast<float>(brng::binomial_inv64(n, p, grid(m)));
+      return flip ? k < kb : k > kb;
+    });
+    for (int d = -3; d <= 3; ++d)
+      if (static_cast<long long>(j) + d >= 0 && j + d < (1u << 24)) t.run(false, n, p, grid(j + d));
+  }
+}
+
 int main(int argc, char** argv) {
   if (argc != 4) return 2;
+  if (std::strcmp(argv[1], "inv") == 0 || std::strcmp(argv[1], "inv_edges") == 0) {
+    g_state = std::strtoull(argv[3], nullptr, 10);
+    InvTally t;
+    inversions(argv[1][3] == '_', std::atoll(argv[2]), t);
+    std::printf("{\"draws\": %lld, \"decided32\": %lld, \"decided_ds\": %lld, \"undecided\": %lld, \"mismatches\": %lld}\n",
+                t.draws, t.decided32, t.decided_ds, t.undecided, t.mismatches);
+    return 0;
+  }
   if (std::strcmp(argv[1], "ptrs_edges") == 0 || std::strcmp(argv[1], "btrd_edges") == 0) {
     g_state = std::strtoull(argv[3], nullptr, 10);
     Tally t;

@@ -12,6 +12,11 @@ this also checks that the bands do not depend on one implementation of the
 two functions; the checked GPU build repeats the comparison with CUDA's.
 Random attempts rarely fall near a boundary, so a second mode places them
 there on purpose.
+
+The small-mean inversions (csrc/brng_inversion.cuh) are checked the same
+way: each draw that the FP32 tier or the double-single tier decides must
+equal the FP64 inversion, at random and on the grid points next to the CDF's
+steps.
 """
 import json
 import os
@@ -62,3 +67,26 @@ def test_certified_attempts_equal_fp64(harness, method, seed):
     assert res["attempts"] == n
     assert res["undecided"] <= 3e-3 * n, res  # FP64 for a few attempts in a thousand at most
     assert 0.8 * n < res["accepted"] < 0.95 * n, res  # both outcomes are exercised
+
+
+def test_inversion_tiers_equal_fp64(harness):
+    """Poisson (lambda log-uniform [0.05, 64]) and Binomial (n to 2^24, mean
+    <= 64) draws: the FP32 tier decides nearly all, the double-single tier
+    most of the rest, and every decided draw is the FP64 draw."""
+    r = subprocess.run([harness, "inv", "1000000", "8"], capture_output=True, text=True, check=True)
+    res = json.loads(r.stdout)
+    assert res["mismatches"] == 0, r.stderr
+    assert res["decided_ds"] > 300, res
+    assert res["undecided"] <= 5e-4 * res["draws"], res
+
+
+def test_inversion_tiers_at_cdf_steps(harness):
+    """u on the grid points next to a step of the CDF (within one 2^-24 of
+    it): the FP32 tier abstains on nearly all, the tiers decide only what
+    their bounds allow, and no decided draw differs from FP64."""
+    r = subprocess.run([harness, "inv_edges", "30000", "9"], capture_output=True, text=True, check=True)
+    res = json.loads(r.stdout)
+    assert res["mismatches"] == 0, r.stderr
+    assert res["draws"] > 100000, res
+    assert res["decided32"] < 0.2 * res["draws"], res
+    assert res["decided_ds"] > 1000, res
