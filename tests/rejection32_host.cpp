@@ -17,6 +17,11 @@
 //   rejection32_host {inv|inv_edges} N seed -- N Poisson and N Binomial
 //   draws through the FP32 tier, then the double-single tier, each decided
 //   draw against the FP64 inversion (inv_edges: u next to a CDF step).
+//
+// And the float-float arithmetic the certified decisions rest on
+// (csrc/brng_ff.cuh): rejection32_host ffops N seed -- the largest relative
+// error of each operation on random operands (cancelling sums included),
+// against wider arithmetic, in units of u^2 = 2^-48.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -296,8 +301,75 @@ static void inversions(bool at_steps, long long N, InvTally& t) {
   }
 }
 
+// ---- float-float operations against wider arithmetic -------------------------------
+// The references: a quad-precision type where the compiler has one (the sums
+// of nearly cancelling operands need every bit of both words: hi + lo spans
+// up to ~110 bits here), else long double; products, quotients and roots
+// only need the inputs to ~2^-64, which long double gives.
+#if defined(__x86_64__) && defined(__GNUC__)
+using wide_t = __float128;
+#else
+using wide_t = long double;
+#endif
+// A random double-word: hi with a random exponent in [-30, 30], lo within half
+// an ulp of hi and not below 2^-60 of it (normalised through fast_two_sum).
+static brng::FF rand_ff() {
+  const float hi = static_cast<float>(std::ldexp(1.0 + unif(), static_cast<int>(next64() % 61) - 30)) *
+                   ((next64() & 1) ? -1.0f : 1.0f);
+  const double frac = std::ldexp(1.0 + unif(), -1 - static_cast<int>(next64() % 36));  // [2^-36, 1) / 2
+  const float lo = static_cast<float>(((next64() & 1) ? -frac : frac) * std::ldexp(1.0, std::ilogb(hi) - 23));
+  return brng::fast_two_sum(hi, lo);
+}
+static bool tight(brng::FF x) {  // hi + lo is exact in wide_t
+  return x.lo == 0.0f || std::fabs(x.lo) >= std::ldexp(std::fabs(x.hi), -85);
+}
+static long double ld(brng::FF x) { return static_cast<long double>(x.hi) + static_cast<long double>(x.lo); }
+static wide_t wd(brng::FF x) { return static_cast<wide_t>(x.hi) + static_cast<wide_t>(x.lo); }
+static long double rel_u2(long double got, long double want) {
+  return want == 0.0L ? 0.0L : fabsl((got - want) / want) * 281474976710656.0L;  // / 2^-48
+}
+static long double rel_u2w(wide_t got, wide_t want) {
+  if (want == 0) return 0.0L;
+  const wide_t r = (got - want) / want;
+  return static_cast<long double>(r < 0 ? -r : r) * 281474976710656.0L;
+}
+
+static void ffops(long long N) {
+  long double e_add = 0, e_add_f = 0, e_mul = 0, e_mul_f = 0, e_div_f = 0, e_div = 0, e_sqrt = 0;
+  long long n_add = 0, n_cancel = 0;  // sums checked, and of them those cancelling below 2^-20 |x|
+  for (long long i = 0; i < N; ++i) {
+    const brng::FF x = rand_ff();
+    brng::FF y = rand_ff();
+    if (i % 4 == 0) {  // a nearly cancelling sum: y close to -x
+      const float d = static_cast<float>((unif() - 0.5) * std::ldexp(1.0, std::ilogb(x.hi) - static_cast<int>(next64() % 40)));
+      y = brng::fast_two_sum(-x.hi, -x.lo + d);
+    }
+    const float f = rand_ff().hi;
+    if (tight(x) && tight(y)) {
+      ++n_add;
+      if (std::fabs(static_cast<double>(ld(x) + ld(y))) < std::ldexp(std::fabs(x.hi), -20)) ++n_cancel;
+      e_add = std::max(e_add, rel_u2w(wd(brng::ff_add(x, y)), wd(x) + wd(y)));
+      e_add_f = std::max(e_add_f, rel_u2w(wd(brng::ff_add_f(x, f)), wd(x) + static_cast<wide_t>(f)));
+    }
+    e_mul = std::max(e_mul, rel_u2(ld(brng::ff_mul(x, y)), ld(x) * ld(y)));
+    e_mul_f = std::max(e_mul_f, rel_u2(ld(brng::ff_mul_f(x, f)), ld(x) * f));
+    e_div_f = std::max(e_div_f, rel_u2(ld(brng::ff_div_f(x, f)), ld(x) / f));
+    e_div = std::max(e_div, rel_u2(ld(brng::ff_div(x, y)), ld(x) / ld(y)));
+    const brng::FF ax = brng::ff_abs(x);
+    e_sqrt = std::max(e_sqrt, rel_u2(ld(brng::ff_sqrt(ax)), sqrtl(ld(ax))));
+  }
+  std::printf("{\"add\": %.4Lf, \"add_f\": %.4Lf, \"mul\": %.4Lf, \"mul_f\": %.4Lf, \"div_f\": %.4Lf, "
+              "\"div\": %.4Lf, \"sqrt\": %.4Lf, \"sums\": %lld, \"cancelling_sums\": %lld}\n",
+              e_add, e_add_f, e_mul, e_mul_f, e_div_f, e_div, e_sqrt, n_add, n_cancel);
+}
+
 int main(int argc, char** argv) {
   if (argc != 4) return 2;
+  if (std::strcmp(argv[1], "ffops") == 0) {
+    g_state = std::strtoull(argv[3], nullptr, 10);
+    ffops(std::atoll(argv[2]));
+    return 0;
+  }
   if (std::strcmp(argv[1], "inv") == 0 || std::strcmp(argv[1], "inv_edges") == 0) {
     g_state = std::strtoull(argv[3], nullptr, 10);
     InvTally t;

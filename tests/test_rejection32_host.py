@@ -13,8 +13,9 @@ two functions; the checked GPU build repeats the comparison with CUDA's.
 Random attempts rarely fall near a boundary, so a second mode places them
 there on purpose.
 
-The small-mean inversions (csrc/brng_inversion.cuh) are checked the same
-way: each draw that the FP32 tier or the double-single tier decides must
+The float-float operations themselves are checked against their stated
+error bounds.  The small-mean inversions (csrc/brng_inversion.cuh) are
+checked the same way as the attempts: each draw that the FP32 tier or the double-single tier decides must
 equal the FP64 inversion, at random and on the grid points next to the CDF's
 steps.
 """
@@ -90,3 +91,19 @@ def test_inversion_tiers_at_cdf_steps(harness):
     assert res["draws"] > 100000, res
     assert res["decided32"] < 0.2 * res["draws"], res
     assert res["decided_ds"] > 1000, res
+
+
+def test_float_float_error_bounds(harness):
+    """The float-float operations the certified decisions rest on
+    (csrc/brng_ff.cuh) stay within the relative error bounds their header
+    states (Joldes, Muller and Popescu), in units of u^2 = 2^-48, on random
+    operands over 60 binades, 14 % of the sums cancelling below 2^-20 of
+    their operands; checked against quad-precision sums and long-double
+    products, quotients and roots."""
+    r = subprocess.run([harness, "ffops", "3000000", "3"], capture_output=True, text=True, check=True)
+    res = json.loads(r.stdout)
+    bounds = {"add": 3.0 / (1 - 4 * 2.0 ** -24), "add_f": 2.0, "mul": 5.0, "mul_f": 2.0, "div_f": 3.0,
+              "div": 15.0 + 56 * 2.0 ** -24, "sqrt": 25.0 / 8.0}
+    for op, b in bounds.items():
+        assert res[op] <= b, (op, res)
+    assert res["sums"] > 2_000_000 and res["cancelling_sums"] > 100_000, res
